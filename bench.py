@@ -1,0 +1,391 @@
+"""Benchmark: seconds to k singular triplets at ||r|| <= 1e-10 ||A|| (PHSVDS).
+
+One step = one complete solve of the workload through the C-ABI: handle
+creation from a device-resident CSR (transpose, value formats), the ||A||
+estimate, stage 1 (FP32 phase + FP64-class polish, the "chosen" form) and, if
+needed, stage 2, ending with the triplets and their residuals on the host.
+The plain FP64-class form (no FP32 phase) is timed beside it.
+
+Workload: the 3D grid-difference operator [D(x)I(x)I; I(x)D(x)I; I(x)I(x)D] on a
+128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4,
+Jacobi preconditioner.  Its working set is far larger than L2, so no flush is
+needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid3d_N128"
+K, TARGET, BLOCK, TOL = 10, "smallest", 4, 1e-10
+METRIC = "sec to k triplets at ||r||<=1e-10||A|| (chosen: FP32 stage-1 phase + FP64-class)"
+UNIT = "s"
+# Products with A or A^T (per column) of a full plain FP64-class solve of this
+# workload, measured on a GB300 with this library; the CPU oracle runs the same
+# algorithm, so its full-solve time is extrapolated from its measured cost per
+# matvec on a bounded sample.
+FULL_SOLVE_MATVECS = None
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception as e:  # no nvidia-smi: report no clock data
+            log("clock sampler unavailable:", e)
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def spmm_roofline(A, dev, torch, B, prec, b, reps=30):
+    """Time the CSR SpMM kernels of one C = A^T A application on the workload
+    with CUDA events on their stream; algorithmic bytes per launch:
+    nnz (4 index + value bytes) + 4 (rows + 1) + s b (rows + cols)."""
+    from paper_1607_01404_gb300 import workloads as wl  # noqa: F401
+
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colidx).to(dev)
+    va = torch.from_numpy(A.vals).to(dev)
+    nnz = A.nnz
+    v32 = torch.empty(nnz, dtype=torch.float32, device=dev)
+    v32lo = torch.empty(nnz, dtype=torch.float32, device=dev)
+    v64 = torch.empty(nnz, dtype=torch.float64, device=dev)
+    flags = torch.zeros(4, dtype=torch.int32, device=dev)
+    B.csr_values(va, v32, v32lo, v64, flags)
+    exact = int(flags[0].item()) == 0
+    At = A.to_scipy().T.tocsr()
+    At.sort_indices()
+    rpT = torch.from_numpy(At.indptr.astype(np.int32)).to(dev)
+    ciT = torch.from_numpy(At.indices.astype(np.int32)).to(dev)
+    vaT = torch.from_numpy(At.data).to(dev)
+    v32T = torch.empty(nnz, dtype=torch.float32, device=dev)
+    v32loT = torch.empty(nnz, dtype=torch.float32, device=dev)
+    v64T = torch.empty(nnz, dtype=torch.float64, device=dev)
+    B.csr_values(vaT, v32T, v32loT, v64T, flags)
+    words = 1 if prec == B.PREC_F32 else 2
+    s = 4 if prec == B.PREC_F32 else 8
+    X = torch.randn(A.n * b * words, dtype=torch.float32, device=dev)
+    Y = torch.zeros(A.m * b * words, dtype=torch.float32, device=dev)
+    W = torch.zeros(A.n * b * words, dtype=torch.float32, device=dev)
+    if prec == B.PREC_DF64:
+        X.view(-1, 2)[:, 1] = 0  # valid double-float words
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    lo, loT = (None, None) if exact else (v32lo, v32loT)
+    vbytes = 4 if (prec != B.PREC_F64) else 8
+    if prec == B.PREC_DF64 and not exact:
+        vbytes = 8
+    res = {}
+    for name, (rows, cols, r, c, vv, vl, src, dst) in {
+        "spmm_A": (A.m, A.n, rp, ci, v32, lo, X, Y),
+        "spmm_AT": (A.n, A.m, rpT, ciT, v32T, loT, Y, W),
+    }.items():
+        v64x = v64 if name == "spmm_A" else v64T
+        for _ in range(3):
+            B.spmm(prec, rows, cols, r, c, vv, vl, v64x, src, b, dst, b, b, stream=sp)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            B.spmm(prec, rows, cols, r, c, vv, vl, v64x, src, b, dst, b, b, stream=sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = nnz * (4 + vbytes) + 4 * (rows + 1) + s * b * (rows + cols)
+        res[name] = {"ms": ms, "bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9}
+    return res
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    from paper_1607_01404_gb300 import binding as B
+    from paper_1607_01404_gb300 import workloads as wl
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    B.lib()
+    A, _ = wl.workload(WORKLOAD)
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colidx).to(dev)
+    va = torch.from_numpy(A.vals).to(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    tgt = B.SVDS_SMALLEST if TARGET == "smallest" else B.SVDS_LARGEST
+
+    def opts(chosen, seed):
+        return B.make_opts(maxBlockSize=BLOCK, stage1_precision=B.SVDS_FP32 if chosen else B.SVDS_FP64,
+                           stage1_polish=1, precond=B.SVDS_PRECOND_JACOBI, seed=seed, stream=sp,
+                           maxSeconds=600.0)
+
+    def one_solve(chosen, seed, host_inputs=False):
+        o = opts(chosen, seed)
+        if host_inputs:
+            h = B.svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, o)
+        else:
+            h = B.svds_create(rp, ci, va, A.m, A.n, o, on_device=True)
+        try:
+            out = B.svds_solve(h, K, tgt, TOL)
+        finally:
+            h.close()
+        return out
+
+    def timed(chosen, steps, seed0):
+        times, stats, last = [], [], None
+        for s in range(steps):
+            barrier(world)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = one_solve(chosen, seed0 + s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            times.append(e0.elapsed_time(e1) / 1e3)
+            stats.append(last[5])
+        return times, stats, last
+
+    log(f"[bench] rank {rank}: warmup {args.warmup}")
+    for w in range(args.warmup):
+        one_solve(True, 100 + w + 1000 * rank)
+    clk = ClockSampler(local)
+    clk.start()
+    t_chosen, st_chosen, last = timed(True, args.steps, 1 + 1000 * rank)
+    clocks = clk.stop()
+    sigma, U, V, rnorm, nconv, stats, rc = last
+    exact = np.sort(np.sqrt((4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[:, None, None]
+                            + (4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[None, :, None]
+                            + (4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[None, None, :]).ravel())[:K]
+    relerr = float(np.max(np.abs(sigma - exact) / exact))
+    # plain FP64-class form on the same workload
+    t_plain, st_plain, lastp = timed(False, max(1, min(args.steps, 2)), 500 + 1000 * rank)
+    relerr_p = float(np.max(np.abs(lastp[0] - exact) / exact))
+    # end to end through host buffers
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    oute = one_solve(True, 7 + 1000 * rank, host_inputs=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - te0
+    h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
+    d2h = 8 * K * (A.m + A.n + 2)
+    # roofline of the dominant kernel family (CSR SpMM, FP32 phase and FP64-class)
+    roof32 = spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK)
+    roofdf = spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK)
+    ms_step = statistics.median(t_chosen) * 1e3
+    ms_step = max_over_ranks(ms_step, world)
+    return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
+                t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
+                roof32=roof32, roofdf=roofdf, ms_step=ms_step, A=A, e2e_nconv=oute[4])
+
+
+def cpu_sample(A, seconds=15.0):
+    """The oracle as it stands on a bounded sample: stage 1 (FP64, GD+k, Jacobi)
+    on the same matrix, stopped after a matvec budget sized to ~`seconds`;
+    returns (matvecs, wall seconds, threads)."""
+    import oracle
+    from paper_1607_01404_gb300 import workloads as wl
+
+    V0 = wl.start_block(A.n, BLOCK, 0)
+    # calibrate: a short run, then one sized to the time budget
+    t0 = time.perf_counter()
+    r = oracle.phsvds(A, K, TARGET, TOL, b=BLOCK, V0=V0, max_matvecs=40, stage2=False, normA=1.0)
+    t1 = time.perf_counter() - t0
+    mv1 = r["stats1"].matvecs
+    budget = int(max(40, mv1 * seconds / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    r = oracle.phsvds(A, K, TARGET, TOL, b=BLOCK, V0=V0, max_matvecs=budget, stage2=False, normA=1.0)
+    t2 = time.perf_counter() - t0
+    return r["stats1"].matvecs, t2, os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    from paper_1607_01404_gb300 import workloads as wl
+
+    if args.impl == "reference":
+        # the CPU oracle is the reference arm: rank 0 only
+        if rank != 0:
+            return 0
+        A, _ = wl.workload(WORKLOAD)
+        vals = []
+        for _ in range(args.warmup + args.steps):
+            mv, secs, cores = cpu_sample(A, args.cpu_seconds / 2)
+            vals.append((mv, secs))
+        vals = vals[args.warmup:]
+        per_mv = statistics.median(s / m for m, s in vals)
+        full = FULL_SOLVE_MATVECS or 0
+        value = per_mv * full if full else None
+        line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=statistics.median(s for _, s in vals) * 1e3,
+                    higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    config=dict(workload=WORKLOAD, m=A.m, n=A.n, nnz=A.nnz, k=K, target=TARGET, block=BLOCK, tol=TOL),
+                    cpu_baseline=dict(value=value, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                                      sample=f"oracle stage-1 GD+k on the full matrix stopped after ~{vals[0][0]} "
+                                             f"matvecs per step; seconds/matvec x {full} matvecs of a full solve"),
+                    e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return 0
+
+    world, rank, local = dist_setup(args.gpus)
+    res = run_gpu(args, world, rank, local)
+    if rank != 0:
+        return 0
+    A = res["A"]
+    peak, peak_kind = measured_peaks()
+    # dominant kernel: reported for the FP32 phase SpMM (the bulk of the matvecs)
+    r32 = res["roof32"]
+    dom = "spmm_AT" if r32["spmm_AT"]["ms"] >= r32["spmm_A"]["ms"] else "spmm_A"
+    achieved = r32[dom]["gbs"]
+    st = res["stats"][-1]
+    launches = int(sum(s["kernel_launches"] for s in res["stats"]))
+    mv_plain = int(res["st_plain"][-1]["matvecs_stage1"] + res["st_plain"][-1]["matvecs_stage2"])
+    cpu = None
+    try:
+        mv, secs, cores = cpu_sample(A, args.cpu_seconds)
+        per_mv = secs / mv
+        cpu = dict(value=per_mv * mv_plain, unit=UNIT, cores=cores, kind="oracle",
+                   sample=f"oracle (FP64 numpy/scipy) stage-1 GD+k on the full matrix for {mv} matvecs "
+                          f"({secs:.1f} s); seconds/matvec x {mv_plain} matvecs of the GPU plain FP64-class solve")
+    except Exception as e:  # the baseline is reported, never required
+        cpu = dict(value=None, unit=UNIT, cores=os.cpu_count(), kind="oracle", sample=f"failed: {e}")
+    value = res["ms_step"] / 1e3
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+        ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
+        dtype="f32+df64", data="synthetic",
+        config=dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
+                    k=K, target=TARGET, block=BLOCK, tol=TOL, precond="jacobi",
+                    form="chosen: FP32 stage-1 phase, FP64-class (double-float) polish and stage 2",
+                    l2="working set >> L2 (no flush)", parallelism=f"replicas x{args.gpus}"),
+        max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
+        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
+                        matvecs=mv_plain, max_rel_sigma_err=res["relerr_plain"]),
+        solve_stats=dict(matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
+                         matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
+                         stage2_used=st["stage2_used"], setup_s=st["seconds_setup"]),
+        roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
+                      frac=achieved / peak, peak_kind=peak_kind, traffic=None,
+                      all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
+                           {**{f"f32_{a}": b for a, b in res["roof32"].items()},
+                            **{f"df64_{a}": b for a, b in res["roofdf"].items()}}.items()}),
+        cpu_baseline=cpu,
+        e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
+                 numConverged=res["e2e_nconv"]),
+        gpu_launches=launches,
+        clocks=res["clocks"],
+    )
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,130 @@
+/* PHSVDS on GB300: C-ABI of the two-stage preconditioned SVD solver.
+ *
+ * The problem statement follows the paper's C interface (Wu, Romero,
+ * Stathopoulos, "PRIMME_SVDS", Sec. 3.4 and Fig. 1): find the k largest or
+ * smallest singular triplets (sigma_i, u_i, v_i) of a sparse m x n matrix A so
+ * that the triplet residual of Eq. (res),
+ *     ||r_i|| = sqrt(||A v_i - sigma_i u_i||^2 + ||A^T u_i - sigma_i v_i||^2),
+ * is below tol * ||A||_2.  The method is Algorithm 1 (PHSVDS): a first stage on
+ * C = A^T A and, if needed, a second stage on B = [0 A^T; A 0] (Sec. 3.1).
+ *
+ * All entry points return 0 on success, a negative SVDS_ERR_* code for invalid
+ * arguments (detected before any device work) or SVDS_ERR_CUDA for a device
+ * error, and SVDS_ERR_MAXIT (> 0) when the matvec or time budget ran out.
+ * No function keeps a pointer to caller memory after it returns.
+ */
+#ifndef PHSVDS_H
+#define PHSVDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define SVDS_OK 0
+#define SVDS_ERR_ARG (-1)      /* null pointer or out-of-range scalar argument */
+#define SVDS_ERR_SHAPE (-2)    /* m, n, nnz or k inconsistent */
+#define SVDS_ERR_CSR (-3)      /* rowptr not monotone, column index unsorted or out of range */
+#define SVDS_ERR_VALUE (-4)    /* non-finite matrix value */
+#define SVDS_ERR_NOMEM (-5)    /* device or host allocation failed, or workspace too small */
+#define SVDS_ERR_CUDA (-6)     /* CUDA runtime error; svds_last_error() has the message */
+#define SVDS_ERR_NUMERIC (-7)  /* unrecoverable breakdown in a small dense problem */
+#define SVDS_ERR_MAXIT 1       /* budget exhausted: the first *numConverged triplets are valid */
+
+/* ---- enumerations ---- */
+#define SVDS_LARGEST 0
+#define SVDS_SMALLEST 1
+
+#define SVDS_GDPK 0  /* GD+k (generalised Davidson with +k restarting) */
+
+#define SVDS_FP64 3  /* FP64-class stage 1 (double-float arithmetic on the GPU) */
+#define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
+#define SVDS_NATIVE_FP64 4 /* native FP64 arithmetic everywhere (check mode; slow on GB300) */
+
+#define SVDS_PRECOND_NONE 0
+#define SVDS_PRECOND_JACOBI 1
+
+/* Sparse matrix in CSR form (0-based).  Column indices must be strictly
+ * increasing inside each row and values finite.  When on_device is non-zero
+ * the three arrays are CUDA device pointers, otherwise host pointers.  The
+ * caller keeps ownership; svds_create copies what it needs. */
+typedef struct {
+  int64_t m, n, nnz;
+  const int32_t *rowptr; /* m + 1 entries, rowptr[0] = 0, rowptr[m] = nnz */
+  const int32_t *colidx; /* nnz entries, 0 <= colidx < n */
+  const double *vals;    /* nnz entries */
+  int on_device;
+} svds_csr;
+
+/* Options.  svds_opts_default() fills the paper's defaults (Sec. 3.4):
+ * maxBasisSize 15 / minRestartSize 6 for fewer than 10 largest values, else
+ * 35 / 14 (raised to k + blockSize and minRestart + 2 blockSize when larger),
+ * block size 1, Jacobi preconditioner for the smallest values. */
+typedef struct {
+  int maxBasisSize;     /* 0 = default */
+  int minRestartSize;   /* 0 = default */
+  int maxBlockSize;     /* 0 = 1 */
+  int method_stage1;    /* SVDS_GDPK */
+  int method_stage2;    /* SVDS_GDPK */
+  int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32 or SVDS_NATIVE_FP64 */
+  int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
+                           to the paper's stage-1 criterion before stage 2 (default 1) */
+  int precond;          /* SVDS_PRECOND_JACOBI (default) or SVDS_PRECOND_NONE */
+  double aNorm;         /* ||A||_2 if known, 0 = estimate */
+  int64_t maxMatvecs;   /* budget in products with A or A^T (per column), 0 = unlimited */
+  double maxSeconds;    /* wall-clock budget, 0 = unlimited */
+  uint64_t seed;        /* seed of the random initial block and breakdown replacements */
+  int printLevel;       /* 0 silent .. 3 per-iteration lines on stderr */
+  int initSize;         /* number of initial right vectors in initV (Sec. 3.4 initSize) */
+  const double *initV;  /* host, n x initSize column-major, or NULL */
+  void *stream;         /* cudaStream_t to run on, or NULL for the library's own stream */
+} svds_opts;
+
+/* Performance report (the paper's stats, Sec. 3.4; matvecs count products
+ * with A or A^T per column as in the paper's tables). */
+typedef struct {
+  int64_t matvecs_stage1, matvecs_stage2;
+  int64_t matvecs_stage1_lowprec; /* part of matvecs_stage1 done in FP32 */
+  int64_t outer_stage1, outer_stage2;
+  int64_t restarts, resets;
+  int stage2_used;
+  double aNorm;               /* ||A|| used in the tolerances */
+  double seconds_setup;       /* device setup inside svds_solve (norm estimate, buffers) */
+  double seconds_stage1, seconds_stage2, seconds_total;
+  int64_t kernel_launches;    /* device kernels launched by this call */
+} svds_stats;
+
+typedef struct svds_handle svds_handle;
+
+/* Fill opts with the defaults above. */
+int svds_opts_default(svds_opts *opts);
+
+/* Copy A to the device, build A^T (deterministic transpose), the value formats
+ * of every precision mode and the Jacobi diagonals (Sec. 3.3: the operator must
+ * apply both A and A^T).  *h receives a new handle owned by the caller. */
+int svds_create(svds_handle **h, const svds_csr *A, const svds_opts *opts);
+
+/* Compute k singular triplets (Algorithm 1).  Outputs are caller-owned host
+ * arrays: sigma[k] (descending for SVDS_LARGEST, ascending for SVDS_SMALLEST),
+ * U (m x k column-major, ld m), V (n x k column-major, ld n), rnorm[k] (Eq. res,
+ * recomputed from the returned vectors).  Each v has its largest-magnitude
+ * entry positive.  Any of U, V, rnorm, stats may be NULL.  *numConverged is
+ * the number of leading triplets that meet the tolerance. */
+int svds_solve(svds_handle *h, int k, int target, double tol, double *sigma, double *U, double *V,
+               double *rnorm, int *numConverged, svds_stats *stats);
+
+/* Release the handle and its device memory (NULL is accepted). */
+void svds_destroy(svds_handle *h);
+
+/* Static message for an error code. */
+const char *svds_strerror(int code);
+/* Message of the last SVDS_ERR_CUDA in this thread (empty if none). */
+const char *svds_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHSVDS_H */

@@ -1,0 +1,87 @@
+/* PHSVDS on GB300: kernel-level C-ABI (per-kernel parity tests, custom drivers).
+ *
+ * Every entry point works on caller-owned CUDA device memory, enqueues its
+ * kernels on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * returns 0, SVDS_ERR_ARG for an invalid argument (checked before any launch)
+ * or SVDS_ERR_CUDA on a launch error.  Nothing is allocated: buffers that need
+ * scratch take it from the caller (sizes from the *_bytes queries).
+ *
+ * Precision modes (prec):
+ *   1 = F32  : float storage and arithmetic;
+ *   2 = DF64 : double-float storage (pairs (hi, lo) of floats, 8 bytes per
+ *              element, value hi + lo) and double-float arithmetic (FP64-class);
+ *   3 = F64  : double storage and native FP64 arithmetic.
+ * Blocks of vectors are row-major: element (r, j) of a block with leading
+ * dimension ld is at base[r * ld + j] (in elements of the mode's storage type).
+ * Small coefficient matrices are row-major in the mode's coefficient format
+ * (float, float pair or double; see phsvds_coef_convert).
+ */
+#ifndef PHSVDS_KERNELS_H
+#define PHSVDS_KERNELS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Y (rows x b, ldy) = A X (cols x b, ldx) for CSR A (the user matvec of the
+ * paper's Sec. 3.4; A^T products use the CSR of A^T).  Values: F32 reads v32;
+ * DF64 reads v32 (+ v32lo unless it is NULL, meaning every value is a float);
+ * F64 reads v64. */
+int phsvds_spmm(int prec, int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                const float *v32, const float *v32lo, const double *v64, const void *X, int64_t ldx, void *Y,
+                int64_t ldy, int b, void *stream);
+
+/* G (p x q row-major doubles, device) = P^T Q over rows [r0, r1) (the Table 3
+ * inner products: Rayleigh-Ritz projection V^T W, Gram matrices of CGS and
+ * CholQR).  Accumulation is FP64-class in every mode and the reduction order
+ * is fixed (deterministic).  p <= 256; any q. */
+int phsvds_gram(int prec, int64_t r0, int64_t r1, const void *P, int64_t ldp, int p, const void *Q, int64_t ldq,
+                int q, double *G, void *scratch, size_t scratch_bytes, void *stream);
+size_t phsvds_gram_scratch_bytes(int p, int q);
+
+/* Out (L x q) = alpha In + P coef (p x q), then Out <- Out Rinv when Rinv is
+ * not NULL (q x q upper triangular).  Out may equal P (in-place restart
+ * V <- V Z with q <= p) or In. */
+int phsvds_combine(int prec, int64_t L, const void *P, int64_t ldp, int p, const void *coef, const void *In,
+                   int64_t ldin, int alpha_one, void *Out, int64_t ldout, int q, const void *Rinv, void *stream);
+
+/* Fused Ritz vectors and residuals (Sec. 3.3 residual kernel):
+ * X = V Y, R = W Y - X diag(theta), norms2[j] = ||R_j||^2 (device doubles).
+ * V, W: L x g with leading dimension ldv; X, R: L x nb with leading dimension ldb. */
+int phsvds_ritz_residual(int prec, int64_t L, const void *V, const void *W, int64_t ldv, int g, const void *Y,
+                         const void *theta, void *X, void *R, int64_t ldb, int nb, double *norms2, void *scratch,
+                         size_t scratch_bytes, void *stream);
+size_t phsvds_ritz_scratch_bytes(int nb);
+
+/* Conversions between FP64 column-major (src/dst with leading dimension lds/ldd
+ * counted in rows) and the mode's row-major storage. */
+int phsvds_from_f64(int prec, int64_t L, int nc, const double *src, int64_t lds, void *dst, int64_t ldd, void *stream);
+int phsvds_to_f64(int prec, int64_t L, int nc, const void *src, int64_t lds, double *dst, int64_t ldd, void *stream);
+
+/* Deterministic CSR transpose (rows x cols -> cols x rows, indices increasing in
+ * each row of the result).  work: phsvds_csr_transpose_work_bytes(cols) bytes. */
+int phsvds_csr_transpose(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                         const double *vals, int32_t *rowptrT, int32_t *colidxT, double *valsT, void *work,
+                         size_t work_bytes, void *stream);
+size_t phsvds_csr_transpose_work_bytes(int64_t cols);
+
+/* CSR value formats: v32 = fl32(v), v32lo = fl32(v - v32), v64 = v; *flags |= 1
+ * if any v32lo != 0 (flags is a device int). */
+int phsvds_csr_values(int64_t nnz, const double *vals, float *v32, float *v32lo, double *v64, int *flags, void *stream);
+
+/* Host: convert doubles to the mode's coefficient format (count elements). */
+int phsvds_coef_convert(int prec, const double *src, size_t count, void *dst);
+
+/* Host small dense FP64 problems of the engine (column-major, n <= 512):
+ * symmetric eigendecomposition (ascending) and right singular vectors of a
+ * square matrix (ascending singular values). */
+int phsvds_host_symeig(int n, const double *A, double *w, double *Z);
+int phsvds_host_svd(int n, const double *R, double *s, double *Yr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHSVDS_KERNELS_H */

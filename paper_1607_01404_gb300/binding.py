@@ -1,0 +1,327 @@
+"""ctypes binding of the PHSVDS C-ABI (include/phsvds.h, include/phsvds_kernels.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  There is no fallback: if ``libphsvds.so`` is missing or cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphsvds.so")
+
+SVDS_OK = 0
+SVDS_ERR_ARG = -1
+SVDS_ERR_SHAPE = -2
+SVDS_ERR_CSR = -3
+SVDS_ERR_VALUE = -4
+SVDS_ERR_NOMEM = -5
+SVDS_ERR_CUDA = -6
+SVDS_ERR_NUMERIC = -7
+SVDS_ERR_MAXIT = 1
+SVDS_LARGEST = 0
+SVDS_SMALLEST = 1
+SVDS_GDPK = 0
+SVDS_FP32 = 1
+SVDS_FP64 = 3
+SVDS_NATIVE_FP64 = 4
+SVDS_PRECOND_NONE = 0
+SVDS_PRECOND_JACOBI = 1
+
+PREC_F32, PREC_DF64, PREC_F64 = 1, 2, 3
+
+
+class svds_csr(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p), ("vals", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class svds_opts(C.Structure):
+    _fields_ = [("maxBasisSize", C.c_int), ("minRestartSize", C.c_int), ("maxBlockSize", C.c_int),
+                ("method_stage1", C.c_int), ("method_stage2", C.c_int), ("stage1_precision", C.c_int),
+                ("stage1_polish", C.c_int), ("precond", C.c_int), ("aNorm", C.c_double),
+                ("maxMatvecs", C.c_int64), ("maxSeconds", C.c_double), ("seed", C.c_uint64),
+                ("printLevel", C.c_int), ("initSize", C.c_int), ("initV", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
+class svds_stats(C.Structure):
+    _fields_ = [("matvecs_stage1", C.c_int64), ("matvecs_stage2", C.c_int64),
+                ("matvecs_stage1_lowprec", C.c_int64), ("outer_stage1", C.c_int64),
+                ("outer_stage2", C.c_int64), ("restarts", C.c_int64), ("resets", C.c_int64),
+                ("stage2_used", C.c_int), ("aNorm", C.c_double), ("seconds_setup", C.c_double),
+                ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
+                ("seconds_total", C.c_double), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# exported symbol -> (restype, argtypes)
+_SIGS = {
+    "svds_opts_default": (C.c_int, [C.POINTER(svds_opts)]),
+    "svds_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(svds_csr), C.POINTER(svds_opts)]),
+    "svds_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.POINTER(C.c_int), C.POINTER(svds_stats)]),
+    "svds_destroy": (None, [C.c_void_p]),
+    "svds_strerror": (C.c_char_p, [C.c_int]),
+    "svds_last_error": (C.c_char_p, []),
+    "phsvds_spmm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,
+                              C.c_void_p]),
+    "phsvds_gram": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
+                              C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "phsvds_gram_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "phsvds_combine": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "phsvds_ritz_residual": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "phsvds_ritz_scratch_bytes": (C.c_size_t, [C.c_int]),
+    "phsvds_from_f64": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                  C.c_void_p]),
+    "phsvds_to_f64": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                C.c_void_p]),
+    "phsvds_csr_transpose": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "phsvds_csr_transpose_work_bytes": (C.c_size_t, [C.c_int64]),
+    "phsvds_csr_values": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "phsvds_coef_convert": (C.c_int, [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "phsvds_host_symeig": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_host_svd": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def lib():
+    """Load libphsvds.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1607_01404_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+class SvdsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().svds_strerror(code).decode()
+        extra = lib().svds_last_error().decode() if code == SVDS_ERR_CUDA else ""
+        super().__init__(f"{where}: {msg} ({code}) {extra}".strip())
+        self.code = code
+
+
+def _check(code: int, where: str, allow_maxit: bool = False):
+    if code == SVDS_OK or (allow_maxit and code == SVDS_ERR_MAXIT):
+        return code
+    raise SvdsError(code, where)
+
+
+def svds_opts_default() -> svds_opts:
+    o = svds_opts()
+    _check(lib().svds_opts_default(C.byref(o)), "svds_opts_default")
+    return o
+
+
+def svds_strerror(code: int) -> str:
+    return lib().svds_strerror(code).decode()
+
+
+@dataclass
+class Handle:
+    ptr: C.c_void_p
+    m: int
+    n: int
+    _keep: tuple = ()
+
+    def close(self):
+        if self.ptr:
+            lib().svds_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(**kw) -> svds_opts:
+    o = svds_opts_default()
+    keep = []
+    for k, v in kw.items():
+        if k == "initV" and v is not None:
+            arr = np.asfortranarray(np.asarray(v, dtype=np.float64))
+            keep.append(arr)
+            o.initV = arr.ctypes.data
+            o.initSize = arr.shape[1] if arr.ndim == 2 else 1
+        elif k == "stream":
+            o.stream = v
+        elif v is not None:
+            setattr(o, k, v)
+    o._keep = keep  # keep the guesses alive until svds_create copied them
+    return o
+
+
+def svds_create(rowptr, colidx, vals, m: int, n: int, opts: svds_opts | None = None, on_device: bool = False) -> Handle:
+    """Create a handle from CSR arrays (numpy host arrays, or torch CUDA tensors with on_device=True)."""
+    if on_device:
+        rp, ci, va = rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr()
+        nnz = int(colidx.numel())
+        keep = (rowptr, colidx, vals)
+    else:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        rp, ci, va = rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data
+        nnz = int(colidx.shape[0])
+        keep = (rowptr, colidx, vals)
+    A = svds_csr(m, n, nnz, rp, ci, va, 1 if on_device else 0)
+    h = C.c_void_p()
+    _check(lib().svds_create(C.byref(h), C.byref(A), C.byref(opts) if opts is not None else None), "svds_create")
+    return Handle(h, m, n, keep)
+
+
+def svds_solve(h: Handle, k: int, target: int, tol: float, want_vectors: bool = True):
+    """Returns (sigma, U, V, rnorm, numConverged, stats dict, return code)."""
+    sigma = np.zeros(k)
+    rnorm = np.zeros(k)
+    U = np.zeros((h.m, k), order="F") if want_vectors else None
+    V = np.zeros((h.n, k), order="F") if want_vectors else None
+    nconv = C.c_int(0)
+    st = svds_stats()
+    rc = lib().svds_solve(h.ptr, k, target, tol, sigma.ctypes.data,
+                          U.ctypes.data if U is not None else None,
+                          V.ctypes.data if V is not None else None,
+                          rnorm.ctypes.data, C.byref(nconv), C.byref(st))
+    _check(rc, "svds_solve", allow_maxit=True)
+    return sigma, U, V, rnorm, nconv.value, st.as_dict(), rc
+
+
+def svds_destroy(h: Handle):
+    h.close()
+
+
+def svds(A, k: int, target: str = "largest", tol: float = 1e-10, **opts):
+    """Convenience: A is a workloads.CSR (host); returns a dict like the oracle's."""
+    o = make_opts(**opts)
+    h = svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, o)
+    try:
+        tgt = SVDS_LARGEST if target == "largest" else SVDS_SMALLEST
+        sigma, U, V, rnorm, nconv, stats, rc = svds_solve(h, k, tgt, tol)
+    finally:
+        h.close()
+    return dict(sigma=sigma, U=U, V=V, rnorm=rnorm, nconv=nconv, stats=stats, rc=rc)
+
+
+# ---- kernel-level wrappers (torch CUDA tensors; for parity tests) ----
+def _stream(stream):
+    return None if stream is None else stream
+
+
+def spmm(prec, rows, cols, rowptr, colidx, v32, v32lo, v64, X, ldx, Y, ldy, b, stream=None):
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    nnz = int(colidx.numel())
+    _check(lib().phsvds_spmm(prec, rows, cols, nnz, ptr(rowptr), ptr(colidx), ptr(v32), ptr(v32lo), ptr(v64),
+                             ptr(X), ldx, ptr(Y), ldy, b, _stream(stream)), "phsvds_spmm")
+
+
+def gram(prec, r0, r1, P, ldp, p, Q, ldq, q, G, scratch, stream=None):
+    _check(lib().phsvds_gram(prec, r0, r1, P.data_ptr(), ldp, p, Q.data_ptr(), ldq, q, G.data_ptr(),
+                             scratch.data_ptr(), scratch.numel() * scratch.element_size(), _stream(stream)),
+           "phsvds_gram")
+
+
+def gram_scratch_bytes(p, q):
+    return int(lib().phsvds_gram_scratch_bytes(p, q))
+
+
+def combine(prec, L, P, ldp, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv=None, stream=None):
+    _check(lib().phsvds_combine(prec, L, P.data_ptr(), ldp, p, coef.data_ptr(),
+                                In.data_ptr() if In is not None else None, ldin, alpha_one, Out.data_ptr(), ldout, q,
+                                Rinv.data_ptr() if Rinv is not None else None, _stream(stream)), "phsvds_combine")
+
+
+def ritz_residual(prec, L, V, W, ldv, g, Y, theta, X, R, ldb, nb, norms2, scratch, stream=None):
+    _check(lib().phsvds_ritz_residual(prec, L, V.data_ptr(), W.data_ptr(), ldv, g, Y.data_ptr(), theta.data_ptr(),
+                                      X.data_ptr(), R.data_ptr(), ldb, nb, norms2.data_ptr(), scratch.data_ptr(),
+                                      scratch.numel() * scratch.element_size(), _stream(stream)),
+           "phsvds_ritz_residual")
+
+
+def ritz_scratch_bytes(nb):
+    return int(lib().phsvds_ritz_scratch_bytes(nb))
+
+
+def from_f64(prec, L, nc, src, lds, dst, ldd, stream=None):
+    _check(lib().phsvds_from_f64(prec, L, nc, src.data_ptr(), lds, dst.data_ptr(), ldd, _stream(stream)),
+           "phsvds_from_f64")
+
+
+def to_f64(prec, L, nc, src, lds, dst, ldd, stream=None):
+    _check(lib().phsvds_to_f64(prec, L, nc, src.data_ptr(), lds, dst.data_ptr(), ldd, _stream(stream)),
+           "phsvds_to_f64")
+
+
+def csr_transpose(rows, cols, rowptr, colidx, vals, rowptrT, colidxT, valsT, work, stream=None):
+    nnz = int(colidx.numel())
+    _check(lib().phsvds_csr_transpose(rows, cols, nnz, rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(),
+                                      rowptrT.data_ptr(), colidxT.data_ptr(), valsT.data_ptr(), work.data_ptr(),
+                                      work.numel() * work.element_size(), _stream(stream)), "phsvds_csr_transpose")
+
+
+def csr_transpose_work_bytes(cols):
+    return int(lib().phsvds_csr_transpose_work_bytes(cols))
+
+
+def csr_values(vals, v32, v32lo, v64, flags, stream=None):
+    _check(lib().phsvds_csr_values(int(vals.numel()), vals.data_ptr(), v32.data_ptr(), v32lo.data_ptr(),
+                                   v64.data_ptr(), flags.data_ptr(), _stream(stream)), "phsvds_csr_values")
+
+
+def coef_convert(prec, src: np.ndarray) -> np.ndarray:
+    """Host conversion of doubles to the mode's coefficient format (returned as raw float32/float64 words)."""
+    src = np.ascontiguousarray(src, dtype=np.float64).ravel()
+    if prec == PREC_F32:
+        out = np.zeros(src.size, dtype=np.float32)
+    elif prec == PREC_DF64:
+        out = np.zeros(2 * src.size, dtype=np.float32)
+    else:
+        out = np.zeros(src.size, dtype=np.float64)
+    _check(lib().phsvds_coef_convert(prec, src.ctypes.data, src.size, out.ctypes.data), "phsvds_coef_convert")
+    return out
+
+
+def host_symeig(A: np.ndarray):
+    A = np.asfortranarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    Z = np.zeros((n, n), order="F")
+    _check(lib().phsvds_host_symeig(n, A.ctypes.data, w.ctypes.data, Z.ctypes.data), "phsvds_host_symeig")
+    return w, Z
+
+
+def host_svd(R: np.ndarray):
+    R = np.asfortranarray(R, dtype=np.float64)
+    n = R.shape[0]
+    s = np.zeros(n)
+    Y = np.zeros((n, n), order="F")
+    _check(lib().phsvds_host_svd(n, R.ctypes.data, s.ctypes.data, Y.ctypes.data), "phsvds_host_svd")
+    return s, Y

@@ -1,0 +1,1224 @@
+// PHSVDS solver engine: the host control loop of Algorithm 1 driving the
+// device kernels.  Long vectors never leave the device; per outer iteration
+// only the small projections (Gram blocks and residual norms) are copied to
+// the host and only small coefficient matrices are copied back (Sec. 3.3: the
+// small objects are replicated, the long ones distributed / device-resident).
+#include "engine.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hostla.h"
+
+namespace phsvds {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct CudaFail {
+  cudaError_t e;
+  const char* where;
+};
+struct NumFail {
+  const char* what;
+};
+struct BudgetOut {};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t _e = (x);                       \
+    if (_e != cudaSuccess) throw CudaFail{_e, #x}; \
+  } while (0)
+
+enum { OP_C = 0, OP_B = 1 };
+
+// Unit roundoff of each storage/arithmetic mode (double-float: the sloppy
+// addition of two double-words keeps about 2^-48 relative accuracy).
+double unit_roundoff(int prec) {
+  if (prec == kF32) return std::ldexp(1.0, -24);
+  if (prec == kDF64) return std::ldexp(1.0, -48);
+  return std::ldexp(1.0, -53);
+}
+
+// ---------------------------------------------------------------------------
+// Per-solve device context
+// ---------------------------------------------------------------------------
+struct Ctx {
+  svds_handle* h = nullptr;
+  cudaStream_t st = nullptr;
+  const DevMatrix* A = nullptr;
+  void* partial = nullptr;
+  int maxblk = 0;
+  double* dG = nullptr;
+  double* hG = nullptr;
+  size_t gcap = 0;  // doubles
+  char* hstage = nullptr;
+  char* dstage = nullptr;
+  int nslots = 0;
+  size_t slot_bytes = 0;
+  int next_slot = 0;
+  std::vector<long long> slot_epoch;
+  long long epoch = 1;
+  long long mv = 0;
+  long long launches = 0;
+  long long max_mv = 0;
+  double max_sec = 0;
+  Clock::time_point t0;
+  int print = 0;
+  unsigned long long seed = 0, seed_ctr = 0;
+  long long restarts = 0, resets = 0;
+
+  void sync() {
+    CK(cudaStreamSynchronize(st));
+    ++epoch;
+  }
+  double elapsed() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+  void budget() {
+    if (max_mv > 0 && mv >= max_mv) throw BudgetOut{};
+    if (max_sec > 0 && elapsed() > max_sec) throw BudgetOut{};
+  }
+  // Upload a coefficient array (host doubles, the kernel's row-major layout)
+  // converted to the mode's coefficient format; stream-ordered.
+  const void* upload(int prec, const double* src, size_t count) {
+    const size_t bytes = count * coef_bytes(prec);
+    if (bytes > slot_bytes) throw NumFail{"coefficient block larger than the staging slot"};
+    const int s = next_slot;
+    next_slot = (next_slot + 1) % nslots;
+    if (slot_epoch[s] == epoch) sync();
+    host_coef_convert(prec, src, count, hstage + (size_t)s * slot_bytes);
+    CK(cudaMemcpyAsync(dstage + (size_t)s * slot_bytes, hstage + (size_t)s * slot_bytes, bytes,
+                       cudaMemcpyHostToDevice, st));
+    slot_epoch[s] = epoch;
+    return dstage + (size_t)s * slot_bytes;
+  }
+};
+
+inline char* off(void* p, long long elems, int prec) { return reinterpret_cast<char*>(p) + elems * (long long)elem_bytes(prec); }
+inline const char* off(const void* p, long long elems, int prec) {
+  return reinterpret_cast<const char*>(p) + elems * (long long)elem_bytes(prec);
+}
+
+int spmm_launches(int b) {
+  int n = 0;
+  while (b > 0) {
+    b -= b >= 8 ? 8 : b >= 4 ? 4 : b >= 2 ? 2 : 1;
+    ++n;
+  }
+  return n;
+}
+
+// Gram G = [P...]^T Q over rows [r0, r1); result p x q row-major (host).
+std::vector<double> gram(Ctx& c, int prec, long long r0, long long r1, const std::vector<SegV>& P, SegV Q) {
+  int p = 0;
+  for (auto& s : P) p += s.nc;
+  const int q = Q.nc;
+  if (p > 256 || p < 1 || q < 1) throw NumFail{"gram shape out of range"};
+  if ((size_t)p * q > c.gcap) throw NumFail{"gram result larger than the staging buffer"};
+  std::vector<double> out((size_t)p * q);
+  for (int c0 = 0; c0 < q; c0 += 8) {
+    const int qc = std::min(8, q - c0);
+    SegV Qc{off(Q.p, c0, prec), Q.ld, qc};
+    int nb = 0;
+    CK(launch_gram(prec, r0, r1, P.data(), (int)P.size(), Qc, c.partial, c.maxblk, &nb, c.st));
+    CK(launch_gram_reduce(prec, c.partial, nb, p * qc, c.dG + (size_t)p * c0, c.st));
+    c.launches += 2;
+  }
+  CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * p * q, cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  for (int c0 = 0; c0 < q; c0 += 8) {
+    const int qc = std::min(8, q - c0);
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < qc; ++j) out[(size_t)i * q + c0 + j] = c.hG[(size_t)p * c0 + (size_t)i * qc + j];
+  }
+  return out;
+}
+
+void combine(Ctx& c, int prec, long long L, const std::vector<SegV>& P, const std::vector<double>& coef_rm,
+             const void* In, long long ldin, bool alpha_one, void* Out, long long ldout, int q,
+             const std::vector<double>* Rinv_rm = nullptr, void* Out2 = nullptr, long long ldout2 = 0) {
+  const void* dcoef = c.upload(prec, coef_rm.data(), coef_rm.size());
+  const void* dR = Rinv_rm ? c.upload(prec, Rinv_rm->data(), Rinv_rm->size()) : nullptr;
+  CK(launch_combine(prec, L, P.data(), (int)P.size(), dcoef, In, ldin, alpha_one ? 1 : 0, Out, ldout, q, dR, Out2,
+                    ldout2, c.st));
+  c.launches += 1;
+}
+
+// Apply C = A^T A (through tmp, m x nb, ld nb) or B = [0 A^T; A 0].
+void apply_op(Ctx& c, int prec, int op, const void* X, long long ldx, void* Y, long long ldy, int nb, void* tmp,
+              int tmp_cols) {
+  const DevMatrix& A = *c.A;
+  for (int c0 = 0; c0 < nb; c0 += tmp_cols) {
+    const int w = std::min(tmp_cols, nb - c0);
+    const void* Xc = off(X, c0, prec);
+    void* Yc = off(Y, c0, prec);
+    if (op == OP_C) {
+      CK(launch_spmm(prec, A.csr(false), Xc, ldx, tmp, w, w, c.st));
+      CK(launch_spmm(prec, A.csr(true), tmp, w, Yc, ldy, w, c.st));
+    } else {
+      CK(launch_spmm(prec, A.csr(true), off(Xc, A.n * ldx, prec), ldx, Yc, ldy, w, c.st));
+      CK(launch_spmm(prec, A.csr(false), Xc, ldx, off(Yc, A.n * ldy, prec), ldy, w, c.st));
+    }
+    c.launches += 2 * spmm_launches(w);
+    c.mv += 2LL * w;
+  }
+}
+
+// small helpers on column-major host matrices
+std::vector<double> rowmajor(int rows, int cols, const double* cm, int ld) {
+  std::vector<double> r((size_t)rows * cols);
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) r[(size_t)i * cols + j] = cm[(size_t)j * ld + i];
+  return r;
+}
+
+struct OrthoRes {
+  std::vector<double> C;  // p x nb row-major: coefficients on the basis
+  std::vector<double> R;  // nb x nb row-major upper triangular
+  bool replaced = false;
+};
+
+// Orthonormalise T (L x nb, ld ldt) against the orthonormal basis segments:
+// classical Gram-Schmidt twice, then Cholesky-QR twice (the second CGS Gram is
+// fused with the first Cholesky Gram).  T0 = basis * C + T_final * R.
+OrthoRes ortho(Ctx& c, int prec, long long L, const std::vector<SegV>& basis, void* T, long long ldt, int nb,
+               void* Out2, long long ldo2, int depth = 0) {
+  int p = 0;
+  for (auto& s : basis) p += s.nc;
+  SegV Ts{T, ldt, nb};
+  std::vector<SegV> PT = basis;
+  PT.push_back(Ts);
+  OrthoRes res;
+  res.C.assign((size_t)p * nb, 0.0);
+  std::vector<double> G = gram(c, prec, 0, L, PT, Ts);  // (p + nb) x nb
+  std::vector<double> norms0(nb);
+  for (int j = 0; j < nb; ++j) norms0[j] = G[(size_t)(p + j) * nb + j];
+  std::vector<double> S((size_t)nb * nb);  // row-major
+  std::vector<double> C2((size_t)p * nb, 0.0);
+  if (p > 0) {
+    std::vector<double> negC((size_t)p * nb);
+    for (size_t e = 0; e < negC.size(); ++e) {
+      negC[e] = -G[e];
+      res.C[e] = G[e];
+    }
+    combine(c, prec, L, basis, negC, T, ldt, true, T, ldt, nb);
+    G = gram(c, prec, 0, L, PT, Ts);
+    for (size_t e = 0; e < C2.size(); ++e) C2[e] = G[e];
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double s = G[(size_t)(p + i) * nb + j];
+        for (int l = 0; l < p; ++l) s -= C2[(size_t)l * nb + i] * C2[(size_t)l * nb + j];
+        S[(size_t)i * nb + j] = s;
+      }
+    for (size_t e = 0; e < C2.size(); ++e) res.C[e] += C2[e];
+  } else {
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) S[(size_t)i * nb + j] = G[(size_t)i * nb + j];
+  }
+  // breakdown: a column that lost (almost) all of its norm is replaced by a
+  // random vector and the whole block is orthonormalised again
+  std::vector<int> bad;
+  for (int j = 0; j < nb; ++j)
+    if (!(S[(size_t)j * nb + j] > 1e-20 * std::max(norms0[j], 1e-300))) bad.push_back(j);
+  if (!bad.empty()) {
+    if (depth >= 3) throw NumFail{"orthogonalisation breakdown persists"};
+    for (int j : bad) {
+      CK(launch_fill_normal(prec, L, off(T, j, prec), ldt, 1, c.seed + 0x1000 + (++c.seed_ctr), c.st));
+      c.launches += 1;
+    }
+    OrthoRes r2 = ortho(c, prec, L, basis, T, ldt, nb, Out2, ldo2, depth + 1);
+    r2.replaced = true;
+    return r2;
+  }
+  // first Cholesky-QR (shifted if needed, Fukaya et al. 2020)
+  std::vector<double> Scm((size_t)nb * nb), R1((size_t)nb * nb), R1i((size_t)nb * nb);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) Scm[(size_t)j * nb + i] = S[(size_t)i * nb + j];
+  bool extra = false;
+  if (!hla::chol_upper(nb, Scm.data(), R1.data())) {
+    double tr = 0;
+    for (int j = 0; j < nb; ++j) tr += std::fabs(Scm[(size_t)j * nb + j]);
+    const double shift = 11.0 * ((double)L * nb + (double)nb * (nb + 1)) * unit_roundoff(prec) * tr;
+    for (int j = 0; j < nb; ++j) Scm[(size_t)j * nb + j] += shift;
+    if (!hla::chol_upper(nb, Scm.data(), R1.data())) throw NumFail{"shifted Cholesky-QR failed"};
+    extra = true;
+  }
+  hla::tri_inv_upper(nb, R1.data(), R1i.data());
+  std::vector<double> R1i_rm = rowmajor(nb, nb, R1i.data(), nb);
+  if (p > 0) {
+    std::vector<double> negC2((size_t)p * nb);
+    for (size_t e = 0; e < C2.size(); ++e) negC2[e] = -C2[e];
+    combine(c, prec, L, basis, negC2, T, ldt, true, T, ldt, nb, &R1i_rm);
+  } else {
+    combine(c, prec, L, {Ts}, R1i_rm, nullptr, 0, false, T, ldt, nb);
+  }
+  std::vector<double> Rtot = R1;  // column-major
+  const int passes = extra ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
+    std::vector<double> G3 = gram(c, prec, 0, L, {Ts}, Ts);
+    std::vector<double> G3cm((size_t)nb * nb), R2((size_t)nb * nb), R2i((size_t)nb * nb);
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) G3cm[(size_t)j * nb + i] = G3[(size_t)i * nb + j];
+    if (!hla::chol_upper(nb, G3cm.data(), R2.data())) throw NumFail{"second Cholesky-QR failed"};
+    hla::tri_inv_upper(nb, R2.data(), R2i.data());
+    const bool last = pass + 1 == passes;
+    combine(c, prec, L, {Ts}, rowmajor(nb, nb, R2i.data(), nb), nullptr, 0, false, T, ldt, nb, nullptr,
+            last ? Out2 : nullptr, ldo2);
+    std::vector<double> Rn((size_t)nb * nb, 0.0);
+    hla::gemm_nn(nb, nb, nb, R2.data(), nb, Rtot.data(), nb, Rn.data(), nb);
+    Rtot = Rn;
+  }
+  res.R = rowmajor(nb, nb, Rtot.data(), nb);
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// Buffers of one eigensolver run
+// ---------------------------------------------------------------------------
+struct RunBufs {
+  int prec = kDF64;
+  long long L = 0;
+  long long ldv = 0;
+  int b = 1;
+  void* V = nullptr;
+  void* W = nullptr;
+  void* Q = nullptr;      // refined extraction only
+  void* Xb = nullptr;     // L x b
+  void* Rb = nullptr;     // L x b
+  void* Tb = nullptr;     // L x b
+  void* Zb = nullptr;     // L x b (refined)
+  void* BXb = nullptr;    // L x b (stage-2 checks)
+  void* tmp = nullptr;    // m x b (C op)
+  void* Xlock = nullptr;  // L x k (refined)
+};
+
+using ConvFn = std::function<void(const double* theta, const double* rn, int off, int nc, char* ok)>;
+
+struct RunCfg {
+  int op = OP_C;
+  int k = 1, b = 1, mb = 15, mr = 6;
+  bool smallest = true;
+  double normop = 0, u = 0;
+  const void* dscale = nullptr;
+  const void* V0 = nullptr;
+  long long ldv0 = 0;
+  int b0 = 1;
+  ConvFn conv;
+  const char* name = "";
+};
+
+struct RunOut {
+  std::vector<double> theta;
+  long long outer = 0;
+};
+
+void put_block_rm(std::vector<double>& dst, int g, const double* Ycm, int ldy, const std::vector<int>& cols) {
+  const int q = (int)cols.size();
+  dst.assign((size_t)g * q, 0.0);
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < q; ++j) dst[(size_t)i * q + j] = Ycm[(size_t)cols[j] * ldy + i];
+}
+
+// Ritz vectors / residuals / norms for the coefficient columns `cols` of Y
+// (column-major g x g) into columns [o, o + |cols|) of Xb and Rb.
+std::vector<double> ritz_cols(Ctx& c, RunBufs& B, int g, const std::vector<double>& Ycm,
+                              const std::vector<double>& theta, const std::vector<int>& cols, int o,
+                              const void* dscale = nullptr) {
+  const int prec = B.prec;
+  const int nt = (int)cols.size();
+  std::vector<double> Ysel;
+  put_block_rm(Ysel, g, Ycm.data(), g, cols);
+  std::vector<double> th(nt);
+  for (int j = 0; j < nt; ++j) th[j] = theta[cols[j]];
+  const void* dY = c.upload(prec, Ysel.data(), Ysel.size());
+  const void* dT = c.upload(prec, th.data(), th.size());
+  int nbl = 0;
+  CK(launch_ritz_residual(prec, B.L, SegV{B.V, B.ldv, g}, SegV{B.W, B.ldv, g}, g, dY, dT, off(B.Xb, o, prec),
+                          off(B.Rb, o, prec), B.b, nt, dscale, dscale ? off(B.Tb, o, prec) : nullptr, c.partial,
+                          c.maxblk, &nbl, c.st));
+  CK(launch_gram_reduce(prec, c.partial, nbl, nt, c.dG, c.st));
+  c.launches += 2;
+  CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  std::vector<double> rn(nt);
+  for (int j = 0; j < nt; ++j) rn[j] = std::sqrt(std::max(c.hG[j], 0.0));
+  return rn;
+}
+
+void init_basis(Ctx& c, RunBufs& B, const RunCfg& cfg, int op, int& g, std::vector<double>& H,
+                const std::vector<SegV>& against) {
+  const int prec = B.prec;
+  CK(launch_copy_cols(prec, B.L, cfg.V0, cfg.ldv0, B.V, B.ldv, cfg.b0, c.st));
+  c.launches += 1;
+  ortho(c, prec, B.L, against, B.V, B.ldv, cfg.b0, nullptr, 0);
+  apply_op(c, prec, op, B.V, B.ldv, B.W, B.ldv, cfg.b0, B.tmp, B.b);
+  g = cfg.b0;
+  std::vector<double> Hr = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g}}, SegV{B.W, B.ldv, g});
+  H.assign((size_t)g * g, 0.0);
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < g; ++j) H[(size_t)j * g + i] = 0.5 * (Hr[(size_t)i * g + j] + Hr[(size_t)j * g + i]);
+}
+
+void extend_H(std::vector<double>& H, int g, int nbk, const std::vector<double>& Hext /*(g+nbk) x nbk rm*/) {
+  const int gn = g + nbk;
+  std::vector<double> Hn((size_t)gn * gn, 0.0);
+  for (int j = 0; j < g; ++j)
+    for (int i = 0; i < g; ++i) Hn[(size_t)j * gn + i] = H[(size_t)j * g + i];
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < nbk; ++j) {
+      const double v = Hext[(size_t)i * nbk + j];
+      Hn[(size_t)(g + j) * gn + i] = v;
+      Hn[(size_t)i * gn + (g + j)] = v;
+    }
+  for (int i = 0; i < nbk; ++i)
+    for (int j = 0; j < nbk; ++j)
+      Hn[(size_t)(g + j) * gn + (g + i)] =
+          0.5 * (Hext[(size_t)(g + i) * nbk + j] + Hext[(size_t)(g + j) * nbk + i]);
+  H.swap(Hn);
+}
+
+// Z^T H Z for column-major H (g x g) and Z (g x gz).
+std::vector<double> project_H(const std::vector<double>& H, int g, const std::vector<double>& Z, int gz) {
+  std::vector<double> HZ((size_t)g * gz), Hn((size_t)gz * gz);
+  hla::gemm_nn(g, gz, g, H.data(), g, Z.data(), g, HZ.data(), g);
+  hla::gemm_tn(gz, gz, g, Z.data(), g, HZ.data(), g, Hn.data(), gz);
+  for (int i = 0; i < gz; ++i)
+    for (int j = i + 1; j < gz; ++j) {
+      const double v = 0.5 * (Hn[(size_t)j * gz + i] + Hn[(size_t)i * gz + j]);
+      Hn[(size_t)j * gz + i] = v;
+      Hn[(size_t)i * gz + j] = v;
+    }
+  return Hn;
+}
+
+void reset_basis(Ctx& c, RunBufs& B, int op, int g, std::vector<double>& H, const std::vector<SegV>& against) {
+  const int prec = B.prec;
+  ortho(c, prec, B.L, against, B.V, B.ldv, g, nullptr, 0);
+  apply_op(c, prec, op, B.V, B.ldv, B.W, B.ldv, g, B.tmp, B.b);
+  std::vector<double> Hr = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g}}, SegV{B.W, B.ldv, g});
+  H.assign((size_t)g * g, 0.0);
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < g; ++j) H[(size_t)j * g + i] = 0.5 * (Hr[(size_t)i * g + j] + Hr[(size_t)j * g + i]);
+  c.resets += 1;
+}
+
+// ---------------------------------------------------------------------------
+// GD+k with Rayleigh-Ritz and soft locking (stage 1 on C; stage 2 largest on B)
+// ---------------------------------------------------------------------------
+RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long ldx) {
+  const int prec = B.prec;
+  const int k = cfg.k, b = cfg.b;
+  RunOut out;
+  int g = 0;
+  std::vector<double> H;
+  init_basis(c, B, cfg, cfg.op, g, H, {});
+  std::vector<char> flags(k, 0);
+  std::vector<double> Yprev;  // g x nprev column-major
+  int nprev = 0;
+  int rsr = 0;
+  std::vector<double> w, Z;
+  while (true) {
+    c.budget();
+    ++out.outer;
+    w.assign(g, 0.0);
+    Z.assign((size_t)g * g, 0.0);
+    if (!hla::sym_eig(g, H.data(), w.data(), Z.data())) throw NumFail{"projected eigenproblem did not converge"};
+    std::vector<double> theta(g), Y((size_t)g * g);
+    for (int j = 0; j < g; ++j) {
+      const int src = cfg.smallest ? j : g - 1 - j;
+      theta[j] = w[src];
+      std::memcpy(&Y[(size_t)j * g], &Z[(size_t)src * g], sizeof(double) * g);
+    }
+    const int ncand = std::min(k, g);
+    std::vector<int> block;
+    std::vector<double> rnb;
+    std::vector<int> cand;
+    for (int j = 0; j < ncand; ++j)
+      if (!flags[j]) cand.push_back(j);
+    size_t ci = 0;
+    int nbk = 0;
+    auto test_and_compact = [&](const std::vector<int>& take, const std::vector<double>& rn) {
+      std::vector<double> th(take.size());
+      for (size_t t = 0; t < take.size(); ++t) th[t] = theta[take[t]];
+      std::vector<char> ok(take.size(), 0);
+      cfg.conv(th.data(), rn.data(), nbk, (int)take.size(), ok.data());
+      int wpos = nbk;
+      for (size_t t = 0; t < take.size(); ++t) {
+        if (ok[t]) {
+          flags[take[t]] = 1;
+          continue;
+        }
+        const int src = nbk + (int)t;
+        if (src != wpos) {
+          CK(launch_copy_cols(prec, B.L, off(B.Xb, src, prec), b, off(B.Xb, wpos, prec), b, 1, c.st));
+          CK(launch_copy_cols(prec, B.L, off(B.Rb, src, prec), b, off(B.Rb, wpos, prec), b, 1, c.st));
+          c.launches += 2;
+        }
+        block.push_back(take[t]);
+        rnb.push_back(rn[t]);
+        ++wpos;
+      }
+      nbk = wpos;
+    };
+    while (ci < cand.size() && nbk < b) {
+      std::vector<int> take;
+      while (ci < cand.size() && (int)take.size() < b - nbk) take.push_back(cand[ci++]);
+      std::vector<double> rn = ritz_cols(c, B, g, Y, theta, take, nbk);
+      test_and_compact(take, rn);
+    }
+    bool allflag = ncand == k;
+    for (int j = 0; j < k && allflag; ++j) allflag = flags[j] != 0;
+    if (allflag) {
+      // verification of all k flagged pairs together
+      std::vector<int> fails;
+      for (int c0 = 0; c0 < k; c0 += b) {
+        std::vector<int> chunk;
+        for (int j = c0; j < std::min(k, c0 + b); ++j) chunk.push_back(j);
+        std::vector<double> rn = ritz_cols(c, B, g, Y, theta, chunk, 0);
+        std::vector<double> th(chunk.size());
+        for (size_t t = 0; t < chunk.size(); ++t) th[t] = theta[chunk[t]];
+        std::vector<char> ok(chunk.size(), 0);
+        cfg.conv(th.data(), rn.data(), 0, (int)chunk.size(), ok.data());
+        for (size_t t = 0; t < chunk.size(); ++t)
+          if (!ok[t]) fails.push_back(chunk[t]);
+      }
+      if (fails.empty()) {
+        std::vector<int> all(k);
+        for (int j = 0; j < k; ++j) all[j] = j;
+        std::vector<double> Yk;
+        put_block_rm(Yk, g, Y.data(), g, all);
+        combine(c, prec, B.L, {SegV{B.V, B.ldv, g}}, Yk, nullptr, 0, false, Xout, ldx, k);
+        out.theta.assign(theta.begin(), theta.begin() + k);
+        return out;
+      }
+      for (int j = 0; j < k; ++j) flags[j] = 1;
+      for (int j : fails) flags[j] = 0;
+      block.clear();
+      rnb.clear();
+      std::vector<int> take(fails.begin(), fails.begin() + std::min((int)fails.size(), b));
+      rnb = ritz_cols(c, B, g, Y, theta, take, 0);
+      block = take;
+      nbk = (int)take.size();
+    }
+    if (nbk == 0) {
+      std::vector<int> take;
+      for (int j = 0; j < std::min(b, ncand); ++j) take.push_back(j);
+      rnb = ritz_cols(c, B, g, Y, theta, take, 0);
+      block = take;
+      nbk = (int)take.size();
+    }
+    if (c.print >= 3) {
+      double mn = 1e300;
+      for (double r : rnb) mn = std::min(mn, r);
+      int nf = 0;
+      for (char f : flags) nf += f;
+      std::fprintf(stderr, "[%s] it %lld g %d conv %d/%d theta0 %.10e minres %.3e mv %lld\n", cfg.name, out.outer, g,
+                   nf, k, theta[0], mn, c.mv);
+    }
+    // reset of V and W (Sec. 3.2)
+    double rmin = 1e300;
+    for (double r : rnb) rmin = std::min(rmin, r);
+    if (rsr > 0 && cfg.u > 0 && rmin < std::sqrt((double)rsr) * cfg.normop * cfg.u) {
+      reset_basis(c, B, cfg.op, g, H, {});
+      rsr = 0;
+      nprev = 0;
+      Yprev.clear();
+      continue;
+    }
+    // correction T = M R (Jacobi) or T = R
+    void* T = B.Rb;
+    if (cfg.dscale) {
+      CK(launch_scale_rows(prec, B.L, cfg.dscale, B.Rb, b, B.Tb, b, nbk, c.st));
+      c.launches += 1;
+      T = B.Tb;
+    }
+    std::vector<double> Ycur((size_t)g * nbk);
+    for (int j = 0; j < nbk; ++j) std::memcpy(&Ycur[(size_t)j * g], &Y[(size_t)block[j] * g], sizeof(double) * g);
+    if (g + nbk > cfg.mb) {
+      // GD+k restart: the min_restart Ritz vectors plus the previous block's
+      const int mr = std::min(cfg.mr, g);
+      std::vector<double> cols((size_t)g * (mr + nprev));
+      std::memcpy(cols.data(), Y.data(), sizeof(double) * g * mr);
+      if (nprev) std::memcpy(&cols[(size_t)g * mr], Yprev.data(), sizeof(double) * g * nprev);
+      const int gz = hla::orth_cols(g, mr + nprev, cols.data(), 1e-12);
+      std::vector<double> Zr = rowmajor(g, gz, cols.data(), g);
+      combine(c, prec, B.L, {SegV{B.V, B.ldv, g}}, Zr, nullptr, 0, false, B.V, B.ldv, gz);
+      combine(c, prec, B.L, {SegV{B.W, B.ldv, g}}, Zr, nullptr, 0, false, B.W, B.ldv, gz);
+      H = project_H(H, g, cols, gz);
+      std::vector<double> Yn((size_t)gz * nbk);
+      hla::gemm_tn(gz, nbk, g, cols.data(), g, Ycur.data(), g, Yn.data(), gz);
+      Ycur.swap(Yn);
+      g = gz;
+      ++rsr;
+      c.restarts += 1;
+    }
+    ortho(c, prec, B.L, {SegV{B.V, B.ldv, g}}, T, b, nbk, off(B.V, g, prec), B.ldv);
+    apply_op(c, prec, cfg.op, T, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
+    std::vector<double> Hext = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk});
+    extend_H(H, g, nbk, Hext);
+    // previous-iteration coefficients padded with zeros for the new columns
+    nprev = nbk;
+    Yprev.assign((size_t)(g + nbk) * nbk, 0.0);
+    for (int j = 0; j < nbk; ++j) std::memcpy(&Yprev[(size_t)j * (g + nbk)], &Ycur[(size_t)j * g], sizeof(double) * g);
+    g += nbk;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2 smallest: simplified refined extraction (constant shift per target,
+// incremental QR of (B - tau I) V) with hard locking (Sec. 3.2)
+// ---------------------------------------------------------------------------
+struct RefinedCfg : RunCfg {
+  std::vector<double> taus;
+};
+
+// Fresh QR of (W - tau V): Q <- W - tau V, then CholQR2; returns R (column-major).
+std::vector<double> fresh_qr(Ctx& c, RunBufs& B, int g, double tau) {
+  const int prec = B.prec;
+  std::vector<double> coef((size_t)2 * g * g, 0.0);
+  for (int j = 0; j < g; ++j) {
+    coef[(size_t)j * g + j] = 1.0;             // W rows of the coefficient (first g rows)
+    coef[(size_t)(g + j) * g + j] = -tau;      // V rows
+  }
+  combine(c, prec, B.L, {SegV{B.W, B.ldv, g}, SegV{B.V, B.ldv, g}}, coef, nullptr, 0, false, B.Q, B.ldv, g);
+  OrthoRes o = ortho(c, prec, B.L, {}, B.Q, B.ldv, g, nullptr, 0);
+  std::vector<double> R((size_t)g * g);
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < g; ++j) R[(size_t)j * g + i] = o.R[(size_t)i * g + j];
+  return R;
+}
+
+RunOut run_refined(Ctx& c, RunBufs& B, const RefinedCfg& cfg, std::vector<double>& locked_theta) {
+  const int prec = B.prec;
+  const int k = cfg.k, b = cfg.b;
+  RunOut out;
+  int g = 0;
+  std::vector<double> H;
+  init_basis(c, B, cfg, OP_B, g, H, {});
+  int i = 0;
+  std::vector<double> Rq = fresh_qr(c, B, g, cfg.taus[0]);
+  std::vector<double> Yprev;
+  int nprev = 0, rsr = 0;
+  locked_theta.clear();
+  while (i < k) {
+    c.budget();
+    ++out.outer;
+    const double tau = cfg.taus[i];
+    std::vector<double> s(g), Yr((size_t)g * g);
+    hla::svd_right(g, Rq.data(), s.data(), Yr.data());
+    const int nbk = std::min(b, g);
+    std::vector<double> theta(g, 0.0);
+    for (int j = 0; j < nbk; ++j) {
+      const double* y = &Yr[(size_t)j * g];
+      double acc = 0;
+      for (int a = 0; a < g; ++a) {
+        double hy = 0;
+        for (int bb = 0; bb < g; ++bb) hy += H[(size_t)bb * g + a] * y[bb];
+        acc += y[a] * hy;
+      }
+      theta[j] = acc;
+    }
+    std::vector<int> cols(nbk);
+    for (int j = 0; j < nbk; ++j) cols[j] = j;
+    std::vector<double> rn = ritz_cols(c, B, g, Yr, theta, cols, 0);
+    std::vector<char> ok(1, 0);
+    cfg.conv(theta.data(), rn.data(), 0, 1, ok.data());
+    if (c.print >= 3)
+      std::fprintf(stderr, "[%s] it %lld g %d locked %d tau %.10e theta %.10e res %.3e smin %.3e mv %lld\n", cfg.name,
+                   out.outer, g, i, tau, theta[0], rn[0], s[0], c.mv);
+    if (ok[0]) {
+      CK(launch_copy_cols(prec, B.L, B.Xb, b, off(B.Xlock, i, prec), k, 1, c.st));
+      c.launches += 1;
+      locked_theta.push_back(theta[0]);
+      ++i;
+      if (i == k) break;
+      // forced restart without the locked direction; QR recomputed with the next shift
+      const int gk = std::min(g - 1, cfg.mr);
+      std::vector<double> keep((size_t)g * gk);
+      std::memcpy(keep.data(), &Yr[(size_t)g], sizeof(double) * g * gk);
+      std::vector<double> Kr = rowmajor(g, gk, keep.data(), g);
+      combine(c, prec, B.L, {SegV{B.V, B.ldv, g}}, Kr, nullptr, 0, false, B.V, B.ldv, gk);
+      combine(c, prec, B.L, {SegV{B.W, B.ldv, g}}, Kr, nullptr, 0, false, B.W, B.ldv, gk);
+      H = project_H(H, g, keep, gk);
+      g = gk;
+      if (g == 0) throw NumFail{"refined extraction lost its basis"};
+      Rq = fresh_qr(c, B, g, cfg.taus[i]);
+      nprev = 0;
+      Yprev.clear();
+      ++rsr;
+      c.restarts += 1;
+      continue;
+    }
+    if (rsr > 0 && rn[0] < std::sqrt((double)rsr) * cfg.normop * cfg.u) {
+      std::vector<SegV> ag;
+      if (i > 0) ag.push_back(SegV{B.Xlock, k, i});
+      reset_basis(c, B, OP_B, g, H, ag);
+      Rq = fresh_qr(c, B, g, tau);
+      rsr = 0;
+      nprev = 0;
+      Yprev.clear();
+      continue;
+    }
+    std::vector<double> Ycur((size_t)g * nbk);
+    std::memcpy(Ycur.data(), Yr.data(), sizeof(double) * g * nbk);
+    if (g + nbk > cfg.mb) {
+      const int mr = std::min(cfg.mr, g);
+      std::vector<double> zc((size_t)g * (mr + nprev));
+      std::memcpy(zc.data(), Yr.data(), sizeof(double) * g * mr);
+      if (nprev) std::memcpy(&zc[(size_t)g * mr], Yprev.data(), sizeof(double) * g * nprev);
+      const int gz = hla::orth_cols(g, mr + nprev, zc.data(), 1e-12);
+      std::vector<double> Zr = rowmajor(g, gz, zc.data(), g);
+      combine(c, prec, B.L, {SegV{B.V, B.ldv, g}}, Zr, nullptr, 0, false, B.V, B.ldv, gz);
+      combine(c, prec, B.L, {SegV{B.W, B.ldv, g}}, Zr, nullptr, 0, false, B.W, B.ldv, gz);
+      H = project_H(H, g, zc, gz);
+      // QR restart: R Z = Qt Rt, Q <- Q Qt, R <- Rt
+      std::vector<double> RZ((size_t)g * gz);
+      hla::gemm_nn(g, gz, g, Rq.data(), g, zc.data(), g, RZ.data(), g);
+      std::vector<double> Qt = RZ;
+      const int kept = hla::orth_cols(g, gz, Qt.data(), 1e-14);
+      std::vector<double> Yn((size_t)gz * nbk);
+      hla::gemm_tn(gz, nbk, g, zc.data(), g, Ycur.data(), g, Yn.data(), gz);
+      Ycur.swap(Yn);
+      if (kept == gz) {
+        std::vector<double> Rt((size_t)gz * gz);
+        hla::gemm_tn(gz, gz, g, Qt.data(), g, RZ.data(), g, Rt.data(), gz);
+        for (int jj = 0; jj < gz; ++jj)
+          for (int ii = jj + 1; ii < gz; ++ii) Rt[(size_t)jj * gz + ii] = 0.0;
+        combine(c, prec, B.L, {SegV{B.Q, B.ldv, g}}, rowmajor(g, gz, Qt.data(), g), nullptr, 0, false, B.Q, B.ldv, gz);
+        g = gz;
+        Rq = Rt;
+      } else {
+        g = gz;
+        Rq = fresh_qr(c, B, g, tau);
+      }
+      ++rsr;
+      c.restarts += 1;
+    }
+    std::vector<SegV> basis;
+    if (i > 0) basis.push_back(SegV{B.Xlock, k, i});
+    basis.push_back(SegV{B.V, B.ldv, g});
+    ortho(c, prec, B.L, basis, B.Rb, b, nbk, off(B.V, g, prec), B.ldv);
+    apply_op(c, prec, OP_B, B.Rb, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
+    // Z = W T - tau T, orthonormalised against Q: extends (B - tau I)V = QR
+    std::vector<double> coef((size_t)2 * nbk * nbk, 0.0);
+    for (int j = 0; j < nbk; ++j) {
+      coef[(size_t)j * nbk + j] = 1.0;
+      coef[(size_t)(nbk + j) * nbk + j] = -tau;
+    }
+    combine(c, prec, B.L, {SegV{off(B.W, g, prec), B.ldv, nbk}, SegV{B.Rb, b, nbk}}, coef, nullptr, 0, false, B.Zb, b,
+            nbk);
+    OrthoRes oz = ortho(c, prec, B.L, {SegV{B.Q, B.ldv, g}}, B.Zb, b, nbk, off(B.Q, g, prec), B.ldv);
+    std::vector<double> Hext = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk});
+    extend_H(H, g, nbk, Hext);
+    const int gn = g + nbk;
+    if (oz.replaced) {
+      g = gn;
+      Rq = fresh_qr(c, B, g, tau);
+    } else {
+      std::vector<double> Rn((size_t)gn * gn, 0.0);
+      for (int jj = 0; jj < g; ++jj)
+        for (int ii = 0; ii <= jj; ++ii) Rn[(size_t)jj * gn + ii] = Rq[(size_t)jj * g + ii];
+      for (int jj = 0; jj < nbk; ++jj) {
+        for (int ii = 0; ii < g; ++ii) Rn[(size_t)(g + jj) * gn + ii] = oz.C[(size_t)ii * nbk + jj];
+        for (int ii = 0; ii <= jj; ++ii) Rn[(size_t)(g + jj) * gn + g + ii] = oz.R[(size_t)ii * nbk + jj];
+      }
+      Rq.swap(Rn);
+      g = gn;
+    }
+    nprev = nbk;
+    Yprev.assign((size_t)g * nbk, 0.0);
+    for (int j = 0; j < nbk; ++j)
+      std::memcpy(&Yprev[(size_t)j * g], &Ycur[(size_t)j * (g - nbk)], sizeof(double) * (g - nbk));
+  }
+  out.theta = locked_theta;
+  return out;
+}
+
+// Sizes: paper defaults (Sec. 3.4) with the reading for larger k and b.
+void default_sizes(int k, int b, bool smallest, int& mb, int& mr) {
+  if (!smallest && k < 10) {
+    mb = 15;
+    mr = 6;
+  } else {
+    mb = 35;
+    mr = 14;
+  }
+  mr = std::max(mr, k + b);
+  mb = std::max(mb, mr + 2 * b);
+}
+
+}  // namespace
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& s) { g_last_error = s; }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+// ===========================================================================
+// Algorithm 1
+// ===========================================================================
+int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* Uout, double* Vout, double* rnorm,
+          int* numConverged, svds_stats* stats) {
+  const auto tstart = Clock::now();
+  DevMatrix& A = h->A;
+  const svds_opts& o = h->opts;
+  const long long m = A.m, n = A.n, L2 = m + n;
+  const bool smallest = target == SVDS_SMALLEST;
+  const int b = std::max(1, o.maxBlockSize);
+  int mb, mr;
+  default_sizes(k, b, smallest, mb, mr);
+  if (o.maxBasisSize > 0) mb = o.maxBasisSize;
+  if (o.minRestartSize > 0) mr = o.minRestartSize;
+  if (mr < k + b - 1 || mb < mr + b || mb > 240) return SVDS_ERR_ARG;
+  const bool lowprec = o.stage1_precision == SVDS_FP32;
+  const int p2 = o.stage1_precision == SVDS_NATIVE_FP64 ? kF64 : kDF64;  // FP64-class mode
+  const int p1a = lowprec ? kF32 : p2;
+  const bool polish = !lowprec || o.stage1_polish;
+  const long long ldv = (mb + 3) & ~3LL;
+  const int kk = std::max(std::max(k, b), std::min(std::max(o.initSize, 0), k));
+
+  Ctx c;
+  c.h = h;
+  c.st = h->stream;
+  c.A = &A;
+  c.max_mv = o.maxMatvecs;
+  c.max_sec = o.maxSeconds;
+  c.t0 = tstart;
+  c.print = o.printLevel;
+  c.seed = o.seed;
+  svds_stats S{};
+  try {
+    // ---- workspace ----
+    struct Req {
+      void** p;
+      size_t bytes;
+    };
+    std::vector<Req> reqs;
+    RunBufs B1a, B1, B2;
+    auto plan_run = [&](RunBufs& R, int prec, long long L, bool refined) {
+      const size_t e = elem_bytes(prec);
+      R.prec = prec;
+      R.L = L;
+      R.ldv = ldv;
+      R.b = b;
+      reqs.push_back({&R.V, (size_t)L * ldv * e});
+      reqs.push_back({&R.W, (size_t)L * ldv * e});
+      reqs.push_back({&R.Xb, (size_t)L * b * e});
+      reqs.push_back({&R.Rb, (size_t)L * b * e});
+      reqs.push_back({&R.Tb, (size_t)L * b * e});
+      reqs.push_back({&R.BXb, (size_t)L * b * e});
+      reqs.push_back({&R.tmp, (size_t)m * b * e});
+      if (refined) {
+        reqs.push_back({&R.Q, (size_t)L * ldv * e});
+        reqs.push_back({&R.Zb, (size_t)L * b * e});
+        reqs.push_back({&R.Xlock, (size_t)L * k * e});
+      }
+    };
+    if (lowprec) plan_run(B1a, kF32, n, false);
+    plan_run(B1, p2, n, false);
+    plan_run(B2, p2, L2, smallest);
+    const size_t e2 = elem_bytes(p2);
+    void *X1a = nullptr, *X1 = nullptr, *CX = nullptr, *Xfin = nullptr, *BXfin = nullptr, *R2 = nullptr,
+         *Xout2 = nullptr, *d1a = nullptr, *d1 = nullptr, *dout = nullptr;
+    if (lowprec) reqs.push_back({&X1a, (size_t)n * kk * 4});
+    reqs.push_back({&X1, (size_t)n * kk * e2});
+    reqs.push_back({&CX, (size_t)n * kk * e2});
+    reqs.push_back({&R2, (size_t)n * kk * e2});
+    reqs.push_back({&Xfin, (size_t)L2 * kk * e2});
+    reqs.push_back({&BXfin, (size_t)L2 * kk * e2});
+    reqs.push_back({&Xout2, (size_t)L2 * kk * e2});
+    if (lowprec) reqs.push_back({&d1a, (size_t)n * 4});
+    reqs.push_back({&d1, (size_t)n * e2});
+    reqs.push_back({&dout, (size_t)L2 * kk * 8});
+    c.maxblk = gram_default_blocks();
+    c.gcap = 256 * 256;
+    reqs.push_back({&c.partial, gram_partial_bytes(std::max(c.maxblk, 152 * 16), 256, 8)});
+    reqs.push_back({(void**)&c.dG, c.gcap * 8});
+    c.nslots = 64;
+    c.slot_bytes = (size_t)2 * 256 * 256 * 8 / 8;
+    reqs.push_back({(void**)&c.dstage, (size_t)c.nslots * c.slot_bytes});
+    size_t total = 0;
+    for (auto& r : reqs) total += (r.bytes + 255) & ~size_t(255);
+    total += 4096;
+    if (h->arena.cap < total) {
+      if (h->arena.base) cudaFree(h->arena.base);
+      h->arena = Arena{};
+      if (cudaMalloc(&h->arena.base, total) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("workspace allocation failed");
+        return SVDS_ERR_NOMEM;
+      }
+      h->arena.cap = total;
+    }
+    h->arena.used = 0;
+    for (auto& r : reqs) *r.p = h->arena.take(r.bytes);
+    const size_t hneed = c.gcap * 8 + (size_t)c.nslots * c.slot_bytes;
+    if (h->hpin_bytes < hneed) {
+      if (h->hpin) cudaFreeHost(h->hpin);
+      h->hpin = nullptr;
+      h->hpin_bytes = 0;
+      if (cudaMallocHost(&h->hpin, hneed) != cudaSuccess) {
+        cudaGetLastError();
+        return SVDS_ERR_NOMEM;
+      }
+      h->hpin_bytes = hneed;
+    }
+    c.hG = reinterpret_cast<double*>(h->hpin);
+    c.hstage = reinterpret_cast<char*>(h->hpin) + c.gcap * 8;
+    c.slot_epoch.assign(c.nslots, 0);
+    B1.Xlock = nullptr;
+
+    // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
+    double normA = o.aNorm > 0 ? o.aNorm * A.scale : 0.0;
+    if (normA <= 0) {
+      RunCfg cn;
+      cn.op = OP_C;
+      cn.k = 1;
+      cn.b = 1;
+      cn.mb = 15;
+      cn.mr = 6;
+      cn.smallest = false;
+      cn.normop = 0;
+      cn.u = 0;
+      cn.name = "norm";
+      RunBufs& Bn = lowprec ? B1a : B1;
+      Bn.b = 1;
+      CK(launch_fill_normal(Bn.prec, n, Bn.Xb, 1, 1, o.seed ^ 0x5eedULL, c.st));
+      cn.V0 = Bn.Xb;
+      cn.ldv0 = 1;
+      cn.b0 = 1;
+      cn.conv = [](const double* th, const double* rn, int, int nc, char* ok) {
+        for (int j = 0; j < nc; ++j) ok[j] = rn[j] <= 1e-3 * std::fabs(th[j]);
+      };
+      void* Xn = lowprec ? X1a : X1;
+      RunOut rn = run_gdk_rr(c, Bn, cn, Xn, kk);
+      Bn.b = b;
+      normA = std::sqrt(std::fabs(rn.theta[0]));
+    }
+    const double normC = normA * normA;
+    S.seconds_setup = c.elapsed();
+
+    // ---- stage 1 on C (Algorithm 1 lines 1-3) ----
+    auto stage1_conv = [&](double u) {
+      return [=](const double* th, const double* rn, int, int nc, char* ok) {
+        for (int j = 0; j < nc; ++j)
+          ok[j] = rn[j] <= std::max(std::sqrt(std::fabs(th[j]) * normC) * tol, 10.0 * u * normC);
+      };
+    };
+    const bool jac = smallest && o.precond == SVDS_PRECOND_JACOBI;
+    if (jac) {
+      if (lowprec) CK(launch_make_dscale(kF32, n, A.colsq, 0, d1a, c.st));
+      CK(launch_make_dscale(p2, n, A.colsq, 0, d1, c.st));
+      c.launches += lowprec ? 2 : 1;
+    }
+    // initial block: user guesses then seeded N(0,1) columns
+    // initial block (ncols columns, leading dimension ld): user guesses first
+    // (initSize, initV), then seeded N(0,1) columns
+    auto init_block = [&](int prec, void* dst, long long ld, int ncols) {
+      int given = 0;
+      if (o.initV && o.initSize > 0) {
+        given = std::min(o.initSize, ncols);
+        double* dtmp = reinterpret_cast<double*>(dout);
+        CK(cudaMemcpyAsync(dtmp, o.initV, sizeof(double) * n * given, cudaMemcpyHostToDevice, c.st));
+        CK(launch_from_f64_colmajor(prec, n, given, dtmp, n, dst, ld, 1.0, c.st));
+        c.launches += 1;
+      }
+      if (given < ncols) {
+        CK(launch_fill_normal(prec, n, off(dst, given, prec), ld, ncols - given, o.seed, c.st));
+        c.launches += 1;
+      }
+    };
+    const int b0 = std::max(b, std::min(o.initSize, k));
+    const double t1 = c.elapsed();
+    const long long mv0 = c.mv;
+    RunCfg c1;
+    c1.op = OP_C;
+    c1.k = k;
+    c1.b = b;
+    c1.mb = mb;
+    c1.mr = mr;
+    c1.smallest = smallest;
+    c1.normop = normC;
+    c1.b0 = b0;
+    if (lowprec) {
+      init_block(kF32, X1a, kk, b0);
+      c1.u = unit_roundoff(kF32);
+      c1.conv = stage1_conv(c1.u);
+      c1.dscale = jac ? d1a : nullptr;
+      c1.V0 = X1a;
+      c1.ldv0 = kk;
+      c1.name = "stage1-fp32";
+      RunOut ra = run_gdk_rr(c, B1a, c1, X1a, kk);
+      S.outer_stage1 += ra.outer;
+      S.matvecs_stage1_lowprec = c.mv - mv0;
+      // hand the FP32 Ritz vectors to the FP64-class phase
+      double* dtmp = reinterpret_cast<double*>(dout);
+      CK(launch_to_f64_colmajor(kF32, n, k, X1a, kk, dtmp, n, 1.0, c.st));
+      CK(launch_from_f64_colmajor(p2, n, k, dtmp, n, X1, kk, 1.0, c.st));
+      c.launches += 2;
+    } else {
+      init_block(p2, X1, kk, b0);
+    }
+    std::vector<double> lam;
+    if (polish) {
+      c1.u = unit_roundoff(p2);
+      c1.conv = stage1_conv(c1.u);
+      c1.dscale = jac ? d1 : nullptr;
+      c1.V0 = X1;
+      c1.ldv0 = kk;
+      c1.b0 = lowprec ? k : b0;
+      c1.name = "stage1";
+      RunOut r1 = run_gdk_rr(c, B1, c1, X1, kk);
+      S.outer_stage1 += r1.outer;
+      lam = r1.theta;
+    }
+    // ---- Algorithm 1 lines 4-5: Rayleigh-Ritz on the returned vectors ----
+    ortho(c, p2, n, {}, X1, kk, k, nullptr, 0);
+    apply_op(c, p2, OP_C, X1, kk, CX, kk, k, B1.tmp, b);
+    std::vector<double> Hk = gram(c, p2, 0, n, {SegV{X1, kk, k}}, SegV{CX, kk, k});
+    std::vector<double> Hkc((size_t)k * k), wk(k), Zk((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Hkc[(size_t)j * k + i] = 0.5 * (Hk[(size_t)i * k + j] + Hk[(size_t)j * k + i]);
+    if (!hla::sym_eig(k, Hkc.data(), wk.data(), Zk.data())) throw NumFail{"final Rayleigh-Ritz failed"};
+    std::vector<double> lk(k), Yk((size_t)k * k);
+    for (int j = 0; j < k; ++j) {
+      const int src = smallest ? j : k - 1 - j;
+      lk[j] = wk[src];
+      std::memcpy(&Yk[(size_t)j * k], &Zk[(size_t)src * k], sizeof(double) * k);
+    }
+    std::vector<double> Ykr = rowmajor(k, k, Yk.data(), k);
+    const void* dY = c.upload(p2, Ykr.data(), Ykr.size());
+    const void* dth = c.upload(p2, lk.data(), lk.size());
+    int nbl = 0;
+    // v = x (top n rows of Xfin), r^C = C x - lambda x
+    CK(launch_ritz_residual(p2, n, SegV{X1, kk, k}, SegV{CX, kk, k}, k, dY, dth, Xfin, R2, kk, k, nullptr, nullptr,
+                            c.partial, c.maxblk, &nbl, c.st));
+    CK(launch_gram_reduce(p2, c.partial, nbl, k, c.dG, c.st));
+    c.launches += 2;
+    CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * k, cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    std::vector<double> rC(k), sig(k);
+    for (int j = 0; j < k; ++j) {
+      rC[j] = std::sqrt(std::max(c.hG[j], 0.0));
+      sig[j] = std::sqrt(std::fabs(lk[j]));
+    }
+    for (int j = 0; j < k; ++j) normA = std::max(normA, smallest ? 0.0 : sig[j]);
+    // u = A v / sigma (bottom m rows of Xfin)
+    void* Ufin = off(Xfin, n * kk, p2);
+    CK(launch_spmm(p2, A.csr(false), Xfin, kk, Ufin, kk, k, c.st));
+    c.launches += spmm_launches(k);
+    c.mv += k;
+    {
+      std::vector<double> D((size_t)k * k, 0.0);
+      for (int j = 0; j < k; ++j) D[(size_t)j * k + j] = sig[j] > 0 ? 1.0 / sig[j] : 1.0;
+      combine(c, p2, m, {SegV{Ufin, kk, k}}, D, nullptr, 0, false, Ufin, kk, k);
+    }
+    // Eq. (res) for the stage-1 triplets, recomputed with fresh products
+    auto triplet_res = [&](void* X, const std::vector<double>& s, int nc) {
+      apply_op(c, p2, OP_B, X, kk, BXfin, kk, nc, B2.tmp, b);
+      std::vector<double> cf((size_t)4 * nc);
+      for (int j = 0; j < nc; ++j) {
+        cf[j] = 1.0;
+        cf[nc + j] = s[j];
+        cf[2 * nc + j] = 1.0;
+        cf[3 * nc + j] = s[j];
+      }
+      std::vector<double> r(nc, 0.0);
+      for (int c0 = 0; c0 < nc; c0 += 8) {
+        const int w = std::min(8, nc - c0);
+        std::vector<double> cfc((size_t)4 * w);
+        for (int j = 0; j < w; ++j) {
+          cfc[j] = 1.0;
+          cfc[w + j] = s[c0 + j];
+          cfc[2 * w + j] = 1.0;
+          cfc[3 * w + j] = s[c0 + j];
+        }
+        const void* dcf = c.upload(p2, cfc.data(), cfc.size());
+        int nb2 = 0;
+        CK(launch_split_resnorm(p2, L2, n, off(X, c0, p2), off(BXfin, c0, p2), kk, w, dcf, c.partial, c.maxblk, &nb2,
+                                c.st));
+        CK(launch_gram_reduce(p2, c.partial, nb2, w, c.dG, c.st));
+        c.launches += 2;
+        CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * w, cudaMemcpyDeviceToHost, c.st));
+        c.sync();
+        for (int j = 0; j < w; ++j) r[c0 + j] = std::sqrt(std::max(c.hG[j], 0.0));
+      }
+      return r;
+    };
+    std::vector<double> res = triplet_res(Xfin, sig, k);
+    S.matvecs_stage1 = c.mv - mv0;
+    S.seconds_stage1 = c.elapsed() - t1;
+    bool all_ok = true;
+    for (int j = 0; j < k; ++j) all_ok = all_ok && res[j] < normA * tol;
+    void* Xres = Xfin;
+    if (!all_ok) {
+      // ---- stage 2 on B (Algorithm 1 lines 9-20) ----
+      S.stage2_used = 1;
+      const double t2 = c.elapsed();
+      const long long mv2 = c.mv;
+      RunCfg c2;
+      c2.op = OP_B;
+      c2.k = k;
+      c2.b = b;
+      int mb2, mr2;
+      default_sizes(k, b, smallest, mb2, mr2);
+      c2.mb = o.maxBasisSize > 0 ? mb : mb2;
+      c2.mr = o.minRestartSize > 0 ? mr : mr2;
+      if (c2.mb > mb) c2.mb = mb;  // buffers sized for mb
+      c2.mr = std::min(c2.mr, c2.mb - b);
+      c2.smallest = smallest;
+      c2.normop = normA;
+      c2.u = unit_roundoff(p2);
+      c2.V0 = Xfin;
+      c2.ldv0 = kk;
+      c2.b0 = k;
+      c2.name = "stage2";
+      RunBufs& Bs = B2;
+      const double thr1 = std::sqrt(2.0) * normA * tol;
+      // Eq. B_secondCriterion then Eq. (res) on the normalised halves
+      c2.conv = [&](const double* th, const double* rn, int o0, int nc, char* ok) {
+        bool any = false;
+        for (int j = 0; j < nc; ++j) {
+          ok[j] = rn[j] <= thr1;
+          any = any || ok[j];
+        }
+        if (!any) return;
+        void* Xc = off(Bs.Xb, o0, p2);
+        apply_op(c, p2, OP_B, Xc, b, Bs.BXb, b, nc, Bs.tmp, b);
+        std::vector<double> Gv = gram(c, p2, 0, n, {SegV{Xc, b, nc}}, SegV{Xc, b, nc});
+        std::vector<double> Gu = gram(c, p2, n, L2, {SegV{Xc, b, nc}}, SegV{Xc, b, nc});
+        std::vector<double> Gd = gram(c, p2, n, L2, {SegV{Xc, b, nc}}, SegV{Bs.BXb, b, nc});
+        std::vector<double> cf((size_t)4 * nc);
+        for (int j = 0; j < nc; ++j) {
+          const double nv = std::sqrt(std::max(Gv[(size_t)j * nc + j], 1e-300));
+          const double nu = std::sqrt(std::max(Gu[(size_t)j * nc + j], 1e-300));
+          const double s = Gd[(size_t)j * nc + j] / (nv * nu);
+          cf[j] = 1.0 / nu;           // rows < n: A^T u = (Bx)_v / ||x_u||
+          cf[nc + j] = s / nv;        //           sigma v
+          cf[2 * nc + j] = 1.0 / nv;  // rows >= n: A v = (Bx)_u / ||x_v||
+          cf[3 * nc + j] = s / nu;    //           sigma u
+        }
+        const void* dcf = c.upload(p2, cf.data(), cf.size());
+        int nb2 = 0;
+        CK(launch_split_resnorm(p2, L2, n, Xc, Bs.BXb, b, nc, dcf, c.partial, c.maxblk, &nb2, c.st));
+        CK(launch_gram_reduce(p2, c.partial, nb2, nc, c.dG, c.st));
+        c.launches += 2;
+        CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.st));
+        c.sync();
+        for (int j = 0; j < nc; ++j) ok[j] = ok[j] && std::sqrt(std::max(c.hG[j], 0.0)) < normA * tol;
+      };
+      void* XB = nullptr;
+      if (smallest) {
+        RefinedCfg cr;
+        static_cast<RunCfg&>(cr) = c2;
+        cr.taus.resize(k);
+        for (int j = 0; j < k; ++j) {
+          // Algorithm 1 line 15: tau_i = max(s_i - sqrt(2) ||r^C_i|| / s_i, ||A|| eps)
+          const double lb = sig[j] > 0 ? sig[j] - std::sqrt(2.0) * rC[j] / sig[j] : 0.0;
+          cr.taus[j] = std::max(lb, normA * unit_roundoff(p2));
+        }
+        std::vector<double> lt;
+        RunOut r2 = run_refined(c, Bs, cr, lt);
+        S.outer_stage2 = r2.outer;
+        XB = Bs.Xlock;
+      } else {
+        RunOut r2 = run_gdk_rr(c, Bs, c2, Xout2, kk);
+        S.outer_stage2 = r2.outer;
+        XB = Xout2;
+      }
+      // Algorithm 1 line 19: normalise the halves; sigma = u^T A v (reading)
+      long long ldxb = smallest ? k : kk;
+      std::vector<double> Gv = gram(c, p2, 0, n, {SegV{XB, ldxb, k}}, SegV{XB, ldxb, k});
+      std::vector<double> Gu = gram(c, p2, n, L2, {SegV{XB, ldxb, k}}, SegV{XB, ldxb, k});
+      std::vector<double> Dv((size_t)k * k, 0.0), Du((size_t)k * k, 0.0);
+      for (int j = 0; j < k; ++j) {
+        Dv[(size_t)j * k + j] = 1.0 / std::sqrt(std::max(Gv[(size_t)j * k + j], 1e-300));
+        Du[(size_t)j * k + j] = 1.0 / std::sqrt(std::max(Gu[(size_t)j * k + j], 1e-300));
+      }
+      combine(c, p2, n, {SegV{XB, ldxb, k}}, Dv, nullptr, 0, false, Xfin, kk, k);
+      combine(c, p2, m, {SegV{off(XB, n * ldxb, p2), ldxb, k}}, Du, nullptr, 0, false, off(Xfin, n * kk, p2), kk, k);
+      apply_op(c, p2, OP_B, Xfin, kk, BXfin, kk, k, B2.tmp, b);
+      // sigma_j = u_j^T (A v_j): rows [n, n + m) of Xfin against those of B Xfin
+      std::vector<double> Gs = gram(c, p2, n, L2, {SegV{Xfin, kk, k}}, SegV{BXfin, kk, k});
+      for (int j = 0; j < k; ++j) sig[j] = Gs[(size_t)j * k + j];
+      res = triplet_res(Xfin, sig, k);
+      S.matvecs_stage2 = c.mv - mv2;
+      S.seconds_stage2 = c.elapsed() - t2;
+    }
+    // ---- outputs ----
+    std::vector<int> order(k);
+    for (int j = 0; j < k; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int bb) { return smallest ? sig[a] < sig[bb] : sig[a] > sig[bb]; });
+    double* dtmp = reinterpret_cast<double*>(dout);
+    CK(launch_to_f64_colmajor(p2, L2, k, Xres, kk, dtmp, L2, 1.0, c.st));
+    c.launches += 1;
+    std::vector<double> hX((size_t)L2 * k);
+    CK(cudaMemcpyAsync(hX.data(), dtmp, sizeof(double) * L2 * k, cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    int nconv = 0;
+    bool prefix = true;
+    const long long mu = A.transposed ? n : m;  // user rows
+    const long long nu = A.transposed ? m : n;  // user cols
+    for (int jj = 0; jj < k; ++jj) {
+      const int j = order[jj];
+      const double* xv = &hX[(size_t)j * L2];
+      const double* xu = xv + n;
+      long long imax = 0;
+      for (long long r = 1; r < n; ++r)
+        if (std::fabs(xv[r]) > std::fabs(xv[imax])) imax = r;
+      double sg = xv[imax] < 0 ? -1.0 : 1.0;
+      if (A.transposed) {  // user A = (device A)^T: swap the roles of u and v
+        imax = 0;
+        for (long long r = 1; r < m; ++r)
+          if (std::fabs(xu[r]) > std::fabs(xu[imax])) imax = r;
+        sg = xu[imax] < 0 ? -1.0 : 1.0;
+      }
+      const double* vsrc = A.transposed ? xu : xv;
+      const double* usrc = A.transposed ? xv : xu;
+      if (Vout)
+        for (long long r = 0; r < nu; ++r) Vout[(size_t)jj * nu + r] = sg * vsrc[r];
+      if (Uout)
+        for (long long r = 0; r < mu; ++r) Uout[(size_t)jj * mu + r] = sg * usrc[r];
+      sigma[jj] = sig[j] / A.scale;
+      if (rnorm) rnorm[jj] = res[j] / A.scale;
+      if (prefix && res[j] < normA * tol)
+        ++nconv;
+      else
+        prefix = false;
+    }
+    if (numConverged) *numConverged = nconv;
+    S.aNorm = normA / A.scale;
+    S.restarts = c.restarts;
+    S.resets = c.resets;
+    S.kernel_launches = c.launches;
+    S.seconds_total = c.elapsed();
+    if (stats) *stats = S;
+    h->launches += c.launches;
+    return SVDS_OK;
+  } catch (const CudaFail& f) {
+    set_last_error(std::string(cudaGetErrorString(f.e)) + " at " + f.where);
+    cudaGetLastError();
+    if (stats) *stats = S;
+    return SVDS_ERR_CUDA;
+  } catch (const NumFail& f) {
+    set_last_error(f.what);
+    if (stats) *stats = S;
+    return SVDS_ERR_NUMERIC;
+  } catch (const BudgetOut&) {
+    cudaStreamSynchronize(c.st);
+    if (numConverged) *numConverged = 0;
+    S.seconds_total = c.elapsed();
+    S.kernel_launches = c.launches;
+    if (stats) *stats = S;
+    return SVDS_ERR_MAXIT;
+  }
+}
+
+}  // namespace phsvds

@@ -1,0 +1,994 @@
+// Device kernels of the PHSVDS hot path (sm_103a).
+//
+// * k_spmm            : CSR SpMM Y = A X over row-major blocks (the user matvec
+//                       of the paper's Sec. 3.4 with transpose 0/1 through an
+//                       explicit CSR of A^T, Sec. 3.3 "operations with both the
+//                       matrix and its transpose").
+// * k_gram / reduce   : tall-skinny projections [P0 P1 P2]^T Q (Rayleigh-Ritz
+//                       projection V^T W, CGS and CholQR Gram matrices; Table 3
+//                       "Inner Prods"), deterministic two-level reduction.
+// * k_combine         : tall-skinny times small (Table 3 "MM": V Y, restart
+//                       V <- V Z in place, T <- (T - V C) R^-1).
+// * k_ritz_residual   : fused Ritz vectors, residuals and norms (Sec. 3.3: the
+//                       residual kernel that minimises memory accesses).
+// * setup kernels     : deterministic CSR transpose, value formats, diagonal of
+//                       A^T A, validation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace phsvds {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return (int)g;
+}
+
+struct SegArr {
+  const void* p[3];
+  long long ld[3];
+  int nc[3];
+  int n;
+};
+
+template <class S>
+__device__ __forceinline__ const S* seg_col(const SegArr& sa, int c, long long* ld) {
+  int s = 0;
+  while (s < sa.n - 1 && c >= sa.nc[s]) {
+    c -= sa.nc[s];
+    ++s;
+  }
+  *ld = sa.ld[s];
+  return reinterpret_cast<const S*>(sa.p[s]) + c;
+}
+
+// ---------------------------------------------------------------------------
+// SpMM
+// ---------------------------------------------------------------------------
+// VMODE: 0 float values (F32), 1 float values into double-float (DF64, exact
+// values), 2 double-float values (DF64), 3 double values (F64).
+template <class P, int NB, int VMODE>
+__global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ colidx, const float* __restrict__ v32,
+                                                   const float* __restrict__ v32lo, const double* __restrict__ v64,
+                                                   const typename P::S* __restrict__ X, long long ldx,
+                                                   typename P::S* __restrict__ Y, long long ldy) {
+  using A = typename P::A;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  A acc[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) acc[c] = P::zero();
+  const int k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
+  for (int k = k0; k < k1; ++k) {
+    const int j = __ldg(colidx + k);
+    const typename P::S* xr = X + (long long)j * ldx;
+    if constexpr (VMODE == 0) {
+      const float a = __ldg(v32 + k);
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] = fmaf(P::load(xr + c), a, acc[c]);
+    } else if constexpr (VMODE == 1) {
+      const float a = __ldg(v32 + k);
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] = df_fma_f(acc[c], P::load(xr + c), a);
+    } else if constexpr (VMODE == 2) {
+      const df a = {__ldg(v32 + k), __ldg(v32lo + k)};
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] = df_fma(acc[c], P::load(xr + c), a);
+    } else {
+      const double a = __ldg(v64 + k);
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] = ::fma(P::load(xr + c), a, acc[c]);
+    }
+  }
+  typename P::S* yr = Y + i * ldy;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) P::store(yr + c, acc[c]);
+}
+
+template <class P, int NB>
+cudaError_t spmm_nb(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t st) {
+  using S = typename P::S;
+  const int grid = grid_for(A.rows, kThreads);
+  const S* x = reinterpret_cast<const S*>(X);
+  S* y = reinterpret_cast<S*>(Y);
+  if constexpr (P::id == kF32) {
+    k_spmm<P, NB, 0><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y, ldy);
+  } else if constexpr (P::id == kDF64) {
+    if (A.v32lo == nullptr)
+      k_spmm<P, NB, 1><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y, ldy);
+    else
+      k_spmm<P, NB, 2><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, A.v32lo, nullptr, x, ldx, y, ldy);
+  } else {
+    k_spmm<P, NB, 3><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, nullptr, nullptr, A.v64, x, ldx, y, ldy);
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t spmm_p(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, int b, cudaStream_t st) {
+  using S = typename P::S;
+  int c0 = 0;
+  while (c0 < b) {
+    const int rem = b - c0;
+    const S* x = reinterpret_cast<const S*>(X) + c0;
+    S* y = reinterpret_cast<S*>(Y) + c0;
+    cudaError_t e;
+    int w;
+    if (rem >= 8) {
+      w = 8;
+      e = spmm_nb<P, 8>(A, x, ldx, y, ldy, st);
+    } else if (rem >= 4) {
+      w = 4;
+      e = spmm_nb<P, 4>(A, x, ldx, y, ldy, st);
+    } else if (rem >= 2) {
+      w = 2;
+      e = spmm_nb<P, 2>(A, x, ldx, y, ldy, st);
+    } else {
+      w = 1;
+      e = spmm_nb<P, 1>(A, x, ldx, y, ldy, st);
+    }
+    if (e != cudaSuccess) return e;
+    c0 += w;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Gram: partial[blk][i][j] = sum over the block's rows of P[r, i] Q[r, j]
+// ---------------------------------------------------------------------------
+constexpr int kGramThreads = 256;
+constexpr int kGramQ = 8;
+
+template <class P>
+__global__ void __launch_bounds__(kGramThreads) k_gram(long long r0, long long r1, SegArr segs, int p,
+                                                       const typename P::S* __restrict__ Q, long long ldq, int q,
+                                                       typename P::G* __restrict__ partial) {
+  using S = typename P::S;
+  using G = typename P::G;
+  __shared__ G sm[kGramThreads * kGramQ];
+  const int t = threadIdx.x;
+  const int ngroups = kGramThreads / p;
+  const int i = t % p, rg = t / p;
+  const bool active = rg < ngroups;
+  long long ld;
+  const S* base = seg_col<S>(segs, active ? i : 0, &ld);
+  const long long total = r1 - r0;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long cr0 = r0 + (long long)blockIdx.x * per;
+  const long long cr1 = cr0 + per < r1 ? cr0 + per : r1;
+  G acc[kGramQ];
+#pragma unroll
+  for (int j = 0; j < kGramQ; ++j) acc[j] = P::gzero();
+  if (active) {
+#pragma unroll 2
+    for (long long r = cr0 + rg; r < cr1; r += ngroups) {
+      const auto x = P::load(base + r * ld);
+      const S* qr = Q + r * ldq;
+#pragma unroll
+      for (int j = 0; j < kGramQ; ++j)
+        if (j < q) acc[j] = P::gfma(acc[j], x, P::load(qr + j));
+    }
+    for (int j = 0; j < q; ++j) sm[(rg * p + i) * q + j] = acc[j];
+  }
+  __syncthreads();
+  const int pq = p * q;
+  for (int e = t; e < pq; e += kGramThreads) {
+    G s = sm[e];
+    for (int g = 1; g < ngroups; ++g) s = P::gadd(s, sm[g * pq + e]);
+    partial[(long long)blockIdx.x * pq + e] = s;
+  }
+}
+
+template <class P>
+__global__ void k_gram_reduce(const typename P::G* __restrict__ partial, int nblocks, int pq, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= pq) return;
+  typename P::G s = partial[e];
+  for (int b = 1; b < nblocks; ++b) s = P::gadd(s, partial[(long long)b * pq + e]);
+  G[e] = P::gval(s);
+}
+
+template <class P>
+cudaError_t gram_p(long long r0, long long r1, const SegArr& sa, int p, SegV Q, void* partial, int max_blocks,
+                   int* nblocks, cudaStream_t st) {
+  long long rows = r1 - r0;
+  long long want = (rows + 255) / 256;  // at least ~256 rows per block
+  int nb = (int)(want < max_blocks ? want : max_blocks);
+  if (nb < 1) nb = 1;
+  *nblocks = nb;
+  k_gram<P><<<nb, kGramThreads, 0, st>>>(r0, r1, sa, p, reinterpret_cast<const typename P::S*>(Q.p), Q.ld, Q.nc,
+                                         reinterpret_cast<typename P::G*>(partial));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Combine: Out = alpha In + P coef, then Out <- Out Rinv
+// ---------------------------------------------------------------------------
+constexpr int kCmbRows = 32;
+constexpr int kCmbThreads = 128;
+
+template <class P>
+__global__ void __launch_bounds__(kCmbThreads) k_combine(long long L, SegArr segs, int p,
+                                                         const typename P::C* __restrict__ coef,
+                                                         const typename P::S* In, long long ldin, int alpha_one,
+                                                         typename P::S* Out, long long ldout, int q,
+                                                         const typename P::C* __restrict__ Rinv,
+                                                         typename P::S* Out2, long long ldout2) {
+  using S = typename P::S;
+  using A = typename P::A;
+  using C = typename P::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pst = p + 1;
+  A* Ps = reinterpret_cast<A*>(smraw);
+  C* Cs = reinterpret_cast<C*>(Ps + kCmbRows * pst);
+  A* Os = reinterpret_cast<A*>(Cs + p * q);
+  C* Rs = reinterpret_cast<C*>(Os + kCmbRows * q);
+  const int t = threadIdx.x;
+  for (int e = t; e < p * q; e += kCmbThreads) Cs[e] = coef[e];
+  if (Rinv)
+    for (int e = t; e < q * q; e += kCmbThreads) Rs[e] = Rinv[e];
+  for (long long row0 = (long long)blockIdx.x * kCmbRows; row0 < L; row0 += (long long)gridDim.x * kCmbRows) {
+    const int nrows = (int)(L - row0 < kCmbRows ? L - row0 : kCmbRows);
+    __syncthreads();
+    for (int e = t; e < nrows * p; e += kCmbThreads) {
+      const int r = e / p, c = e % p;
+      long long ld;
+      const S* b = seg_col<S>(segs, c, &ld);
+      Ps[r * pst + c] = P::load(b + (row0 + r) * ld);
+    }
+    __syncthreads();
+    for (int e = t; e < nrows * q; e += kCmbThreads) {
+      const int r = e / q, j = e % q;
+      A acc = alpha_one ? P::load(In + (row0 + r) * ldin + j) : P::zero();
+      for (int c = 0; c < p; ++c) acc = P::fmac(acc, Ps[r * pst + c], Cs[c * q + j]);
+      if (Rinv) {
+        Os[r * q + j] = acc;
+      } else {
+        P::store(Out + (row0 + r) * ldout + j, acc);
+        if (Out2) P::store(Out2 + (row0 + r) * ldout2 + j, acc);
+      }
+    }
+    if (Rinv) {
+      __syncthreads();
+      for (int e = t; e < nrows * q; e += kCmbThreads) {
+        const int r = e / q, j = e % q;
+        A acc = P::zero();
+        for (int l = 0; l <= j; ++l) acc = P::fmac(acc, Os[r * q + l], Rs[l * q + j]);
+        P::store(Out + (row0 + r) * ldout + j, acc);
+        if (Out2) P::store(Out2 + (row0 + r) * ldout2 + j, acc);
+      }
+    }
+  }
+}
+
+template <class P>
+size_t combine_smem(int p, int q, bool rinv) {
+  return sizeof(typename P::A) * (size_t)kCmbRows * (p + 1) + sizeof(typename P::C) * (size_t)p * q +
+         sizeof(typename P::A) * (size_t)kCmbRows * q + (rinv ? sizeof(typename P::C) * (size_t)q * q : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Fused Ritz vectors / residuals / norms
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void __launch_bounds__(kCmbThreads) k_ritz_residual(long long L, const typename P::S* V, long long ldv,
+                                                               const typename P::S* W, long long ldw, int g,
+                                                               const typename P::C* __restrict__ Y,
+                                                               const typename P::C* __restrict__ theta,
+                                                               typename P::S* X, typename P::S* R, long long ldb,
+                                                               int nb, const typename P::S* __restrict__ dscale,
+                                                               typename P::S* T, typename P::G* __restrict__ partial) {
+  using A = typename P::A;
+  using C = typename P::C;
+  using G = typename P::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int gst = g + 1;
+  A* Vs = reinterpret_cast<A*>(smraw);
+  A* Ws = Vs + kCmbRows * gst;
+  C* Ys = reinterpret_cast<C*>(Ws + kCmbRows * gst);
+  C* Th = Ys + g * nb;
+  G* Ns = reinterpret_cast<G*>(Th + nb);
+  const int t = threadIdx.x;
+  for (int e = t; e < g * nb; e += kCmbThreads) Ys[e] = Y[e];
+  for (int e = t; e < nb; e += kCmbThreads) Th[e] = theta[e];
+  G nacc = P::gzero();  // thread j < nb accumulates column j
+  for (long long row0 = (long long)blockIdx.x * kCmbRows; row0 < L; row0 += (long long)gridDim.x * kCmbRows) {
+    const int nrows = (int)(L - row0 < kCmbRows ? L - row0 : kCmbRows);
+    __syncthreads();
+    for (int e = t; e < nrows * g; e += kCmbThreads) {
+      const int r = e / g, c = e % g;
+      Vs[r * gst + c] = P::load(V + (row0 + r) * ldv + c);
+      Ws[r * gst + c] = P::load(W + (row0 + r) * ldw + c);
+    }
+    __syncthreads();
+    for (int e = t; e < nrows * nb; e += kCmbThreads) {
+      const int r = e / nb, j = e % nb;
+      A x = P::zero(), w = P::zero();
+      for (int c = 0; c < g; ++c) {
+        x = P::fmac(x, Vs[r * gst + c], Ys[c * nb + j]);
+        w = P::fmac(w, Ws[r * gst + c], Ys[c * nb + j]);
+      }
+      const A res = P::sub(w, P::mulc(x, Th[j]));
+      const long long o = (row0 + r) * ldb + j;
+      P::store(X + o, x);
+      P::store(R + o, res);
+      if (T) P::store(T + o, P::mulc(res, P::load(dscale + row0 + r)));
+      Ns[r * nb + j] = P::gfma(P::gzero(), res, res);
+    }
+    __syncthreads();
+    if (t < nb)
+      for (int r = 0; r < nrows; ++r) nacc = P::gadd(nacc, Ns[r * nb + t]);
+  }
+  if (t < nb) partial[(long long)blockIdx.x * nb + t] = nacc;
+}
+
+// ---------------------------------------------------------------------------
+// Stage-2 split residual norms
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void __launch_bounds__(kThreads) k_split_resnorm(long long L, long long n, const typename P::S* X,
+                                                            const typename P::S* BX, long long ldb, int nb,
+                                                            const typename P::C* __restrict__ cf,
+                                                            typename P::G* __restrict__ partial) {
+  using A = typename P::A;
+  using G = typename P::G;
+  __shared__ G sm[kThreads * 8];
+  G acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = P::gzero();
+  const long long total = L * nb;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const long long r = e / nb;
+    const int j = (int)(e % nb);
+    const int off = r < n ? 0 : 2 * nb;
+    const A v = P::sub(P::mulc(P::load(BX + r * ldb + j), cf[off + j]), P::mulc(P::load(X + r * ldb + j), cf[off + nb + j]));
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      if (jj == j) acc[jj] = P::gfma(acc[jj], v, v);
+  }
+  for (int j = 0; j < nb; ++j) sm[threadIdx.x * 8 + j] = acc[j];
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    G s = sm[threadIdx.x];
+    for (int tt = 1; tt < blockDim.x; ++tt) s = P::gadd(s, sm[tt * 8 + threadIdx.x]);
+    partial[(long long)blockIdx.x * nb + threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void k_scale_rows(long long L, const typename P::S* d, const typename P::S* R, long long ldr,
+                             typename P::S* T, long long ldt, int nb) {
+  const long long total = L * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / nb;
+    const int j = (int)(e % nb);
+    auto dv = P::load(d + r);
+    auto rv = P::load(R + r * ldr + j);
+    if constexpr (P::id == kDF64)
+      P::store(T + r * ldt + j, df_mul(rv, dv));
+    else
+      P::store(T + r * ldt + j, rv * dv);
+  }
+}
+
+template <class P>
+__global__ void k_copy_cols(long long L, const typename P::S* Src, long long lds, typename P::S* Dst, long long ldd,
+                            int nb) {
+  const long long total = L * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / nb;
+    const int j = (int)(e % nb);
+    Dst[r * ldd + j] = Src[r * lds + j];
+  }
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  // Steele, Lea, Flood, "Fast splittable pseudorandom number generators", 2014.
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+template <class P>
+__global__ void k_fill_normal(long long L, typename P::S* Dst, long long ldd, int nb, unsigned long long seed) {
+  const long long total = L * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / nb;
+    const int j = (int)(e % nb);
+    unsigned long long h = splitmix64(seed ^ splitmix64((unsigned long long)e));
+    double u1 = ((h >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    unsigned long long h2 = splitmix64(h);
+    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+    double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    if constexpr (P::id == kF32) {
+      Dst[r * ldd + j] = (float)z;
+    } else if constexpr (P::id == kDF64) {
+      float hi = (float)z;
+      Dst[r * ldd + j] = df{hi, (float)(z - (double)hi)};
+    } else {
+      Dst[r * ldd + j] = z;
+    }
+  }
+}
+
+template <class P>
+__global__ void k_from_f64(long long L, int nc, const double* src, long long lds, typename P::S* dst, long long ldd,
+                           double scale) {
+  const long long total = L * nc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % L;
+    const int j = (int)(e / L);
+    const double z = src[(long long)j * lds + r] * scale;
+    if constexpr (P::id == kF32) {
+      dst[r * ldd + j] = (float)z;
+    } else if constexpr (P::id == kDF64) {
+      float hi = (float)z;
+      dst[r * ldd + j] = df{hi, (float)(z - (double)hi)};
+    } else {
+      dst[r * ldd + j] = z;
+    }
+  }
+}
+
+template <class P>
+__global__ void k_to_f64(long long L, int nc, const typename P::S* src, long long lds, double* dst, long long ldd,
+                         double scale) {
+  const long long total = L * nc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % L;
+    const int j = (int)(e / L);
+    double z;
+    if constexpr (P::id == kDF64) {
+      df v = src[r * lds + j];
+      z = (double)v.hi + (double)v.lo;
+    } else {
+      z = (double)src[r * lds + j];
+    }
+    dst[(long long)j * ldd + r] = z * scale;
+  }
+}
+
+template <class P>
+__global__ void k_make_dscale(long long L, const double* s, int use_sqrt, typename P::S* d) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < L; r += (long long)gridDim.x * blockDim.x) {
+    double v = s[r];
+    if (use_sqrt) v = sqrt(v);
+    double z = v > 0 ? 1.0 / v : 1.0;
+    if constexpr (P::id == kF32) {
+      d[r] = (float)z;
+    } else if constexpr (P::id == kDF64) {
+      float hi = (float)z;
+      d[r] = df{hi, (float)(z - (double)hi)};
+    } else {
+      d[r] = z;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels
+// ---------------------------------------------------------------------------
+__global__ void k_absmax(long long nnz, const double* vals, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    double a = fabs(vals[k]);
+    unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    m = b > m ? b : m;
+  }
+  atomicMax(out, m);
+}
+
+__global__ void k_csr_values(long long nnz, const double* vals, double scale, float* v32, float* v32lo, double* v64,
+                             int* flags) {
+  int any = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const double z = vals[k] * scale;
+    const float hi = (float)z;
+    const float lo = (float)(z - (double)hi);
+    v32[k] = hi;
+    v32lo[k] = lo;
+    v64[k] = z;
+    any |= (lo != 0.f);
+  }
+  if (any) atomicOr(flags, 1);
+}
+
+__global__ void k_count_cols(long long nnz, const int* colidx, int* cnt) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+    atomicAdd(cnt + colidx[k], 1);
+}
+
+constexpr int kScanChunk = 2048;
+
+__global__ void k_scan_block_sums(long long n, const int* in, long long* bsum) {
+  __shared__ long long sm[kThreads];
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  long long s = 0;
+  for (int e = threadIdx.x; e < kScanChunk; e += kThreads)
+    if (base + e < n) s += in[base + e];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = sm[0];
+}
+
+// Exclusive scan of bsum (nb entries) by one block, sequential over chunks.
+__global__ void k_scan_bsums(int nb, long long* bsum) {
+  __shared__ long long sm[1024];
+  long long carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    long long v = i < nb ? bsum[i] : 0;
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 1; w < 1024; w <<= 1) {  // Hillis-Steele inclusive scan
+      long long add = threadIdx.x >= w ? sm[threadIdx.x - w] : 0;
+      __syncthreads();
+      sm[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sm[threadIdx.x] - v;
+    carry += sm[1023];
+    __syncthreads();
+  }
+}
+
+// out[0] = 0, out[i + 1] = sum_{t <= i} in[t] (int32 result, checked on host).
+__global__ void k_scan_apply(long long n, const int* in, const long long* boff, int* out) {
+  __shared__ long long sm[kScanChunk];
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  for (int e = threadIdx.x; e < kScanChunk; e += kThreads) sm[e] = base + e < n ? in[base + e] : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = boff[blockIdx.x];
+    for (int e = 0; e < kScanChunk; ++e) {
+      s += sm[e];
+      sm[e] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kScanChunk; e += kThreads)
+    if (base + e < n) out[base + e + 1] = (int)sm[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+__global__ void k_scatter_t(long long rows, const int* rowptr, const int* colidx, const double* vals,
+                            const int* rowptrT, int* cursor, int* colidxT, double* valsT) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int j = colidx[k];
+      const int pos = rowptrT[j] + atomicAdd(cursor + j, 1);
+      colidxT[pos] = (int)i;
+      valsT[pos] = vals[k];
+    }
+  }
+}
+
+__device__ void sift_down(int* key, double* val, int start, int end) {
+  int root = start;
+  while (2 * root + 1 <= end) {
+    int child = 2 * root + 1, sw = root;
+    if (key[sw] < key[child]) sw = child;
+    if (child + 1 <= end && key[sw] < key[child + 1]) sw = child + 1;
+    if (sw == root) return;
+    int tk = key[root];
+    key[root] = key[sw];
+    key[sw] = tk;
+    double tv = val[root];
+    val[root] = val[sw];
+    val[sw] = tv;
+    root = sw;
+  }
+}
+
+// Sort each row segment of the transposed CSR by index (makes the atomic
+// scatter order irrelevant, so the result is deterministic).
+__global__ void k_sort_segments(long long rowsT, const int* rowptrT, int* colidxT, double* valsT) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < rowsT; j += (long long)gridDim.x * blockDim.x) {
+    const int k0 = rowptrT[j], len = rowptrT[j + 1] - k0;
+    int* key = colidxT + k0;
+    double* val = valsT + k0;
+    if (len <= 32) {
+      for (int a = 1; a < len; ++a) {
+        int kk = key[a];
+        double vv = val[a];
+        int b = a - 1;
+        while (b >= 0 && key[b] > kk) {
+          key[b + 1] = key[b];
+          val[b + 1] = val[b];
+          --b;
+        }
+        key[b + 1] = kk;
+        val[b + 1] = vv;
+      }
+    } else {  // heapsort
+      for (int s = (len - 2) / 2; s >= 0; --s) sift_down(key, val, s, len - 1);
+      for (int end = len - 1; end > 0; --end) {
+        int tk = key[end];
+        key[end] = key[0];
+        key[0] = tk;
+        double tv = val[end];
+        val[end] = val[0];
+        val[0] = tv;
+        sift_down(key, val, 0, end - 1);
+      }
+    }
+  }
+}
+
+__global__ void k_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += vals[k] * vals[k];
+    out[i] = s;
+  }
+}
+
+__global__ void k_csr_validate(long long rows, long long cols, const int* rowptr, const int* colidx, const double* vals,
+                               int* flags) {
+  int f = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
+    const int k0 = rowptr[i], k1 = rowptr[i + 1];
+    if (k1 < k0) {
+      f |= 2;
+      continue;
+    }
+    int prev = -1;
+    for (int k = k0; k < k1; ++k) {
+      const int c = colidx[k];
+      if (c < 0 || c >= cols || c <= prev) f |= 2;
+      prev = c;
+      if (!isfinite(vals[k])) f |= 4;
+    }
+  }
+  if (f) atomicOr(flags, f);
+}
+
+inline int persistent_grid(long long work_items, int per_block) {
+  long long g = (work_items + per_block - 1) / per_block;
+  const long long cap = 152LL * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class P, class F>
+cudaError_t dispatch(int prec, F&& f) {
+  (void)sizeof(P);
+  return f();
+}
+
+}  // namespace
+
+// ===========================================================================
+// Launch wrappers
+// ===========================================================================
+#define PHSVDS_DISPATCH(prec, CALL)        \
+  switch (prec) {                          \
+    case kF32: {                           \
+      using P = PF32;                      \
+      return CALL;                         \
+    }                                      \
+    case kDF64: {                          \
+      using P = PDF64;                     \
+      return CALL;                         \
+    }                                      \
+    case kF64: {                           \
+      using P = PF64;                      \
+      return CALL;                         \
+    }                                      \
+    default:                               \
+      return cudaErrorInvalidValue;        \
+  }
+
+static SegArr make_segs(const SegV* P, int nseg, int* ptotal) {
+  SegArr sa{};
+  int tot = 0;
+  for (int s = 0; s < 3; ++s) {
+    sa.p[s] = s < nseg ? P[s].p : nullptr;
+    sa.ld[s] = s < nseg ? P[s].ld : 0;
+    sa.nc[s] = s < nseg ? P[s].nc : 0;
+    if (s < nseg) tot += P[s].nc;
+  }
+  sa.n = nseg;
+  *ptotal = tot;
+  return sa;
+}
+
+cudaError_t launch_spmm(int prec, const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, int b,
+                        cudaStream_t st) {
+  if (A.rows == 0 || b == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, spmm_p<P>(A, X, ldx, Y, ldy, b, st))
+}
+
+size_t gram_partial_bytes(int max_blocks, int p, int q) { return (size_t)max_blocks * p * q * 8; }
+int gram_default_blocks() { return 152 * 4; }
+
+cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* Pp, int nseg, SegV Q, void* partial,
+                        int max_blocks, int* nblocks, cudaStream_t st) {
+  int p;
+  SegArr sa = make_segs(Pp, nseg, &p);
+  if (p < 1 || p > kGramThreads || Q.nc < 1 || Q.nc > kGramQ || nseg < 1 || nseg > 3) return cudaErrorInvalidValue;
+  if (r1 <= r0) {  // empty row range: one block of zeros
+    r1 = r0;
+  }
+  PHSVDS_DISPATCH(prec, gram_p<P>(r0, r1, sa, p, Q, partial, max_blocks, nblocks, st))
+}
+
+cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st) {
+  const int grid = grid_for(pq, kThreads);
+  switch (prec) {
+    case kF32:
+      k_gram_reduce<PF32><<<grid, kThreads, 0, st>>>(reinterpret_cast<const df*>(partial), nblocks, pq, G);
+      break;
+    case kDF64:
+      k_gram_reduce<PDF64><<<grid, kThreads, 0, st>>>(reinterpret_cast<const df*>(partial), nblocks, pq, G);
+      break;
+    case kF64:
+      k_gram_reduce<PF64><<<grid, kThreads, 0, st>>>(reinterpret_cast<const double*>(partial), nblocks, pq, G);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t combine_p(long long L, const SegArr& sa, int p, const void* coef, const void* In, long long ldin,
+                             int alpha_one, void* Out, long long ldout, int q, const void* Rinv, void* Out2,
+                             long long ldout2, cudaStream_t st) {
+  using S = typename P::S;
+  using C = typename P::C;
+  const size_t sm = combine_smem<P>(p, q, Rinv != nullptr);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set[4] = {false, false, false, false};
+  if (!attr_set[P::id]) {
+    cudaFuncSetAttribute(k_combine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[P::id] = true;
+  }
+  const int grid = persistent_grid((L + kCmbRows - 1) / kCmbRows, 1);
+  k_combine<P><<<grid, kCmbThreads, sm, st>>>(L, sa, p, reinterpret_cast<const C*>(coef), reinterpret_cast<const S*>(In),
+                                              ldin, alpha_one, reinterpret_cast<S*>(Out), ldout, q,
+                                              reinterpret_cast<const C*>(Rinv), reinterpret_cast<S*>(Out2), ldout2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, const void* coef, const void* In,
+                           long long ldin, int alpha_one, void* Out, long long ldout, int q, const void* Rinv,
+                           void* Out2, long long ldout2, cudaStream_t st) {
+  if (L == 0 || q == 0) return cudaSuccess;
+  int p;
+  SegArr sa = make_segs(Pp, nseg, &p);
+  if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
+  PHSVDS_DISPATCH(prec, combine_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2, st))
+}
+
+template <class P>
+static cudaError_t ritz_p(long long L, SegV V, SegV W, int g, const void* Y, const void* theta, void* X, void* R,
+                          long long ldb, int nb, const void* dscale, void* T, void* partial, int max_blocks,
+                          int* nblocks, cudaStream_t st) {
+  using S = typename P::S;
+  using C = typename P::C;
+  using A = typename P::A;
+  using G = typename P::G;
+  const size_t sm = sizeof(A) * 2 * (size_t)kCmbRows * (g + 1) + sizeof(C) * ((size_t)g * nb + nb) +
+                    sizeof(G) * (size_t)kCmbRows * nb + 16;
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set[4] = {false, false, false, false};
+  if (!attr_set[P::id]) {
+    cudaFuncSetAttribute(k_ritz_residual<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[P::id] = true;
+  }
+  int grid = persistent_grid((L + kCmbRows - 1) / kCmbRows, 1);
+  if (grid > max_blocks) grid = max_blocks;
+  *nblocks = grid;
+  k_ritz_residual<P><<<grid, kCmbThreads, sm, st>>>(
+      L, reinterpret_cast<const S*>(V.p), V.ld, reinterpret_cast<const S*>(W.p), W.ld, g,
+      reinterpret_cast<const C*>(Y), reinterpret_cast<const C*>(theta), reinterpret_cast<S*>(X),
+      reinterpret_cast<S*>(R), ldb, nb, reinterpret_cast<const S*>(dscale), reinterpret_cast<S*>(T),
+      reinterpret_cast<G*>(partial));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_residual(int prec, long long L, SegV V, SegV W, int g, const void* Y, const void* theta,
+                                 void* X, void* R, long long ldb, int nb, const void* dscale, void* T,
+                                 void* norm_partial, int max_blocks, int* nblocks, cudaStream_t st) {
+  if (g < 1 || nb < 1) return cudaErrorInvalidValue;
+  PHSVDS_DISPATCH(prec, ritz_p<P>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial, max_blocks, nblocks, st))
+}
+
+template <class P>
+static cudaError_t split_p(long long L, long long n, const void* X, const void* BX, long long ldb, int nb,
+                           const void* coefs, void* partial, int max_blocks, int* nblocks, cudaStream_t st) {
+  int grid = persistent_grid(L * nb, kThreads * 8);
+  if (grid > max_blocks) grid = max_blocks;
+  *nblocks = grid;
+  k_split_resnorm<P><<<grid, kThreads, 0, st>>>(L, n, reinterpret_cast<const typename P::S*>(X),
+                                                reinterpret_cast<const typename P::S*>(BX), ldb, nb,
+                                                reinterpret_cast<const typename P::C*>(coefs),
+                                                reinterpret_cast<typename P::G*>(partial));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_resnorm(int prec, long long L, long long n, const void* X, const void* BX, long long ldb,
+                                 int nb, const void* coefs, void* partial, int max_blocks, int* nblocks,
+                                 cudaStream_t st) {
+  if (nb < 1 || nb > 8) return cudaErrorInvalidValue;
+  PHSVDS_DISPATCH(prec, split_p<P>(L, n, X, BX, ldb, nb, coefs, partial, max_blocks, nblocks, st))
+}
+
+template <class P>
+static cudaError_t scale_rows_p(long long L, const void* d, const void* R, long long ldr, void* T, long long ldt,
+                                int nb, cudaStream_t st) {
+  using S = typename P::S;
+  k_scale_rows<P><<<persistent_grid(L * nb, kThreads), kThreads, 0, st>>>(
+      L, reinterpret_cast<const S*>(d), reinterpret_cast<const S*>(R), ldr, reinterpret_cast<S*>(T), ldt, nb);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_rows(int prec, long long L, const void* d, const void* R, long long ldr, void* T,
+                              long long ldt, int nb, cudaStream_t st) {
+  if (L * nb == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, scale_rows_p<P>(L, d, R, ldr, T, ldt, nb, st))
+}
+
+template <class P>
+static cudaError_t copy_cols_p(long long L, const void* Src, long long lds, void* Dst, long long ldd, int nb,
+                               cudaStream_t st) {
+  using S = typename P::S;
+  k_copy_cols<P><<<persistent_grid(L * nb, kThreads), kThreads, 0, st>>>(L, reinterpret_cast<const S*>(Src), lds,
+                                                                         reinterpret_cast<S*>(Dst), ldd, nb);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy_cols(int prec, long long L, const void* Src, long long lds, void* Dst, long long ldd, int nb,
+                             cudaStream_t st) {
+  if (L * nb == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, copy_cols_p<P>(L, Src, lds, Dst, ldd, nb, st))
+}
+
+template <class P>
+static cudaError_t fill_p(long long L, void* Dst, long long ldd, int nb, unsigned long long seed, cudaStream_t st) {
+  k_fill_normal<P><<<persistent_grid(L * nb, kThreads), kThreads, 0, st>>>(L, reinterpret_cast<typename P::S*>(Dst),
+                                                                           ldd, nb, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_normal(int prec, long long L, void* Dst, long long ldd, int nb, unsigned long long seed,
+                               cudaStream_t st) {
+  if (L * nb == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, fill_p<P>(L, Dst, ldd, nb, seed, st))
+}
+
+template <class P>
+static cudaError_t from_p(long long L, int nc, const double* src, long long lds, void* dst, long long ldd,
+                          double scale, cudaStream_t st) {
+  k_from_f64<P><<<persistent_grid(L * nc, kThreads), kThreads, 0, st>>>(L, nc, src, lds,
+                                                                        reinterpret_cast<typename P::S*>(dst), ldd, scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_from_f64_colmajor(int prec, long long L, int nc, const double* src, long long lds, void* dst,
+                                     long long ldd, double scale, cudaStream_t st) {
+  if (L * nc == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, from_p<P>(L, nc, src, lds, dst, ldd, scale, st))
+}
+
+template <class P>
+static cudaError_t to_p(long long L, int nc, const void* src, long long lds, double* dst, long long ldd, double scale,
+                        cudaStream_t st) {
+  k_to_f64<P><<<persistent_grid(L * nc, kThreads), kThreads, 0, st>>>(
+      L, nc, reinterpret_cast<const typename P::S*>(src), lds, dst, ldd, scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_to_f64_colmajor(int prec, long long L, int nc, const void* src, long long lds, double* dst,
+                                   long long ldd, double scale, cudaStream_t st) {
+  if (L * nc == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, to_p<P>(L, nc, src, lds, dst, ldd, scale, st))
+}
+
+size_t coef_bytes(int prec) { return prec == kF32 ? 4 : 8; }
+
+void host_coef_convert(int prec, const double* src, size_t count, void* dst) {
+  if (prec == kF32) {
+    float* d = reinterpret_cast<float*>(dst);
+    for (size_t i = 0; i < count; ++i) d[i] = (float)src[i];
+  } else if (prec == kDF64) {
+    float* d = reinterpret_cast<float*>(dst);
+    for (size_t i = 0; i < count; ++i) {
+      float hi = (float)src[i];
+      d[2 * i] = hi;
+      d[2 * i + 1] = (float)(src[i] - (double)hi);
+    }
+  } else {
+    std::memcpy(dst, src, count * sizeof(double));
+  }
+}
+
+cudaError_t launch_absmax(long long nnz, const double* vals, unsigned long long* out_bits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (nnz == 0) return cudaSuccess;
+  k_absmax<<<persistent_grid(nnz, kThreads), kThreads, 0, st>>>(nnz, vals, out_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_values(long long nnz, const double* vals, double scale, float* v32, float* v32lo, double* v64,
+                              int* flags, cudaStream_t st) {
+  if (nnz == 0) return cudaSuccess;
+  k_csr_values<<<persistent_grid(nnz, kThreads), kThreads, 0, st>>>(nnz, vals, scale, v32, v32lo, v64, flags);
+  return cudaGetLastError();
+}
+
+size_t transpose_work_ints(long long cols) {
+  const long long nb = (cols + kScanChunk - 1) / kScanChunk + 1;
+  return (size_t)(2 * (cols + 1) + 2 * nb + 4);
+}
+
+cudaError_t launch_csr_transpose(long long rows, long long cols, long long nnz, const int* rowptr, const int* colidx,
+                                 const double* vals, int* rowptrT, int* colidxT, double* valsT, int* work,
+                                 cudaStream_t st) {
+  int* cnt = work;
+  int* cursor = work + (cols + 1);
+  long long* bsum = reinterpret_cast<long long*>(work + 2 * (cols + 1) + ((2 * (cols + 1)) & 1));
+  const int nb = (int)((cols + kScanChunk - 1) / kScanChunk);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (cols + 1), st);
+  if (e != cudaSuccess) return e;
+  if (nnz > 0) k_count_cols<<<persistent_grid(nnz, kThreads), kThreads, 0, st>>>(nnz, colidx, cnt);
+  if (nb > 0) {
+    k_scan_block_sums<<<nb, kThreads, 0, st>>>(cols, cnt, bsum);
+    k_scan_bsums<<<1, 1024, 0, st>>>(nb, bsum);
+    k_scan_apply<<<nb, kThreads, 0, st>>>(cols, cnt, bsum, rowptrT);
+  } else {
+    e = cudaMemsetAsync(rowptrT, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (rows > 0 && nnz > 0) {
+    k_scatter_t<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, rowptr, colidx, vals, rowptrT, cursor,
+                                                                      colidxT, valsT);
+    k_sort_segments<<<persistent_grid(cols, kThreads), kThreads, 0, st>>>(cols, rowptrT, colidxT, valsT);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  k_row_sumsq<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, rowptr, vals, out);
+  return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t dscale_p(long long L, const double* s, int use_sqrt, void* d, cudaStream_t st) {
+  k_make_dscale<P><<<persistent_grid(L, kThreads), kThreads, 0, st>>>(L, s, use_sqrt, reinterpret_cast<typename P::S*>(d));
+  return cudaGetLastError();
+}
+cudaError_t launch_make_dscale(int prec, long long L, const double* s, int use_sqrt, void* d, cudaStream_t st) {
+  if (L == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, dscale_p<P>(L, s, use_sqrt, d, st))
+}
+
+cudaError_t launch_csr_validate(long long rows, long long cols, const int* rowptr, const int* colidx,
+                                const double* vals, int* flags, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  k_csr_validate<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, cols, rowptr, colidx, vals, flags);
+  return cudaGetLastError();
+}
+
+void kernels_init() {}
+
+}  // namespace phsvds

@@ -1,0 +1,115 @@
+// Host-side launch wrappers of the device kernels (internal C++ interface).
+//
+// Layout conventions: a "block" of vectors with L rows and c columns is stored
+// row-major with leading dimension ld (element (r, j) at ptr[r * ld + j]); all
+// long vectors of the solver use this layout, so the b entries of one row that
+// a CSR nonzero gathers are contiguous.  Storage element type per mode:
+// F32 -> float, DF64 -> float2 (hi, lo), F64 -> double.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phsvds {
+
+enum Prec { kF32 = 1, kDF64 = 2, kF64 = 3 };
+
+inline size_t elem_bytes(int prec) { return prec == kF32 ? 4 : 8; }
+
+// Column segment of a row-major block: columns [0, nc) of ptr with stride ld.
+struct SegV {
+  const void* p;
+  long long ld;
+  int nc;
+};
+
+// CSR matrix values in the formats of one mode.
+struct CsrDev {
+  long long rows = 0, cols = 0, nnz = 0;
+  const int* rowptr = nullptr;
+  const int* colidx = nullptr;
+  const float* v32 = nullptr;     // F32 values (also the hi part of DF64)
+  const float* v32lo = nullptr;   // DF64 lo part, nullptr when every value is a float
+  const double* v64 = nullptr;    // F64 values
+};
+
+// Y (rows x b, ldy) = A X (cols x b, ldx).
+cudaError_t launch_spmm(int prec, const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy,
+                        int b, cudaStream_t st);
+
+// Partial Gram sums: for rows [r0, r1), G = [P0 P1 P2]^T Q (p = sum of nc, q <= 8)
+// into `partial` (nblocks x p x q accumulators, 8 bytes each); returns the
+// number of blocks used via *nblocks.  `max_blocks` bounds the grid.
+cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* P, int nseg, SegV Q,
+                        void* partial, int max_blocks, int* nblocks, cudaStream_t st);
+// Sum the partials in fixed order into G (p x q, row-major doubles, device).
+cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st);
+// Bytes of partial storage that launch_gram may use.
+size_t gram_partial_bytes(int max_blocks, int p, int q);
+int gram_default_blocks();
+
+// Out[:, 0:q] = alpha * In[:, 0:q] + [P0 P1 P2] * coef  (coef p x q, row-major,
+// device, in the mode's coefficient format), then, if Rinv != nullptr,
+// Out[r, :] <- Out[r, :] * Rinv (q x q upper triangular, row-major).  Out may
+// alias P0 (in-place restart: every CTA stages its rows before writing).  If
+// Out2 != nullptr the result is also written there.
+cudaError_t launch_combine(int prec, long long L, const SegV* P, int nseg, const void* coef,
+                           const void* In, long long ldin, int alpha_one, void* Out, long long ldout, int q,
+                           const void* Rinv, void* Out2, long long ldout2, cudaStream_t st);
+
+// Fused Ritz vectors, residuals and residual norms:
+//   X = V Y, R = W Y - X diag(theta), norm_partial <- sum_r R^2 per column,
+// optionally T = diag(dscale) R (preconditioner) when T != nullptr.
+cudaError_t launch_ritz_residual(int prec, long long L, SegV V, SegV W, int g, const void* Y,
+                                 const void* theta, void* X, void* R, long long ldb, int nb,
+                                 const void* dscale, void* T, void* norm_partial, int max_blocks,
+                                 int* nblocks, cudaStream_t st);
+
+// Stage-2 residual of Eq. res from x = [x_v; x_u] and Bx = [A^T x_u; A x_v]:
+// per column j, sum over rows of (a_j Bx - c_j x)^2 with (a, c) = (av, cv) for
+// rows < n and (au, cu) for rows >= n.  Partials as launch_gram with q = nb.
+cudaError_t launch_split_resnorm(int prec, long long L, long long n, const void* X, const void* BX,
+                                 long long ldb, int nb, const void* coefs /*4*nb coef*/, void* partial,
+                                 int max_blocks, int* nblocks, cudaStream_t st);
+
+// Elementwise T[r, j] = d[r] * R[r, j] (d in storage format).
+cudaError_t launch_scale_rows(int prec, long long L, const void* d, const void* R, long long ldr, void* T,
+                              long long ldt, int nb, cudaStream_t st);
+// Copy columns: Dst[r, 0:nb] = Src[r, 0:nb].
+cudaError_t launch_copy_cols(int prec, long long L, const void* Src, long long lds, void* Dst, long long ldd,
+                             int nb, cudaStream_t st);
+// Seeded N(0,1) fill of a block (splitmix64 counter hash + Box-Muller).
+cudaError_t launch_fill_normal(int prec, long long L, void* Dst, long long ldd, int nb, unsigned long long seed,
+                               cudaStream_t st);
+
+// Conversions between FP64 column-major (device) and mode storage row-major.
+cudaError_t launch_from_f64_colmajor(int prec, long long L, int nc, const double* src, long long lds, void* dst,
+                                     long long ldd, double scale, cudaStream_t st);
+cudaError_t launch_to_f64_colmajor(int prec, long long L, int nc, const void* src, long long lds, double* dst,
+                                   long long ldd, double scale, cudaStream_t st);
+// Convert a coefficient array of doubles to the mode's coefficient format (host side).
+size_t coef_bytes(int prec);
+void host_coef_convert(int prec, const double* src, size_t count, void* dst);
+
+// ---- setup (CSR) ----
+cudaError_t launch_absmax(long long nnz, const double* vals, unsigned long long* out_bits, cudaStream_t st);
+// Values: v32 = round(scale * v), v32lo = round(scale * v - v32), v64 = scale * v; flags[0] |= 1 if any lo != 0.
+cudaError_t launch_csr_values(long long nnz, const double* vals, double scale, float* v32, float* v32lo,
+                              double* v64, int* flags, cudaStream_t st);
+// Deterministic transpose: (rowptr, colidx, vals) of an rows x cols CSR to its
+// cols x rows CSR with increasing column (= original row) indices per row.
+cudaError_t launch_csr_transpose(long long rows, long long cols, long long nnz, const int* rowptr,
+                                 const int* colidx, const double* vals, int* rowptrT, int* colidxT,
+                                 double* valsT, int* work /* cols + 1 + scan scratch */, cudaStream_t st);
+size_t transpose_work_ints(long long cols);
+// out[i] = sum_k vals[k]^2 over row i (FP64).
+cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st);
+// Jacobi scale in storage format: d[r] = 1 / s[r] (1 where s[r] == 0), optionally sqrt'ed first.
+cudaError_t launch_make_dscale(int prec, long long L, const double* s, int use_sqrt, void* d, cudaStream_t st);
+// CSR validation: sorted, in range, finite values; flags bit 1 = bad index/order, bit 2 = non-finite.
+cudaError_t launch_csr_validate(long long rows, long long cols, const int* rowptr, const int* colidx,
+                                const double* vals, int* flags, cudaStream_t st);
+
+void kernels_init();
+
+}  // namespace phsvds

@@ -1,0 +1,108 @@
+"""CPU checks of the C-ABI library: it loads, exports what the headers declare,
+and rejects invalid arguments before touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1607_01404_gb300 import binding as B
+from paper_1607_01404_gb300 import build as BLD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    BLD.build()
+
+
+def _declared():
+    names = []
+    for h in ("phsvds.h", "phsvds_kernels.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(svds_\w+|phsvds_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.CDLL(B.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(declared) == set(B.exported_symbols())
+
+
+def test_strerror_and_defaults():
+    assert B.svds_strerror(0) == "success"
+    assert "CSR" in B.svds_strerror(B.SVDS_ERR_CSR)
+    o = B.svds_opts_default()
+    assert o.maxBlockSize == 1 and o.stage1_precision == B.SVDS_FP64 and o.precond == B.SVDS_PRECOND_JACOBI
+
+
+def test_host_symeig_matches_lapack():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 35, 64):
+        M = rng.standard_normal((n, n))
+        A = M + M.T
+        w, Z = B.host_symeig(A)
+        np.testing.assert_allclose(w, np.linalg.eigvalsh(A), atol=1e-13 * max(1, np.abs(w).max()))
+        assert np.abs(Z.T @ Z - np.eye(n)).max() < 1e-13
+        assert np.abs(A @ Z - Z * w).max() < 1e-13 * max(1, np.abs(w).max())
+
+
+def test_host_svd_smallest_vector_accurate():
+    rng = np.random.default_rng(4)
+    for n in (1, 5, 30):
+        R = np.triu(rng.standard_normal((n, n)))
+        R[:, 0] *= 1e-9  # tiny singular value: the refined extraction needs its vector
+        s, Y = B.host_svd(R)
+        sr = np.linalg.svd(R, compute_uv=False)[::-1]
+        np.testing.assert_allclose(s, sr, rtol=1e-12, atol=1e-15 * sr.max())
+        assert np.linalg.norm(R @ Y[:, 0]) <= s[0] * (1 + 1e-10) + 1e-15 * sr.max()
+
+
+def test_coef_convert_double_float_split():
+    x = np.array([1.0 / 3.0, -2.5, 1e-20, 123456.789])
+    out = B.coef_convert(B.PREC_DF64, x).reshape(-1, 2)
+    recon = out[:, 0].astype(np.float64) + out[:, 1].astype(np.float64)
+    assert np.all(np.abs(recon - x) <= 2.0 ** -47 * np.abs(x))
+
+
+def _bad_csr(kind):
+    rp = np.array([0, 2, 3], dtype=np.int32)
+    ci = np.array([0, 1, 1], dtype=np.int32)
+    va = np.array([1.0, 2.0, 3.0])
+    if kind == "unsorted":
+        ci = np.array([1, 0, 1], dtype=np.int32)
+    elif kind == "range":
+        ci = np.array([0, 5, 1], dtype=np.int32)
+    elif kind == "nan":
+        va = np.array([1.0, np.nan, 3.0])
+    elif kind == "rowptr":
+        rp = np.array([0, 2, 2], dtype=np.int32)
+    return rp, ci, va
+
+
+@pytest.mark.parametrize("kind,code", [("unsorted", B.SVDS_ERR_CSR), ("range", B.SVDS_ERR_CSR),
+                                       ("nan", B.SVDS_ERR_VALUE), ("rowptr", B.SVDS_ERR_CSR)])
+def test_create_rejects_malformed_csr_before_any_launch(kind, code):
+    rp, ci, va = _bad_csr(kind)
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 2, 2)
+    assert e.value.code == code
+
+
+def test_create_rejects_bad_shapes_and_options():
+    rp, ci, va = _bad_csr("ok")
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 0, 2)
+    assert e.value.code == B.SVDS_ERR_SHAPE
+    o = B.svds_opts_default()
+    o.stage1_precision = 7
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 2, 2, o)
+    assert e.value.code == B.SVDS_ERR_ARG

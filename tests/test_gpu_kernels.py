@@ -1,0 +1,182 @@
+"""Per-kernel parity of the CUDA path against the oracle / FP64 definitions.
+
+Tolerances: FP64-class modes (DF64, F64) must agree normwise to 1e-13 relative
+to ||(|A| |X|)|| (the spec SpMM bar, read normwise because element-wise
+relative error is unbounded under cancellation); the F32 mode to a few units
+of 2^-24 times the same normaliser.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_01404_gb300 import binding as B
+from paper_1607_01404_gb300 import build as BLD
+from paper_1607_01404_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from gpu_util import coef_device, csr_device, to_device, to_host  # noqa: E402
+
+TOL = {B.PREC_F32: 2e-6, B.PREC_DF64: 1e-13, B.PREC_F64: 1e-13}
+PRECS = [B.PREC_F32, B.PREC_DF64, B.PREC_F64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    BLD.build()
+    B.lib()
+
+
+def _matrices():
+    return [
+        wl.random_illconditioned(3001, 1203, 16, seed=3),  # ragged rows, empty rows
+        wl.grid_difference(9, 3),
+        wl.weighted_grid(23, 2, seed=1),
+    ]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("b", [1, 2, 3, 4, 5, 8, 11])
+def test_spmm_matches_oracle(prec, b):
+    for A in _matrices():
+        d = csr_device(A)
+        X = wl.dense_block(A.n, b, seed=b)
+        Xd = to_device(prec, X)
+        Xs = to_host(prec, Xd, A.n, b)  # the stored (rounded) input
+        Yd = to_device(prec, np.zeros((A.m, b)))
+        lo = None if d["exact"] else d["v32lo"]
+        B.spmm(prec, A.m, A.n, d["rp"], d["ci"], d["v32"], lo, d["v64"], Xd, b, Yd, b, b)
+        Y = to_host(prec, Yd, A.m, b)
+        Aabs = A.to_scipy().copy()
+        Aabs.data = np.abs(Aabs.data)
+        norm = np.abs(Aabs @ np.abs(Xs)).max()
+        ref = oracle.spmm(A, Xs)
+        err = np.abs(Y - ref).max() / norm
+        assert err <= TOL[prec], (A.name, err)
+
+
+@pytest.mark.parametrize("prec", [B.PREC_DF64, B.PREC_F64])
+def test_spmm_transpose_and_ld(prec):
+    A = wl.random_illconditioned(2000, 700, 16, seed=9)
+    d = csr_device(A)
+    # explicit transpose on the device, then A^T Y with strided blocks (ld > b)
+    At = A.to_scipy().T.tocsr()
+    At.sort_indices()
+    AT = wl.CSR(A.n, A.m, At.indptr.astype(np.int32), At.indices.astype(np.int32), At.data, "AT")
+    dt = csr_device(AT)
+    b, ld = 4, 7
+    Yh = wl.dense_block(A.m, ld, seed=5)
+    Yd = to_device(prec, Yh)
+    Ys = to_host(prec, Yd, A.m, ld)[:, :b]
+    Xd = to_device(prec, np.zeros((A.n, ld)))
+    B.spmm(prec, A.n, A.m, dt["rp"], dt["ci"], dt["v32"], None if dt["exact"] else dt["v32lo"], dt["v64"],
+           Yd, ld, Xd, ld, b)
+    X = to_host(prec, Xd, A.n, ld)
+    ref = oracle.spmm_t(A, Ys)
+    Aabs = abs(At)
+    norm = np.abs(Aabs @ np.abs(Ys)).max()
+    assert np.abs(X[:, :b] - ref).max() / norm <= TOL[prec]
+    assert np.all(X[:, b:] == 0)  # columns beyond b untouched
+
+
+def test_csr_transpose_bit_exact_and_deterministic():
+    for A in _matrices() + [wl.random_illconditioned(500, 20, 16, seed=1)]:  # long columns use heapsort path
+        d = csr_device(A)
+        dev = d["rp"].device
+        rpT = torch.zeros(A.n + 1, dtype=torch.int32, device=dev)
+        ciT = torch.zeros(max(A.nnz, 1), dtype=torch.int32, device=dev)
+        vaT = torch.zeros(max(A.nnz, 1), dtype=torch.float64, device=dev)
+        work = torch.zeros(B.csr_transpose_work_bytes(A.n), dtype=torch.uint8, device=dev)
+        B.csr_transpose(A.m, A.n, d["rp"], d["ci"], d["va"], rpT, ciT, vaT, work)
+        torch.cuda.synchronize()
+        S = A.to_scipy()
+        # definition: entry (i, j) of A becomes (j, i); rows of A^T sorted by i
+        rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
+        order = np.lexsort((rows, A.colidx))
+        ref_ci = rows[order]
+        ref_va = A.vals[order]
+        ref_rp = np.concatenate([[0], np.cumsum(np.bincount(A.colidx, minlength=A.n))])
+        assert np.array_equal(rpT.cpu().numpy(), ref_rp)
+        assert np.array_equal(ciT.cpu().numpy()[:A.nnz], ref_ci)
+        assert np.array_equal(vaT.cpu().numpy()[:A.nnz], ref_va)
+        ci1 = ciT.clone()
+        B.csr_transpose(A.m, A.n, d["rp"], d["ci"], d["va"], rpT, ciT, vaT, work)
+        torch.cuda.synchronize()
+        assert torch.equal(ci1, ciT)
+        assert S.shape == (A.m, A.n)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("p,q,r0,r1", [(35, 4, 0, 100003), (9, 1, 17, 5000), (3, 8, 0, 1), (40, 13, 5, 77777),
+                                       (256, 2, 0, 3000)])
+def test_gram_matches_fp64(prec, p, q, r0, r1):
+    L = max(r1, 10)
+    P = wl.dense_block(L, p, seed=1)
+    Q = wl.dense_block(L, q, seed=2)
+    Pd, Qd = to_device(prec, P, ld=p + 3), to_device(prec, Q)
+    Ps, Qs = to_host(prec, Pd, L, p + 3)[:, :p], to_host(prec, Qd, L, q)
+    G = torch.zeros(p * q, dtype=torch.float64, device="cuda:0")
+    scratch = torch.zeros(B.gram_scratch_bytes(p, q), dtype=torch.uint8, device="cuda:0")
+    B.gram(prec, r0, r1, Pd, p + 3, p, Qd, q, q, G, scratch)
+    Gh = G.cpu().numpy().reshape(p, q)
+    ref = Ps[r0:r1].T @ Qs[r0:r1]
+    norm = np.abs(Ps[r0:r1]).T @ np.abs(Qs[r0:r1])
+    # FP64-class accumulation in every mode
+    assert np.all(np.abs(Gh - ref) <= 1e-13 * norm + 1e-300)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_combine_and_inplace_restart(prec):
+    L, p, q = 20011, 21, 4
+    P = wl.dense_block(L, p, seed=3)
+    In = wl.dense_block(L, q, seed=4)
+    Cm = wl.dense_block(p, q, seed=5)
+    R = np.triu(wl.dense_block(q, q, seed=6)) + 3 * np.eye(q)
+    Ri = np.linalg.inv(R)
+    Pd, Ind = to_device(prec, P), to_device(prec, In)
+    Ps, Ins = to_host(prec, Pd, L, p), to_host(prec, Ind, L, q)
+    Cs = B.coef_convert(prec, Cm)
+    Cd, Rd = coef_device(prec, Cm), coef_device(prec, Ri)
+    Out = to_device(prec, np.zeros((L, q)))
+    B.combine(prec, L, Pd, p, p, Cd, Ind, q, 1, Out, q, q, Rd)
+    got = to_host(prec, Out, L, q)
+    ref = (Ins + Ps @ Cm) @ Ri
+    scale = (np.abs(Ins) + np.abs(Ps) @ np.abs(Cm)) @ np.abs(Ri)
+    assert np.all(np.abs(got - ref) <= 4 * TOL[prec] * scale)
+    # in place: V <- V Z (q <= p) writes the first q columns of P's own buffer
+    Z = np.linalg.qr(wl.dense_block(p, 7, seed=7))[0]
+    Zd = coef_device(prec, Z)
+    B.combine(prec, L, Pd, p, p, Zd, None, 0, 0, Pd, p, 7)
+    got = to_host(prec, Pd, L, p)
+    ref = Ps @ Z
+    assert np.abs(got[:, :7] - ref).max() <= 4 * TOL[prec] * (np.abs(Ps) @ np.abs(Z)).max()
+    assert np.array_equal(got[:, 7:], Ps[:, 7:])
+    del Cs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8)])
+def test_ritz_residual(prec, g, nb):
+    L = 50001
+    V = wl.dense_block(L, g, seed=8)
+    W = wl.dense_block(L, g, seed=9)
+    Y = wl.dense_block(g, nb, seed=10)
+    th = wl.dense_block(nb, 1, seed=11).ravel()
+    Vd, Wd = to_device(prec, V), to_device(prec, W)
+    Vs, Ws = to_host(prec, Vd, L, g), to_host(prec, Wd, L, g)
+    Yd, Td = coef_device(prec, Y), coef_device(prec, th)
+    Xd, Rd = to_device(prec, np.zeros((L, nb))), to_device(prec, np.zeros((L, nb)))
+    n2 = torch.zeros(nb, dtype=torch.float64, device="cuda:0")
+    scratch = torch.zeros(B.ritz_scratch_bytes(nb), dtype=torch.uint8, device="cuda:0")
+    B.ritz_residual(prec, L, Vd, Wd, g, g, Yd, Td, Xd, Rd, nb, nb, n2, scratch)
+    X, R = to_host(prec, Xd, L, nb), to_host(prec, Rd, L, nb)
+    Xr = Vs @ Y
+    Rr = Ws @ Y - Xr * th
+    sx = np.abs(Vs) @ np.abs(Y)
+    assert np.all(np.abs(X - Xr) <= 4 * TOL[prec] * sx)
+    assert np.all(np.abs(R - Rr) <= 4 * TOL[prec] * (np.abs(Ws) @ np.abs(Y) + sx * np.abs(th)))
+    nr = np.sum(R * R, axis=0)
+    np.testing.assert_allclose(n2.cpu().numpy(), nr, rtol=1e-12)

@@ -1,0 +1,191 @@
+"""End-to-end parity: triplets from the CUDA path (through the C-ABI) against
+the oracle, closed forms and certificates recomputed on the host in FP64.
+
+Bars (from the method's accuracy statement): relative singular-value error
+<= 1e-10, triplet residual of Eq. (res) <= tol ||A|| recomputed in FP64 from
+the returned vectors, sin(angle) to the exact singular subspace <= 1e-8 for
+values separated by more than 1e-2 ||A||, else <= ||r|| / gap.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_01404_gb300 import binding as B
+from paper_1607_01404_gb300 import build as BLD
+from paper_1607_01404_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    BLD.build()
+    B.lib()
+
+
+def _grid_sigma(N, dims):
+    t = 4.0 * np.sin(np.arange(1, N + 1) * np.pi / (2 * (N + 1))) ** 2
+    s = t[:, None] + t[None, :] if dims == 2 else t[:, None, None] + t[None, :, None] + t[None, None, :]
+    return np.sort(np.sqrt(s.ravel()))
+
+
+def _sin_angle(x, basis):
+    x = x / np.linalg.norm(x)
+    return np.linalg.norm(x - basis @ (basis.T @ x))
+
+
+def _check_certificate(A, r, tol, normA, k):
+    assert r["nconv"] == k, r
+    res = oracle.triplet_residuals(A, r["sigma"], r["U"], r["V"])
+    assert res.max() <= tol * normA * 1.0000001, res / normA
+    # the library evaluates Eq. (res) in double-float (unit 2^-48): agreement up to
+    # a few units of 2^-48 ||A|| absolute
+    np.testing.assert_allclose(r["rnorm"], res, rtol=1e-3, atol=16 * 2.0 ** -48 * normA)
+    assert np.abs(r["V"].T @ r["V"] - np.eye(k)).max() < 1e-8
+    assert np.abs(r["U"].T @ r["U"] - np.eye(k)).max() < 1e-8
+
+
+def _compare_to_dense(A, r, target, k, tol):
+    D = A.to_scipy().toarray()
+    U, s, Vt = np.linalg.svd(D, full_matrices=False)
+    idx = np.arange(k) if target == "largest" else np.arange(len(s) - 1, len(s) - 1 - k, -1)
+    np.testing.assert_allclose(r["sigma"], s[idx], rtol=1e-10)
+    _check_certificate(A, r, tol, s[0], k)
+    for j, i in enumerate(idx):
+        gap = min(abs(s[i] - s[i2]) for i2 in range(len(s)) if i2 != i)
+        bound = 2 * tol * s[0] / gap + 1e-12
+        if gap > 1e-2 * s[0]:
+            bound = min(bound, 1e-8)
+        assert _sin_angle(r["V"][:, j], Vt[i][:, None]) <= bound
+        assert _sin_angle(r["U"][:, j], U[:, i][:, None]) <= bound
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_grid2d_closed_form_and_oracle(target):
+    A = wl.grid_difference(32, 2)
+    s = _grid_sigma(32, 2)
+    ex = s[:5] if target == "smallest" else s[::-1][:5]
+    r = B.svds(A, 5, target, 1e-10, maxBlockSize=1, initV=wl.start_block(A.n, 1, 0), maxMatvecs=200000)
+    o = oracle.phsvds(A, 5, target, 1e-10, b=1, V0=wl.start_block(A.n, 1, 0))
+    np.testing.assert_allclose(r["sigma"], ex, rtol=1e-10)
+    np.testing.assert_allclose(r["sigma"], o["sigma"], rtol=1e-10)
+    _check_certificate(A, r, 1e-10, s[-1], 5)
+    assert abs(r["stats"]["aNorm"] - s[-1]) < 1e-4 * s[-1]
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_random_vs_dense_and_oracle(target, b):
+    A = wl.random_illconditioned(1500, 500, 16, seed=11)
+    k = 4
+    r = B.svds(A, k, target, 1e-10, maxBlockSize=b, initV=wl.start_block(A.n, b, 1), maxMatvecs=400000)
+    _compare_to_dense(A, r, target, k, 1e-10)
+    o = oracle.phsvds(A, k, target, 1e-10, b=b, V0=wl.start_block(A.n, b, 1))
+    np.testing.assert_allclose(r["sigma"], o["sigma"], rtol=1e-10)
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_stage2_tight_tolerance(target):
+    """tol 1e-13: the FP64-class stage-1 floor exceeds the smallest values' bound,
+    so stage 2 on B (refined extraction for the smallest) must finish the job."""
+    A = wl.random_illconditioned(900, 300, 16, seed=13)
+    r = B.svds(A, 3, target, 1e-13, maxBlockSize=2, initV=wl.start_block(A.n, 2, 2), maxMatvecs=600000)
+    _compare_to_dense(A, r, target, 3, 1e-13)
+    if target == "smallest":
+        assert r["stats"]["stage2_used"] == 1
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+@pytest.mark.parametrize("polish", [1, 0])
+def test_mixed_precision_stage1(target, polish):
+    A = wl.grid_difference(24, 2)
+    s = _grid_sigma(24, 2)
+    ex = s[:4] if target == "smallest" else s[::-1][:4]
+    r = B.svds(A, 4, target, 1e-10, maxBlockSize=2, stage1_precision=B.SVDS_FP32, stage1_polish=polish,
+               initV=wl.start_block(A.n, 2, 3), maxMatvecs=400000)
+    np.testing.assert_allclose(r["sigma"], ex, rtol=1e-10)
+    _check_certificate(A, r, 1e-10, s[-1], 4)
+    assert r["stats"]["matvecs_stage1_lowprec"] > 0
+    if not polish:
+        assert r["stats"]["stage2_used"] == 1
+
+
+def test_native_fp64_mode():
+    A = wl.random_illconditioned(1200, 400, 16, seed=17)
+    r = B.svds(A, 3, "smallest", 1e-10, maxBlockSize=2, stage1_precision=B.SVDS_NATIVE_FP64, maxMatvecs=400000)
+    _compare_to_dense(A, r, "smallest", 3, 1e-10)
+
+
+def test_wide_matrix():
+    A = wl.random_illconditioned(700, 250, 16, seed=19)
+    At = A.to_scipy().T.tocsr()
+    At.sort_indices()
+    W = wl.CSR(At.shape[0], At.shape[1], At.indptr.astype(np.int32), At.indices.astype(np.int32), At.data, "wide")
+    r = B.svds(W, 3, "largest", 1e-10, maxBlockSize=1, maxMatvecs=200000)
+    assert r["U"].shape == (250, 3) and r["V"].shape == (700, 3)
+    _compare_to_dense(W, r, "largest", 3, 1e-10)
+
+
+def test_grid3d_closed_form_block4():
+    A = wl.grid_difference(10, 3)
+    s = _grid_sigma(10, 3)
+    r = B.svds(A, 4, "smallest", 1e-10, maxBlockSize=4, maxMatvecs=400000)
+    np.testing.assert_allclose(r["sigma"], s[:4], rtol=1e-10)
+    _check_certificate(A, r, 1e-10, s[-1], 4)
+
+
+def test_weighted_grid_vs_oracle_and_jacobi_none():
+    A = wl.weighted_grid(20, 2, seed=10000)
+    s = np.linalg.svd(A.to_scipy().toarray(), compute_uv=False)
+    rj = B.svds(A, 4, "smallest", 1e-10, maxBlockSize=2, precond=B.SVDS_PRECOND_JACOBI, maxMatvecs=600000)
+    rn = B.svds(A, 4, "smallest", 1e-10, maxBlockSize=2, precond=B.SVDS_PRECOND_NONE, maxMatvecs=600000)
+    for r in (rj, rn):
+        np.testing.assert_allclose(r["sigma"], s[::-1][:4], rtol=1e-10)
+        _check_certificate(A, r, 1e-10, s[0], 4)
+
+
+def test_odd_block_k1_and_sign_convention():
+    A = wl.random_illconditioned(800, 300, 16, seed=23)
+    r = B.svds(A, 1, "largest", 1e-10, maxBlockSize=3, maxMatvecs=200000)
+    _compare_to_dense(A, r, "largest", 1, 1e-10)
+    v = r["V"][:, 0]
+    assert v[np.argmax(np.abs(v))] > 0
+
+
+def test_budget_exhausted_returns_maxit():
+    A = wl.grid_difference(32, 2)
+    r = B.svds(A, 5, "smallest", 1e-10, maxBlockSize=1, maxMatvecs=50)
+    assert r["rc"] == B.SVDS_ERR_MAXIT
+    assert r["nconv"] == 0
+
+
+def test_device_csr_input_and_repeat_solves():
+    A = wl.random_illconditioned(1000, 400, 16, seed=29)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colidx).to(dev)
+    va = torch.from_numpy(A.vals).to(dev)
+    h = B.svds_create(rp, ci, va, A.m, A.n, B.make_opts(maxBlockSize=2, maxMatvecs=300000), on_device=True)
+    try:
+        s1 = B.svds_solve(h, 3, B.SVDS_LARGEST, 1e-10)
+        s2 = B.svds_solve(h, 3, B.SVDS_LARGEST, 1e-10)
+    finally:
+        h.close()
+    np.testing.assert_array_equal(s1[0], s2[0])  # deterministic
+    D = A.to_scipy().toarray()
+    np.testing.assert_allclose(s1[0], np.linalg.svd(D, compute_uv=False)[:3], rtol=1e-10)
+
+
+def test_device_csr_validation():
+    dev = torch.device("cuda:0")
+    rp = torch.tensor([0, 2, 3], dtype=torch.int32, device=dev)
+    ci = torch.tensor([1, 0, 1], dtype=torch.int32, device=dev)  # unsorted row 0
+    va = torch.tensor([1.0, 2.0, 3.0], dtype=torch.float64, device=dev)
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 2, 2, on_device=True)
+    assert e.value.code == B.SVDS_ERR_CSR
