@@ -1081,6 +1081,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c2.name = "stage2";
       RunBufs& Bs = B2;
       const double thr1 = std::sqrt(2.0) * normA * tol;
+      // second level: Eq. (res) with a margin of the evaluation's own rounding
+      // noise (a few units of the mode's roundoff times ||A||), so that a pair
+      // accepted here also passes the final recomputation
+      const double thr2 = normA * std::max(tol - 4.0 * unit_roundoff(p2), 0.5 * tol);
       // Eq. B_secondCriterion then Eq. (res) on the normalised halves
       c2.conv = [&](const double* th, const double* rn, int o0, int nc, char* ok) {
         bool any = false;
@@ -1111,7 +1115,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
         c.launches += 2;
         CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.st));
         c.sync();
-        for (int j = 0; j < nc; ++j) ok[j] = ok[j] && std::sqrt(std::max(c.hG[j], 0.0)) < normA * tol;
+        for (int j = 0; j < nc; ++j) ok[j] = ok[j] && std::sqrt(std::max(c.hG[j], 0.0)) < thr2;
       };
       void* XB = nullptr;
       if (smallest) {

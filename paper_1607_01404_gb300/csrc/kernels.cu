@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tiled.h"
 
 namespace phsvds {
 
@@ -731,10 +732,22 @@ cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* Pp, in
   if (r1 <= r0) {  // empty row range: one block of zeros
     r1 = r0;
   }
+  {
+    SegV all[4];
+    for (int s = 0; s < nseg; ++s) all[s] = Pp[s];
+    all[nseg] = Q;
+    TileDesc T;
+    if (make_tiles(all, nseg + 1, elem_bytes(prec), false, &T))
+      return tiled_gram(prec, T, r0, r1, p, Q.nc, partial, max_blocks, nblocks, st);
+  }
   PHSVDS_DISPATCH(prec, gram_p<P>(r0, r1, sa, p, Q, partial, max_blocks, nblocks, st))
 }
 
 cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st) {
+  return tiled_reduce(prec, partial, nblocks, pq, G, st);
+}
+
+cudaError_t launch_gram_reduce_serial(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st) {
   const int grid = grid_for(pq, kThreads);
   switch (prec) {
     case kF32:
@@ -779,6 +792,13 @@ cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, cons
   int p;
   SegArr sa = make_segs(Pp, nseg, &p);
   if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
+  {
+    TileDesc T;
+    if (make_tiles(Pp, nseg, elem_bytes(prec), true, &T)) {
+      cudaError_t e = tiled_combine(prec, T, L, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2, st);
+      if (e != cudaErrorInvalidValue) return e;
+    }
+  }
   PHSVDS_DISPATCH(prec, combine_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2, st))
 }
 
@@ -813,6 +833,14 @@ cudaError_t launch_ritz_residual(int prec, long long L, SegV V, SegV W, int g, c
                                  void* X, void* R, long long ldb, int nb, const void* dscale, void* T,
                                  void* norm_partial, int max_blocks, int* nblocks, cudaStream_t st) {
   if (g < 1 || nb < 1) return cudaErrorInvalidValue;
+  {
+    SegV vw[2] = {SegV{V.p, V.ld, g}, SegV{W.p, W.ld, g}};
+    TileDesc TD;
+    if (nb <= 16 && make_tiles(vw, 2, elem_bytes(prec), true, &TD)) {
+      cudaError_t e = tiled_ritz(prec, TD, L, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial, max_blocks, nblocks, st);
+      if (e != cudaErrorInvalidValue) return e;
+    }
+  }
   PHSVDS_DISPATCH(prec, ritz_p<P>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial, max_blocks, nblocks, st))
 }
 

@@ -109,18 +109,28 @@ def test_csr_transpose_bit_exact_and_deterministic():
         assert S.shape == (A.m, A.n)
 
 
+def _ld(p, aligned):
+    """Leading dimension: a multiple of 4 elements takes the tiled (cp.async) path,
+    p + 3 (odd row stride) the generic path."""
+    return ((p + 3) // 4) * 4 if aligned else p + 3
+
+
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("p,q,r0,r1", [(35, 4, 0, 100003), (9, 1, 17, 5000), (3, 8, 0, 1), (40, 13, 5, 77777),
-                                       (256, 2, 0, 3000)])
-def test_gram_matches_fp64(prec, p, q, r0, r1):
+                                       (256, 2, 0, 3000), (7, 3, 64, 64)])
+def test_gram_matches_fp64(prec, aligned, p, q, r0, r1):
     L = max(r1, 10)
     P = wl.dense_block(L, p, seed=1)
-    Q = wl.dense_block(L, q, seed=2)
-    Pd, Qd = to_device(prec, P, ld=p + 3), to_device(prec, Q)
-    Ps, Qs = to_host(prec, Pd, L, p + 3)[:, :p], to_host(prec, Qd, L, q)
+    Q = wl.dense_block(L, q + 1, seed=2)
+    ldp, ldq = _ld(p, aligned), _ld(q + 1, aligned)
+    Pd, Qd = to_device(prec, P, ld=ldp), to_device(prec, Q, ld=ldq)
+    Ps, Qs = to_host(prec, Pd, L, ldp)[:, :p], to_host(prec, Qd, L, ldq)[:, 1:q + 1]
     G = torch.zeros(p * q, dtype=torch.float64, device="cuda:0")
     scratch = torch.zeros(B.gram_scratch_bytes(p, q), dtype=torch.uint8, device="cuda:0")
-    B.gram(prec, r0, r1, Pd, p + 3, p, Qd, q, q, G, scratch)
+    esz = 1 if prec == B.PREC_F32 or prec == B.PREC_F64 else 2
+    # Q starts at column 1: a window that is not 16-byte aligned inside its row
+    B.gram(prec, r0, r1, Pd, ldp, p, Qd[esz:], ldq, q, G, scratch)
     Gh = G.cpu().numpy().reshape(p, q)
     ref = Ps[r0:r1].T @ Qs[r0:r1]
     norm = np.abs(Ps[r0:r1]).T @ np.abs(Qs[r0:r1])
@@ -129,49 +139,58 @@ def test_gram_matches_fp64(prec, p, q, r0, r1):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_combine_and_inplace_restart(prec):
-    L, p, q = 20011, 21, 4
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("p,q", [(21, 4), (35, 1), (6, 8), (44, 30)])
+def test_combine_and_inplace_restart(prec, aligned, p, q):
+    L = 20011
+    ldp, ldq = _ld(p, aligned), _ld(q, aligned)
     P = wl.dense_block(L, p, seed=3)
     In = wl.dense_block(L, q, seed=4)
     Cm = wl.dense_block(p, q, seed=5)
     R = np.triu(wl.dense_block(q, q, seed=6)) + 3 * np.eye(q)
     Ri = np.linalg.inv(R)
-    Pd, Ind = to_device(prec, P), to_device(prec, In)
-    Ps, Ins = to_host(prec, Pd, L, p), to_host(prec, Ind, L, q)
-    Cs = B.coef_convert(prec, Cm)
+    Pd, Ind = to_device(prec, P, ld=ldp), to_device(prec, In, ld=ldq)
+    Ps, Ins = to_host(prec, Pd, L, ldp)[:, :p], to_host(prec, Ind, L, ldq)[:, :q]
     Cd, Rd = coef_device(prec, Cm), coef_device(prec, Ri)
-    Out = to_device(prec, np.zeros((L, q)))
-    B.combine(prec, L, Pd, p, p, Cd, Ind, q, 1, Out, q, q, Rd)
-    got = to_host(prec, Out, L, q)
+    Out = to_device(prec, np.zeros((L, ldq)))
+    B.combine(prec, L, Pd, ldp, p, Cd, Ind, ldq, 1, Out, ldq, q, Rd)
+    got = to_host(prec, Out, L, ldq)[:, :q]
     ref = (Ins + Ps @ Cm) @ Ri
     scale = (np.abs(Ins) + np.abs(Ps) @ np.abs(Cm)) @ np.abs(Ri)
     assert np.all(np.abs(got - ref) <= 4 * TOL[prec] * scale)
-    # in place: V <- V Z (q <= p) writes the first q columns of P's own buffer
-    Z = np.linalg.qr(wl.dense_block(p, 7, seed=7))[0]
+    # without R^-1 and without In
+    Out2 = to_device(prec, np.zeros((L, ldq)))
+    B.combine(prec, L, Pd, ldp, p, Cd, None, 0, 0, Out2, ldq, q)
+    got = to_host(prec, Out2, L, ldq)[:, :q]
+    assert np.all(np.abs(got - Ps @ Cm) <= 4 * TOL[prec] * (np.abs(Ps) @ np.abs(Cm)))
+    # in place: V <- V Z (columns <= p) writes the first columns of P's own buffer
+    nz = min(p, 7)
+    Z = np.linalg.qr(wl.dense_block(p, nz, seed=7))[0]
     Zd = coef_device(prec, Z)
-    B.combine(prec, L, Pd, p, p, Zd, None, 0, 0, Pd, p, 7)
-    got = to_host(prec, Pd, L, p)
+    B.combine(prec, L, Pd, ldp, p, Zd, None, 0, 0, Pd, ldp, nz)
+    got = to_host(prec, Pd, L, ldp)[:, :p]
     ref = Ps @ Z
-    assert np.abs(got[:, :7] - ref).max() <= 4 * TOL[prec] * (np.abs(Ps) @ np.abs(Z)).max()
-    assert np.array_equal(got[:, 7:], Ps[:, 7:])
-    del Cs
+    assert np.abs(got[:, :nz] - ref).max() <= 4 * TOL[prec] * (np.abs(Ps) @ np.abs(Z)).max()
+    assert np.array_equal(got[:, nz:], Ps[:, nz:])
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8)])
-def test_ritz_residual(prec, g, nb):
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8), (20, 13)])
+def test_ritz_residual(prec, aligned, g, nb):
     L = 50001
+    ldv = _ld(g, aligned)
     V = wl.dense_block(L, g, seed=8)
     W = wl.dense_block(L, g, seed=9)
     Y = wl.dense_block(g, nb, seed=10)
     th = wl.dense_block(nb, 1, seed=11).ravel()
-    Vd, Wd = to_device(prec, V), to_device(prec, W)
-    Vs, Ws = to_host(prec, Vd, L, g), to_host(prec, Wd, L, g)
+    Vd, Wd = to_device(prec, V, ld=ldv), to_device(prec, W, ld=ldv)
+    Vs, Ws = to_host(prec, Vd, L, ldv)[:, :g], to_host(prec, Wd, L, ldv)[:, :g]
     Yd, Td = coef_device(prec, Y), coef_device(prec, th)
     Xd, Rd = to_device(prec, np.zeros((L, nb))), to_device(prec, np.zeros((L, nb)))
     n2 = torch.zeros(nb, dtype=torch.float64, device="cuda:0")
     scratch = torch.zeros(B.ritz_scratch_bytes(nb), dtype=torch.uint8, device="cuda:0")
-    B.ritz_residual(prec, L, Vd, Wd, g, g, Yd, Td, Xd, Rd, nb, nb, n2, scratch)
+    B.ritz_residual(prec, L, Vd, Wd, ldv, g, Yd, Td, Xd, Rd, nb, nb, n2, scratch)
     X, R = to_host(prec, Xd, L, nb), to_host(prec, Rd, L, nb)
     Xr = Vs @ Y
     Rr = Ws @ Y - Xr * th
