@@ -95,6 +95,9 @@ typedef struct {
   double seconds_setup;       /* device setup inside svds_solve (norm estimate, buffers) */
   double seconds_stage1, seconds_stage2, seconds_total;
   int64_t kernel_launches;    /* device kernels launched by this call */
+  double seconds_host_eig;    /* host time in the projected eigenproblems */
+  double seconds_sync_wait;   /* host time blocked on the device (small results coming back) */
+  int64_t host_syncs;         /* device-to-host round trips */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

@@ -57,7 +57,8 @@ class svds_stats(C.Structure):
                 ("outer_stage2", C.c_int64), ("restarts", C.c_int64), ("resets", C.c_int64),
                 ("stage2_used", C.c_int), ("aNorm", C.c_double), ("seconds_setup", C.c_double),
                 ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
-                ("seconds_total", C.c_double), ("kernel_launches", C.c_int64)]
+                ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
+                ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

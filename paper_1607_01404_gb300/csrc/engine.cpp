@@ -75,9 +75,21 @@ struct Ctx {
   int print = 0;
   unsigned long long seed = 0, seed_ctr = 0;
   long long restarts = 0, resets = 0;
+  // device-side orthogonalisation scratch
+  double* dGo = nullptr;   // Gram results of the device CGS2 + CholQR2
+  double* dwork = nullptr;
+  void* dco[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* dstatus = nullptr;  // breakdown flags raised by the device steps
+  int* hstatus = nullptr;  // pinned copy
+  bool device_ortho = true;
 
+  double t_sync = 0, t_eig = 0;
+  long long nsync = 0;
   void sync() {
+    const auto a = Clock::now();
     CK(cudaStreamSynchronize(st));
+    t_sync += std::chrono::duration<double>(Clock::now() - a).count();
+    ++nsync;
     ++epoch;
   }
   double elapsed() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -139,6 +151,17 @@ std::vector<double> gram(Ctx& c, int prec, long long r0, long long r1, const std
       for (int j = 0; j < qc; ++j) out[(size_t)i * q + c0 + j] = c.hG[(size_t)p * c0 + (size_t)i * qc + j];
   }
   return out;
+}
+
+// Gram into device memory (no host round trip): dst = [P...]^T Q, p x q row-major, q <= 8.
+void gram_dev(Ctx& c, int prec, long long r0, long long r1, const std::vector<SegV>& P, SegV Q, double* dst) {
+  int p = 0;
+  for (auto& sgm : P) p += sgm.nc;
+  if (p > 256 || p < 1 || Q.nc < 1 || Q.nc > 8) throw NumFail{"device gram shape out of range"};
+  int nb = 0;
+  CK(launch_gram(prec, r0, r1, P.data(), (int)P.size(), Q, c.partial, c.maxblk, &nb, c.st));
+  CK(launch_gram_reduce(prec, c.partial, nb, p * Q.nc, dst, c.st));
+  c.launches += 2;
 }
 
 void combine(Ctx& c, int prec, long long L, const std::vector<SegV>& P, const std::vector<double>& coef_rm,
@@ -279,6 +302,39 @@ OrthoRes ortho(Ctx& c, int prec, long long L, const std::vector<SegV>& basis, vo
   return res;
 }
 
+// Device-side CGS2 + CholQR2 of T (L x nb, nb <= 8) against one orthonormal
+// basis segment: the same passes as ortho(), with the small dense steps
+// (negated coefficients, Cholesky factors and their inverses) computed by a
+// one-CTA kernel, so no host round trip is needed.  A breakdown (a column that
+// lost almost all of its norm, or a Gram that is not positive definite) sets
+// c.dstatus; the caller checks it at its next synchronisation and redoes the
+// step with ortho().  The result is written to T and to Out2.
+void ortho_dev(Ctx& c, int prec, long long L, SegV basis, void* T, long long ldt, int nb, void* Out2, long long ldo2) {
+  const int g = basis.nc;
+  SegV Ts{T, ldt, nb};
+  const std::vector<SegV> PT = {basis, Ts};
+  gram_dev(c, prec, 0, L, PT, Ts, c.dGo);
+  CK(launch_ortho_small(1, prec, g, nb, c.dGo, c.dwork, c.dco[0], nullptr, c.dstatus, 0.0, c.st));
+  CK(launch_combine(prec, L, &basis, 1, c.dco[0], T, ldt, 1, T, ldt, nb, nullptr, nullptr, 0, c.st));
+  gram_dev(c, prec, 0, L, PT, Ts, c.dGo);
+  CK(launch_ortho_small(2, prec, g, nb, c.dGo, c.dwork, c.dco[1], c.dco[2], c.dstatus, 1e-20, c.st));
+  CK(launch_combine(prec, L, &basis, 1, c.dco[1], T, ldt, 1, T, ldt, nb, c.dco[2], nullptr, 0, c.st));
+  gram_dev(c, prec, 0, L, {Ts}, Ts, c.dGo);
+  CK(launch_ortho_small(3, prec, 0, nb, c.dGo, c.dwork, c.dco[3], nullptr, c.dstatus, 0.0, c.st));
+  CK(launch_combine(prec, L, &Ts, 1, c.dco[3], nullptr, 0, 0, T, ldt, nb, nullptr, Out2, ldo2, c.st));
+  c.launches += 6;
+}
+
+// Copy the device status word to the host with the next synchronisation and
+// clear it; returns the flags.
+int take_status(Ctx& c) {
+  CK(cudaMemcpyAsync(c.hstatus, c.dstatus, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  const int v = *c.hstatus;
+  if (v) CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), c.st));
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Buffers of one eigensolver run
 // ---------------------------------------------------------------------------
@@ -326,17 +382,28 @@ void put_block_rm(std::vector<double>& dst, int g, const double* Ycm, int ldy, c
     for (int j = 0; j < q; ++j) dst[(size_t)i * q + j] = Ycm[(size_t)cols[j] * ldy + i];
 }
 
+// Ritz vectors / residuals / norms for the coefficient block Ysel (g x nt,
+// row-major) into columns [o, o + nt) of Xb and Rb.
+std::vector<double> ritz_block(Ctx& c, RunBufs& B, int g, const std::vector<double>& Ysel,
+                               const std::vector<double>& th, int o, const void* dscale = nullptr);
+
 // Ritz vectors / residuals / norms for the coefficient columns `cols` of Y
 // (column-major g x g) into columns [o, o + |cols|) of Xb and Rb.
 std::vector<double> ritz_cols(Ctx& c, RunBufs& B, int g, const std::vector<double>& Ycm,
                               const std::vector<double>& theta, const std::vector<int>& cols, int o,
                               const void* dscale = nullptr) {
-  const int prec = B.prec;
   const int nt = (int)cols.size();
   std::vector<double> Ysel;
   put_block_rm(Ysel, g, Ycm.data(), g, cols);
   std::vector<double> th(nt);
   for (int j = 0; j < nt; ++j) th[j] = theta[cols[j]];
+  return ritz_block(c, B, g, Ysel, th, o, dscale);
+}
+
+std::vector<double> ritz_block(Ctx& c, RunBufs& B, int g, const std::vector<double>& Ysel,
+                               const std::vector<double>& th, int o, const void* dscale) {
+  const int prec = B.prec;
+  const int nt = (int)th.size();
   const void* dY = c.upload(prec, Ysel.data(), Ysel.size());
   const void* dT = c.upload(prec, th.data(), th.size());
   int nbl = 0;
@@ -429,7 +496,11 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
     ++out.outer;
     w.assign(g, 0.0);
     Z.assign((size_t)g * g, 0.0);
-    if (!hla::sym_eig(g, H.data(), w.data(), Z.data())) throw NumFail{"projected eigenproblem did not converge"};
+    {
+      const auto a = Clock::now();
+      if (!hla::sym_eig(g, H.data(), w.data(), Z.data())) throw NumFail{"projected eigenproblem did not converge"};
+      c.t_eig += std::chrono::duration<double>(Clock::now() - a).count();
+    }
     std::vector<double> theta(g), Y((size_t)g * g);
     for (int j = 0; j < g; ++j) {
       const int src = cfg.smallest ? j : g - 1 - j;
@@ -559,9 +630,32 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       ++rsr;
       c.restarts += 1;
     }
-    ortho(c, prec, B.L, {SegV{B.V, B.ldv, g}}, T, b, nbk, off(B.V, g, prec), B.ldv);
-    apply_op(c, prec, cfg.op, T, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
-    std::vector<double> Hext = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk});
+    std::vector<double> Hext;
+    if (c.device_ortho && nbk <= 8 && g + nbk <= 256) {
+      ortho_dev(c, prec, B.L, SegV{B.V, B.ldv, g}, T, b, nbk, off(B.V, g, prec), B.ldv);
+      apply_op(c, prec, cfg.op, T, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
+      gram_dev(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk}, c.dG);
+      CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * (g + nbk) * nbk, cudaMemcpyDeviceToHost, c.st));
+      if (take_status(c) == 0) {
+        Hext.assign(c.hG, c.hG + (size_t)(g + nbk) * nbk);
+      } else {
+        // breakdown in the device orthogonalisation: rebuild the block and
+        // redo the step with the host-driven path (random replacements)
+        std::vector<double> Yb = rowmajor(g, nbk, Ycur.data(), g), thb(nbk);
+        for (int j = 0; j < nbk; ++j) thb[j] = theta[block[j]];
+        ritz_block(c, B, g, Yb, thb, 0);
+        T = B.Rb;
+        if (cfg.dscale) {
+          CK(launch_scale_rows(prec, B.L, cfg.dscale, B.Rb, b, B.Tb, b, nbk, c.st));
+          T = B.Tb;
+        }
+      }
+    }
+    if (Hext.empty()) {
+      ortho(c, prec, B.L, {SegV{B.V, B.ldv, g}}, T, b, nbk, off(B.V, g, prec), B.ldv);
+      apply_op(c, prec, cfg.op, T, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
+      Hext = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk});
+    }
     extend_H(H, g, nbk, Hext);
     // previous-iteration coefficients padded with zeros for the new columns
     nprev = nbk;
@@ -840,6 +934,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c.gcap = 256 * 256;
     reqs.push_back({&c.partial, gram_partial_bytes(std::max(c.maxblk, 152 * 16), 256, 8)});
     reqs.push_back({(void**)&c.dG, c.gcap * 8});
+    reqs.push_back({(void**)&c.dGo, sizeof(double) * 264 * 8});
+    reqs.push_back({(void**)&c.dwork, sizeof(double) * 128});
+    for (int i = 0; i < 4; ++i) reqs.push_back({&c.dco[i], sizeof(double) * 264 * 8});
+    reqs.push_back({(void**)&c.dstatus, 256});
     c.nslots = 64;
     c.slot_bytes = (size_t)2 * 256 * 256 * 8 / 8;
     reqs.push_back({(void**)&c.dstage, (size_t)c.nslots * c.slot_bytes});
@@ -858,7 +956,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     }
     h->arena.used = 0;
     for (auto& r : reqs) *r.p = h->arena.take(r.bytes);
-    const size_t hneed = c.gcap * 8 + (size_t)c.nslots * c.slot_bytes;
+    const size_t hneed = c.gcap * 8 + (size_t)c.nslots * c.slot_bytes + 256;
     if (h->hpin_bytes < hneed) {
       if (h->hpin) cudaFreeHost(h->hpin);
       h->hpin = nullptr;
@@ -872,6 +970,8 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c.hG = reinterpret_cast<double*>(h->hpin);
     c.hstage = reinterpret_cast<char*>(h->hpin) + c.gcap * 8;
     c.slot_epoch.assign(c.nslots, 0);
+    c.hstatus = reinterpret_cast<int*>(c.hstage + (size_t)c.nslots * c.slot_bytes);
+    CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), c.st));
     B1.Xlock = nullptr;
 
     // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
@@ -1203,6 +1303,9 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.resets = c.resets;
     S.kernel_launches = c.launches;
     S.seconds_total = c.elapsed();
+    S.seconds_host_eig = c.t_eig;
+    S.seconds_sync_wait = c.t_sync;
+    S.host_syncs = c.nsync;
     if (stats) *stats = S;
     h->launches += c.launches;
     return SVDS_OK;

@@ -664,6 +664,91 @@ __global__ void k_csr_validate(long long rows, long long cols, const int* rowptr
   if (f) atomicOr(flags, f);
 }
 
+// ---------------------------------------------------------------------------
+// Small dense steps of the block orthogonalisation, on the device so that the
+// CGS2 + CholQR2 sequence needs no host round trip.  One CTA of 64 threads.
+//   stage 1: G = [V T]^T T ((g+nb) x nb): coef = -G[0:g], work[0:nb] = diag(T^T T)
+//   stage 2: G = [V T']^T T': C2 = G[0:g], S = G[g:] - C2^T C2, R1 = chol(S);
+//            coef = -C2, rinv = R1^-1; status bit 1 if a column kept less than
+//            sqrt(drop2) of its norm, bit 2 if S is not positive definite
+//   stage 3: G = T''^T T'' (nb x nb): R2 = chol(G), coef = R2^-1
+// Coefficients are written in the mode's coefficient format (row-major).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_coef(int prec, void* out, int idx, double v) {
+  if (prec == kF32) {
+    reinterpret_cast<float*>(out)[idx] = (float)v;
+  } else if (prec == kDF64) {
+    const float hi = (float)v;
+    reinterpret_cast<float*>(out)[2 * idx] = hi;
+    reinterpret_cast<float*>(out)[2 * idx + 1] = (float)(v - (double)hi);
+  } else {
+    reinterpret_cast<double*>(out)[idx] = v;
+  }
+}
+
+// Upper Cholesky of the nb x nb row-major matrix S into R (row-major) and its
+// inverse into Ri; returns false if S is not numerically positive definite.
+__device__ bool dev_chol_inv(int nb, const double* S, double* R, double* Ri) {
+  for (int e = 0; e < nb * nb; ++e) R[e] = Ri[e] = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    double d = S[j * nb + j];
+    for (int k = 0; k < j; ++k) d -= R[k * nb + j] * R[k * nb + j];
+    if (!(d > 0.0) || !isfinite(d)) return false;
+    const double rjj = sqrt(d);
+    R[j * nb + j] = rjj;
+    for (int i = j + 1; i < nb; ++i) {
+      double t = 0.5 * (S[j * nb + i] + S[i * nb + j]);
+      for (int k = 0; k < j; ++k) t -= R[k * nb + j] * R[k * nb + i];
+      R[j * nb + i] = t / rjj;
+    }
+  }
+  for (int j = 0; j < nb; ++j) {
+    Ri[j * nb + j] = 1.0 / R[j * nb + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double t = 0.0;
+      for (int k = i + 1; k <= j; ++k) t += R[i * nb + k] * Ri[k * nb + j];
+      Ri[i * nb + j] = -t / R[i * nb + i];
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(64) k_ortho_small(int stage, int prec, int g, int nb, const double* __restrict__ G,
+                                                    double* work, void* coef, void* rinv, int* status, double drop2) {
+  __shared__ double S[64], R[64], Ri[64];
+  const int t = threadIdx.x;
+  if (stage == 1) {
+    for (int e = t; e < g * nb; e += blockDim.x) store_coef(prec, coef, e, -G[e]);
+    if (t < nb) work[t] = G[(g + t) * nb + t];
+    return;
+  }
+  if (stage == 2) {
+    for (int e = t; e < g * nb; e += blockDim.x) store_coef(prec, coef, e, -G[e]);
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e % nb;
+      double v = G[(g + i) * nb + j];
+      for (int l = 0; l < g; ++l) v -= G[l * nb + i] * G[l * nb + j];
+      S[e] = v;
+    }
+  } else {
+    for (int e = t; e < nb * nb; e += blockDim.x) S[e] = G[e];
+  }
+  __syncthreads();
+  if (t == 0) {
+    int st = 0;
+    if (stage == 2)
+      for (int j = 0; j < nb; ++j)
+        if (!(S[j * nb + j] > drop2 * fmax(work[j], 1e-300))) st |= 1;
+    if (!dev_chol_inv(nb, S, R, Ri)) {
+      st |= 2;
+      for (int e = 0; e < nb * nb; ++e) Ri[e] = (e / nb == e % nb) ? 1.0 : 0.0;
+    }
+    if (st) atomicOr(status, st);
+  }
+  __syncthreads();
+  for (int e = t; e < nb * nb; e += blockDim.x) store_coef(prec, stage == 2 ? rinv : coef, e, Ri[e]);
+}
+
 inline int persistent_grid(long long work_items, int per_block) {
   long long g = (work_items + per_block - 1) / per_block;
   const long long cap = 152LL * 16;
@@ -1014,6 +1099,13 @@ cudaError_t launch_csr_validate(long long rows, long long cols, const int* rowpt
                                 const double* vals, int* flags, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   k_csr_validate<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, cols, rowptr, colidx, vals, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ortho_small(int stage, int prec, int g, int nb, const double* G, double* work, void* coef,
+                               void* rinv, int* status, double drop2, cudaStream_t st) {
+  if (nb < 1 || nb > 8 || g < 0) return cudaErrorInvalidValue;
+  k_ortho_small<<<1, 64, 0, st>>>(stage, prec, g, nb, G, work, coef, rinv, status, drop2);
   return cudaGetLastError();
 }
 

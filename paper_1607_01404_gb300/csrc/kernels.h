@@ -110,6 +110,10 @@ cudaError_t launch_make_dscale(int prec, long long L, const double* s, int use_s
 cudaError_t launch_csr_validate(long long rows, long long cols, const int* rowptr, const int* colidx,
                                 const double* vals, int* flags, cudaStream_t st);
 
+// Small dense steps of the device-side CGS2 + CholQR2 (see kernels.cu).
+cudaError_t launch_ortho_small(int stage, int prec, int g, int nb, const double* G, double* work, void* coef,
+                               void* rinv, int* status, double drop2, cudaStream_t st);
+
 void kernels_init();
 
 }  // namespace phsvds
