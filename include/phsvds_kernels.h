@@ -48,6 +48,21 @@ size_t phsvds_gram_scratch_bytes(int p, int q);
 int phsvds_combine(int prec, int64_t L, const void *P, int64_t ldp, int p, const void *coef, const void *In,
                    int64_t ldin, int alpha_one, void *Out, int64_t ldout, int q, const void *Rinv, void *stream);
 
+/* Allocation-free variant of phsvds_gram, for callers that cannot allocate
+ * device memory (host callbacks, allocator hooks, plug-ins that must not touch
+ * their host application's device heap).  The paper has no counterpart: it is
+ * an interface convenience of this library.  Its scratch is a fixed device
+ * array inside the library (2,490,368 bytes, held on every GPU that loads the
+ * library until the process exits), so it serves p <= 64 and q <= 8 and returns
+ * SVDS_ERR_ARG beyond that.  It allocates nothing.  The first call on each
+ * device (with that device current) resolves the array's device address;
+ * make it before any stream capture.  All calls share the one array: calls
+ * whose kernels overlap on the GPU (different streams, or different host
+ * threads) race on it; serialise them.  Each call overwrites the part of the
+ * array it uses, so the previous call's contents do not affect its result. */
+int phsvds_gram_noalloc(int prec, int64_t r0, int64_t r1, const void *P, int64_t ldp, int p, const void *Q,
+                        int64_t ldq, int q, double *G, void *stream);
+
 /* Fused Ritz vectors and residuals (Sec. 3.3 residual kernel):
  * X = V Y, R = W Y - X diag(theta), norms2[j] = ||R_j||^2 (device doubles).
  * V, W: L x g with leading dimension ldv; X, R: L x nb with leading dimension ldb. */

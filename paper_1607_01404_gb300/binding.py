@@ -81,6 +81,8 @@ _SIGS = {
     "phsvds_gram": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                               C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "phsvds_gram_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "phsvds_gram_noalloc": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
+                                      C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "phsvds_combine": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "phsvds_ritz_residual": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
@@ -248,6 +250,12 @@ def gram(prec, r0, r1, P, ldp, p, Q, ldq, q, G, scratch, stream=None):
     _check(lib().phsvds_gram(prec, r0, r1, P.data_ptr(), ldp, p, Q.data_ptr(), ldq, q, G.data_ptr(),
                              scratch.data_ptr(), scratch.numel() * scratch.element_size(), _stream(stream)),
            "phsvds_gram")
+
+
+def gram_noalloc(prec, r0, r1, P, ldp, p, Q, ldq, q, G, stream=None):
+    """phsvds_gram without caller scratch (fixed library-internal scratch; p <= 64, q <= 8)."""
+    _check(lib().phsvds_gram_noalloc(prec, r0, r1, P.data_ptr(), ldp, p, Q.data_ptr(), ldq, q, G.data_ptr(),
+                                     _stream(stream)), "phsvds_gram_noalloc")
 
 
 def gram_scratch_bytes(p, q):
