@@ -2,9 +2,12 @@
 
 One step = one complete solve of the workload through the C-ABI: handle
 creation from a device-resident CSR (transpose, value formats), the ||A||
-estimate, stage 1 (FP32 phase + FP64-class polish, the "chosen" form) and, if
-needed, stage 2, ending with the triplets and their residuals on the host.
-The plain FP64-class form (no FP32 phase) is timed beside it.
+estimate, stage 1 and, if needed, stage 2, ending with the triplets and their
+residuals on the host.  The timed "chosen" form runs JDQMR in both stages with
+FP32 inner solves and an FP32 first phase of stage 1 (FP64-class outer
+iteration after it); beside it are timed the plain FP64-class form (the same
+JDQMR with FP64-class inner and outer iterations, no FP32 anywhere) and the
+plain FP64-class GD+k.
 
 Workload: the 3D grid-difference operator [D(x)I(x)I; I(x)D(x)I; I(x)I(x)D] on a
 128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4,
@@ -32,13 +35,14 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "grid3d_N128"
 K, TARGET, BLOCK, TOL = 10, "smallest", 4, 1e-10
-METRIC = "sec to k triplets at ||r||<=1e-10||A|| (chosen: FP32 stage-1 phase + FP64-class)"
+METRIC = "sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner solves and FP32 stage-1 phase)"
 UNIT = "s"
-# Products with A or A^T (per column) of a full plain FP64-class solve of this
-# workload, measured on a GB300 with this library; the CPU oracle runs the same
-# algorithm, so its full-solve time is extrapolated from its measured cost per
-# matvec on a bounded sample.
-FULL_SOLVE_MATVECS = None
+# Products with A or A^T (per column) of a full GD+k FP64-class solve of this
+# workload, measured on a GB300 with this library (the plain GD+k line of the
+# bench reports it live); the CPU oracle runs the same GD+k algorithm, so its
+# full-solve time is extrapolated from its measured cost per matvec on a bounded
+# sample when the reference arm runs alone.
+FULL_SOLVE_MATVECS = 12292
 
 
 def log(*a):
@@ -213,13 +217,21 @@ def run_gpu(args, world, rank, local):
     sp = stream.cuda_stream
     tgt = B.SVDS_SMALLEST if TARGET == "smallest" else B.SVDS_LARGEST
 
-    def opts(chosen, seed):
-        return B.make_opts(maxBlockSize=BLOCK, stage1_precision=B.SVDS_FP32 if chosen else B.SVDS_FP64,
-                           stage1_polish=1, precond=B.SVDS_PRECOND_JACOBI, seed=seed, stream=sp,
-                           maxSeconds=600.0)
+    def opts(form, seed):
+        kw = dict(maxBlockSize=BLOCK, stage1_polish=1, precond=B.SVDS_PRECOND_JACOBI, seed=seed, stream=sp,
+                  maxSeconds=600.0)
+        if form == "chosen":
+            kw.update(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+                      innerPrecision=B.SVDS_FP32)
+        elif form == "plain":
+            kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+                      innerPrecision=B.SVDS_FP64)
+        else:  # plain GD+k
+            kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_GDPK, method_stage2=B.SVDS_GDPK)
+        return B.make_opts(**kw)
 
-    def one_solve(chosen, seed, host_inputs=False):
-        o = opts(chosen, seed)
+    def one_solve(form, seed, host_inputs=False):
+        o = opts(form, seed)
         if host_inputs:
             h = B.svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, o)
         else:
@@ -230,7 +242,7 @@ def run_gpu(args, world, rank, local):
             h.close()
         return out
 
-    def timed(chosen, steps, seed0):
+    def timed(form, steps, seed0):
         times, stats, last = [], [], None
         for s in range(steps):
             barrier(world)
@@ -238,7 +250,7 @@ def run_gpu(args, world, rank, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            last = one_solve(chosen, seed0 + s)
+            last = one_solve(form, seed0 + s)
             e1.record(stream)
             torch.cuda.synchronize()
             barrier(world)
@@ -248,23 +260,25 @@ def run_gpu(args, world, rank, local):
 
     log(f"[bench] rank {rank}: warmup {args.warmup}")
     for w in range(args.warmup):
-        one_solve(True, 100 + w + 1000 * rank)
+        one_solve("chosen", 100 + w + 1000 * rank)
     clk = ClockSampler(local)
     clk.start()
-    t_chosen, st_chosen, last = timed(True, args.steps, 1 + 1000 * rank)
+    t_chosen, st_chosen, last = timed("chosen", args.steps, 1 + 1000 * rank)
     clocks = clk.stop()
     sigma, U, V, rnorm, nconv, stats, rc = last
     exact = np.sort(np.sqrt((4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[:, None, None]
                             + (4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[None, :, None]
                             + (4 * np.sin(np.arange(1, 129) * np.pi / 258) ** 2)[None, None, :]).ravel())[:K]
     relerr = float(np.max(np.abs(sigma - exact) / exact))
-    # plain FP64-class form on the same workload
-    t_plain, st_plain, lastp = timed(False, max(1, min(args.steps, 2)), 500 + 1000 * rank)
+    # plain FP64-class forms on the same workload
+    t_plain, st_plain, lastp = timed("plain", max(1, min(args.steps, 2)), 500 + 1000 * rank)
     relerr_p = float(np.max(np.abs(lastp[0] - exact) / exact))
+    t_gdk, st_gdk, lastg = timed("gdk", 1, 700 + 1000 * rank)
+    relerr_g = float(np.max(np.abs(lastg[0] - exact) / exact))
     # end to end through host buffers
     torch.cuda.synchronize()
     te0 = time.perf_counter()
-    oute = one_solve(True, 7 + 1000 * rank, host_inputs=True)
+    oute = one_solve("chosen", 7 + 1000 * rank, host_inputs=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - te0
     h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
@@ -275,7 +289,8 @@ def run_gpu(args, world, rank, local):
     ms_step = statistics.median(t_chosen) * 1e3
     ms_step = max_over_ranks(ms_step, world)
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
-                t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
+                t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
+                relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
                 roof32=roof32, roofdf=roofdf, ms_step=ms_step, A=A, e2e_nconv=oute[4])
 
 
@@ -306,7 +321,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time only the SpMM kernels of the workload (no solver; used for ncu captures)")
     args = ap.parse_args()
+    if args.kernels_only:
+        import torch
+
+        from paper_1607_01404_gb300 import binding as B
+        from paper_1607_01404_gb300 import workloads as wl
+
+        A, _ = wl.workload(WORKLOAD)
+        dev = torch.device("cuda", 0)
+        B.lib()
+        out = {"f32": spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK, reps=args.steps),
+               "df64": spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK, reps=args.steps)}
+        print(json.dumps(out))
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     from paper_1607_01404_gb300 import workloads as wl
@@ -348,13 +378,15 @@ def main():
     st = res["stats"][-1]
     launches = int(sum(s["kernel_launches"] for s in res["stats"]))
     mv_plain = int(res["st_plain"][-1]["matvecs_stage1"] + res["st_plain"][-1]["matvecs_stage2"])
+    mv_gdk = int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"])
     cpu = None
     try:
         mv, secs, cores = cpu_sample(A, args.cpu_seconds)
         per_mv = secs / mv
-        cpu = dict(value=per_mv * mv_plain, unit=UNIT, cores=cores, kind="oracle",
+        cpu = dict(value=per_mv * mv_gdk, unit=UNIT, cores=cores, kind="oracle",
                    sample=f"oracle (FP64 numpy/scipy) stage-1 GD+k on the full matrix for {mv} matvecs "
-                          f"({secs:.1f} s); seconds/matvec x {mv_plain} matvecs of the GPU plain FP64-class solve")
+                          f"({secs:.1f} s); seconds/matvec x {mv_gdk} matvecs of the same GD+k algorithm's full "
+                          f"solve (GPU FP64-class GD+k count)")
     except Exception as e:  # the baseline is reported, never required
         cpu = dict(value=None, unit=UNIT, cores=os.cpu_count(), kind="oracle", sample=f"failed: {e}")
     value = res["ms_step"] / 1e3
@@ -364,14 +396,17 @@ def main():
         dtype="f32+df64", data="synthetic",
         config=dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
                     k=K, target=TARGET, block=BLOCK, tol=TOL, precond="jacobi",
-                    form="chosen: FP32 stage-1 phase, FP64-class (double-float) polish and stage 2",
+                    form="chosen: JDQMR (inner QMR solves in FP32), FP32 stage-1 phase, FP64-class outer polish/stage 2",
                     l2="working set >> L2 (no flush)", parallelism=f"replicas x{args.gpus}"),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
-        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
+        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT, form="JDQMR, FP64-class inner and outer",
                         matvecs=mv_plain, max_rel_sigma_err=res["relerr_plain"]),
+        plain_fp64_gdk=dict(value=res["t_gdk"][0], unit=UNIT, form="GD+k, FP64-class",
+                            matvecs=int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"]),
+                            max_rel_sigma_err=res["relerr_gdk"]),
         solve_stats=dict(matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
                          matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
-                         stage2_used=st["stage2_used"], setup_s=st["seconds_setup"]),
+                         inner_steps=st["inner_steps"], stage2_used=st["stage2_used"], setup_s=st["seconds_setup"]),
         roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
                       frac=achieved / peak, peak_kind=peak_kind, traffic=None,
                       all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in

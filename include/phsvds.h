@@ -39,6 +39,8 @@ extern "C" {
 #define SVDS_SMALLEST 1
 
 #define SVDS_GDPK 0  /* GD+k (generalised Davidson with +k restarting) */
+#define SVDS_JDQMR 1 /* JDQMR: GD+k outer basis, corrections from symmetric QMR on the
+                        Jacobi-Davidson correction equation (FP32 inner solves) */
 
 #define SVDS_FP64 3  /* FP64-class stage 1 (double-float arithmetic on the GPU) */
 #define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
@@ -67,8 +69,8 @@ typedef struct {
   int maxBasisSize;     /* 0 = default */
   int minRestartSize;   /* 0 = default */
   int maxBlockSize;     /* 0 = 1 */
-  int method_stage1;    /* SVDS_GDPK */
-  int method_stage2;    /* SVDS_GDPK */
+  int method_stage1;    /* SVDS_GDPK (default) or SVDS_JDQMR */
+  int method_stage2;    /* SVDS_GDPK (default) or SVDS_JDQMR */
   int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
                            to the paper's stage-1 criterion before stage 2 (default 1) */
@@ -81,6 +83,11 @@ typedef struct {
   int initSize;         /* number of initial right vectors in initV (Sec. 3.4 initSize) */
   const double *initV;  /* host, n x initSize column-major, or NULL */
   void *stream;         /* cudaStream_t to run on, or NULL for the library's own stream */
+  int innerMaxIt;       /* JDQMR: inner steps per correction, 0 = 30 */
+  double innerRelTol;   /* JDQMR: stop an inner solve when its QMR residual bound falls below
+                           this fraction of the right-hand side, 0 = 0.1 */
+  int innerPrecision;   /* JDQMR inner solves: SVDS_FP32 (default) or SVDS_FP64 (the FP64-class
+                           mode of the outer iteration) */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -98,6 +105,7 @@ typedef struct {
   double seconds_host_eig;    /* host time in the projected eigenproblems */
   double seconds_sync_wait;   /* host time blocked on the device (small results coming back) */
   int64_t host_syncs;         /* device-to-host round trips */
+  int64_t inner_steps;        /* JDQMR inner sQMR steps (each applies the operator to the block) */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

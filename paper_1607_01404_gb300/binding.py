@@ -27,6 +27,7 @@ SVDS_ERR_MAXIT = 1
 SVDS_LARGEST = 0
 SVDS_SMALLEST = 1
 SVDS_GDPK = 0
+SVDS_JDQMR = 1
 SVDS_FP32 = 1
 SVDS_FP64 = 3
 SVDS_NATIVE_FP64 = 4
@@ -48,7 +49,8 @@ class svds_opts(C.Structure):
                 ("stage1_polish", C.c_int), ("precond", C.c_int), ("aNorm", C.c_double),
                 ("maxMatvecs", C.c_int64), ("maxSeconds", C.c_double), ("seed", C.c_uint64),
                 ("printLevel", C.c_int), ("initSize", C.c_int), ("initV", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("innerMaxIt", C.c_int), ("innerRelTol", C.c_double),
+                ("innerPrecision", C.c_int)]
 
 
 class svds_stats(C.Structure):
@@ -58,7 +60,8 @@ class svds_stats(C.Structure):
                 ("stage2_used", C.c_int), ("aNorm", C.c_double), ("seconds_setup", C.c_double),
                 ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
                 ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
-                ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64)]
+                ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
+                ("inner_steps", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

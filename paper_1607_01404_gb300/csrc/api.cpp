@@ -159,6 +159,7 @@ int svds_opts_default(svds_opts* o) {
   o->stage1_polish = 1;
   o->precond = SVDS_PRECOND_JACOBI;
   o->seed = 1;
+  o->innerPrecision = SVDS_FP32;
   return SVDS_OK;
 }
 
@@ -176,6 +177,10 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
   if (o.stage1_precision != SVDS_FP64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_NATIVE_FP64)
     return SVDS_ERR_ARG;
   if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
+  if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR) ||
+      (o.method_stage2 != SVDS_GDPK && o.method_stage2 != SVDS_JDQMR) || o.innerMaxIt < 0 || o.innerRelTol < 0)
+    return SVDS_ERR_ARG;
+  if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_FP64) return SVDS_ERR_ARG;
   if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
   if (!A->on_device) {
     int rc = validate_host_csr(A);

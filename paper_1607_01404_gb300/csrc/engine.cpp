@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "hostla.h"
+#include "jdqmr.h"
 
 namespace phsvds {
 
@@ -82,6 +83,7 @@ struct Ctx {
   int* dstatus = nullptr;  // breakdown flags raised by the device steps
   int* hstatus = nullptr;  // pinned copy
   bool device_ortho = true;
+  long long inner = 0;     // JDQMR inner steps
 
   double t_sync = 0, t_eig = 0;
   long long nsync = 0;
@@ -353,6 +355,11 @@ struct RunBufs {
   void* BXb = nullptr;    // L x b (stage-2 checks)
   void* tmp = nullptr;    // m x b (C op)
   void* Xlock = nullptr;  // L x k (refined)
+  // JDQMR inner-solve scratch (L x b each, inner mode): x, rhs, K^-1 x, q, r, d, sol, op(q)
+  void* jd[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* jtmp = nullptr;  // m x b (inner-mode C op)
+  QmrState* jS = nullptr;
+  double* jdots = nullptr;
 };
 
 using ConvFn = std::function<void(const double* theta, const double* rn, int off, int nc, char* ok)>;
@@ -368,6 +375,12 @@ struct RunCfg {
   int b0 = 1;
   ConvFn conv;
   const char* name = "";
+  // JDQMR corrections instead of the preconditioned residual
+  bool jd = false;
+  int jd_prec = kF32;            // mode of the inner solves
+  const void* jdinv = nullptr;   // Jacobi diagonal in the inner mode's storage, or nullptr
+  int jd_maxk = 30;
+  double jd_xi = 0.1;
 };
 
 struct RunOut {
@@ -474,6 +487,47 @@ void reset_basis(Ctx& c, RunBufs& B, int op, int g, std::vector<double>& H, cons
   for (int i = 0; i < g; ++i)
     for (int j = 0; j < g; ++j) H[(size_t)j * g + i] = 0.5 * (Hr[(size_t)i * g + j] + Hr[(size_t)j * g + i]);
   c.resets += 1;
+}
+
+// ---------------------------------------------------------------------------
+// JDQMR correction for the nbk block columns of (Xb, Rb): approximate solution
+// of (I - x x^T)(op - eta I)(I - x x^T) t = -r (t orthogonal to x) by block
+// symmetric QMR in FP32, with right-hand sides scaled to unit norm (the outer
+// basis is orthonormalised afterwards, so the scale of t is immaterial).
+// Result in B.Tb in the outer precision.
+// ---------------------------------------------------------------------------
+void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::vector<double>& eta,
+                   const std::vector<double>& rn) {
+  const int prec = B.prec, pin = cfg.jd_prec;
+  const long long L = B.L;
+  std::vector<double> one(nbk, 1.0), scr(nbk);
+  for (int j = 0; j < nbk; ++j) scr[j] = rn[j] > 0 ? -1.0 / rn[j] : 0.0;
+  const double* d1 = reinterpret_cast<const double*>(c.upload(kF64, one.data(), nbk));
+  const double* d2 = reinterpret_cast<const double*>(c.upload(kF64, scr.data(), nbk));
+  const double* de = reinterpret_cast<const double*>(c.upload(kF64, eta.data(), nbk));
+  void *x = B.jd[0], *bv = B.jd[1], *kx = B.jd[2], *q = B.jd[3], *r = B.jd[4], *d = B.jd[5], *sol = B.jd[6],
+       *w = B.jd[7];
+  CK(convert_cols(prec, B.Xb, B.b, pin, x, nbk, L, nbk, d1, c.st));
+  CK(convert_cols(prec, B.Rb, B.b, pin, bv, nbk, L, nbk, d2, c.st));
+  CK(qmr_init(pin, L, nbk, x, bv, cfg.jdinv, kx, q, r, d, sol, B.jS, c.partial, B.jdots, c.st));
+  c.launches += 2 + qmr_init_launches();
+  for (int k = 0; k < cfg.jd_maxk; ++k) {
+    apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
+    CK(qmr_step(pin, L, nbk, x, w, kx, cfg.jdinv, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol, B.jS, c.partial, B.jdots,
+                c.st));
+    c.launches += qmr_step_launches();
+    c.inner += 1;
+    if ((k + 1) % 8 == 0 && k + 1 < cfg.jd_maxk) {
+      CK(cudaMemcpyAsync(c.hG, B.jS, sizeof(QmrState) * nbk, cudaMemcpyDeviceToHost, c.st));
+      c.sync();
+      const QmrState* hs = reinterpret_cast<const QmrState*>(c.hG);
+      bool any = false;
+      for (int j = 0; j < nbk; ++j) any = any || hs[j].active;
+      if (!any) break;
+    }
+  }
+  CK(convert_cols(pin, sol, nbk, prec, B.Tb, B.b, L, nbk, d1, c.st));
+  c.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -603,9 +657,14 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       Yprev.clear();
       continue;
     }
-    // correction T = M R (Jacobi) or T = R
+    // correction: JDQMR, or T = M R (Jacobi), or T = R
     void* T = B.Rb;
-    if (cfg.dscale) {
+    if (cfg.jd) {
+      std::vector<double> eta(nbk);
+      for (int j = 0; j < nbk; ++j) eta[j] = theta[block[j]];
+      jd_correction(c, B, cfg, nbk, eta, rnb);
+      T = B.Tb;
+    } else if (cfg.dscale) {
       CK(launch_scale_rows(prec, B.L, cfg.dscale, B.Rb, b, B.Tb, b, nbk, c.st));
       c.launches += 1;
       T = B.Tb;
@@ -795,18 +854,24 @@ RunOut run_refined(Ctx& c, RunBufs& B, const RefinedCfg& cfg, std::vector<double
       ++rsr;
       c.restarts += 1;
     }
+    void* Tc = B.Rb;
+    if (cfg.jd) {
+      // the lower bound tau is the shift of the correction equation (Sec. 3.1)
+      jd_correction(c, B, cfg, nbk, std::vector<double>(nbk, tau), rn);
+      Tc = B.Tb;
+    }
     std::vector<SegV> basis;
     if (i > 0) basis.push_back(SegV{B.Xlock, k, i});
     basis.push_back(SegV{B.V, B.ldv, g});
-    ortho(c, prec, B.L, basis, B.Rb, b, nbk, off(B.V, g, prec), B.ldv);
-    apply_op(c, prec, OP_B, B.Rb, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
+    ortho(c, prec, B.L, basis, Tc, b, nbk, off(B.V, g, prec), B.ldv);
+    apply_op(c, prec, OP_B, Tc, b, off(B.W, g, prec), B.ldv, nbk, B.tmp, b);
     // Z = W T - tau T, orthonormalised against Q: extends (B - tau I)V = QR
     std::vector<double> coef((size_t)2 * nbk * nbk, 0.0);
     for (int j = 0; j < nbk; ++j) {
       coef[(size_t)j * nbk + j] = 1.0;
       coef[(size_t)(nbk + j) * nbk + j] = -tau;
     }
-    combine(c, prec, B.L, {SegV{off(B.W, g, prec), B.ldv, nbk}, SegV{B.Rb, b, nbk}}, coef, nullptr, 0, false, B.Zb, b,
+    combine(c, prec, B.L, {SegV{off(B.W, g, prec), B.ldv, nbk}, SegV{Tc, b, nbk}}, coef, nullptr, 0, false, B.Zb, b,
             nbk);
     OrthoRes oz = ortho(c, prec, B.L, {SegV{B.Q, B.ldv, g}}, B.Zb, b, nbk, off(B.Q, g, prec), B.ldv);
     std::vector<double> Hext = gram(c, prec, 0, B.L, {SegV{B.V, B.ldv, g + nbk}}, SegV{off(B.W, g, prec), B.ldv, nbk});
@@ -895,7 +960,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     };
     std::vector<Req> reqs;
     RunBufs B1a, B1, B2;
-    auto plan_run = [&](RunBufs& R, int prec, long long L, bool refined) {
+    auto plan_run = [&](RunBufs& R, int prec, long long L, bool refined, bool jdrun) {
       const size_t e = elem_bytes(prec);
       R.prec = prec;
       R.L = L;
@@ -908,15 +973,24 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       reqs.push_back({&R.Tb, (size_t)L * b * e});
       reqs.push_back({&R.BXb, (size_t)L * b * e});
       reqs.push_back({&R.tmp, (size_t)m * b * e});
+      if (jdrun) {
+        for (int i = 0; i < 8; ++i) reqs.push_back({&R.jd[i], (size_t)L * b * 8});
+        reqs.push_back({&R.jtmp, (size_t)m * b * 8});
+        reqs.push_back({(void**)&R.jS, sizeof(QmrState) * 8});
+        reqs.push_back({(void**)&R.jdots, sizeof(double) * 64});
+      }
       if (refined) {
         reqs.push_back({&R.Q, (size_t)L * ldv * e});
         reqs.push_back({&R.Zb, (size_t)L * b * e});
         reqs.push_back({&R.Xlock, (size_t)L * k * e});
       }
     };
-    if (lowprec) plan_run(B1a, kF32, n, false);
-    plan_run(B1, p2, n, false);
-    plan_run(B2, p2, L2, smallest);
+    const bool jd1 = o.method_stage1 == SVDS_JDQMR, jd2 = o.method_stage2 == SVDS_JDQMR;
+    if (lowprec) plan_run(B1a, kF32, n, false, jd1);
+    plan_run(B1, p2, n, false, jd1);
+    plan_run(B2, p2, L2, smallest, jd2);
+    float* dj32 = nullptr;
+    if (jd1) reqs.push_back({(void**)&dj32, (size_t)n * 4});
     const size_t e2 = elem_bytes(p2);
     void *X1a = nullptr, *X1 = nullptr, *CX = nullptr, *Xfin = nullptr, *BXfin = nullptr, *R2 = nullptr,
          *Xout2 = nullptr, *d1a = nullptr, *d1 = nullptr, *dout = nullptr;
@@ -1016,7 +1090,14 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       if (lowprec) CK(launch_make_dscale(kF32, n, A.colsq, 0, d1a, c.st));
       CK(launch_make_dscale(p2, n, A.colsq, 0, d1, c.st));
       c.launches += lowprec ? 2 : 1;
+      if (jd1) {
+        CK(launch_make_dscale(kF32, n, A.colsq, 0, dj32, c.st));
+        c.launches += 1;
+      }
     }
+    const int jd_prec = o.innerPrecision == SVDS_FP64 ? p2 : kF32;
+    const int jd_maxk = o.innerMaxIt > 0 ? o.innerMaxIt : 30;
+    const double jd_xi = o.innerRelTol > 0 ? o.innerRelTol : 0.1;
     // initial block: user guesses then seeded N(0,1) columns
     // initial block (ncols columns, leading dimension ld): user guesses first
     // (initSize, initV), then seeded N(0,1) columns
@@ -1046,6 +1127,11 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.smallest = smallest;
     c1.normop = normC;
     c1.b0 = b0;
+    c1.jd = jd1;
+    c1.jd_prec = jd_prec;
+    c1.jdinv = jac ? (jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1)) : nullptr;
+    c1.jd_maxk = jd_maxk;
+    c1.jd_xi = jd_xi;
     if (lowprec) {
       init_block(kF32, X1a, kk, b0);
       c1.u = unit_roundoff(kF32);
@@ -1179,6 +1265,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c2.ldv0 = kk;
       c2.b0 = k;
       c2.name = "stage2";
+      c2.jd = jd2;
+      c2.jd_prec = jd_prec;
+      c2.jd_maxk = jd_maxk;
+      c2.jd_xi = jd_xi;
       RunBufs& Bs = B2;
       const double thr1 = std::sqrt(2.0) * normA * tol;
       // second level: Eq. (res) with a margin of the evaluation's own rounding
@@ -1306,6 +1396,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.seconds_host_eig = c.t_eig;
     S.seconds_sync_wait = c.t_sync;
     S.host_syncs = c.nsync;
+    S.inner_steps = c.inner;
     if (stats) *stats = S;
     h->launches += c.launches;
     return SVDS_OK;

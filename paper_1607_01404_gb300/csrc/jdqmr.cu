@@ -1,0 +1,540 @@
+// Inner solver of JDQMR: symmetric QMR (quasi-minimal residual smoothing of
+// preconditioned CG, Freund & Nachtigal 1994) on the Jacobi-Davidson
+// correction equation
+//     (I - x x^T)(op - eta I)(I - x x^T) t = -r,   t orthogonal to x,
+// for a block of nb columns at once (one independent system per column), with
+// the projected preconditioner K~^-1 z = K^-1 z - K^-1 x (x^T K^-1 z)/(x^T K^-1 x)
+// (K = Jacobi diagonal or identity).  The paper runs JDQMR as the stage-2
+// method (Sec. 3.4) and uses it in stage 1 in its experiments (Sec. 4).
+//
+// The vectors use the storage/arithmetic of one mode: FP32 by default (the
+// correction only needs about one digit, and the outer iteration keeps its own
+// precision), or the FP64-class mode.  Per inner step: one operator apply and
+// three streaming kernels with fixed-order FP64-class reductions; the scalar
+// recurrences run in one-thread-per-column kernels, so no host round trip is
+// needed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "jdqmr.h"
+#include "kernels.h"
+
+namespace phsvds {
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxNb = 8;
+
+// conversion of a double scalar to the mode's coefficient type
+template <class P>
+__device__ __forceinline__ typename P::C to_c(double v);
+template <>
+__device__ __forceinline__ float to_c<PF32>(double v) {
+  return (float)v;
+}
+template <>
+__device__ __forceinline__ df to_c<PDF64>(double v) {
+  const float hi = (float)v;
+  return df{hi, (float)(v - (double)hi)};
+}
+template <>
+__device__ __forceinline__ double to_c<PF64>(double v) {
+  return v;
+}
+
+__device__ __forceinline__ df shfl_down(df v, int o) {
+  return df{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+
+// Per-CTA partial sums of ND dot products per column (FP64-class accumulation,
+// fixed order), written to partial[blk][d * nb + j].
+template <class P, int ND>
+__device__ __forceinline__ void block_reduce_store(typename P::G (&acc)[ND][kMaxNb], int nb, typename P::G* partial) {
+  using G = typename P::G;
+  __shared__ G red[kT / 32][ND * kMaxNb];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) {
+      G v = acc[d][j];
+      for (int o = 16; o > 0; o >>= 1) v = P::gadd(v, shfl_down(v, o));
+      if (lane == 0) red[warp][d * kMaxNb + j] = v;
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ND * nb; e += kT) {
+    const int d = e / nb, j = e % nb;
+    G v = red[0][d * kMaxNb + j];
+    for (int w = 1; w < kT / 32; ++w) v = P::gadd(v, red[w][d * kMaxNb + j]);
+    partial[(long long)blockIdx.x * ND * nb + e] = v;
+  }
+}
+
+template <class P>
+__device__ __forceinline__ typename P::A ld_or_one(const typename P::S* p, long long i) {
+  if (p) return P::load(p + i);
+  if constexpr (P::id == kDF64)
+    return df{1.f, 0.f};
+  else
+    return (typename P::A)1;
+}
+
+template <class P>
+__device__ __forceinline__ typename P::A mul(typename P::A a, typename P::A b) {
+  if constexpr (P::id == kDF64)
+    return df_mul(a, b);
+  else
+    return a * b;
+}
+
+// Row access of an L x nb block with leading dimension nb: NB (>= nb) slots,
+// 16-byte vector loads when VEC (nb == NB and rows are 16-byte multiples).
+template <class P, int NB, bool VEC>
+__device__ __forceinline__ void ldrow(const typename P::S* __restrict__ p, long long row, int nb,
+                                      typename P::A (&v)[NB]) {
+  using S = typename P::S;
+  const S* rp = p + row * nb;
+  if constexpr (VEC) {
+    constexpr int W = (int)(NB * sizeof(S) / 16);
+    const float4* q4 = reinterpret_cast<const float4*>(rp);
+    float buf[NB * sizeof(S) / 4];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const float4 t = q4[i];
+      buf[4 * i] = t.x;
+      buf[4 * i + 1] = t.y;
+      buf[4 * i + 2] = t.z;
+      buf[4 * i + 3] = t.w;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v[j] = P::load(reinterpret_cast<const S*>(buf) + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v[j] = j < nb ? P::load(rp + j) : P::zero();
+  }
+}
+
+template <class P, int NB, bool VEC>
+__device__ __forceinline__ void strow(typename P::S* __restrict__ p, long long row, int nb,
+                                      const typename P::A (&v)[NB]) {
+  using S = typename P::S;
+  S* rp = p + row * nb;
+  if constexpr (VEC) {
+    constexpr int W = (int)(NB * sizeof(S) / 16);
+    float buf[NB * sizeof(S) / 4];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) P::store(reinterpret_cast<S*>(buf) + j, v[j]);
+    float4* q4 = reinterpret_cast<float4*>(rp);
+#pragma unroll
+    for (int i = 0; i < W; ++i) q4[i] = make_float4(buf[4 * i], buf[4 * i + 1], buf[4 * i + 2], buf[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < nb) P::store(rp + j, v[j]);
+  }
+}
+
+// ---- initialisation ----
+// kx = K^-1 x, u = K^-1 b, dots: x^T kx, x^T u, b^T b, b^T u, b^T kx
+template <class P>
+__global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const typename P::S* __restrict__ x,
+                                                 const typename P::S* __restrict__ b,
+                                                 const typename P::S* __restrict__ dinv, typename P::S* __restrict__ kx,
+                                                 typename P::G* __restrict__ partial) {
+  using G = typename P::G;
+  G acc[5][kMaxNb];
+#pragma unroll
+  for (int d = 0; d < 5; ++d)
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+  for (long long r = blockIdx.x * (long long)kT + threadIdx.x; r < L; r += (long long)gridDim.x * kT) {
+    const auto s = ld_or_one<P>(dinv, r);
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j)
+      if (j < nb) {
+        const long long o = r * nb + j;
+        const auto xv = P::load(x + o), bv = P::load(b + o);
+        const auto kv = mul<P>(s, xv), uv = mul<P>(s, bv);
+        P::store(kx + o, kv);
+        acc[0][j] = P::gfma(acc[0][j], xv, kv);
+        acc[1][j] = P::gfma(acc[1][j], xv, uv);
+        acc[2][j] = P::gfma(acc[2][j], bv, bv);
+        acc[3][j] = P::gfma(acc[3][j], bv, uv);
+        acc[4][j] = P::gfma(acc[4][j], bv, kv);
+      }
+  }
+  block_reduce_store<P, 5>(acc, nb, partial);
+}
+
+__global__ void k_qmr_init_scalars(int nb, const double* __restrict__ dots, QmrState* S) {
+  const int j = threadIdx.x;
+  if (j >= nb) return;
+  const double xkx = dots[0 * nb + j], xu = dots[1 * nb + j], bb = dots[2 * nb + j], bu = dots[3 * nb + j],
+               bkx = dots[4 * nb + j];
+  QmrState s{};
+  s.xkx = xkx > 0 ? xkx : 1.0;
+  s.gamma = xu / s.xkx;
+  s.rho = bu - bkx * s.gamma;
+  s.tau = sqrt(bb);
+  s.tau0 = s.tau;
+  s.theta = 0.0;
+  s.active = (s.tau > 0 && s.rho != 0.0) ? 1 : 0;
+  s.k = 0;
+  S[j] = s;
+}
+
+// q = K^-1 b - kx gamma ; r = b ; d = 0 ; sol = 0
+template <class P>
+__global__ void __launch_bounds__(kT) k_qmr_init_vec(long long L, int nb, const typename P::S* __restrict__ b,
+                                                     const typename P::S* __restrict__ dinv,
+                                                     const typename P::S* __restrict__ kx, const QmrState* __restrict__ S,
+                                                     typename P::S* __restrict__ q, typename P::S* __restrict__ r,
+                                                     typename P::S* __restrict__ d, typename P::S* __restrict__ sol) {
+  __shared__ typename P::C gm[kMaxNb];
+  if (threadIdx.x < nb) gm[threadIdx.x] = to_c<P>(S[threadIdx.x].gamma);
+  __syncthreads();
+  const long long total = L * nb;
+  for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < total; e += (long long)gridDim.x * kT) {
+    const long long row = e / nb;
+    const int j = (int)(e % nb);
+    const auto sv = ld_or_one<P>(dinv, row);
+    const auto bv = P::load(b + e);
+    P::store(q + e, P::sub(mul<P>(sv, bv), P::mulc(P::load(kx + e), gm[j])));
+    P::store(r + e, bv);
+    P::store(d + e, P::zero());
+    P::store(sol + e, P::zero());
+  }
+}
+
+// ---- per inner step ----
+// after w = op(q): dots x^T w, q^T w, x^T q, q^T q (one thread per row)
+template <class P, int NB, bool VEC>
+__global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typename P::S* __restrict__ x,
+                                                  const typename P::S* __restrict__ q,
+                                                  const typename P::S* __restrict__ w,
+                                                  typename P::G* __restrict__ partial) {
+  using G = typename P::G;
+  using A = typename P::A;
+  G acc[4][kMaxNb];
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+  for (long long r = blockIdx.x * (long long)kT + threadIdx.x; r < L; r += (long long)gridDim.x * kT) {
+    A xv[NB], qv[NB], wv[NB];
+    ldrow<P, NB, VEC>(x, r, nb, xv);
+    ldrow<P, NB, VEC>(q, r, nb, qv);
+    ldrow<P, NB, VEC>(w, r, nb, wv);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc[0][j] = P::gfma(acc[0][j], xv[j], wv[j]);
+      acc[1][j] = P::gfma(acc[1][j], qv[j], wv[j]);
+      acc[2][j] = P::gfma(acc[2][j], xv[j], qv[j]);
+      acc[3][j] = P::gfma(acc[3][j], qv[j], qv[j]);
+    }
+  }
+  block_reduce_store<P, 4>(acc, nb, partial);
+}
+
+// sigma = q^T t with t = w - eta q - x (x^T w - eta x^T q); alpha = rho / sigma
+__global__ void k_qmr_scalars1(int nb, const double* __restrict__ dots, const double* __restrict__ eta,
+                               QmrState* S) {
+  const int j = threadIdx.x;
+  if (j >= nb) return;
+  QmrState s = S[j];
+  const double xw = dots[0 * nb + j], qw = dots[1 * nb + j], xq = dots[2 * nb + j], qq = dots[3 * nb + j];
+  s.c1 = xw - eta[j] * xq;
+  const double sigma = (qw - eta[j] * qq) - xq * s.c1;
+  if (s.active && sigma != 0.0 && isfinite(sigma)) {
+    s.alpha = s.rho / sigma;
+  } else {
+    s.alpha = 0.0;
+    s.active = 0;
+  }
+  S[j] = s;
+}
+
+// t = w - eta q - x c1 ; r -= alpha t ; u = K^-1 r ; dots r^T r, r^T u, x^T u, r^T kx
+template <class P, int NB, bool VEC>
+__global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const typename P::S* __restrict__ x,
+                                                    const typename P::S* __restrict__ q,
+                                                    const typename P::S* __restrict__ w,
+                                                    const typename P::S* __restrict__ kx,
+                                                    const typename P::S* __restrict__ dinv,
+                                                    const double* __restrict__ eta, const QmrState* __restrict__ S,
+                                                    typename P::S* __restrict__ r, typename P::G* __restrict__ partial) {
+  using G = typename P::G;
+  using C = typename P::C;
+  using A = typename P::A;
+  __shared__ C sa[kMaxNb], sc[kMaxNb], se[kMaxNb];
+  if (threadIdx.x < kMaxNb) {
+    const bool ok = threadIdx.x < nb;
+    sa[threadIdx.x] = to_c<P>(ok && S[threadIdx.x].active ? S[threadIdx.x].alpha : 0.0);
+    sc[threadIdx.x] = to_c<P>(ok ? S[threadIdx.x].c1 : 0.0);
+    se[threadIdx.x] = to_c<P>(ok ? eta[threadIdx.x] : 0.0);
+  }
+  __syncthreads();
+  G acc[4][kMaxNb];
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+  for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
+    const auto sv = ld_or_one<P>(dinv, row);
+    A xv[NB], qv[NB], wv[NB], rv[NB], kv[NB];
+    ldrow<P, NB, VEC>(x, row, nb, xv);
+    ldrow<P, NB, VEC>(q, row, nb, qv);
+    ldrow<P, NB, VEC>(w, row, nb, wv);
+    ldrow<P, NB, VEC>(r, row, nb, rv);
+    ldrow<P, NB, VEC>(kx, row, nb, kv);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const A t = P::sub(P::sub(wv[j], P::mulc(qv[j], se[j])), P::mulc(xv[j], sc[j]));
+      rv[j] = P::sub(rv[j], P::mulc(t, sa[j]));
+      const A uv = mul<P>(sv, rv[j]);
+      acc[0][j] = P::gfma(acc[0][j], rv[j], rv[j]);
+      acc[1][j] = P::gfma(acc[1][j], rv[j], uv);
+      acc[2][j] = P::gfma(acc[2][j], xv[j], uv);
+      acc[3][j] = P::gfma(acc[3][j], rv[j], kv[j]);
+    }
+    strow<P, NB, VEC>(r, row, nb, rv);
+  }
+  block_reduce_store<P, 4>(acc, nb, partial);
+}
+
+// QMR smoothing scalars, stopping test, next search-direction coefficients
+__global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
+  const int j = threadIdx.x;
+  if (j >= nb) return;
+  QmrState s = S[j];
+  s.coefd = 0.0;
+  s.coefq = 0.0;
+  s.beta = 0.0;
+  s.upd = 0;
+  if (s.active) {
+    const double rr = dots[0 * nb + j], ru = dots[1 * nb + j], xu = dots[2 * nb + j], rkx = dots[3 * nb + j];
+    const double theta = sqrt(fmax(rr, 0.0)) / s.tau;
+    const double c = 1.0 / sqrt(1.0 + theta * theta);
+    s.coefd = c * c * s.theta * s.theta;
+    s.coefq = c * c * s.alpha;
+    s.theta = theta;
+    s.tau = s.tau * theta * c;
+    s.k += 1;
+    s.upd = 1;
+    s.gamma = xu / s.xkx;
+    const double rho_new = ru - rkx * s.gamma;
+    // stop: QMR residual bound tau sqrt(k + 1) below xi ||b||, or budget, or breakdown
+    if (s.tau * sqrt((double)s.k + 1.0) <= xi * s.tau0 || s.k >= maxk || rho_new == 0.0 || !isfinite(rho_new)) {
+      s.active = 0;
+    } else {
+      s.beta = rho_new / s.rho;
+      s.rho = rho_new;
+    }
+  }
+  S[j] = s;
+}
+
+// d = coefd d + coefq q ; sol += d ; q = (K^-1 r - kx gamma) + beta q   (active columns)
+template <class P, int NB, bool VEC>
+__global__ void __launch_bounds__(kT) k_qmr_update2(long long L, int nb, const typename P::S* __restrict__ r,
+                                                    const typename P::S* __restrict__ kx,
+                                                    const typename P::S* __restrict__ dinv,
+                                                    const QmrState* __restrict__ S, typename P::S* __restrict__ q,
+                                                    typename P::S* __restrict__ d, typename P::S* __restrict__ sol) {
+  using C = typename P::C;
+  using A = typename P::A;
+  __shared__ C cd[kMaxNb], cq[kMaxNb], gm[kMaxNb], bt[kMaxNb];
+  __shared__ int up[kMaxNb], ac[kMaxNb];
+  if (threadIdx.x < kMaxNb) {
+    const bool ok = threadIdx.x < nb;
+    const QmrState s = ok ? S[threadIdx.x] : QmrState{};
+    cd[threadIdx.x] = to_c<P>(ok ? s.coefd : 0.0);
+    cq[threadIdx.x] = to_c<P>(ok ? s.coefq : 0.0);
+    gm[threadIdx.x] = to_c<P>(ok ? s.gamma : 0.0);
+    bt[threadIdx.x] = to_c<P>(ok ? s.beta : 0.0);
+    up[threadIdx.x] = ok ? s.upd : 0;
+    ac[threadIdx.x] = ok ? s.active : 0;
+  }
+  __syncthreads();
+  bool anyup = false;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) anyup = anyup || up[j];
+  if (!anyup) return;
+  for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
+    A qv[NB], dv[NB], sv_[NB], rv[NB], kv[NB];
+    ldrow<P, NB, VEC>(q, row, nb, qv);
+    ldrow<P, NB, VEC>(d, row, nb, dv);
+    ldrow<P, NB, VEC>(sol, row, nb, sv_);
+    ldrow<P, NB, VEC>(r, row, nb, rv);
+    ldrow<P, NB, VEC>(kx, row, nb, kv);
+    const auto s = ld_or_one<P>(dinv, row);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (!up[j]) continue;
+      dv[j] = P::add(P::mulc(dv[j], cd[j]), P::mulc(qv[j], cq[j]));
+      sv_[j] = P::add(sv_[j], dv[j]);
+      if (ac[j]) qv[j] = P::add(P::sub(mul<P>(s, rv[j]), P::mulc(kv[j], gm[j])), P::mulc(qv[j], bt[j]));
+    }
+    strow<P, NB, VEC>(q, row, nb, qv);
+    strow<P, NB, VEC>(d, row, nb, dv);
+    strow<P, NB, VEC>(sol, row, nb, sv_);
+  }
+}
+
+int qmr_grid(long long L) {
+  long long g = (L + kT - 1) / kT;
+  if (g > 152 * 4) g = 152 * 4;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class P>
+__global__ void k_reduce_g(const typename P::G* __restrict__ partial, int nblocks, int n, double* __restrict__ out) {
+  using G = typename P::G;
+  __shared__ G red[128];
+  const int e = blockIdx.x;
+  G v = P::gzero();
+  for (int b = threadIdx.x; b < nblocks; b += 128) v = P::gadd(v, partial[(long long)b * n + e]);
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = P::gadd(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[e] = P::gval(red[0]);
+}
+
+// convert columns between modes with a per-column scale
+template <class PS, class PD>
+__global__ void k_convert_cols(long long L, int nc, const typename PS::S* src, long long lds, typename PD::S* dst,
+                               long long ldd, const double* __restrict__ scale) {
+  const long long total = L * nc;
+  for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < total; e += (long long)gridDim.x * kT) {
+    const long long row = e / nc;
+    const int j = (int)(e % nc);
+    double v;
+    const typename PS::S sv = src[row * lds + j];
+    if constexpr (PS::id == kDF64)
+      v = (double)sv.hi + (double)sv.lo;
+    else
+      v = (double)sv;
+    v *= scale[j];
+    if constexpr (PD::id == kDF64) {
+      const float hi = (float)v;
+      dst[row * ldd + j] = df{hi, (float)(v - (double)hi)};
+    } else {
+      dst[row * ldd + j] = (typename PD::S)v;
+    }
+  }
+}
+
+template <class P>
+cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void* dinv, void* kx, void* q, void* r,
+                   void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+  using SS = typename P::S;
+  using G = typename P::G;
+  const int g = qmr_grid(L);
+  G* pd = reinterpret_cast<G*>(partial);
+  k_qmr_init<P><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)b, (const SS*)dinv, (SS*)kx, pd);
+  k_reduce_g<P><<<5 * nb, 128, 0, st>>>(pd, g, 5 * nb, dots);
+  k_qmr_init_scalars<<<1, 32, 0, st>>>(nb, dots, S);
+  k_qmr_init_vec<P><<<qmr_grid(L * nb), kT, 0, st>>>(L, nb, (const SS*)b, (const SS*)dinv, (const SS*)kx, S, (SS*)q,
+                                                     (SS*)r, (SS*)d, (SS*)sol);
+  return cudaGetLastError();
+}
+
+template <class P, int NB, bool VEC>
+cudaError_t step_nb(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
+                    const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
+                    void* partial, double* dots, cudaStream_t st) {
+  using SS = typename P::S;
+  using G = typename P::G;
+  const int g = qmr_grid(L);
+  G* pd = reinterpret_cast<G*>(partial);
+  k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
+  k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
+  k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
+                                              (const SS*)dinv, eta, S, (SS*)r, pd);
+  k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
+  k_qmr_update2<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv, S, (SS*)q,
+                                              (SS*)d, (SS*)sol);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t step_p(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
+                   const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
+                   void* partial, double* dots, cudaStream_t st) {
+  constexpr size_t es = sizeof(typename P::S);
+#define STEP(NBv)                                                                                                  \
+  ((nb == NBv && (NBv * es) % 16 == 0)                                                                            \
+       ? step_nb<P, NBv, true>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st)          \
+       : step_nb<P, NBv, false>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
+  if (nb <= 1) return STEP(1);
+  if (nb <= 2) return STEP(2);
+  if (nb <= 4) return STEP(4);
+  return STEP(8);
+#undef STEP
+}
+
+}  // namespace
+
+cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, void* kx, void* q,
+                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+  if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+  switch (prec) {
+    case kF32: return init_p<PF32>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
+    case kDF64: return init_p<PDF64>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
+    case kF64: return init_p<PF64>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
+                     const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
+                     void* partial, double* dots, cudaStream_t st) {
+  if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+  switch (prec) {
+    case kF32: return step_p<PF32>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+    case kDF64: return step_p<PDF64>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+    case kF64: return step_p<PF64>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int qmr_step_launches() { return 7; }
+int qmr_init_launches() { return 4; }
+
+cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,
+                         long long L, int nc, const double* scale, cudaStream_t st) {
+  const int g = qmr_grid(L * nc);
+#define CONV(PS_, PD_)                                                                                           \
+  k_convert_cols<PS_, PD_><<<g, kT, 0, st>>>(L, nc, reinterpret_cast<const typename PS_::S*>(src), lds,      \
+                                             reinterpret_cast<typename PD_::S*>(dst), ldd, scale)
+  if (src_prec == kDF64 && dst_prec == kF32)
+    CONV(PDF64, PF32);
+  else if (src_prec == kF64 && dst_prec == kF32)
+    CONV(PF64, PF32);
+  else if (src_prec == kF32 && dst_prec == kF32)
+    CONV(PF32, PF32);
+  else if (src_prec == kF32 && dst_prec == kDF64)
+    CONV(PF32, PDF64);
+  else if (src_prec == kF32 && dst_prec == kF64)
+    CONV(PF32, PF64);
+  else if (src_prec == kDF64 && dst_prec == kDF64)
+    CONV(PDF64, PDF64);
+  else if (src_prec == kF64 && dst_prec == kF64)
+    CONV(PF64, PF64);
+  else
+    return cudaErrorInvalidValue;
+#undef CONV
+  return cudaGetLastError();
+}
+
+}  // namespace phsvds

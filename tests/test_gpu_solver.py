@@ -189,3 +189,49 @@ def test_device_csr_validation():
     with pytest.raises(B.SvdsError) as e:
         B.svds_create(rp, ci, va, 2, 2, on_device=True)
     assert e.value.code == B.SVDS_ERR_CSR
+
+
+# ---------------------------------------------------------------- JDQMR
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_jdqmr_stage1_grid2d_closed_form(target):
+    A = wl.grid_difference(32, 2)
+    s = _grid_sigma(32, 2)
+    ex = s[:5] if target == "smallest" else s[::-1][:5]
+    r = B.svds(A, 5, target, 1e-10, maxBlockSize=2, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+               initV=wl.start_block(A.n, 2, 0), maxMatvecs=400000)
+    np.testing.assert_allclose(r["sigma"], ex, rtol=1e-10)
+    _check_certificate(A, r, 1e-10, s[-1], 5)
+    assert r["stats"]["inner_steps"] > 0
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_jdqmr_stage2_tight_tolerance(target):
+    A = wl.random_illconditioned(900, 300, 16, seed=13)
+    r = B.svds(A, 3, target, 1e-13, maxBlockSize=2, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+               initV=wl.start_block(A.n, 2, 2), maxMatvecs=600000)
+    _compare_to_dense(A, r, target, 3, 1e-13)
+
+
+def test_jdqmr_mixed_precision_3d_block4():
+    A = wl.grid_difference(12, 3)
+    s = _grid_sigma(12, 3)
+    r = B.svds(A, 6, "smallest", 1e-10, maxBlockSize=4, method_stage1=B.SVDS_JDQMR, stage1_precision=B.SVDS_FP32,
+               maxMatvecs=800000)
+    np.testing.assert_allclose(r["sigma"], s[:6], rtol=1e-10)
+    _check_certificate(A, r, 1e-10, s[-1], 6)
+
+
+def test_jdqmr_weighted_grid_jacobi():
+    A = wl.weighted_grid(20, 2, seed=10001)
+    sv = np.linalg.svd(A.to_scipy().toarray(), compute_uv=False)
+    r = B.svds(A, 4, "smallest", 1e-10, maxBlockSize=2, method_stage1=B.SVDS_JDQMR, maxMatvecs=800000)
+    np.testing.assert_allclose(r["sigma"], sv[::-1][:4], rtol=1e-10)
+    _check_certificate(A, r, 1e-10, sv[0], 4)
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_jdqmr_fp64_inner_solves(target):
+    A = wl.random_illconditioned(1500, 500, 16, seed=11)
+    r = B.svds(A, 4, target, 1e-10, maxBlockSize=4, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+               innerPrecision=B.SVDS_FP64, maxMatvecs=600000)
+    _compare_to_dense(A, r, target, 4, 1e-10)
