@@ -50,17 +50,17 @@ __device__ __forceinline__ df shfl_down(df v, int o) {
 }
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 
-// Per-CTA partial sums of ND dot products per column (FP64-class accumulation,
-// fixed order), written to partial[blk][d * nb + j].
-template <class P, int ND>
-__device__ __forceinline__ void block_reduce_store(typename P::G (&acc)[ND][kMaxNb], int nb, typename P::G* partial) {
+// Per-CTA partial sums of ND dot products for each of the NW <= 8 columns
+// (FP64-class accumulation, fixed order), written to partial[blk][d * nb + j].
+template <class P, int ND, int NW>
+__device__ __forceinline__ void block_reduce_store(typename P::G (&acc)[ND][NW], int nb, typename P::G* partial) {
   using G = typename P::G;
   __shared__ G red[kT / 32][ND * kMaxNb];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int d = 0; d < ND; ++d)
 #pragma unroll
-    for (int j = 0; j < kMaxNb; ++j) {
+    for (int j = 0; j < NW; ++j) {
       G v = acc[d][j];
       for (int o = 16; o > 0; o >>= 1) v = P::gadd(v, shfl_down(v, o));
       if (lane == 0) red[warp][d * kMaxNb + j] = v;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const type
         acc[4][j] = P::gfma(acc[4][j], bv, kv);
       }
   }
-  block_reduce_store<P, 5>(acc, nb, partial);
+  block_reduce_store<P, 5, kMaxNb>(acc, nb, partial);
 }
 
 __global__ void k_qmr_init_scalars(int nb, const double* __restrict__ dots, QmrState* S) {
@@ -219,11 +219,11 @@ __global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typ
                                                   typename P::G* __restrict__ partial) {
   using G = typename P::G;
   using A = typename P::A;
-  G acc[4][kMaxNb];
+  G acc[4][NB];
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
-    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
   for (long long r = blockIdx.x * (long long)kT + threadIdx.x; r < L; r += (long long)gridDim.x * kT) {
     A xv[NB], qv[NB], wv[NB];
     ldrow<P, NB, VEC>(x, r, nb, xv);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typ
       acc[3][j] = P::gfma(acc[3][j], qv[j], qv[j]);
     }
   }
-  block_reduce_store<P, 4>(acc, nb, partial);
+  block_reduce_store<P, 4, NB>(acc, nb, partial);
 }
 
 // sigma = q^T t with t = w - eta q - x (x^T w - eta x^T q); alpha = rho / sigma
@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
     se[threadIdx.x] = to_c<P>(ok ? eta[threadIdx.x] : 0.0);
   }
   __syncthreads();
-  G acc[4][kMaxNb];
+  G acc[4][NB];
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
-    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
   for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
     const auto sv = ld_or_one<P>(dinv, row);
     A xv[NB], qv[NB], wv[NB], rv[NB], kv[NB];
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
     }
     strow<P, NB, VEC>(r, row, nb, rv);
   }
-  block_reduce_store<P, 4>(acc, nb, partial);
+  block_reduce_store<P, 4, NB>(acc, nb, partial);
 }
 
 // QMR smoothing scalars, stopping test, next search-direction coefficients
@@ -385,9 +385,11 @@ __global__ void __launch_bounds__(kT) k_qmr_update2(long long L, int nb, const t
   }
 }
 
+// Persistent grid of three 256-thread CTAs per SM (the widest sQMR kernels hold
+// three per SM at their register counts, so there is no tail wave).
 int qmr_grid(long long L) {
   long long g = (L + kT - 1) / kT;
-  if (g > 152 * 4) g = 152 * 4;
+  if (g > 152 * 3) g = 152 * 3;
   if (g < 1) g = 1;
   return (int)g;
 }

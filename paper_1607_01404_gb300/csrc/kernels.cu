@@ -134,8 +134,101 @@ __global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __
   }
 }
 
+// Short rows (at most a few nonzeros): each thread handles two consecutive rows
+// and interleaves their gathers, doubling the loads in flight per thread.
+template <class P, int NB, int VMODE, bool VEC>
+__device__ __forceinline__ void spmm_accum(const int k, const float* __restrict__ v32, const float* __restrict__ v32lo,
+                                           const double* __restrict__ v64, const typename P::A (&xv)[NB],
+                                           typename P::A (&acc)[NB]) {
+  if constexpr (VMODE == 0) {
+    const float a = __ldg(v32 + k);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = fmaf(xv[c], a, acc[c]);
+  } else if constexpr (VMODE == 1) {
+    const float a = __ldg(v32 + k);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = df_fma_f(acc[c], xv[c], a);
+  } else if constexpr (VMODE == 2) {
+    const df a = {__ldg(v32 + k), __ldg(v32lo + k)};
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = df_fma(acc[c], xv[c], a);
+  } else {
+    const double a = __ldg(v64 + k);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = ::fma(xv[c], a, acc[c]);
+  }
+}
+
+template <class P, int NB, bool VEC>
+__device__ __forceinline__ void store_yrow(typename P::S* yr, const typename P::A (&acc)[NB]) {
+  using S = typename P::S;
+  if constexpr (VEC) {
+    constexpr int W = (int)(NB * sizeof(S) / 16);
+    float buf[NB * sizeof(S) / 4];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) P::store(reinterpret_cast<S*>(buf) + c, acc[c]);
+    float4* q4 = reinterpret_cast<float4*>(yr);
+#pragma unroll
+    for (int t = 0; t < W; ++t) q4[t] = make_float4(buf[4 * t], buf[4 * t + 1], buf[4 * t + 2], buf[4 * t + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) P::store(yr + c, acc[c]);
+  }
+}
+
+template <class P, int NB, int VMODE, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_spmm2(long long rows, const int* __restrict__ rowptr,
+                                                    const int* __restrict__ colidx, const float* __restrict__ v32,
+                                                    const float* __restrict__ v32lo, const double* __restrict__ v64,
+                                                    const typename P::S* __restrict__ X, long long ldx,
+                                                    typename P::S* __restrict__ Y, long long ldy) {
+  using A = typename P::A;
+  const long long i0 = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  if (i0 >= rows) return;
+  const bool two = i0 + 1 < rows;
+  const int ka = __ldg(rowptr + i0), kb = __ldg(rowptr + i0 + 1), kc = two ? __ldg(rowptr + i0 + 2) : kb;
+  A acc0[NB], acc1[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) acc0[c] = acc1[c] = P::zero();
+  const int na = kb - ka, nbn = kc - kb;
+  const int nmax = na > nbn ? na : nbn;
+  for (int t = 0; t < nmax; ++t) {
+    const bool ua = t < na, ub = t < nbn;
+    const int ja = ua ? __ldg(colidx + ka + t) : 0;
+    const int jb = ub ? __ldg(colidx + kb + t) : 0;
+    A xa[NB], xb[NB];
+    if (ua) load_xrow<P, NB, VEC>(X + (long long)ja * ldx, xa);
+    if (ub) load_xrow<P, NB, VEC>(X + (long long)jb * ldx, xb);
+    if (ua) spmm_accum<P, NB, VMODE, VEC>(ka + t, v32, v32lo, v64, xa, acc0);
+    if (ub) spmm_accum<P, NB, VMODE, VEC>(kb + t, v32, v32lo, v64, xb, acc1);
+  }
+  store_yrow<P, NB, VEC>(Y + i0 * ldy, acc0);
+  if (two) store_yrow<P, NB, VEC>(Y + (i0 + 1) * ldy, acc1);
+}
+
 template <class P, int NB, bool VEC>
 cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t st) {
+  if (P::id == kF32 && A.rows > 0 && A.nnz <= 4 * A.rows) {  // short rows (FP32): two rows per thread
+    using S = typename P::S;
+    const int grid = grid_for((A.rows + 1) / 2, kThreads);
+    const S* x = reinterpret_cast<const S*>(X);
+    S* y = reinterpret_cast<S*>(Y);
+    if constexpr (P::id == kF32) {
+      k_spmm2<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
+                                                        ldy);
+    } else if constexpr (P::id == kDF64) {
+      if (A.v32lo == nullptr)
+        k_spmm2<P, NB, 1, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx,
+                                                          y, ldy);
+      else
+        k_spmm2<P, NB, 2, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, A.v32lo, nullptr, x, ldx,
+                                                          y, ldy);
+    } else {
+      k_spmm2<P, NB, 3, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, nullptr, nullptr, A.v64, x, ldx, y,
+                                                        ldy);
+    }
+    return cudaGetLastError();
+  }
   using S = typename P::S;
   const int grid = grid_for(A.rows, kThreads);
   const S* x = reinterpret_cast<const S*>(X);
