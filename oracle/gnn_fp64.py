@@ -1,0 +1,213 @@
+"""FP64 CPU oracle of the learned sparse-approximate-inverse preconditioner
+(test infrastructure, never on the product path).
+
+The paper has no learned component; this restates the design of this
+repository's learned preconditioner so that the GPU forward and backward
+kernels can be checked against it.  Every function is plain numpy/scipy.
+
+* Graph: the structural sparsity pattern of C = A^T A (nodes = columns of A,
+  symmetric, diagonal included; entries that cancel numerically are kept).  c_ii = diagonal of C, deg_i = off-diagonal neighbours.
+* Edge weights: e_ij = c_ij / sqrt(c_ii c_jj) for i != j (0 on the diagonal).
+* Node features: x_i = [log c_ii - mean_j log c_jj, deg_i / max_j deg_j].
+* Message passing, 4 layers of width 32:
+      z^l = h^l W1_l + (E h^l) W2_l + b_l,  h^{l+1} = relu(z^l),  h^0 = x.
+* Heads: u_i = h_i . ws,  d_i = softplus(h_i . wd + bd),  delta_i = d_i / c_ii,
+      s_ij = tanh(u_i + u_j + we e_ij + bs)   (symmetric by construction).
+* M on the pattern of C:  m_ii = delta_i,
+      m_ij = rho s_ij min(delta_i, delta_j) / max(deg_i, deg_j)   (i != j),
+  so sum_{j != i} |m_ij| <= rho delta_i < m_ii: M is symmetric, strictly
+  diagonally dominant with a positive diagonal, hence SPD (Gershgorin).
+* Loss (invariant to the scale of M): for pairs (r_p, t_p) and (y_q, x_q),
+      L = mean_p (1 - cos^2(M r_p, t_p)) + lam mean_q (1 - cos^2(M y_q, x_q)).
+
+Parity status: gradients pinned by central finite differences in the tests;
+the SPD property checked directly.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+WIDTH = 32
+LAYERS = 4
+RHO = 0.9
+LAM = 0.5
+
+
+def param_shapes():
+    """Ordered parameter list: (name, shape)."""
+    shapes = []
+    for l in range(LAYERS):
+        fin = 2 if l == 0 else WIDTH
+        shapes += [(f"W1_{l}", (fin, WIDTH)), (f"W2_{l}", (fin, WIDTH)), (f"b_{l}", (WIDTH,))]
+    shapes += [("ws", (WIDTH,)), ("wd", (WIDTH,)), ("we", ()), ("bs", ()), ("bd", ())]
+    return shapes
+
+
+def n_params():
+    return int(sum(int(np.prod(s)) for _, s in param_shapes()))
+
+
+def unflatten(theta):
+    out, o = {}, 0
+    for name, shp in param_shapes():
+        k = int(np.prod(shp))
+        out[name] = np.asarray(theta[o:o + k], dtype=np.float64).reshape(shp)
+        o += k
+    return out
+
+
+def flatten(params):
+    return np.concatenate([np.asarray(params[name], dtype=np.float64).ravel() for name, _ in param_shapes()])
+
+
+def init_params(seed=0):
+    """Glorot-style random initialisation (seeded)."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, shp in param_shapes():
+        if name.startswith("W"):
+            p[name] = rng.standard_normal(shp) * np.sqrt(2.0 / (shp[0] + shp[1]))
+        elif name in ("ws", "wd"):
+            p[name] = rng.standard_normal(shp) * np.sqrt(1.0 / WIDTH)
+        elif name == "bd":
+            p[name] = np.array(0.5)
+        else:
+            p[name] = np.zeros(shp)
+    return p
+
+
+class Graph:
+    """Pattern of C = A^T A with the quantities the network uses."""
+
+    def __init__(self, A):
+        A = sp.csr_matrix(A)
+        # structural pattern of A^T A (a product of 0/1 matrices cannot cancel)
+        S = sp.csr_matrix((np.ones_like(A.data), A.indices, A.indptr), shape=A.shape)
+        C = (S.T @ S).tocsr()
+        C.sort_indices()
+        rr = np.repeat(np.arange(C.shape[0]), np.diff(C.indptr))
+        C.data = np.asarray((A.T @ A).tocsr()[rr, C.indices]).ravel().astype(np.float64)
+        self.C = C
+        n = C.shape[0]
+        self.n = n
+        self.indptr = C.indptr.astype(np.int64)
+        self.indices = C.indices.astype(np.int64)
+        self.cval = C.data.astype(np.float64)
+        diag = C.diagonal().astype(np.float64)
+        diag = np.where(diag > 0, diag, 1.0)
+        self.cdiag = diag
+        self.rows = np.repeat(np.arange(n), np.diff(self.indptr))
+        self.offdiag = self.rows != self.indices
+        self.deg = np.bincount(self.rows[self.offdiag], minlength=n).astype(np.float64)
+        e = np.zeros_like(self.cval)
+        r, c = self.rows[self.offdiag], self.indices[self.offdiag]
+        e[self.offdiag] = self.cval[self.offdiag] / np.sqrt(diag[r] * diag[c])
+        self.e = e
+        self.E = sp.csr_matrix((e, self.indices, self.indptr), shape=(n, n))
+        lc = np.log(diag)
+        dmax = max(self.deg.max(), 1.0)
+        self.x0 = np.stack([lc - lc.mean(), self.deg / dmax], axis=1)
+
+
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def sigmoid(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * x))
+
+
+def forward(G: Graph, params, keep=False):
+    """Values of M on the pattern of C (same order as G.indices)."""
+    h = G.x0
+    cache = {"h": [h], "z": []}
+    for l in range(LAYERS):
+        z = h @ params[f"W1_{l}"] + (G.E @ h) @ params[f"W2_{l}"] + params[f"b_{l}"]
+        h = np.maximum(z, 0.0)
+        cache["z"].append(z)
+        cache["h"].append(h)
+    u = h @ params["ws"]
+    gpre = h @ params["wd"] + params["bd"]
+    d = softplus(gpre)
+    delta = d / G.cdiag
+    r, c = G.rows, G.indices
+    a = u[r] + u[c] + params["we"] * G.e + params["bs"]
+    s = np.tanh(a)
+    mu = np.minimum(delta[r], delta[c])
+    D = np.maximum(G.deg[r], G.deg[c])
+    D = np.where(D > 0, D, 1.0)
+    m = np.where(G.offdiag, RHO * s * mu / D, delta[r])
+    if keep:
+        cache.update(u=u, gpre=gpre, d=d, delta=delta, s=s, mu=mu, D=D)
+        return m, cache
+    return m
+
+
+def M_matrix(G: Graph, m):
+    return sp.csr_matrix((m, G.indices, G.indptr), shape=(G.n, G.n))
+
+
+def _cos2_loss_and_grad(Z, T):
+    """mean over columns of 1 - cos^2(z, t) and its gradient w.r.t. Z."""
+    zt = np.sum(Z * T, axis=0)
+    zz = np.sum(Z * Z, axis=0)
+    tt = np.sum(T * T, axis=0)
+    f = zt * zt / (zz * tt)
+    P = Z.shape[1]
+    loss = float(np.mean(1.0 - f))
+    dZ = -(2.0 * zt / (zz * tt) * T - 2.0 * zt * zt / (zz * zz * tt) * Z) / P
+    return loss, dZ
+
+
+def loss_and_grad(G: Graph, params, R, T, Y=None, X=None):
+    """Loss and gradient (dict like params) for pairs (R, T) and (Y, X)."""
+    m, cache = forward(G, params, keep=True)
+    M = M_matrix(G, m)
+    loss, dZ = _cos2_loss_and_grad(M @ R, T)
+    # dm_ij = sum_p dZ_ip R_jp
+    dm = np.einsum("kp,kp->k", dZ[G.rows], R[G.indices])
+    if Y is not None and Y.shape[1] > 0:
+        l2, dW = _cos2_loss_and_grad(M @ Y, X)
+        loss += LAM * l2
+        dm += LAM * np.einsum("kp,kp->k", dW[G.rows], Y[G.indices])
+    return loss, backward(G, params, cache, dm)
+
+
+def backward(G: Graph, params, cache, dm):
+    r, c = G.rows, G.indices
+    off = G.offdiag
+    s, mu, D, delta = cache["s"], cache["mu"], cache["D"], cache["delta"]
+    n = G.n
+    ddelta = np.zeros(n)
+    np.add.at(ddelta, r[~off], dm[~off])
+    ds = np.where(off, dm * RHO * mu / D, 0.0)
+    dmu = np.where(off, dm * RHO * s / D, 0.0)
+    # min(delta_i, delta_j): the gradient goes to the smaller (ties: the lower index)
+    to_i = (delta[r] < delta[c]) | ((delta[r] == delta[c]) & (r < c))
+    np.add.at(ddelta, r[off & to_i], dmu[off & to_i])
+    np.add.at(ddelta, c[off & ~to_i], dmu[off & ~to_i])
+    da = ds * (1.0 - s * s)
+    du = np.zeros(n)
+    np.add.at(du, r, da)
+    np.add.at(du, c, da)
+    grads = {}
+    grads["we"] = np.array(np.sum(da * G.e))
+    grads["bs"] = np.array(np.sum(da))
+    dd = ddelta / G.cdiag
+    dg = dd * sigmoid(cache["gpre"])
+    h = cache["h"][LAYERS]
+    grads["wd"] = h.T @ dg
+    grads["bd"] = np.array(np.sum(dg))
+    grads["ws"] = h.T @ du
+    dh = np.outer(dg, params["wd"]) + np.outer(du, params["ws"])
+    for l in range(LAYERS - 1, -1, -1):
+        z = cache["z"][l]
+        hl = cache["h"][l]
+        dz = dh * (z > 0)
+        Eh = G.E @ hl
+        grads[f"W1_{l}"] = hl.T @ dz
+        grads[f"W2_{l}"] = Eh.T @ dz
+        grads[f"b_{l}"] = dz.sum(axis=0)
+        dh = dz @ params[f"W1_{l}"].T + G.E.T @ (dz @ params[f"W2_{l}"].T)
+    return grads

@@ -104,6 +104,17 @@ _SIGS = {
     "phsvds_coef_convert": (C.c_int, [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "phsvds_host_symeig": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_host_svd": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    # learned preconditioner (phsvds_gnn.h)
+    "phsvds_gnn_num_params": (C.c_int, []),
+    "phsvds_gnn_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(svds_csr), C.c_void_p]),
+    "phsvds_gnn_destroy": (None, [C.c_void_p]),
+    "phsvds_gnn_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "phsvds_gnn_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_gnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_gnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                       C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "phsvds_gnn_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.c_float]),
 }
 
 
@@ -337,3 +348,77 @@ def host_svd(R: np.ndarray):
     Y = np.zeros((n, n), order="F")
     _check(lib().phsvds_host_svd(n, R.ctypes.data, s.ctypes.data, Y.ctypes.data), "phsvds_host_svd")
     return s, Y
+
+
+# ---- learned preconditioner ----
+def gnn_num_params() -> int:
+    return int(lib().phsvds_gnn_num_params())
+
+
+class Gnn:
+    """Graph of C = A^T A on the device plus the network's forward/backward
+    (argument marshalling only; every step runs in libphsvds.so)."""
+
+    def __init__(self, rowptr, colidx, vals, m: int, n: int, stream=None):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        A = svds_csr(m, n, int(colidx.shape[0]), rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data, 0)
+        self.ptr = C.c_void_p()
+        _check(lib().phsvds_gnn_create(C.byref(self.ptr), C.byref(A), stream), "phsvds_gnn_create")
+        nn, nz = C.c_int64(), C.c_int64()
+        _check(lib().phsvds_gnn_shape(self.ptr, C.byref(nn), C.byref(nz)), "phsvds_gnn_shape")
+        self.n, self.nnz = nn.value, nz.value
+        self.np = gnn_num_params()
+
+    def close(self):
+        if self.ptr:
+            lib().phsvds_gnn_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pattern(self):
+        rp = np.zeros(self.n + 1, dtype=np.int32)
+        ci = np.zeros(self.nnz, dtype=np.int32)
+        _check(lib().phsvds_gnn_pattern(self.ptr, rp.ctypes.data, ci.ctypes.data), "phsvds_gnn_pattern")
+        return rp, ci
+
+    def _params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.shape != (self.np,):
+            raise ValueError(f"expected {self.np} parameters")
+        return theta
+
+    def forward(self, theta) -> np.ndarray:
+        theta = self._params(theta)
+        m = np.zeros(self.nnz, dtype=np.float32)
+        _check(lib().phsvds_gnn_forward(self.ptr, theta.ctypes.data, m.ctypes.data), "phsvds_gnn_forward")
+        return m
+
+    def loss_grad(self, theta, R, T, Y=None, X=None):
+        theta = self._params(theta)
+        R = np.asfortranarray(R, dtype=np.float64)
+        T = np.asfortranarray(T, dtype=np.float64)
+        q = 0 if Y is None else Y.shape[1]
+        Yf = np.asfortranarray(Y, dtype=np.float64) if q else None
+        Xf = np.asfortranarray(X, dtype=np.float64) if q else None
+        loss = C.c_double(0.0)
+        grad = np.zeros(self.np)
+        rc = lib().phsvds_gnn_loss_grad(self.ptr, theta.ctypes.data, R.ctypes.data, T.ctypes.data, R.shape[1],
+                                        Yf.ctypes.data if q else None, Xf.ctypes.data if q else None, q,
+                                        C.byref(loss), grad.ctypes.data)
+        _check(rc, "phsvds_gnn_loss_grad")
+        return loss.value, grad
+
+    def adam(self, theta, grad, m, v, step: int, lr: float):
+        """In-place Adam step on float32 arrays theta, m, v."""
+        grad = np.ascontiguousarray(grad, dtype=np.float64)
+        for a in (theta, m, v):
+            assert a.dtype == np.float32 and a.flags.c_contiguous and a.shape == (self.np,)
+        _check(lib().phsvds_gnn_adam(self.ptr, theta.ctypes.data, grad.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                     step, lr), "phsvds_gnn_adam")

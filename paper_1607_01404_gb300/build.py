@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphsvds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "tiled.cu", "engine.cpp", "hostla.cpp", "api.cpp", "noalloc.cu", "jdqmr.cu"]
+SOURCES = ["kernels.cu", "tiled.cu", "engine.cpp", "hostla.cpp", "api.cpp", "noalloc.cu", "jdqmr.cu", "gnn.cu"]
 
 
 def nvcc() -> str:
@@ -30,8 +30,6 @@ def _compile(src: str) -> str:
     obj = os.path.join(BUILD, src + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-c",
            os.path.join(CSRC, src), "-o", obj]
-    if src.endswith(".cpp"):
-        cmd[1:1] = ["-x", "cu"] if False else []
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -42,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    hdrs += [os.path.join(HERE, "..", "include", f) for f in ("phsvds.h", "phsvds_kernels.h")]
+    hdrs += [os.path.join(HERE, "..", "include", f) for f in ("phsvds.h", "phsvds_kernels.h", "phsvds_gnn.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(f) < t for f in srcs + hdrs + [__file__]):

@@ -1,0 +1,769 @@
+// Learned sparse-approximate-inverse preconditioner: graph of C = A^T A,
+// forward and backward kernels of the message-passing network, Adam.  The
+// network and the loss are described in include/phsvds_gnn.h.  Node features
+// are FP32; all reductions (weight gradients, loss dots) go through the
+// FP64-class Gram kernel with a fixed summation order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/phsvds.h"
+#include "../../include/phsvds_gnn.h"
+#include "common.cuh"
+#include "engine.h"
+#include "kernels.h"
+
+namespace phsvds {
+
+namespace {
+
+constexpr int kW = 32;      // width
+constexpr int kLayers = 4;
+constexpr float kRho = 0.9f;
+constexpr double kLam = 0.5;
+constexpr int kT = 256;
+constexpr int kMaxMerge = 64;  // rows of A^T longer than this are not supported for the graph
+
+int grid1(long long n) {
+  long long g = (n + kT - 1) / kT;
+  if (g < 1) g = 1;
+  if (g > 152LL * 16) g = 152LL * 16;
+  return (int)g;
+}
+
+// ---- graph of C = A^T A ----------------------------------------------------
+// Row j of C merges the sorted rows i of A with a_ij != 0 (the entries of row j
+// of A^T); count = number of distinct columns.
+__global__ void k_c_count(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
+                          const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ cnt,
+                          int* __restrict__ err) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
+    if (nl > kMaxMerge) {
+      atomicOr(err, 1);
+      cnt[j] = 0;
+      continue;
+    }
+    int cur[kMaxMerge], end[kMaxMerge];
+    for (int t = 0; t < nl; ++t) {
+      const int i = ciT[t0 + t];
+      cur[t] = rp[i];
+      end[t] = rp[i + 1];
+    }
+    int count = 0;
+    while (true) {
+      int mn = 0x7fffffff;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
+      if (mn == 0x7fffffff) break;
+      ++count;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] == mn) ++cur[t];
+    }
+    cnt[j] = count;
+  }
+}
+
+__global__ void k_c_fill(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
+                         const double* __restrict__ vT, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const double* __restrict__ va, double unscale, const int* __restrict__ cptr,
+                         int* __restrict__ cidx, double* __restrict__ cval) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
+    if (nl > kMaxMerge) continue;
+    int cur[kMaxMerge], end[kMaxMerge];
+    for (int t = 0; t < nl; ++t) {
+      const int i = ciT[t0 + t];
+      cur[t] = rp[i];
+      end[t] = rp[i + 1];
+    }
+    int o = cptr[j];
+    while (true) {
+      int mn = 0x7fffffff;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
+      if (mn == 0x7fffffff) break;
+      double v = 0.0;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] == mn) {
+          v += vT[t0 + t] * va[cur[t]];  // a_{i j} a_{i mn}
+          ++cur[t];
+        }
+      cidx[o] = mn;
+      cval[o] = v * unscale;
+      ++o;
+    }
+  }
+}
+
+__global__ void k_diag_deg(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                           const double* __restrict__ cval, double* __restrict__ cdiag, float* __restrict__ deg,
+                           int* __restrict__ degmax) {
+  int dm = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    int k = 0;
+    for (int p = cptr[i]; p < cptr[i + 1]; ++p) {
+      if (cidx[p] == i)
+        d = cval[p];
+      else
+        ++k;
+    }
+    cdiag[i] = d > 0 ? d : 1.0;
+    deg[i] = (float)k;
+    dm = k > dm ? k : dm;
+  }
+  atomicMax(degmax, dm);
+}
+
+__global__ void k_edges(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                        const double* __restrict__ cval, const double* __restrict__ cdiag, float* __restrict__ e,
+                        int* __restrict__ tpos, float* __restrict__ logc) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    logc[i] = (float)log(cdiag[i]);
+    for (int p = cptr[i]; p < cptr[i + 1]; ++p) {
+      const int j = cidx[p];
+      e[p] = j == i ? 0.f : (float)(cval[p] / sqrt(cdiag[i] * cdiag[j]));
+      // position of (j, i): binary search in the sorted row j
+      int lo = cptr[j], hi = cptr[j + 1] - 1, pos = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int c = cidx[mid];
+        if (c == i) {
+          pos = mid;
+          break;
+        }
+        if (c < i)
+          lo = mid + 1;
+        else
+          hi = mid - 1;
+      }
+      tpos[p] = pos >= 0 ? pos : p;
+    }
+  }
+}
+
+__global__ void k_x0(long long n, const float* __restrict__ logc, const float* __restrict__ deg, float logmean,
+                     float degmax, float* __restrict__ x0) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x0[2 * i] = logc[i] - logmean;
+    x0[2 * i + 1] = deg[i] / degmax;
+  }
+}
+
+// ---- forward ----------------------------------------------------------------
+// z = h W1 + Eh W2 + b, hout = relu(z); one thread per row, weights in shared memory.
+template <int FIN>
+__global__ void __launch_bounds__(kT) k_layer_fwd(long long n, const float* __restrict__ h,
+                                                  const float* __restrict__ Eh, const float* __restrict__ W1,
+                                                  const float* __restrict__ W2, const float* __restrict__ b,
+                                                  float* __restrict__ z, float* __restrict__ hout) {
+  __shared__ float w1[FIN * kW], w2[FIN * kW], bb[kW];
+  for (int e = threadIdx.x; e < FIN * kW; e += blockDim.x) {
+    w1[e] = W1[e];
+    w2[e] = W2[e];
+  }
+  if (threadIdx.x < kW) bb[threadIdx.x] = b[threadIdx.x];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float acc[kW];
+#pragma unroll
+    for (int j = 0; j < kW; ++j) acc[j] = bb[j];
+    for (int c = 0; c < FIN; ++c) {
+      const float hv = h[i * FIN + c], ev = Eh[i * FIN + c];
+#pragma unroll
+      for (int j = 0; j < kW; ++j) acc[j] = fmaf(hv, w1[c * kW + j], fmaf(ev, w2[c * kW + j], acc[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+      z[i * kW + j] = acc[j];
+      hout[i * kW + j] = fmaxf(acc[j], 0.f);
+    }
+  }
+}
+
+__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
+
+__global__ void k_heads_node(long long n, const float* __restrict__ h, const float* __restrict__ ws,
+                             const float* __restrict__ wd, const float* __restrict__ bd,
+                             const double* __restrict__ cdiag, float* __restrict__ u, float* __restrict__ gpre,
+                             float* __restrict__ delta) {
+  __shared__ float sws[kW], swd[kW];
+  if (threadIdx.x < kW) {
+    sws[threadIdx.x] = ws[threadIdx.x];
+    swd[threadIdx.x] = wd[threadIdx.x];
+  }
+  __syncthreads();
+  const float b = *bd;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float a = 0.f, g = b;
+#pragma unroll
+    for (int c = 0; c < kW; ++c) {
+      a = fmaf(h[i * kW + c], sws[c], a);
+      g = fmaf(h[i * kW + c], swd[c], g);
+    }
+    u[i] = a;
+    gpre[i] = g;
+    delta[i] = (float)(softplusf(g) / cdiag[i]);
+  }
+}
+
+__global__ void k_heads_edge(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                             const float* __restrict__ e, const float* __restrict__ u, const float* __restrict__ delta,
+                             const float* __restrict__ deg, const float* __restrict__ we, const float* __restrict__ bs,
+                             float* __restrict__ s, float* __restrict__ m) {
+  const float w = *we, b = *bs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    for (int p = cptr[i]; p < cptr[i + 1]; ++p) {
+      const int j = cidx[p];
+      if (j == i) {
+        s[p] = 0.f;
+        m[p] = delta[i];
+      } else {
+        const float sv = tanhf(u[i] + u[j] + w * e[p] + b);
+        const float mu = fminf(delta[i], delta[j]);
+        const float D = fmaxf(fmaxf(deg[i], deg[j]), 1.f);
+        s[p] = sv;
+        m[p] = kRho * sv * mu / D;
+      }
+    }
+  }
+}
+
+// ---- backward ---------------------------------------------------------------
+__global__ void k_lin_comb(long long total, const float* __restrict__ a, const float* __restrict__ b,
+                           const double* __restrict__ ca, const double* __restrict__ cb, int P,
+                           float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e % P);
+    out[e] = (float)(ca[p] * (double)a[e] + cb[p] * (double)b[e]);
+  }
+}
+
+// dm[k] (+)= scale * sum_p dZ[i, p] R[j, p] for entry k = (i, j)
+__global__ void k_dm(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                     const float* __restrict__ dZ, const float* __restrict__ R, int P, float scale, int accumulate,
+                     float* __restrict__ dm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    for (int k = cptr[i]; k < cptr[i + 1]; ++k) {
+      const int j = cidx[k];
+      float acc = 0.f;
+      for (int p = 0; p < P; ++p) acc = fmaf(dZ[i * P + p], R[(long long)j * P + p], acc);
+      dm[k] = accumulate ? dm[k] + scale * acc : scale * acc;
+    }
+  }
+}
+
+// heads backward per row: ddelta_i, du_i; per-entry da_k = dm_k rho mu / D (1 - s^2)
+// for the we / bs gradients (written to da and dae = da * e).
+__global__ void k_heads_bwd(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                            const int* __restrict__ tpos, const float* __restrict__ dm, const float* __restrict__ s,
+                            const float* __restrict__ delta, const float* __restrict__ deg,
+                            const float* __restrict__ e, float* __restrict__ ddelta, float* __restrict__ du,
+                            float* __restrict__ da, float* __restrict__ dae) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float dd = 0.f, duu = 0.f;
+    for (int k = cptr[i]; k < cptr[i + 1]; ++k) {
+      const int j = cidx[k];
+      if (j == i) {
+        dd += dm[k];
+        da[k] = 0.f;
+        dae[k] = 0.f;
+        continue;
+      }
+      const float di = delta[i], dj = delta[j];
+      const float mu = fminf(di, dj);
+      const float D = fmaxf(fmaxf(deg[i], deg[j]), 1.f);
+      const float sv = s[k];
+      const float dpair = dm[k] + dm[tpos[k]];
+      const float t = 1.f - sv * sv;
+      duu += dpair * kRho * mu / D * t;
+      const bool to_i = (di < dj) || (di == dj && i < j);
+      if (to_i) dd += dpair * kRho * sv / D;
+      const float dak = dm[k] * kRho * mu / D * t;
+      da[k] = dak;
+      dae[k] = dak * e[k];
+    }
+    ddelta[i] = dd;
+    du[i] = duu;
+  }
+}
+
+// dg = ddelta / c_ii * sigmoid(gpre); dh[i, c] = dg wd[c] + du ws[c]; gu = [dg, du]
+__global__ void k_node_bwd(long long n, const float* __restrict__ ddelta, const float* __restrict__ du,
+                           const float* __restrict__ gpre, const double* __restrict__ cdiag,
+                           const float* __restrict__ ws, const float* __restrict__ wd, float* __restrict__ gu,
+                           float* __restrict__ dh) {
+  __shared__ float sws[kW], swd[kW];
+  if (threadIdx.x < kW) {
+    sws[threadIdx.x] = ws[threadIdx.x];
+    swd[threadIdx.x] = wd[threadIdx.x];
+  }
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float dg = (float)(ddelta[i] / cdiag[i]) * sigmoidf_(gpre[i]);
+    const float dv = du[i];
+    gu[2 * i] = dg;
+    gu[2 * i + 1] = dv;
+#pragma unroll
+    for (int c = 0; c < kW; ++c) dh[i * kW + c] = dg * swd[c] + dv * sws[c];
+  }
+}
+
+__global__ void k_relu_bwd(long long total, const float* __restrict__ z, const float* __restrict__ dh,
+                           float* __restrict__ dz) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    dz[e] = z[e] > 0.f ? dh[e] : 0.f;
+}
+
+// out[i, c] = (add ? add[i, c] : 0) + sum_j dz[i, j] W[c, j]   (W: FOUT x 32, i.e. dz W^T)
+template <int FOUT>
+__global__ void __launch_bounds__(kT) k_rowmat_t(long long n, const float* __restrict__ dz, const float* __restrict__ W,
+                                                 const float* __restrict__ add, float* __restrict__ out) {
+  __shared__ float w[FOUT * kW];
+  for (int e = threadIdx.x; e < FOUT * kW; e += blockDim.x) w[e] = W[e];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float d[kW];
+#pragma unroll
+    for (int j = 0; j < kW; ++j) d[j] = dz[i * kW + j];
+    for (int c = 0; c < FOUT; ++c) {
+      float acc = add ? add[i * FOUT + c] : 0.f;
+#pragma unroll
+      for (int j = 0; j < kW; ++j) acc = fmaf(d[j], w[c * kW + j], acc);
+      out[i * FOUT + c] = acc;
+    }
+  }
+}
+
+__global__ void k_fill1(long long n, float* __restrict__ x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = 1.f;
+}
+
+__global__ void k_adam(int np, float* __restrict__ p, const double* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const float gi = (float)g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+struct Offsets {
+  int W1[kLayers], W2[kLayers], b[kLayers], ws, wd, we, bs, bd, total;
+  Offsets() {
+    int o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      const int fin = l == 0 ? 2 : kW;
+      W1[l] = o;
+      o += fin * kW;
+      W2[l] = o;
+      o += fin * kW;
+      b[l] = o;
+      o += kW;
+    }
+    ws = o;
+    o += kW;
+    wd = o;
+    o += kW;
+    we = o++;
+    bs = o++;
+    bd = o++;
+    total = o;
+  }
+};
+
+}  // namespace
+}  // namespace phsvds
+
+using namespace phsvds;
+
+struct phsvds_gnn {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  long long n = 0, nnz = 0;
+  std::vector<void*> allocs;
+  int *cptr = nullptr, *cidx = nullptr, *tpos = nullptr;
+  double *cval = nullptr, *cdiag = nullptr;
+  float *deg = nullptr, *e = nullptr, *x0 = nullptr, *logc = nullptr;
+  float* prm = nullptr;  // device parameters
+  float* h[kLayers + 1] = {};
+  float* Eh[kLayers] = {};
+  float* z[kLayers] = {};
+  float *u = nullptr, *gpre = nullptr, *delta = nullptr, *s = nullptr, *m = nullptr;
+  float *dm = nullptr, *da = nullptr, *dae = nullptr, *ddelta = nullptr, *du = nullptr, *gu = nullptr;
+  float *dh = nullptr, *dz = nullptr, *tmp = nullptr, *tmp2 = nullptr, *ones = nullptr;
+  float *R = nullptr, *T = nullptr, *Z = nullptr, *dZ = nullptr;
+  double *dcoef = nullptr, *dG = nullptr, *dstage = nullptr, *grad = nullptr;
+  float *am = nullptr, *av = nullptr;
+  void* partial = nullptr;
+  int cap_pairs = 0;
+  Offsets off;
+};
+
+namespace {
+
+int gfail(cudaError_t e, const char* where) {
+  phsvds::set_last_error(std::string(cudaGetErrorString(e)) + " at " + where);
+  cudaGetLastError();
+  return SVDS_ERR_CUDA;
+}
+#define GK(x)                                    \
+  do {                                           \
+    cudaError_t _e = (x);                        \
+    if (_e != cudaSuccess) return gfail(_e, #x); \
+  } while (0)
+
+template <class T>
+int galloc(phsvds_gnn* g, T** p, size_t count) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    return SVDS_ERR_NOMEM;
+  }
+  g->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return 0;
+}
+
+CsrDev Ecsr(const phsvds_gnn* g, const float* vals) {
+  CsrDev c;
+  c.rows = g->n;
+  c.cols = g->n;
+  c.nnz = g->nnz;
+  c.rowptr = g->cptr;
+  c.colidx = g->cidx;
+  c.v32 = vals;
+  return c;
+}
+
+// G (p x q row-major, host) = P^T Q over all rows (FP64-class accumulation)
+int gram_host(phsvds_gnn* g, const float* P, int p, const float* Q, int ldq, int q0, int q, std::vector<double>& out) {
+  out.assign((size_t)p * q, 0.0);
+  for (int c0 = 0; c0 < q; c0 += 8) {
+    const int qc = q - c0 < 8 ? q - c0 : 8;
+    SegV Ps{P, p, p};
+    SegV Qs{Q + q0 + c0, ldq, qc};
+    int nb = 0;
+    GK(launch_gram(kF32, 0, g->n, &Ps, 1, Qs, g->partial, gram_default_blocks(), &nb, g->st));
+    GK(launch_gram_reduce(kF32, g->partial, nb, p * qc, g->dG, g->st));
+    std::vector<double> h((size_t)p * qc);
+    GK(cudaMemcpyAsync(h.data(), g->dG, sizeof(double) * p * qc, cudaMemcpyDeviceToHost, g->st));
+    GK(cudaStreamSynchronize(g->st));
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < qc; ++j) out[(size_t)i * q + c0 + j] = h[(size_t)i * qc + j];
+  }
+  return 0;
+}
+
+int forward_impl(phsvds_gnn* g, const float* params_host) {
+  const Offsets& o = g->off;
+  GK(cudaMemcpyAsync(g->prm, params_host, sizeof(float) * o.total, cudaMemcpyHostToDevice, g->st));
+  const long long n = g->n;
+  const int gr = grid1(n);
+  for (int l = 0; l < kLayers; ++l) {
+    const int fin = l == 0 ? 2 : kW;
+    GK(launch_spmm(kF32, Ecsr(g, g->e), g->h[l], fin, g->Eh[l], fin, fin, g->st));
+    if (l == 0)
+      k_layer_fwd<2><<<gr, kT, 0, g->st>>>(n, g->h[l], g->Eh[l], g->prm + o.W1[l], g->prm + o.W2[l], g->prm + o.b[l],
+                                           g->z[l], g->h[l + 1]);
+    else
+      k_layer_fwd<kW><<<gr, kT, 0, g->st>>>(n, g->h[l], g->Eh[l], g->prm + o.W1[l], g->prm + o.W2[l],
+                                            g->prm + o.b[l], g->z[l], g->h[l + 1]);
+  }
+  k_heads_node<<<gr, kT, 0, g->st>>>(n, g->h[kLayers], g->prm + o.ws, g->prm + o.wd, g->prm + o.bd, g->cdiag, g->u,
+                                     g->gpre, g->delta);
+  k_heads_edge<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->e, g->u, g->delta, g->deg, g->prm + o.we,
+                                     g->prm + o.bs, g->s, g->m);
+  GK(cudaGetLastError());
+  return 0;
+}
+
+int ensure_pairs(phsvds_gnn* g, int P) {
+  if (P <= g->cap_pairs) return 0;
+  int rc;
+  const size_t cnt = (size_t)g->n * P;
+  if ((rc = galloc(g, &g->R, cnt)) || (rc = galloc(g, &g->T, cnt)) || (rc = galloc(g, &g->Z, cnt)) ||
+      (rc = galloc(g, &g->dZ, cnt)))
+    return rc;
+  g->cap_pairs = P;
+  return 0;
+}
+
+// loss term mean(1 - cos^2(M R, T)) for P <= 8 pairs; adds scale * dL/dm to g->dm
+int pair_term(phsvds_gnn* g, const double* Rh, const double* Th, int P, double scale, int accumulate, double* loss) {
+  const long long n = g->n;
+  double* dtmp = g->dstage;
+  GK(cudaMemcpyAsync(dtmp, Rh, sizeof(double) * n * P, cudaMemcpyHostToDevice, g->st));
+  GK(launch_from_f64_colmajor(kF32, n, P, dtmp, n, g->R, P, 1.0, g->st));
+  GK(cudaMemcpyAsync(dtmp, Th, sizeof(double) * n * P, cudaMemcpyHostToDevice, g->st));
+  GK(launch_from_f64_colmajor(kF32, n, P, dtmp, n, g->T, P, 1.0, g->st));
+  GK(launch_spmm(kF32, Ecsr(g, g->m), g->R, P, g->Z, P, P, g->st));
+  std::vector<double> zt, zz, tt;
+  int rc;
+  if ((rc = gram_host(g, g->Z, P, g->T, P, 0, P, zt)) || (rc = gram_host(g, g->Z, P, g->Z, P, 0, P, zz)) ||
+      (rc = gram_host(g, g->T, P, g->T, P, 0, P, tt)))
+    return rc;
+  std::vector<double> ca(P), cb(P);
+  double L = 0.0;
+  for (int p = 0; p < P; ++p) {
+    const double a = zt[(size_t)p * P + p], b = zz[(size_t)p * P + p], c = tt[(size_t)p * P + p];
+    const double f = a * a / (b * c);
+    L += 1.0 - f;
+    // d/dZ of mean(1 - f): -(2 a / (b c) T - 2 a^2 / (b^2 c) Z) / P
+    ca[p] = -scale * (2.0 * a / (b * c)) / P;
+    cb[p] = scale * (2.0 * a * a / (b * b * c)) / P;
+  }
+  *loss += scale * L / P;
+  std::vector<double> cc(2 * P);
+  for (int p = 0; p < P; ++p) {
+    cc[p] = ca[p];
+    cc[P + p] = cb[p];
+  }
+  GK(cudaMemcpyAsync(g->dcoef, cc.data(), sizeof(double) * 2 * P, cudaMemcpyHostToDevice, g->st));
+  k_lin_comb<<<grid1(n * P), kT, 0, g->st>>>(n * P, g->T, g->Z, g->dcoef, g->dcoef + P, P, g->dZ);
+  k_dm<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, g->dZ, g->R, P, 1.0f, accumulate, g->dm);
+  GK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int phsvds_gnn_num_params(void) { return Offsets().total; }
+
+int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
+  if (!out || !A || A->m < 1 || A->n < 1 || A->nnz < 0 || !A->rowptr) return SVDS_ERR_ARG;
+  *out = nullptr;
+  // the device copy, transpose and validation of svds_create are reused
+  svds_opts o;
+  svds_opts_default(&o);
+  o.stream = stream;
+  svds_handle* h = nullptr;
+  int rc = svds_create(&h, A, &o);
+  if (rc) return rc;
+  phsvds_gnn* g = new phsvds_gnn();
+  g->st = h->stream;
+  const DevMatrix& D = h->A;
+  // nodes = columns of the user's matrix
+  const bool tr = D.transposed;
+  const long long n = tr ? D.m : D.n;
+  const int* rp = tr ? D.rowptrT : D.rowptr;   // rows of the user's A
+  const int* ci = tr ? D.colidxT : D.colidx;
+  const int* rpT = tr ? D.rowptr : D.rowptrT;  // rows of the user's A^T
+  const int* ciT = tr ? D.colidx : D.colidxT;
+  const double* va = tr ? D.v64T : D.v64;
+  const double* vT = tr ? D.v64 : D.v64T;
+  g->n = n;
+  int *cnt = nullptr, *err = nullptr, *work = nullptr, *dmax = nullptr;
+  auto fail = [&](int code) {
+    for (void* p : g->allocs) cudaFree(p);
+    delete g;
+    svds_destroy(h);
+    return code;
+  };
+  if ((rc = galloc(g, &g->cptr, n + 1)) || (rc = galloc(g, &cnt, n + 1)) || (rc = galloc(g, &err, 4)) ||
+      (rc = galloc(g, &work, scan_work_ints(n) + 4)) || (rc = galloc(g, &dmax, 4)))
+    return fail(rc);
+  cudaStream_t st = g->st;
+  if (cudaMemsetAsync(err, 0, 4 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(dmax, 0, 4 * sizeof(int), st) != cudaSuccess)
+    return fail(gfail(cudaGetLastError(), "memset"));
+  k_c_count<<<grid1(n), kT, 0, st>>>(n, rpT, ciT, rp, ci, cnt, err);
+  if (launch_exclusive_scan(n, cnt, g->cptr, work, st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "scan"));
+  int herr = 0, hnnz = 0;
+  cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&hnnz, g->cptr + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph count"));
+  if (herr) {
+    phsvds::set_last_error("phsvds_gnn_create: a column of A has more than 64 nonzeros");
+    return fail(SVDS_ERR_SHAPE);
+  }
+  g->nnz = hnnz;
+  const long long nnz = hnnz;
+  if ((rc = galloc(g, &g->cidx, nnz)) || (rc = galloc(g, &g->cval, nnz)) || (rc = galloc(g, &g->cdiag, n)) ||
+      (rc = galloc(g, &g->deg, n)) || (rc = galloc(g, &g->e, nnz)) || (rc = galloc(g, &g->tpos, nnz)) ||
+      (rc = galloc(g, &g->logc, n)) || (rc = galloc(g, &g->prm, g->off.total)) ||
+      (rc = galloc(g, &g->u, n)) || (rc = galloc(g, &g->gpre, n)) || (rc = galloc(g, &g->delta, n)) ||
+      (rc = galloc(g, &g->s, nnz)) || (rc = galloc(g, &g->m, nnz)) || (rc = galloc(g, &g->dm, nnz)) ||
+      (rc = galloc(g, &g->da, nnz)) || (rc = galloc(g, &g->dae, nnz)) || (rc = galloc(g, &g->ddelta, n)) ||
+      (rc = galloc(g, &g->du, n)) || (rc = galloc(g, &g->gu, 2 * n)) || (rc = galloc(g, &g->dh, n * kW)) ||
+      (rc = galloc(g, &g->dz, n * kW)) || (rc = galloc(g, &g->tmp, n * kW)) || (rc = galloc(g, &g->tmp2, n * kW)) ||
+      (rc = galloc(g, &g->ones, n > nnz ? n : nnz)) || (rc = galloc(g, &g->dcoef, 64)) || (rc = galloc(g, &g->dG, 64 * 64)) ||
+      (rc = galloc(g, &g->dstage, n * 8)) || (rc = galloc(g, &g->grad, g->off.total)) ||
+      (rc = galloc(g, &g->am, g->off.total)) || (rc = galloc(g, &g->av, g->off.total)))
+    return fail(rc);
+  if ((rc = galloc(g, reinterpret_cast<char**>(&g->partial), gram_partial_bytes(gram_default_blocks(), kW, 8))))
+    return fail(rc);
+  g->h[0] = nullptr;
+  if ((rc = galloc(g, &g->x0, 2 * n))) return fail(rc);
+  g->h[0] = g->x0;
+  for (int l = 0; l < kLayers; ++l) {
+    const int fin = l == 0 ? 2 : kW;
+    if ((rc = galloc(g, &g->Eh[l], n * fin)) || (rc = galloc(g, &g->z[l], n * kW)) ||
+        (rc = galloc(g, &g->h[l + 1], n * kW)))
+      return fail(rc);
+  }
+  // device values are scale * A (a power of two): C in the user's units is exact
+  k_c_fill<<<grid1(n), kT, 0, st>>>(n, rpT, ciT, vT, rp, ci, va, 1.0 / (D.scale * D.scale), g->cptr, g->cidx,
+                                    g->cval);
+  k_diag_deg<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->deg, dmax);
+  k_edges<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->e, g->tpos, g->logc);
+  k_fill1<<<grid1(n > nnz ? n : nnz), kT, 0, st>>>(n > nnz ? n : nnz, g->ones);
+  if (cudaGetLastError() != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph kernels"));
+  // mean of log c_ii (FP64-class Gram of the ones vector with log c)
+  {
+    SegV Ps{g->ones, 1, 1}, Qs{g->logc, 1, 1};
+    int nb = 0;
+    launch_gram(kF32, 0, n, &Ps, 1, Qs, g->partial, gram_default_blocks(), &nb, st);
+    launch_gram_reduce(kF32, g->partial, nb, 1, g->dG, st);
+  }
+  double hsum = 0;
+  int hdmax = 0;
+  cudaMemcpyAsync(&hsum, g->dG, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&hdmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph features"));
+  k_x0<<<grid1(n), kT, 0, st>>>(n, g->logc, g->deg, (float)(hsum / n), (float)(hdmax > 0 ? hdmax : 1), g->x0);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph x0"));
+  // the graph keeps its own copy; the temporary solver handle is released
+  if (h->own_stream) {
+    cudaStream_t s2;
+    cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    g->st = s2;
+    g->own_stream = true;
+  }
+  svds_destroy(h);
+  *out = g;
+  return SVDS_OK;
+}
+
+void phsvds_gnn_destroy(phsvds_gnn* g) {
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  for (void* p : g->allocs) cudaFree(p);
+  if (g->own_stream) cudaStreamDestroy(g->st);
+  delete g;
+}
+
+int phsvds_gnn_shape(const phsvds_gnn* g, int64_t* n, int64_t* nnz) {
+  if (!g || !n || !nnz) return SVDS_ERR_ARG;
+  *n = g->n;
+  *nnz = g->nnz;
+  return SVDS_OK;
+}
+
+int phsvds_gnn_pattern(const phsvds_gnn* g, int32_t* rowptr, int32_t* colidx) {
+  if (!g || !rowptr || !colidx) return SVDS_ERR_ARG;
+  GK(cudaMemcpyAsync(rowptr, g->cptr, sizeof(int) * (g->n + 1), cudaMemcpyDeviceToHost, g->st));
+  GK(cudaMemcpyAsync(colidx, g->cidx, sizeof(int) * g->nnz, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaStreamSynchronize(g->st));
+  return SVDS_OK;
+}
+
+int phsvds_gnn_forward(phsvds_gnn* g, const float* params, float* mvals) {
+  if (!g || !params) return SVDS_ERR_ARG;
+  int rc = forward_impl(g, params);
+  if (rc) return rc;
+  if (mvals) GK(cudaMemcpyAsync(mvals, g->m, sizeof(float) * g->nnz, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaStreamSynchronize(g->st));
+  return SVDS_OK;
+}
+
+int phsvds_gnn_loss_grad(phsvds_gnn* g, const float* params, const double* R, const double* T, int P,
+                         const double* Y, const double* X, int Q, double* loss, double* grad) {
+  if (!g || !params || !R || !T || P < 1 || P > 8 || Q < 0 || Q > 8 || (Q > 0 && (!Y || !X)) || !loss || !grad)
+    return SVDS_ERR_ARG;
+  const Offsets& o = g->off;
+  const long long n = g->n;
+  const int gr = grid1(n);
+  int rc = forward_impl(g, params);
+  if (rc) return rc;
+  if ((rc = ensure_pairs(g, P > Q ? P : Q))) return rc;
+  double L = 0.0;
+  if ((rc = pair_term(g, R, T, P, 1.0, 0, &L))) return rc;
+  if (Q > 0 && (rc = pair_term(g, Y, X, Q, kLam, 1, &L))) return rc;
+  std::vector<double> gr_h(o.total, 0.0);
+  // heads
+  k_heads_bwd<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->tpos, g->dm, g->s, g->delta, g->deg, g->e, g->ddelta,
+                                    g->du, g->da, g->dae);
+  k_node_bwd<<<gr, kT, 0, g->st>>>(n, g->ddelta, g->du, g->gpre, g->cdiag, g->prm + o.ws, g->prm + o.wd, g->gu,
+                                   g->dh);
+  GK(cudaGetLastError());
+  std::vector<double> G;
+  // we, bs: sums over the entries of the pattern, against the ones vector (length >= nnz)
+  {
+    SegV Ps{g->ones, 1, 1};
+    for (int w = 0; w < 2; ++w) {
+      SegV Qs{w == 0 ? g->dae : g->da, 1, 1};
+      int nb = 0;
+      GK(launch_gram(kF32, 0, g->nnz, &Ps, 1, Qs, g->partial, gram_default_blocks(), &nb, g->st));
+      GK(launch_gram_reduce(kF32, g->partial, nb, 1, g->dG + w, g->st));
+    }
+    double hv[2];
+    GK(cudaMemcpyAsync(hv, g->dG, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->st));
+    GK(cudaStreamSynchronize(g->st));
+    gr_h[o.we] = hv[0];
+    gr_h[o.bs] = hv[1];
+  }
+  // wd, ws from h4^T [dg du]; bd = sum dg
+  if ((rc = gram_host(g, g->h[kLayers], kW, g->gu, 2, 0, 2, G))) return rc;
+  for (int c = 0; c < kW; ++c) {
+    gr_h[o.wd + c] = G[(size_t)c * 2 + 0];
+    gr_h[o.ws + c] = G[(size_t)c * 2 + 1];
+  }
+  if ((rc = gram_host(g, g->ones, 1, g->gu, 2, 0, 1, G))) return rc;
+  gr_h[o.bd] = G[0];
+  // layers
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const int fin = l == 0 ? 2 : kW;
+    k_relu_bwd<<<grid1(n * kW), kT, 0, g->st>>>(n * kW, g->z[l], g->dh, g->dz);
+    GK(cudaGetLastError());
+    if ((rc = gram_host(g, g->h[l], fin, g->dz, kW, 0, kW, G))) return rc;
+    for (int e = 0; e < fin * kW; ++e) gr_h[o.W1[l] + e] = G[e];
+    if ((rc = gram_host(g, g->Eh[l], fin, g->dz, kW, 0, kW, G))) return rc;
+    for (int e = 0; e < fin * kW; ++e) gr_h[o.W2[l] + e] = G[e];
+    if ((rc = gram_host(g, g->ones, 1, g->dz, kW, 0, kW, G))) return rc;
+    for (int e = 0; e < kW; ++e) gr_h[o.b[l] + e] = G[e];
+    if (l > 0) {
+      // dh_l = dz W1^T + E (dz W2^T)
+      k_rowmat_t<kW><<<gr, kT, 0, g->st>>>(n, g->dz, g->prm + o.W2[l], nullptr, g->tmp);
+      GK(launch_spmm(kF32, Ecsr(g, g->e), g->tmp, kW, g->tmp2, kW, kW, g->st));
+      k_rowmat_t<kW><<<gr, kT, 0, g->st>>>(n, g->dz, g->prm + o.W1[l], g->tmp2, g->dh);
+      GK(cudaGetLastError());
+    }
+  }
+  *loss = L;
+  std::memcpy(grad, gr_h.data(), sizeof(double) * o.total);
+  return SVDS_OK;
+}
+
+int phsvds_gnn_adam(phsvds_gnn* g, float* params, const double* grad, float* m, float* v, int step, float lr) {
+  if (!g || !params || !grad || !m || !v || step < 1 || !(lr > 0)) return SVDS_ERR_ARG;
+  const int np = g->off.total;
+  float* dp = g->prm;
+  GK(cudaMemcpyAsync(dp, params, sizeof(float) * np, cudaMemcpyHostToDevice, g->st));
+  GK(cudaMemcpyAsync(g->grad, grad, sizeof(double) * np, cudaMemcpyHostToDevice, g->st));
+  GK(cudaMemcpyAsync(g->am, m, sizeof(float) * np, cudaMemcpyHostToDevice, g->st));
+  GK(cudaMemcpyAsync(g->av, v, sizeof(float) * np, cudaMemcpyHostToDevice, g->st));
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adam<<<(np + 255) / 256, 256, 0, g->st>>>(np, dp, g->grad, g->am, g->av, lr, b1, b2, 1e-8f, c1, c2);
+  GK(cudaGetLastError());
+  GK(cudaMemcpyAsync(params, dp, sizeof(float) * np, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaMemcpyAsync(m, g->am, sizeof(float) * np, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaMemcpyAsync(v, g->av, sizeof(float) * np, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaStreamSynchronize(g->st));
+  return SVDS_OK;
+}
+
+}  // extern "C"

@@ -1224,6 +1224,22 @@ cudaError_t launch_csr_transpose(long long rows, long long cols, long long nnz, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_exclusive_scan(long long n, const int* in, int* out, int* work, cudaStream_t st) {
+  long long* bsum = reinterpret_cast<long long*>(work);
+  const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
+  if (nb > 0) {
+    k_scan_block_sums<<<nb, kThreads, 0, st>>>(n, in, bsum);
+    k_scan_bsums<<<1, 1024, 0, st>>>(nb, bsum);
+    k_scan_apply<<<nb, kThreads, 0, st>>>(n, in, bsum, out);
+  } else {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+size_t scan_work_ints(long long n) { return (size_t)(2 * ((n + kScanChunk - 1) / kScanChunk) + 4); }
+
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   k_row_sumsq<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, rowptr, vals, out);

@@ -102,6 +102,9 @@ cudaError_t launch_csr_transpose(long long rows, long long cols, long long nnz, 
                                  const int* colidx, const double* vals, int* rowptrT, int* colidxT,
                                  double* valsT, int* work /* cols + 1 + scan scratch */, cudaStream_t st);
 size_t transpose_work_ints(long long cols);
+// out[0] = 0, out[i + 1] = in[0] + ... + in[i] (int32), for n counts; work: scan_work_ints(n) ints.
+cudaError_t launch_exclusive_scan(long long n, const int* in, int* out, int* work, cudaStream_t st);
+size_t scan_work_ints(long long n);
 // out[i] = sum_k vals[k]^2 over row i (FP64).
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st);
 // Jacobi scale in storage format: d[r] = 1 / s[r] (1 where s[r] == 0), optionally sqrt'ed first.

@@ -20,7 +20,7 @@ def built():
 
 def _declared():
     names = []
-    for h in ("phsvds.h", "phsvds_kernels.h"):
+    for h in ("phsvds.h", "phsvds_kernels.h", "phsvds_gnn.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names += re.findall(r"\b(svds_\w+|phsvds_\w+)\s*\(", src)
