@@ -48,6 +48,8 @@ extern "C" {
 
 #define SVDS_PRECOND_NONE 0
 #define SVDS_PRECOND_JACOBI 1
+#define SVDS_PRECOND_LEARNED 2 /* sparse approximate inverse on the pattern of A^T A from the
+                                  graph network of phsvds_gnn.h (stage 1, smallest values) */
 
 /* Sparse matrix in CSR form (0-based).  Column indices must be strictly
  * increasing inside each row and values finite.  When on_device is non-zero
@@ -74,7 +76,7 @@ typedef struct {
   int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
                            to the paper's stage-1 criterion before stage 2 (default 1) */
-  int precond;          /* SVDS_PRECOND_JACOBI (default) or SVDS_PRECOND_NONE */
+  int precond;          /* SVDS_PRECOND_JACOBI (default), SVDS_PRECOND_NONE or SVDS_PRECOND_LEARNED */
   double aNorm;         /* ||A||_2 if known, 0 = estimate */
   int64_t maxMatvecs;   /* budget in products with A or A^T (per column), 0 = unlimited */
   double maxSeconds;    /* wall-clock budget, 0 = unlimited */
@@ -88,6 +90,10 @@ typedef struct {
                            this fraction of the right-hand side, 0 = 0.1 */
   int innerPrecision;   /* JDQMR inner solves: SVDS_FP32 (default) or SVDS_FP64 (the FP64-class
                            mode of the outer iteration) */
+  const float *precondParams; /* SVDS_PRECOND_LEARNED: host array of phsvds_gnn_num_params()
+                                 network parameters (copied by svds_create), or NULL */
+  const char *precondModel;   /* SVDS_PRECOND_LEARNED without precondParams: path of a
+                                 parameter file written by phsvds_gnn_save */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -106,6 +112,7 @@ typedef struct {
   double seconds_sync_wait;   /* host time blocked on the device (small results coming back) */
   int64_t host_syncs;         /* device-to-host round trips */
   int64_t inner_steps;        /* JDQMR inner sQMR steps (each applies the operator to the block) */
+  double seconds_precond;     /* learned preconditioner: graph of A^T A and network inference */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

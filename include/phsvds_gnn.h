@@ -11,10 +11,16 @@
  *   layers  : 4 x (z = h W1 + (E h) W2 + b, h = relu(z)), width 32;
  *   heads   : u = h ws, d = softplus(h wd + bd), delta = d / c_ii,
  *             s_ij = tanh(u_i + u_j + we e_ij + bs);
- *   M       : m_ii = delta_i, m_ij = 0.9 s_ij min(delta_i, delta_j) / max(deg_i, deg_j),
- *             symmetric and strictly diagonally dominant with a positive
- *             diagonal, hence SPD;
- *   loss    : mean(1 - cos^2(M r_p, t_p)) + 0.5 mean(1 - cos^2(M y_q, x_q)).
+ *   M       : m_ii = delta_i, m_ij = 0.9 s_ij min(delta_i, delta_j) |e_ij| / max(E_i, E_j)
+ *             with E_i = sum_j |e_ij|; symmetric and strictly diagonally
+ *             dominant with a positive diagonal, hence SPD;
+ *   loss    : sparse-approximate-inverse residual with one shared scale over
+ *             sampled directions t_p (R = C T):
+ *             L = min_alpha mean_p |alpha M C t_p - t_p|^2 / |t_p|^2
+ *               = 1 - (sum_p a_p)^2 / (P sum_p b_p),
+ *             a_p = <M r_p, t_p> / |t_p|^2, b_p = |M r_p|^2 / |t_p|^2
+ *             (the Frobenius objective of SPAI, Grote & Huckle 1997, on
+ *             samples, invariant to the scale of M).
  *
  * Parameters are a flat float array of phsvds_gnn_num_params() entries in the
  * order W1_0 (2x32), W2_0 (2x32), b_0 (32), W1_l, W2_l (32x32), b_l (32) for
@@ -36,6 +42,13 @@ typedef struct phsvds_gnn phsvds_gnn;
 
 int phsvds_gnn_num_params(void);
 
+/* Seeded initial parameters (host array of phsvds_gnn_num_params() floats):
+ * W1_l, W2_l ~ N(0, 2 / (fan_in + 32)), wd ~ N(0, 1/32), ws ~ N(0, 0.01/32),
+ * bd = 0.5, bs = 1, every other entry 0 (so the initial M is close to a
+ * scaled diagonal plus couplings that follow |e_ij|).  Normal deviates: splitmix64 (Steele, Lea, Flood 2014) feeding
+ * the Box-Muller transform. */
+int phsvds_gnn_init(uint64_t seed, float *params);
+
 /* Build the graph of C = A^T A on the device (pattern by a k-way merge of the
  * rows of A, deterministic).  A may be on the host or the device. */
 int phsvds_gnn_create(phsvds_gnn **g, const svds_csr *A, void *stream);
@@ -48,10 +61,25 @@ int phsvds_gnn_pattern(const phsvds_gnn *g, int32_t *rowptr, int32_t *colidx);
 /* Forward pass: values of M on the pattern of C (host array of nnz floats). */
 int phsvds_gnn_forward(phsvds_gnn *g, const float *params, float *mvals);
 
-/* Loss and gradient for training pairs (R, T) (n x P) and (Y, X) (n x Q), host
- * FP64 column-major (Q may be 0).  grad: host doubles, phsvds_gnn_num_params(). */
+/* Loss and gradient for the samples T and R = C T (host FP64 column-major
+ * n x P, 1 <= P <= 32).  grad: host doubles, phsvds_gnn_num_params();
+ * SVDS_ERR_NUMERIC if M R vanishes. */
 int phsvds_gnn_loss_grad(phsvds_gnn *g, const float *params, const double *R, const double *T, int P,
-                         const double *Y, const double *X, int Q, double *loss, double *grad);
+                         double *loss, double *grad);
+
+/* Training pairs on the graph: T = S^s Z, with S = I - (2/3) diag(C)^-1 C (s
+ * steps of damped Jacobi smoothing of seeded N(0,1) columns Z, which leaves
+ * mostly the low end of the spectrum of C), and R = C T.  Host FP64
+ * column-major n x P arrays, 1 <= P <= 8, 0 <= s <= 1000. */
+int phsvds_gnn_pairs(phsvds_gnn *g, int P, int smooth, uint64_t seed, double *R, double *T);
+/* Y = C X for host FP64 column-major n x q blocks, 1 <= q <= 8. */
+int phsvds_gnn_apply_c(phsvds_gnn *g, const double *X, int q, double *Y);
+
+/* Parameter files: 8-byte tag "PHSGNN01", int32 count, count float32 values
+ * (little-endian).  save writes phsvds_gnn_num_params() values; load reads
+ * them into params (SVDS_ERR_ARG for a missing or malformed file). */
+int phsvds_gnn_save(const char *path, const float *params);
+int phsvds_gnn_load(const char *path, float *params);
 
 /* One Adam step on the device (Kingma & Ba 2015): params, m, v are host
  * arrays of phsvds_gnn_num_params() floats updated in place; step >= 1. */

@@ -6,7 +6,8 @@ repository's learned preconditioner so that the GPU forward and backward
 kernels can be checked against it.  Every function is plain numpy/scipy.
 
 * Graph: the structural sparsity pattern of C = A^T A (nodes = columns of A,
-  symmetric, diagonal included; entries that cancel numerically are kept).  c_ii = diagonal of C, deg_i = off-diagonal neighbours.
+  symmetric, diagonal included; entries that cancel numerically are kept).
+  deg_i = off-diagonal neighbours, E_i = sum_{j != i} |e_ij| (weighted degree).  c_ii = diagonal of C, deg_i = off-diagonal neighbours.
 * Edge weights: e_ij = c_ij / sqrt(c_ii c_jj) for i != j (0 on the diagonal).
 * Node features: x_i = [log c_ii - mean_j log c_jj, deg_i / max_j deg_j].
 * Message passing, 4 layers of width 32:
@@ -14,14 +15,22 @@ kernels can be checked against it.  Every function is plain numpy/scipy.
 * Heads: u_i = h_i . ws,  d_i = softplus(h_i . wd + bd),  delta_i = d_i / c_ii,
       s_ij = tanh(u_i + u_j + we e_ij + bs)   (symmetric by construction).
 * M on the pattern of C:  m_ii = delta_i,
-      m_ij = rho s_ij min(delta_i, delta_j) / max(deg_i, deg_j)   (i != j),
-  so sum_{j != i} |m_ij| <= rho delta_i < m_ii: M is symmetric, strictly
-  diagonally dominant with a positive diagonal, hence SPD (Gershgorin).
-* Loss (invariant to the scale of M): for pairs (r_p, t_p) and (y_q, x_q),
-      L = mean_p (1 - cos^2(M r_p, t_p)) + lam mean_q (1 - cos^2(M y_q, x_q)).
+      m_ij = rho s_ij min(delta_i, delta_j) |e_ij| / max(E_i, E_j)   (i != j),
+  so sum_{j != i} |m_ij| <= rho delta_i sum_j |e_ij| / E_i = rho delta_i < m_ii:
+  M is symmetric, strictly diagonally dominant with a positive diagonal,
+  hence SPD (Gershgorin).  (With s_ij = const the off-diagonal part follows
+  the coupling strength |e_ij|, as a truncated Neumann series of C^-1 does.)
+* Loss: sparse-approximate-inverse residual with one shared scale: for
+  samples t_p (columns of T, with R = C T),
+      L = min_alpha (1/P) sum_p ||alpha M C t_p - t_p||^2 / ||t_p||^2
+        = 1 - (sum_p a_p)^2 / (P sum_p b_p),
+      a_p = <M r_p, t_p> / ||t_p||^2,  b_p = ||M r_p||^2 / ||t_p||^2
+  (the Frobenius objective of SPAI, Grote & Huckle 1997, restricted to
+  sampled directions and made invariant to the scale of M).
 
-Parity status: gradients pinned by central finite differences in the tests;
-the SPD property checked directly.
+Parity status: pinned by closed forms (M = I on eigenvector samples; M = C^-1
+on a diagonal C), central finite differences of the gradient, scale
+invariance and the SPD property.
 """
 from __future__ import annotations
 
@@ -31,7 +40,6 @@ import scipy.sparse as sp
 WIDTH = 32
 LAYERS = 4
 RHO = 0.9
-LAM = 0.5
 
 
 def param_shapes():
@@ -104,6 +112,7 @@ class Graph:
         r, c = self.rows[self.offdiag], self.indices[self.offdiag]
         e[self.offdiag] = self.cval[self.offdiag] / np.sqrt(diag[r] * diag[c])
         self.e = e
+        self.wdeg = np.bincount(self.rows, weights=np.abs(e), minlength=n)
         self.E = sp.csr_matrix((e, self.indices, self.indptr), shape=(n, n))
         lc = np.log(diag)
         dmax = max(self.deg.max(), 1.0)
@@ -135,11 +144,11 @@ def forward(G: Graph, params, keep=False):
     a = u[r] + u[c] + params["we"] * G.e + params["bs"]
     s = np.tanh(a)
     mu = np.minimum(delta[r], delta[c])
-    D = np.maximum(G.deg[r], G.deg[c])
-    D = np.where(D > 0, D, 1.0)
-    m = np.where(G.offdiag, RHO * s * mu / D, delta[r])
+    Emax = np.maximum(G.wdeg[r], G.wdeg[c])
+    wgt = np.where(Emax > 0, np.abs(G.e) / np.where(Emax > 0, Emax, 1.0), 0.0)  # |e_ij| / max(E_i, E_j)
+    m = np.where(G.offdiag, RHO * s * mu * wgt, delta[r])
     if keep:
-        cache.update(u=u, gpre=gpre, d=d, delta=delta, s=s, mu=mu, D=D)
+        cache.update(u=u, gpre=gpre, d=d, delta=delta, s=s, mu=mu, wgt=wgt)
         return m, cache
     return m
 
@@ -148,41 +157,38 @@ def M_matrix(G: Graph, m):
     return sp.csr_matrix((m, G.indices, G.indptr), shape=(G.n, G.n))
 
 
-def _cos2_loss_and_grad(Z, T):
-    """mean over columns of 1 - cos^2(z, t) and its gradient w.r.t. Z."""
-    zt = np.sum(Z * T, axis=0)
-    zz = np.sum(Z * Z, axis=0)
-    tt = np.sum(T * T, axis=0)
-    f = zt * zt / (zz * tt)
-    P = Z.shape[1]
-    loss = float(np.mean(1.0 - f))
-    dZ = -(2.0 * zt / (zz * tt) * T - 2.0 * zt * zt / (zz * zz * tt) * Z) / P
-    return loss, dZ
-
-
-def loss_and_grad(G: Graph, params, R, T, Y=None, X=None):
-    """Loss and gradient (dict like params) for pairs (R, T) and (Y, X)."""
-    m, cache = forward(G, params, keep=True)
+def loss_from_m(G: Graph, m, R, T):
+    """Shared-scale SPAI loss of M on the samples T (R = C T) and dL/dm."""
     M = M_matrix(G, m)
-    loss, dZ = _cos2_loss_and_grad(M @ R, T)
-    # dm_ij = sum_p dZ_ip R_jp
-    dm = np.einsum("kp,kp->k", dZ[G.rows], R[G.indices])
-    if Y is not None and Y.shape[1] > 0:
-        l2, dW = _cos2_loss_and_grad(M @ Y, X)
-        loss += LAM * l2
-        dm += LAM * np.einsum("kp,kp->k", dW[G.rows], Y[G.indices])
+    Z = M @ R
+    P = T.shape[1]
+    tt = np.sum(T * T, axis=0)
+    a = np.sum(Z * T, axis=0) / tt
+    b = np.sum(Z * Z, axis=0) / tt
+    sa, sb = a.sum(), b.sum()
+    loss = float(1.0 - sa * sa / (P * sb))
+    # dL/dZ_p = -2 sa / (P sb) t_p / ||t_p||^2 + 2 sa^2 / (P sb^2) z_p / ||t_p||^2
+    dZ = (-2.0 * sa / (P * sb)) * T / tt + (2.0 * sa * sa / (P * sb * sb)) * Z / tt
+    dm = np.einsum("kp,kp->k", dZ[G.rows], R[G.indices])  # dZ_ip / dm_ij = r_jp
+    return loss, dm
+
+
+def loss_and_grad(G: Graph, params, R, T):
+    """Loss and gradient (dict like params) for the samples T (R = C T)."""
+    m, cache = forward(G, params, keep=True)
+    loss, dm = loss_from_m(G, m, R, T)
     return loss, backward(G, params, cache, dm)
 
 
 def backward(G: Graph, params, cache, dm):
     r, c = G.rows, G.indices
     off = G.offdiag
-    s, mu, D, delta = cache["s"], cache["mu"], cache["D"], cache["delta"]
+    s, mu, wgt, delta = cache["s"], cache["mu"], cache["wgt"], cache["delta"]
     n = G.n
     ddelta = np.zeros(n)
     np.add.at(ddelta, r[~off], dm[~off])
-    ds = np.where(off, dm * RHO * mu / D, 0.0)
-    dmu = np.where(off, dm * RHO * s / D, 0.0)
+    ds = np.where(off, dm * RHO * mu * wgt, 0.0)
+    dmu = np.where(off, dm * RHO * s * wgt, 0.0)
     # min(delta_i, delta_j): the gradient goes to the smaller (ties: the lower index)
     to_i = (delta[r] < delta[c]) | ((delta[r] == delta[c]) & (r < c))
     np.add.at(ddelta, r[off & to_i], dmu[off & to_i])

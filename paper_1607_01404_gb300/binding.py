@@ -33,6 +33,7 @@ SVDS_FP64 = 3
 SVDS_NATIVE_FP64 = 4
 SVDS_PRECOND_NONE = 0
 SVDS_PRECOND_JACOBI = 1
+SVDS_PRECOND_LEARNED = 2
 
 PREC_F32, PREC_DF64, PREC_F64 = 1, 2, 3
 
@@ -50,7 +51,7 @@ class svds_opts(C.Structure):
                 ("maxMatvecs", C.c_int64), ("maxSeconds", C.c_double), ("seed", C.c_uint64),
                 ("printLevel", C.c_int), ("initSize", C.c_int), ("initV", C.c_void_p),
                 ("stream", C.c_void_p), ("innerMaxIt", C.c_int), ("innerRelTol", C.c_double),
-                ("innerPrecision", C.c_int)]
+                ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p)]
 
 
 class svds_stats(C.Structure):
@@ -61,7 +62,7 @@ class svds_stats(C.Structure):
                 ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
                 ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
                 ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
-                ("inner_steps", C.c_int64)]
+                ("inner_steps", C.c_int64), ("seconds_precond", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -106,13 +107,18 @@ _SIGS = {
     "phsvds_host_svd": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     # learned preconditioner (phsvds_gnn.h)
     "phsvds_gnn_num_params": (C.c_int, []),
+    "phsvds_gnn_init": (C.c_int, [C.c_uint64, C.c_void_p]),
     "phsvds_gnn_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(svds_csr), C.c_void_p]),
     "phsvds_gnn_destroy": (None, [C.c_void_p]),
     "phsvds_gnn_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "phsvds_gnn_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_gnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
-    "phsvds_gnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
-                                       C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "phsvds_gnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_double), C.c_void_p]),
+    "phsvds_gnn_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "phsvds_gnn_apply_c": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "phsvds_gnn_save": (C.c_int, [C.c_char_p, C.c_void_p]),
+    "phsvds_gnn_load": (C.c_int, [C.c_char_p, C.c_void_p]),
     "phsvds_gnn_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                   C.c_float]),
 }
@@ -191,6 +197,14 @@ def make_opts(**kw) -> svds_opts:
             o.initSize = arr.shape[1] if arr.ndim == 2 else 1
         elif k == "stream":
             o.stream = v
+        elif k == "precondParams" and v is not None:
+            arr = np.ascontiguousarray(v, dtype=np.float32)
+            keep.append(arr)
+            o.precondParams = arr.ctypes.data
+        elif k == "precondModel" and v is not None:
+            path = os.fsencode(v)
+            keep.append(path)
+            o.precondModel = path
         elif v is not None:
             setattr(o, k, v)
     o._keep = keep  # keep the guesses alive until svds_create copied them
@@ -355,6 +369,26 @@ def gnn_num_params() -> int:
     return int(lib().phsvds_gnn_num_params())
 
 
+def gnn_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters (float32)."""
+    theta = np.zeros(gnn_num_params(), dtype=np.float32)
+    _check(lib().phsvds_gnn_init(seed, theta.ctypes.data), "phsvds_gnn_init")
+    return theta
+
+
+def gnn_save(path, theta):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    if theta.shape != (gnn_num_params(),):
+        raise ValueError("wrong number of parameters")
+    _check(lib().phsvds_gnn_save(os.fsencode(path), theta.ctypes.data), "phsvds_gnn_save")
+
+
+def gnn_load(path) -> np.ndarray:
+    theta = np.zeros(gnn_num_params(), dtype=np.float32)
+    _check(lib().phsvds_gnn_load(os.fsencode(path), theta.ctypes.data), "phsvds_gnn_load")
+    return theta
+
+
 class Gnn:
     """Graph of C = A^T A on the device plus the network's forward/backward
     (argument marshalling only; every step runs in libphsvds.so)."""
@@ -400,20 +434,29 @@ class Gnn:
         _check(lib().phsvds_gnn_forward(self.ptr, theta.ctypes.data, m.ctypes.data), "phsvds_gnn_forward")
         return m
 
-    def loss_grad(self, theta, R, T, Y=None, X=None):
+    def loss_grad(self, theta, R, T):
+        """Loss and gradient for the samples T (n x P, P <= 32) and R = C T."""
         theta = self._params(theta)
-        R = np.asfortranarray(R, dtype=np.float64)
-        T = np.asfortranarray(T, dtype=np.float64)
-        q = 0 if Y is None else Y.shape[1]
-        Yf = np.asfortranarray(Y, dtype=np.float64) if q else None
-        Xf = np.asfortranarray(X, dtype=np.float64) if q else None
+        R, T = (np.asfortranarray(a, dtype=np.float64) for a in (R, T))
         loss = C.c_double(0.0)
         grad = np.zeros(self.np)
         rc = lib().phsvds_gnn_loss_grad(self.ptr, theta.ctypes.data, R.ctypes.data, T.ctypes.data, R.shape[1],
-                                        Yf.ctypes.data if q else None, Xf.ctypes.data if q else None, q,
                                         C.byref(loss), grad.ctypes.data)
         _check(rc, "phsvds_gnn_loss_grad")
         return loss.value, grad
+
+    def pairs(self, P: int, smooth: int, seed: int):
+        """(R, T): T = smoothed seeded N(0,1) columns, R = C T (n x P, FP64)."""
+        R = np.zeros((self.n, P), order="F")
+        T = np.zeros((self.n, P), order="F")
+        _check(lib().phsvds_gnn_pairs(self.ptr, P, smooth, seed, R.ctypes.data, T.ctypes.data), "phsvds_gnn_pairs")
+        return R, T
+
+    def apply_c(self, X):
+        X = np.asfortranarray(X, dtype=np.float64)
+        Y = np.zeros_like(X, order="F")
+        _check(lib().phsvds_gnn_apply_c(self.ptr, X.ctypes.data, X.shape[1], Y.ctypes.data), "phsvds_gnn_apply_c")
+        return Y
 
     def adam(self, theta, grad, m, v, step: int, lr: float):
         """In-place Adam step on float32 arrays theta, m, v."""

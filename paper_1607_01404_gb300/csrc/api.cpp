@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/phsvds.h"
+#include "../../include/phsvds_gnn.h"
 #include "../../include/phsvds_kernels.h"
 #include "engine.h"
 #include "hostla.h"
@@ -182,6 +183,18 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
     return SVDS_ERR_ARG;
   if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_FP64) return SVDS_ERR_ARG;
   if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
+  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED)
+    return SVDS_ERR_ARG;
+  std::vector<float> gnn_params;
+  if (o.precond == SVDS_PRECOND_LEARNED) {
+    gnn_params.resize(phsvds_gnn_num_params());
+    if (o.precondParams) {
+      std::memcpy(gnn_params.data(), o.precondParams, sizeof(float) * gnn_params.size());
+    } else if (!o.precondModel || phsvds_gnn_load(o.precondModel, gnn_params.data()) != SVDS_OK) {
+      phsvds::set_last_error("SVDS_PRECOND_LEARNED needs precondParams or a readable precondModel");
+      return SVDS_ERR_ARG;
+    }
+  }
   if (!A->on_device) {
     int rc = validate_host_csr(A);
     if (rc) return rc;
@@ -190,6 +203,9 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
   h->opts = o;
   h->opts.initV = nullptr;  // initial guesses are per solve: copied from opts at solve time
   h->opts.initSize = 0;
+  h->opts.precondParams = nullptr;  // kept in gnn_params
+  h->opts.precondModel = nullptr;
+  h->gnn_params.swap(gnn_params);
   cudaGetDevice(&h->device);
   if (o.stream) {
     h->stream = reinterpret_cast<cudaStream_t>(o.stream);

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include "../../include/phsvds_gnn.h"
+#include "gnn.h"
 #include "hostla.h"
 #include "jdqmr.h"
 
@@ -358,6 +360,7 @@ struct RunBufs {
   // JDQMR inner-solve scratch (L x b each, inner mode): x, rhs, K^-1 x, q, r, d, sol, op(q)
   void* jd[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* jtmp = nullptr;  // m x b (inner-mode C op)
+  void* ju = nullptr;    // L x b (inner-mode K^-1 r for a sparse preconditioner)
   QmrState* jS = nullptr;
   double* jdots = nullptr;
 };
@@ -379,6 +382,8 @@ struct RunCfg {
   bool jd = false;
   int jd_prec = kF32;            // mode of the inner solves
   const void* jdinv = nullptr;   // Jacobi diagonal in the inner mode's storage, or nullptr
+  const CsrDev* K = nullptr;     // sparse preconditioner (learned M) in the outer mode, or nullptr
+  const CsrDev* jdK = nullptr;   // the same in the inner mode
   int jd_maxk = 30;
   double jd_xi = 0.1;
 };
@@ -509,13 +514,13 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
        *w = B.jd[7];
   CK(convert_cols(prec, B.Xb, B.b, pin, x, nbk, L, nbk, d1, c.st));
   CK(convert_cols(prec, B.Rb, B.b, pin, bv, nbk, L, nbk, d2, c.st));
-  CK(qmr_init(pin, L, nbk, x, bv, cfg.jdinv, kx, q, r, d, sol, B.jS, c.partial, B.jdots, c.st));
-  c.launches += 2 + qmr_init_launches();
+  CK(qmr_init(pin, L, nbk, x, bv, cfg.jdinv, cfg.jdK, B.ju, kx, q, r, d, sol, B.jS, c.partial, B.jdots, c.st));
+  c.launches += 2 + qmr_init_launches(nbk, cfg.jdK != nullptr);
   for (int k = 0; k < cfg.jd_maxk; ++k) {
     apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
-    CK(qmr_step(pin, L, nbk, x, w, kx, cfg.jdinv, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol, B.jS, c.partial, B.jdots,
-                c.st));
-    c.launches += qmr_step_launches();
+    CK(qmr_step(pin, L, nbk, x, w, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol, B.jS,
+                c.partial, B.jdots, c.st));
+    c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr);
     c.inner += 1;
     if ((k + 1) % 8 == 0 && k + 1 < cfg.jd_maxk) {
       CK(cudaMemcpyAsync(c.hG, B.jS, sizeof(QmrState) * nbk, cudaMemcpyDeviceToHost, c.st));
@@ -657,12 +662,16 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       Yprev.clear();
       continue;
     }
-    // correction: JDQMR, or T = M R (Jacobi), or T = R
+    // correction: JDQMR, or T = M R (learned sparse M, or Jacobi), or T = R
     void* T = B.Rb;
     if (cfg.jd) {
       std::vector<double> eta(nbk);
       for (int j = 0; j < nbk; ++j) eta[j] = theta[block[j]];
       jd_correction(c, B, cfg, nbk, eta, rnb);
+      T = B.Tb;
+    } else if (cfg.K) {
+      CK(launch_spmm(prec, *cfg.K, B.Rb, b, B.Tb, b, nbk, c.st));
+      c.launches += spmm_launches(nbk);
       T = B.Tb;
     } else if (cfg.dscale) {
       CK(launch_scale_rows(prec, B.L, cfg.dscale, B.Rb, b, B.Tb, b, nbk, c.st));
@@ -704,7 +713,10 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
         for (int j = 0; j < nbk; ++j) thb[j] = theta[block[j]];
         ritz_block(c, B, g, Yb, thb, 0);
         T = B.Rb;
-        if (cfg.dscale) {
+        if (cfg.K) {
+          CK(launch_spmm(prec, *cfg.K, B.Rb, b, B.Tb, b, nbk, c.st));
+          T = B.Tb;
+        } else if (cfg.dscale) {
           CK(launch_scale_rows(prec, B.L, cfg.dscale, B.Rb, b, B.Tb, b, nbk, c.st));
           T = B.Tb;
         }
@@ -952,6 +964,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
   c.print = o.printLevel;
   c.seed = o.seed;
   svds_stats S{};
+  struct GnnGuard {
+    phsvds_gnn* g = nullptr;
+    ~GnnGuard() { phsvds_gnn_destroy(g); }
+  } gnn_guard;
   try {
     // ---- workspace ----
     struct Req {
@@ -975,6 +991,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       reqs.push_back({&R.tmp, (size_t)m * b * e});
       if (jdrun) {
         for (int i = 0; i < 8; ++i) reqs.push_back({&R.jd[i], (size_t)L * b * 8});
+        reqs.push_back({&R.ju, (size_t)L * b * 8});
         reqs.push_back({&R.jtmp, (size_t)m * b * 8});
         reqs.push_back({(void**)&R.jS, sizeof(QmrState) * 8});
         reqs.push_back({(void**)&R.jdots, sizeof(double) * 64});
@@ -1095,7 +1112,27 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
         c.launches += 1;
       }
     }
+    // learned sparse approximate inverse on the pattern of C (stage 1 only,
+    // smallest values; its scale is immaterial to GD+k and to the sQMR iterates)
+    const bool learned = smallest && o.precond == SVDS_PRECOND_LEARNED && !h->gnn_params.empty();
+    CsrDev K32, K64;
+    if (learned) {
+      const double tp = c.elapsed();
+      phsvds_gnn* gg = nullptr;
+      int grc = gnn_build(&gg, A, false, false, c.st);
+      if (grc == 0) {
+        gnn_guard.g = gg;
+        grc = gnn_precond(gg, h->gnn_params.data(), &K32, p2 == kF64 ? &K64 : nullptr);
+      }
+      if (grc == SVDS_ERR_NOMEM) return SVDS_ERR_NOMEM;
+      if (grc) throw CudaFail{cudaErrorUnknown, "learned preconditioner"};
+      c.launches += gnn_launches(gg);
+      c.sync();
+      S.seconds_precond = c.elapsed() - tp;
+    }
+    const CsrDev* Kouter = learned ? (p2 == kF64 ? &K64 : &K32) : nullptr;
     const int jd_prec = o.innerPrecision == SVDS_FP64 ? p2 : kF32;
+    const CsrDev* Kinner = learned ? (jd_prec == kF64 ? &K64 : &K32) : nullptr;
     const int jd_maxk = o.innerMaxIt > 0 ? o.innerMaxIt : 30;
     const double jd_xi = o.innerRelTol > 0 ? o.innerRelTol : 0.1;
     // initial block: user guesses then seeded N(0,1) columns
@@ -1132,11 +1169,13 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.jdinv = jac ? (jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1)) : nullptr;
     c1.jd_maxk = jd_maxk;
     c1.jd_xi = jd_xi;
+    c1.jdK = Kinner;
     if (lowprec) {
       init_block(kF32, X1a, kk, b0);
       c1.u = unit_roundoff(kF32);
       c1.conv = stage1_conv(c1.u);
       c1.dscale = jac ? d1a : nullptr;
+      c1.K = learned ? &K32 : nullptr;
       c1.V0 = X1a;
       c1.ldv0 = kk;
       c1.name = "stage1-fp32";
@@ -1156,6 +1195,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c1.u = unit_roundoff(p2);
       c1.conv = stage1_conv(c1.u);
       c1.dscale = jac ? d1 : nullptr;
+      c1.K = Kouter;
       c1.V0 = X1;
       c1.ldv0 = kk;
       c1.b0 = lowprec ? k : b0;

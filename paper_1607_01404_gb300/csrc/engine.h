@@ -71,6 +71,7 @@ struct svds_handle {
   size_t hpin_bytes = 0;
   unsigned long long launches = 0;
   std::vector<double> initV;  // copy of the caller's initial guesses (n x initSize)
+  std::vector<float> gnn_params;  // learned preconditioner parameters (SVDS_PRECOND_LEARNED)
 };
 
 namespace phsvds {

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -14,6 +15,7 @@
 #include "../../include/phsvds_gnn.h"
 #include "common.cuh"
 #include "engine.h"
+#include "gnn.h"
 #include "kernels.h"
 
 namespace phsvds {
@@ -23,7 +25,6 @@ namespace {
 constexpr int kW = 32;      // width
 constexpr int kLayers = 4;
 constexpr float kRho = 0.9f;
-constexpr double kLam = 0.5;
 constexpr int kT = 256;
 constexpr int kMaxMerge = 64;  // rows of A^T longer than this are not supported for the graph
 
@@ -119,14 +120,19 @@ __global__ void k_diag_deg(long long n, const int* __restrict__ cptr, const int*
   atomicMax(degmax, dm);
 }
 
+// e_ij = c_ij / sqrt(c_ii c_jj) (0 on the diagonal), weighted degree
+// E_i = sum_j |e_ij|, transpose positions, log c_ii
 __global__ void k_edges(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
                         const double* __restrict__ cval, const double* __restrict__ cdiag, float* __restrict__ e,
-                        int* __restrict__ tpos, float* __restrict__ logc) {
+                        float* __restrict__ wdeg, int* __restrict__ tpos, float* __restrict__ logc) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     logc[i] = (float)log(cdiag[i]);
+    double wd = 0.0;
     for (int p = cptr[i]; p < cptr[i + 1]; ++p) {
       const int j = cidx[p];
-      e[p] = j == i ? 0.f : (float)(cval[p] / sqrt(cdiag[i] * cdiag[j]));
+      const float ev = j == i ? 0.f : (float)(cval[p] / sqrt(cdiag[i] * cdiag[j]));
+      e[p] = ev;
+      wd += fabs((double)ev);
       // position of (j, i): binary search in the sorted row j
       int lo = cptr[j], hi = cptr[j + 1] - 1, pos = -1;
       while (lo <= hi) {
@@ -141,8 +147,9 @@ __global__ void k_edges(long long n, const int* __restrict__ cptr, const int* __
         else
           hi = mid - 1;
       }
-      tpos[p] = pos >= 0 ? pos : p;
+      if (tpos) tpos[p] = pos >= 0 ? pos : p;
     }
+    wdeg[i] = (float)wd;
   }
 }
 
@@ -185,6 +192,12 @@ __global__ void __launch_bounds__(kT) k_layer_fwd(long long n, const float* __re
   }
 }
 
+// |e_ij| / max(E_i, E_j): the off-diagonal weight that keeps M diagonally dominant
+__device__ __forceinline__ float edge_weight(float e, float Ei, float Ej) {
+  const float mx = fmaxf(Ei, Ej);
+  return mx > 0.f ? fabsf(e) / mx : 0.f;
+}
+
 __device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
 
@@ -214,7 +227,7 @@ __global__ void k_heads_node(long long n, const float* __restrict__ h, const flo
 
 __global__ void k_heads_edge(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
                              const float* __restrict__ e, const float* __restrict__ u, const float* __restrict__ delta,
-                             const float* __restrict__ deg, const float* __restrict__ we, const float* __restrict__ bs,
+                             const float* __restrict__ wdeg, const float* __restrict__ we, const float* __restrict__ bs,
                              float* __restrict__ s, float* __restrict__ m) {
   const float w = *we, b = *bs;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -226,9 +239,8 @@ __global__ void k_heads_edge(long long n, const int* __restrict__ cptr, const in
       } else {
         const float sv = tanhf(u[i] + u[j] + w * e[p] + b);
         const float mu = fminf(delta[i], delta[j]);
-        const float D = fmaxf(fmaxf(deg[i], deg[j]), 1.f);
         s[p] = sv;
-        m[p] = kRho * sv * mu / D;
+        m[p] = kRho * sv * mu * edge_weight(e[p], wdeg[i], wdeg[j]);
       }
     }
   }
@@ -258,11 +270,11 @@ __global__ void k_dm(long long n, const int* __restrict__ cptr, const int* __res
   }
 }
 
-// heads backward per row: ddelta_i, du_i; per-entry da_k = dm_k rho mu / D (1 - s^2)
+// heads backward per row: ddelta_i, du_i; per-entry da_k = dm_k rho mu w_ij (1 - s^2)
 // for the we / bs gradients (written to da and dae = da * e).
 __global__ void k_heads_bwd(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
                             const int* __restrict__ tpos, const float* __restrict__ dm, const float* __restrict__ s,
-                            const float* __restrict__ delta, const float* __restrict__ deg,
+                            const float* __restrict__ delta, const float* __restrict__ wdeg,
                             const float* __restrict__ e, float* __restrict__ ddelta, float* __restrict__ du,
                             float* __restrict__ da, float* __restrict__ dae) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -277,14 +289,14 @@ __global__ void k_heads_bwd(long long n, const int* __restrict__ cptr, const int
       }
       const float di = delta[i], dj = delta[j];
       const float mu = fminf(di, dj);
-      const float D = fmaxf(fmaxf(deg[i], deg[j]), 1.f);
+      const float w = edge_weight(e[k], wdeg[i], wdeg[j]);
       const float sv = s[k];
       const float dpair = dm[k] + dm[tpos[k]];
       const float t = 1.f - sv * sv;
-      duu += dpair * kRho * mu / D * t;
+      duu += dpair * kRho * mu * w * t;
       const bool to_i = (di < dj) || (di == dj && i < j);
-      if (to_i) dd += dpair * kRho * sv / D;
-      const float dak = dm[k] * kRho * mu / D * t;
+      if (to_i) dd += dpair * kRho * sv * w;
+      const float dak = dm[k] * kRho * mu * w * t;
       da[k] = dak;
       dae[k] = dak * e[k];
     }
@@ -340,6 +352,19 @@ __global__ void __launch_bounds__(kT) k_rowmat_t(long long n, const float* __res
   }
 }
 
+__global__ void k_to_f64(long long n, const float* __restrict__ x, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// t <- t - omega (C t) / c_ii (damped Jacobi smoothing, row-major n x P)
+__global__ void k_smooth(long long n, int P, const double* __restrict__ ct, const double* __restrict__ cdiag,
+                         double omega, double* __restrict__ t) {
+  const long long total = n * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    t[e] -= omega * ct[e] / cdiag[e / P];
+}
+
 __global__ void k_fill1(long long n, float* __restrict__ x) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = 1.f;
@@ -393,7 +418,7 @@ struct phsvds_gnn {
   std::vector<void*> allocs;
   int *cptr = nullptr, *cidx = nullptr, *tpos = nullptr;
   double *cval = nullptr, *cdiag = nullptr;
-  float *deg = nullptr, *e = nullptr, *x0 = nullptr, *logc = nullptr;
+  float *deg = nullptr, *wdeg = nullptr, *e = nullptr, *x0 = nullptr, *logc = nullptr;
   float* prm = nullptr;  // device parameters
   float* h[kLayers + 1] = {};
   float* Eh[kLayers] = {};
@@ -404,8 +429,12 @@ struct phsvds_gnn {
   float *R = nullptr, *T = nullptr, *Z = nullptr, *dZ = nullptr;
   double *dcoef = nullptr, *dG = nullptr, *dstage = nullptr, *grad = nullptr;
   float *am = nullptr, *av = nullptr;
+  double* m64 = nullptr;  // FP64 copy of M for the FP64 solver mode
+  double *w0 = nullptr, *w1 = nullptr, *w2 = nullptr;  // n x 8 FP64 work blocks (pairs, C products)
   void* partial = nullptr;
   int cap_pairs = 0;
+  bool train = false;
+  long long launches = 0;
   Offsets off;
 };
 
@@ -482,9 +511,10 @@ int forward_impl(phsvds_gnn* g, const float* params_host) {
   }
   k_heads_node<<<gr, kT, 0, g->st>>>(n, g->h[kLayers], g->prm + o.ws, g->prm + o.wd, g->prm + o.bd, g->cdiag, g->u,
                                      g->gpre, g->delta);
-  k_heads_edge<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->e, g->u, g->delta, g->deg, g->prm + o.we,
+  k_heads_edge<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->e, g->u, g->delta, g->wdeg, g->prm + o.we,
                                      g->prm + o.bs, g->s, g->m);
   GK(cudaGetLastError());
+  g->launches += 1 + 4 + 3 * 5 + 2;  // SpMM chunks of 2 and 4 x 8 columns, layers, heads
   return 0;
 }
 
@@ -499,64 +529,71 @@ int ensure_pairs(phsvds_gnn* g, int P) {
   return 0;
 }
 
-// loss term mean(1 - cos^2(M R, T)) for P <= 8 pairs; adds scale * dL/dm to g->dm
-int pair_term(phsvds_gnn* g, const double* Rh, const double* Th, int P, double scale, int accumulate, double* loss) {
+// Shared-scale SPAI loss over P <= 32 samples (host FP64 column-major R = C T
+// and T), in chunks of 8 columns: a_p = <M r_p, t_p> / |t_p|^2,
+// b_p = |M r_p|^2 / |t_p|^2, L = 1 - (sum a)^2 / (P sum b); writes dL/dm.
+int spai_term(phsvds_gnn* g, const double* Rh, const double* Th, int P, double* loss) {
   const long long n = g->n;
-  double* dtmp = g->dstage;
-  GK(cudaMemcpyAsync(dtmp, Rh, sizeof(double) * n * P, cudaMemcpyHostToDevice, g->st));
-  GK(launch_from_f64_colmajor(kF32, n, P, dtmp, n, g->R, P, 1.0, g->st));
-  GK(cudaMemcpyAsync(dtmp, Th, sizeof(double) * n * P, cudaMemcpyHostToDevice, g->st));
-  GK(launch_from_f64_colmajor(kF32, n, P, dtmp, n, g->T, P, 1.0, g->st));
-  GK(launch_spmm(kF32, Ecsr(g, g->m), g->R, P, g->Z, P, P, g->st));
-  std::vector<double> zt, zz, tt;
-  int rc;
-  if ((rc = gram_host(g, g->Z, P, g->T, P, 0, P, zt)) || (rc = gram_host(g, g->Z, P, g->Z, P, 0, P, zz)) ||
-      (rc = gram_host(g, g->T, P, g->T, P, 0, P, tt)))
-    return rc;
-  std::vector<double> ca(P), cb(P);
-  double L = 0.0;
-  for (int p = 0; p < P; ++p) {
-    const double a = zt[(size_t)p * P + p], b = zz[(size_t)p * P + p], c = tt[(size_t)p * P + p];
-    const double f = a * a / (b * c);
-    L += 1.0 - f;
-    // d/dZ of mean(1 - f): -(2 a / (b c) T - 2 a^2 / (b^2 c) Z) / P
-    ca[p] = -scale * (2.0 * a / (b * c)) / P;
-    cb[p] = scale * (2.0 * a * a / (b * b * c)) / P;
+  const int nch = (P + 7) / 8;
+  std::vector<double> a(P), b(P), tt(P);
+  for (int c = 0; c < nch; ++c) {
+    const int c0 = 8 * c, w = P - c0 < 8 ? P - c0 : 8;
+    float *R = g->R + n * c0, *T = g->T + n * c0, *Z = g->Z + n * c0;
+    GK(cudaMemcpyAsync(g->dstage, Rh + n * c0, sizeof(double) * n * w, cudaMemcpyHostToDevice, g->st));
+    GK(launch_from_f64_colmajor(kF32, n, w, g->dstage, n, R, w, 1.0, g->st));
+    GK(cudaMemcpyAsync(g->dstage, Th + n * c0, sizeof(double) * n * w, cudaMemcpyHostToDevice, g->st));
+    GK(launch_from_f64_colmajor(kF32, n, w, g->dstage, n, T, w, 1.0, g->st));
+    GK(launch_spmm(kF32, Ecsr(g, g->m), R, w, Z, w, w, g->st));
+    std::vector<double> zt, zz, t2;
+    int rc;
+    if ((rc = gram_host(g, Z, w, T, w, 0, w, zt)) || (rc = gram_host(g, Z, w, Z, w, 0, w, zz)) ||
+        (rc = gram_host(g, T, w, T, w, 0, w, t2)))
+      return rc;
+    for (int p = 0; p < w; ++p) {
+      tt[c0 + p] = t2[(size_t)p * w + p];
+      a[c0 + p] = zt[(size_t)p * w + p] / tt[c0 + p];
+      b[c0 + p] = zz[(size_t)p * w + p] / tt[c0 + p];
+    }
   }
-  *loss += scale * L / P;
-  std::vector<double> cc(2 * P);
+  double sa = 0.0, sb = 0.0;
   for (int p = 0; p < P; ++p) {
-    cc[p] = ca[p];
-    cc[P + p] = cb[p];
+    sa += a[p];
+    sb += b[p];
   }
-  GK(cudaMemcpyAsync(g->dcoef, cc.data(), sizeof(double) * 2 * P, cudaMemcpyHostToDevice, g->st));
-  k_lin_comb<<<grid1(n * P), kT, 0, g->st>>>(n * P, g->T, g->Z, g->dcoef, g->dcoef + P, P, g->dZ);
-  k_dm<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, g->dZ, g->R, P, 1.0f, accumulate, g->dm);
+  if (!(sb > 0) || !std::isfinite(sa) || !std::isfinite(sb)) {
+    phsvds::set_last_error("phsvds_gnn_loss_grad: M C T vanishes or is not finite");
+    return SVDS_ERR_NUMERIC;
+  }
+  *loss = 1.0 - sa * sa / (P * sb);
+  // dL/dZ_p = (-2 sa / (P sb) t_p + 2 sa^2 / (P sb^2) z_p) / |t_p|^2
+  std::vector<double> cc(2 * 32, 0.0);
+  for (int p = 0; p < P; ++p) {
+    cc[p] = -2.0 * sa / (P * sb) / tt[p];
+    cc[32 + p] = 2.0 * sa * sa / (P * sb * sb) / tt[p];
+  }
+  GK(cudaMemcpyAsync(g->dcoef, cc.data(), sizeof(double) * 64, cudaMemcpyHostToDevice, g->st));
+  for (int c = 0; c < nch; ++c) {
+    const int c0 = 8 * c, w = P - c0 < 8 ? P - c0 : 8;
+    k_lin_comb<<<grid1(n * w), kT, 0, g->st>>>(n * w, g->T + n * c0, g->Z + n * c0, g->dcoef + c0,
+                                                 g->dcoef + 32 + c0, w, g->dZ + n * c0);
+    k_dm<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, g->dZ + n * c0, g->R + n * c0, w, 1.0f, c > 0, g->dm);
+  }
   GK(cudaGetLastError());
+  GK(cudaStreamSynchronize(g->st));  // cc is read by the copy above
   return 0;
 }
 
 }  // namespace
 
-extern "C" {
+namespace phsvds {
 
-int phsvds_gnn_num_params(void) { return Offsets().total; }
-
-int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
-  if (!out || !A || A->m < 1 || A->n < 1 || A->nnz < 0 || !A->rowptr) return SVDS_ERR_ARG;
-  *out = nullptr;
-  // the device copy, transpose and validation of svds_create are reused
-  svds_opts o;
-  svds_opts_default(&o);
-  o.stream = stream;
-  svds_handle* h = nullptr;
-  int rc = svds_create(&h, A, &o);
-  if (rc) return rc;
+int gnn_build(phsvds_gnn** out, const DevMatrix& D, bool user_orientation, bool train, cudaStream_t st) {
+  int rc = 0;
   phsvds_gnn* g = new phsvds_gnn();
-  g->st = h->stream;
-  const DevMatrix& D = h->A;
-  // nodes = columns of the user's matrix
-  const bool tr = D.transposed;
+  g->st = st;
+  // nodes = columns of the user's matrix (user_orientation), else of the
+  // device matrix (the operator C of stage 1)
+  const bool tr = user_orientation && D.transposed;
   const long long n = tr ? D.m : D.n;
   const int* rp = tr ? D.rowptrT : D.rowptr;   // rows of the user's A
   const int* ci = tr ? D.colidxT : D.colidx;
@@ -569,13 +606,11 @@ int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
   auto fail = [&](int code) {
     for (void* p : g->allocs) cudaFree(p);
     delete g;
-    svds_destroy(h);
     return code;
   };
   if ((rc = galloc(g, &g->cptr, n + 1)) || (rc = galloc(g, &cnt, n + 1)) || (rc = galloc(g, &err, 4)) ||
       (rc = galloc(g, &work, scan_work_ints(n) + 4)) || (rc = galloc(g, &dmax, 4)))
     return fail(rc);
-  cudaStream_t st = g->st;
   if (cudaMemsetAsync(err, 0, 4 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(dmax, 0, 4 * sizeof(int), st) != cudaSuccess)
     return fail(gfail(cudaGetLastError(), "memset"));
@@ -592,17 +627,22 @@ int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
   g->nnz = hnnz;
   const long long nnz = hnnz;
   if ((rc = galloc(g, &g->cidx, nnz)) || (rc = galloc(g, &g->cval, nnz)) || (rc = galloc(g, &g->cdiag, n)) ||
-      (rc = galloc(g, &g->deg, n)) || (rc = galloc(g, &g->e, nnz)) || (rc = galloc(g, &g->tpos, nnz)) ||
-      (rc = galloc(g, &g->logc, n)) || (rc = galloc(g, &g->prm, g->off.total)) ||
-      (rc = galloc(g, &g->u, n)) || (rc = galloc(g, &g->gpre, n)) || (rc = galloc(g, &g->delta, n)) ||
-      (rc = galloc(g, &g->s, nnz)) || (rc = galloc(g, &g->m, nnz)) || (rc = galloc(g, &g->dm, nnz)) ||
-      (rc = galloc(g, &g->da, nnz)) || (rc = galloc(g, &g->dae, nnz)) || (rc = galloc(g, &g->ddelta, n)) ||
-      (rc = galloc(g, &g->du, n)) || (rc = galloc(g, &g->gu, 2 * n)) || (rc = galloc(g, &g->dh, n * kW)) ||
-      (rc = galloc(g, &g->dz, n * kW)) || (rc = galloc(g, &g->tmp, n * kW)) || (rc = galloc(g, &g->tmp2, n * kW)) ||
-      (rc = galloc(g, &g->ones, n > nnz ? n : nnz)) || (rc = galloc(g, &g->dcoef, 64)) || (rc = galloc(g, &g->dG, 64 * 64)) ||
-      (rc = galloc(g, &g->dstage, n * 8)) || (rc = galloc(g, &g->grad, g->off.total)) ||
-      (rc = galloc(g, &g->am, g->off.total)) || (rc = galloc(g, &g->av, g->off.total)))
+      (rc = galloc(g, &g->deg, n)) || (rc = galloc(g, &g->wdeg, n)) || (rc = galloc(g, &g->e, nnz)) ||
+      (rc = galloc(g, &g->logc, n)) ||
+      (rc = galloc(g, &g->prm, g->off.total)) || (rc = galloc(g, &g->u, n)) || (rc = galloc(g, &g->gpre, n)) ||
+      (rc = galloc(g, &g->delta, n)) || (rc = galloc(g, &g->s, nnz)) || (rc = galloc(g, &g->m, nnz)) ||
+      (rc = galloc(g, &g->ones, n > nnz ? n : nnz)) || (rc = galloc(g, &g->dG, 64 * 64)))
     return fail(rc);
+  // training buffers (backward pass, loss, Adam)
+  if (train &&
+      ((rc = galloc(g, &g->tpos, nnz)) || (rc = galloc(g, &g->dm, nnz)) || (rc = galloc(g, &g->da, nnz)) ||
+       (rc = galloc(g, &g->dae, nnz)) || (rc = galloc(g, &g->ddelta, n)) || (rc = galloc(g, &g->du, n)) ||
+       (rc = galloc(g, &g->gu, 2 * n)) || (rc = galloc(g, &g->dh, n * kW)) || (rc = galloc(g, &g->dz, n * kW)) ||
+       (rc = galloc(g, &g->tmp, n * kW)) || (rc = galloc(g, &g->tmp2, n * kW)) || (rc = galloc(g, &g->dcoef, 64)) ||
+       (rc = galloc(g, &g->dstage, n * 8)) || (rc = galloc(g, &g->grad, g->off.total)) ||
+       (rc = galloc(g, &g->am, g->off.total)) || (rc = galloc(g, &g->av, g->off.total))))
+    return fail(rc);
+  g->train = train;
   if ((rc = galloc(g, reinterpret_cast<char**>(&g->partial), gram_partial_bytes(gram_default_blocks(), kW, 8))))
     return fail(rc);
   g->h[0] = nullptr;
@@ -618,7 +658,7 @@ int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
   k_c_fill<<<grid1(n), kT, 0, st>>>(n, rpT, ciT, vT, rp, ci, va, 1.0 / (D.scale * D.scale), g->cptr, g->cidx,
                                     g->cval);
   k_diag_deg<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->deg, dmax);
-  k_edges<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->e, g->tpos, g->logc);
+  k_edges<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->e, g->wdeg, g->tpos, g->logc);
   k_fill1<<<grid1(n > nnz ? n : nnz), kT, 0, st>>>(n > nnz ? n : nnz, g->ones);
   if (cudaGetLastError() != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph kernels"));
   // mean of log c_ii (FP64-class Gram of the ones vector with log c)
@@ -634,15 +674,93 @@ int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
   cudaMemcpyAsync(&hdmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph features"));
   k_x0<<<grid1(n), kT, 0, st>>>(n, g->logc, g->deg, (float)(hsum / n), (float)(hdmax > 0 ? hdmax : 1), g->x0);
+  g->launches += 12;  // count, scan (3), fill, diagonal, edges, ones, Gram + reduce, features
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph x0"));
-  // the graph keeps its own copy; the temporary solver handle is released
-  if (h->own_stream) {
+  *out = g;
+  return SVDS_OK;
+}
+
+
+int gnn_precond(phsvds_gnn* g, const float* params, CsrDev* f32, CsrDev* f64) {
+  if (!g || !params || !f32) return SVDS_ERR_ARG;
+  int rc = forward_impl(g, params);
+  if (rc) return rc;
+  *f32 = Ecsr(g, g->m);
+  if (f64) {
+    if (!g->m64 && (rc = galloc(g, &g->m64, g->nnz))) return rc;
+    k_to_f64<<<grid1(g->nnz), kT, 0, g->st>>>(g->nnz, g->m, g->m64);
+    GK(cudaGetLastError());
+    g->launches += 1;
+    *f64 = Ecsr(g, nullptr);
+    f64->v64 = g->m64;
+  }
+  return SVDS_OK;
+}
+
+long long gnn_launches(const phsvds_gnn* g) { return g ? g->launches : 0; }
+
+}  // namespace phsvds
+
+extern "C" {
+
+int phsvds_gnn_num_params(void) { return Offsets().total; }
+
+int phsvds_gnn_init(uint64_t seed, float* params) {
+  if (!params) return SVDS_ERR_ARG;
+  uint64_t st = seed;
+  auto next = [&]() {  // splitmix64
+    st += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  };
+  auto normal = [&]() {  // Box-Muller on two uniforms in (0, 1]
+    const double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+    const double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  const Offsets o;
+  for (int e = 0; e < o.total; ++e) params[e] = 0.f;
+  for (int l = 0; l < kLayers; ++l) {
+    const int fin = l == 0 ? 2 : kW;
+    const double sd = std::sqrt(2.0 / (fin + kW));
+    for (int e = 0; e < fin * kW; ++e) params[o.W1[l] + e] = (float)(sd * normal());
+    for (int e = 0; e < fin * kW; ++e) params[o.W2[l] + e] = (float)(sd * normal());
+  }
+  for (int c = 0; c < kW; ++c) params[o.wd + c] = (float)(std::sqrt(1.0 / kW) * normal());
+  for (int c = 0; c < kW; ++c) params[o.ws + c] = (float)(0.1 * std::sqrt(1.0 / kW) * normal());
+  params[o.bd] = 0.5f;
+  params[o.bs] = 1.f;
+  return SVDS_OK;
+}
+
+int phsvds_gnn_create(phsvds_gnn** out, const svds_csr* A, void* stream) {
+  if (!out || !A || A->m < 1 || A->n < 1 || A->nnz < 0 || !A->rowptr) return SVDS_ERR_ARG;
+  *out = nullptr;
+  // the device copy, transpose and validation of svds_create are reused
+  svds_opts o;
+  svds_opts_default(&o);
+  o.stream = stream;
+  svds_handle* h = nullptr;
+  int rc = svds_create(&h, A, &o);
+  if (rc) return rc;
+  phsvds_gnn* g = nullptr;
+  rc = gnn_build(&g, h->A, true, true, h->stream);
+  if (rc == 0 && h->own_stream) {
+    // the temporary handle's stream goes away with it
     cudaStream_t s2;
-    cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
-    g->st = s2;
-    g->own_stream = true;
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = gfail(cudaGetLastError(), "stream");
+      phsvds_gnn_destroy(g);
+      g = nullptr;
+    } else {
+      g->st = s2;
+      g->own_stream = true;
+    }
   }
   svds_destroy(h);
+  if (rc) return rc;
   *out = g;
   return SVDS_OK;
 }
@@ -680,21 +798,19 @@ int phsvds_gnn_forward(phsvds_gnn* g, const float* params, float* mvals) {
 }
 
 int phsvds_gnn_loss_grad(phsvds_gnn* g, const float* params, const double* R, const double* T, int P,
-                         const double* Y, const double* X, int Q, double* loss, double* grad) {
-  if (!g || !params || !R || !T || P < 1 || P > 8 || Q < 0 || Q > 8 || (Q > 0 && (!Y || !X)) || !loss || !grad)
-    return SVDS_ERR_ARG;
+                         double* loss, double* grad) {
+  if (!g || !g->train || !params || !R || !T || P < 1 || P > 32 || !loss || !grad) return SVDS_ERR_ARG;
   const Offsets& o = g->off;
   const long long n = g->n;
   const int gr = grid1(n);
   int rc = forward_impl(g, params);
   if (rc) return rc;
-  if ((rc = ensure_pairs(g, P > Q ? P : Q))) return rc;
+  if ((rc = ensure_pairs(g, P))) return rc;
   double L = 0.0;
-  if ((rc = pair_term(g, R, T, P, 1.0, 0, &L))) return rc;
-  if (Q > 0 && (rc = pair_term(g, Y, X, Q, kLam, 1, &L))) return rc;
+  if ((rc = spai_term(g, R, T, P, &L))) return rc;
   std::vector<double> gr_h(o.total, 0.0);
   // heads
-  k_heads_bwd<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->tpos, g->dm, g->s, g->delta, g->deg, g->e, g->ddelta,
+  k_heads_bwd<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->tpos, g->dm, g->s, g->delta, g->wdeg, g->e, g->ddelta,
                                     g->du, g->da, g->dae);
   k_node_bwd<<<gr, kT, 0, g->st>>>(n, g->ddelta, g->du, g->gpre, g->cdiag, g->prm + o.ws, g->prm + o.wd, g->gu,
                                    g->dh);
@@ -747,8 +863,99 @@ int phsvds_gnn_loss_grad(phsvds_gnn* g, const float* params, const double* R, co
   return SVDS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+int ensure_work(phsvds_gnn* g) {
+  int rc;
+  if (!g->w0 && ((rc = galloc(g, &g->w0, g->n * 8)) || (rc = galloc(g, &g->w1, g->n * 8)) ||
+                 (rc = galloc(g, &g->w2, g->n * 8))))
+    return rc;
+  return 0;
+}
+
+CsrDev Ccsr(const phsvds_gnn* g) {
+  CsrDev c = Ecsr(g, nullptr);
+  c.v64 = g->cval;
+  return c;
+}
+
+// device row-major n x q (ld q) -> host column-major
+int to_host_cm(phsvds_gnn* g, const double* dsrc, int q, double* host) {
+  GK(launch_to_f64_colmajor(kF64, g->n, q, dsrc, q, g->w2, g->n, 1.0, g->st));
+  GK(cudaMemcpyAsync(host, g->w2, sizeof(double) * g->n * q, cudaMemcpyDeviceToHost, g->st));
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int phsvds_gnn_pairs(phsvds_gnn* g, int P, int smooth, uint64_t seed, double* R, double* T) {
+  if (!g || P < 1 || P > 8 || smooth < 0 || smooth > 1000 || !R || !T) return SVDS_ERR_ARG;
+  int rc = ensure_work(g);
+  if (rc) return rc;
+  const long long n = g->n;
+  GK(launch_fill_normal(kF64, n, g->w0, P, P, seed, g->st));
+  for (int s = 0; s < smooth; ++s) {
+    GK(launch_spmm(kF64, Ccsr(g), g->w0, P, g->w1, P, P, g->st));
+    k_smooth<<<grid1(n * P), kT, 0, g->st>>>(n, P, g->w1, g->cdiag, 2.0 / 3.0, g->w0);
+    GK(cudaGetLastError());
+  }
+  GK(launch_spmm(kF64, Ccsr(g), g->w0, P, g->w1, P, P, g->st));
+  if ((rc = to_host_cm(g, g->w0, P, T))) return rc;
+  GK(cudaStreamSynchronize(g->st));
+  if ((rc = to_host_cm(g, g->w1, P, R))) return rc;
+  GK(cudaStreamSynchronize(g->st));
+  return SVDS_OK;
+}
+
+int phsvds_gnn_apply_c(phsvds_gnn* g, const double* X, int q, double* Y) {
+  if (!g || q < 1 || q > 8 || !X || !Y) return SVDS_ERR_ARG;
+  int rc = ensure_work(g);
+  if (rc) return rc;
+  const long long n = g->n;
+  GK(cudaMemcpyAsync(g->w2, X, sizeof(double) * n * q, cudaMemcpyHostToDevice, g->st));
+  GK(launch_from_f64_colmajor(kF64, n, q, g->w2, n, g->w0, q, 1.0, g->st));
+  GK(launch_spmm(kF64, Ccsr(g), g->w0, q, g->w1, q, q, g->st));
+  if ((rc = to_host_cm(g, g->w1, q, Y))) return rc;
+  GK(cudaStreamSynchronize(g->st));
+  return SVDS_OK;
+}
+
+int phsvds_gnn_save(const char* path, const float* params) {
+  if (!path || !params) return SVDS_ERR_ARG;
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return SVDS_ERR_ARG;
+  const int32_t cnt = Offsets().total;
+  bool ok = std::fwrite("PHSGNN01", 1, 8, f) == 8 && std::fwrite(&cnt, sizeof(cnt), 1, f) == 1 &&
+            std::fwrite(params, sizeof(float), cnt, f) == (size_t)cnt;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SVDS_OK : SVDS_ERR_ARG;
+}
+
+int phsvds_gnn_load(const char* path, float* params) {
+  if (!path || !params) return SVDS_ERR_ARG;
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return SVDS_ERR_ARG;
+  char tag[8];
+  int32_t cnt = 0;
+  const int32_t want = Offsets().total;
+  std::vector<float> buf(want);
+  bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, "PHSGNN01", 8) == 0 &&
+            std::fread(&cnt, sizeof(cnt), 1, f) == 1 && cnt == want &&
+            std::fread(buf.data(), sizeof(float), want, f) == (size_t)want;
+  std::fclose(f);
+  if (!ok) return SVDS_ERR_ARG;
+  for (float v : buf)
+    if (!std::isfinite(v)) return SVDS_ERR_ARG;
+  std::memcpy(params, buf.data(), sizeof(float) * want);
+  return SVDS_OK;
+}
+
 int phsvds_gnn_adam(phsvds_gnn* g, float* params, const double* grad, float* m, float* v, int step, float lr) {
-  if (!g || !params || !grad || !m || !v || step < 1 || !(lr > 0)) return SVDS_ERR_ARG;
+  if (!g || !g->train || !params || !grad || !m || !v || step < 1 || !(lr > 0)) return SVDS_ERR_ARG;
   const int np = g->off.total;
   float* dp = g->prm;
   GK(cudaMemcpyAsync(dp, params, sizeof(float) * np, cudaMemcpyHostToDevice, g->st));

@@ -4,7 +4,8 @@
 //     (I - x x^T)(op - eta I)(I - x x^T) t = -r,   t orthogonal to x,
 // for a block of nb columns at once (one independent system per column), with
 // the projected preconditioner K~^-1 z = K^-1 z - K^-1 x (x^T K^-1 z)/(x^T K^-1 x)
-// (K = Jacobi diagonal or identity).  The paper runs JDQMR as the stage-2
+// (K^-1 = Jacobi diagonal, identity, or a sparse symmetric matrix such as the
+// learned approximate inverse, applied by SpMM).  The paper runs JDQMR as the stage-2
 // method (Sec. 3.4) and uses it in stage 1 in its experiments (Sec. 4).
 //
 // The vectors use the storage/arithmetic of one mode: FP32 by default (the
@@ -140,10 +141,12 @@ __device__ __forceinline__ void strow(typename P::S* __restrict__ p, long long r
 
 // ---- initialisation ----
 // kx = K^-1 x, u = K^-1 b, dots: x^T kx, x^T u, b^T b, b^T u, b^T kx
+// (upre != nullptr: kx = K^-1 x and upre = K^-1 b were computed by SpMM)
 template <class P>
 __global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const typename P::S* __restrict__ x,
                                                  const typename P::S* __restrict__ b,
                                                  const typename P::S* __restrict__ dinv, typename P::S* __restrict__ kx,
+                                                 const typename P::S* __restrict__ upre,
                                                  typename P::G* __restrict__ partial) {
   using G = typename P::G;
   G acc[5][kMaxNb];
@@ -158,8 +161,15 @@ __global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const type
       if (j < nb) {
         const long long o = r * nb + j;
         const auto xv = P::load(x + o), bv = P::load(b + o);
-        const auto kv = mul<P>(s, xv), uv = mul<P>(s, bv);
-        P::store(kx + o, kv);
+        typename P::A kv, uv;
+        if (upre) {
+          kv = P::load(kx + o);
+          uv = P::load(upre + o);
+        } else {
+          kv = mul<P>(s, xv);
+          uv = mul<P>(s, bv);
+          P::store(kx + o, kv);
+        }
         acc[0][j] = P::gfma(acc[0][j], xv, kv);
         acc[1][j] = P::gfma(acc[1][j], xv, uv);
         acc[2][j] = P::gfma(acc[2][j], bv, bv);
@@ -191,9 +201,11 @@ __global__ void k_qmr_init_scalars(int nb, const double* __restrict__ dots, QmrS
 template <class P>
 __global__ void __launch_bounds__(kT) k_qmr_init_vec(long long L, int nb, const typename P::S* __restrict__ b,
                                                      const typename P::S* __restrict__ dinv,
-                                                     const typename P::S* __restrict__ kx, const QmrState* __restrict__ S,
-                                                     typename P::S* __restrict__ q, typename P::S* __restrict__ r,
-                                                     typename P::S* __restrict__ d, typename P::S* __restrict__ sol) {
+                                                     const typename P::S* __restrict__ kx,
+                                                     const typename P::S* __restrict__ upre,
+                                                     const QmrState* __restrict__ S, typename P::S* __restrict__ q,
+                                                     typename P::S* __restrict__ r, typename P::S* __restrict__ d,
+                                                     typename P::S* __restrict__ sol) {
   __shared__ typename P::C gm[kMaxNb];
   if (threadIdx.x < nb) gm[threadIdx.x] = to_c<P>(S[threadIdx.x].gamma);
   __syncthreads();
@@ -201,9 +213,9 @@ __global__ void __launch_bounds__(kT) k_qmr_init_vec(long long L, int nb, const 
   for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < total; e += (long long)gridDim.x * kT) {
     const long long row = e / nb;
     const int j = (int)(e % nb);
-    const auto sv = ld_or_one<P>(dinv, row);
     const auto bv = P::load(b + e);
-    P::store(q + e, P::sub(mul<P>(sv, bv), P::mulc(P::load(kx + e), gm[j])));
+    const auto ub = upre ? P::load(upre + e) : mul<P>(ld_or_one<P>(dinv, row), bv);
+    P::store(q + e, P::sub(ub, P::mulc(P::load(kx + e), gm[j])));
     P::store(r + e, bv);
     P::store(d + e, P::zero());
     P::store(sol + e, P::zero());
@@ -306,6 +318,33 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
   block_reduce_store<P, 4, NB>(acc, nb, partial);
 }
 
+// dots r^T u, x^T u for u = K^-1 r computed by SpMM (sparse K^-1)
+template <class P, int NB, bool VEC>
+__global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const typename P::S* __restrict__ x,
+                                                   const typename P::S* __restrict__ r,
+                                                   const typename P::S* __restrict__ u,
+                                                   typename P::G* __restrict__ partial) {
+  using G = typename P::G;
+  using A = typename P::A;
+  G acc[2][NB];
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+  for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
+    A xv[NB], rv[NB], uv[NB];
+    ldrow<P, NB, VEC>(x, row, nb, xv);
+    ldrow<P, NB, VEC>(r, row, nb, rv);
+    ldrow<P, NB, VEC>(u, row, nb, uv);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc[0][j] = P::gfma(acc[0][j], rv[j], uv[j]);
+      acc[1][j] = P::gfma(acc[1][j], xv[j], uv[j]);
+    }
+  }
+  block_reduce_store<P, 2, NB>(acc, nb, partial);
+}
+
 // QMR smoothing scalars, stopping test, next search-direction coefficients
 __global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
   const int j = threadIdx.x;
@@ -343,6 +382,7 @@ template <class P, int NB, bool VEC>
 __global__ void __launch_bounds__(kT) k_qmr_update2(long long L, int nb, const typename P::S* __restrict__ r,
                                                     const typename P::S* __restrict__ kx,
                                                     const typename P::S* __restrict__ dinv,
+                                                    const typename P::S* __restrict__ upre,
                                                     const QmrState* __restrict__ S, typename P::S* __restrict__ q,
                                                     typename P::S* __restrict__ d, typename P::S* __restrict__ sol) {
   using C = typename P::C;
@@ -369,9 +409,9 @@ __global__ void __launch_bounds__(kT) k_qmr_update2(long long L, int nb, const t
     ldrow<P, NB, VEC>(q, row, nb, qv);
     ldrow<P, NB, VEC>(d, row, nb, dv);
     ldrow<P, NB, VEC>(sol, row, nb, sv_);
-    ldrow<P, NB, VEC>(r, row, nb, rv);
+    ldrow<P, NB, VEC>(upre ? upre : r, row, nb, rv);
     ldrow<P, NB, VEC>(kx, row, nb, kv);
-    const auto s = ld_or_one<P>(dinv, row);
+    const auto s = upre ? ld_or_one<P>(nullptr, row) : ld_or_one<P>(dinv, row);
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if (!up[j]) continue;
@@ -435,49 +475,66 @@ __global__ void k_convert_cols(long long L, int nc, const typename PS::S* src, l
 }
 
 template <class P>
-cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void* dinv, void* kx, void* q, void* r,
-                   void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void* dinv, const CsrDev* K, void* u,
+                   void* kx, void* q, void* r, void* d, void* sol, QmrState* S, void* partial, double* dots,
+                   cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
   const int g = qmr_grid(L);
   G* pd = reinterpret_cast<G*>(partial);
-  k_qmr_init<P><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)b, (const SS*)dinv, (SS*)kx, pd);
+  const SS* upre = nullptr;
+  if (K) {
+    cudaError_t e = launch_spmm(P::id, *K, x, nb, kx, nb, nb, st);
+    if (e == cudaSuccess) e = launch_spmm(P::id, *K, b, nb, u, nb, nb, st);
+    if (e != cudaSuccess) return e;
+    upre = (const SS*)u;
+    dinv = nullptr;
+  }
+  k_qmr_init<P><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)b, (const SS*)dinv, (SS*)kx, upre, pd);
   k_reduce_g<P><<<5 * nb, 128, 0, st>>>(pd, g, 5 * nb, dots);
   k_qmr_init_scalars<<<1, 32, 0, st>>>(nb, dots, S);
-  k_qmr_init_vec<P><<<qmr_grid(L * nb), kT, 0, st>>>(L, nb, (const SS*)b, (const SS*)dinv, (const SS*)kx, S, (SS*)q,
-                                                     (SS*)r, (SS*)d, (SS*)sol);
+  k_qmr_init_vec<P><<<qmr_grid(L * nb), kT, 0, st>>>(L, nb, (const SS*)b, (const SS*)dinv, (const SS*)kx, upre, S,
+                                                     (SS*)q, (SS*)r, (SS*)d, (SS*)sol);
   return cudaGetLastError();
 }
 
 template <class P, int NB, bool VEC>
 cudaError_t step_nb(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                    const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
-                    void* partial, double* dots, cudaStream_t st) {
+                    const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
+                    void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
   const int g = qmr_grid(L);
   G* pd = reinterpret_cast<G*>(partial);
+  if (K) dinv = nullptr;
   k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
   k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
   k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
   k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
                                               (const SS*)dinv, eta, S, (SS*)r, pd);
   k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  if (K) {
+    // u = K^-1 r by SpMM; r^T u and x^T u replace dots 1 and 2
+    const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
+    if (e != cudaSuccess) return e;
+    k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
+    k_reduce_g<P><<<2 * nb, 128, 0, st>>>(pd, g, 2 * nb, dots + nb);
+  }
   k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
-  k_qmr_update2<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv, S, (SS*)q,
-                                              (SS*)d, (SS*)sol);
+  k_qmr_update2<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv,
+                                              K ? (const SS*)u : nullptr, S, (SS*)q, (SS*)d, (SS*)sol);
   return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t step_p(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                   const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
-                   void* partial, double* dots, cudaStream_t st) {
+                   const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
+                   void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   constexpr size_t es = sizeof(typename P::S);
 #define STEP(NBv)                                                                                                  \
   ((nb == NBv && (NBv * es) % 16 == 0)                                                                            \
-       ? step_nb<P, NBv, true>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st)          \
-       : step_nb<P, NBv, false>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
+       ? step_nb<P, NBv, true>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st)    \
+       : step_nb<P, NBv, false>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
   if (nb <= 1) return STEP(1);
   if (nb <= 2) return STEP(2);
   if (nb <= 4) return STEP(4);
@@ -487,31 +544,46 @@ cudaError_t step_p(long long L, int nb, const void* x, const void* w, const void
 
 }  // namespace
 
-cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, void* kx, void* q,
-                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
-  if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, const CsrDev* K,
+                     void* u, void* kx, void* q, void* r, void* d, void* sol, QmrState* S, void* partial,
+                     double* dots, cudaStream_t st) {
+  if (nb < 1 || nb > kMaxNb || (K && !u)) return cudaErrorInvalidValue;
   switch (prec) {
-    case kF32: return init_p<PF32>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
-    case kDF64: return init_p<PDF64>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
-    case kF64: return init_p<PF64>(L, nb, x, b, dinv, kx, q, r, d, sol, S, partial, dots, st);
+    case kF32: return init_p<PF32>(L, nb, x, b, dinv, K, u, kx, q, r, d, sol, S, partial, dots, st);
+    case kDF64: return init_p<PDF64>(L, nb, x, b, dinv, K, u, kx, q, r, d, sol, S, partial, dots, st);
+    case kF64: return init_p<PF64>(L, nb, x, b, dinv, K, u, kx, q, r, d, sol, S, partial, dots, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                     const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
-                     void* partial, double* dots, cudaStream_t st) {
-  if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+                     const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
+                     void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+  if (nb < 1 || nb > kMaxNb || (K && !u)) return cudaErrorInvalidValue;
   switch (prec) {
-    case kF32: return step_p<PF32>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
-    case kDF64: return step_p<PDF64>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
-    case kF64: return step_p<PF64>(L, nb, x, w, kx, dinv, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+    case kF32:
+      return step_p<PF32>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+    case kDF64:
+      return step_p<PDF64>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+    case kF64:
+      return step_p<PF64>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
   }
   return cudaErrorInvalidValue;
 }
 
-int qmr_step_launches() { return 7; }
-int qmr_init_launches() { return 4; }
+namespace {
+int spmm_chunks(int b) {
+  int c = 0;
+  while (b > 0) {
+    b -= b >= 8 ? 8 : b >= 4 ? 4 : b >= 2 ? 2 : 1;
+    ++c;
+  }
+  return c;
+}
+}  // namespace
+
+int qmr_step_launches(int nb, bool sparse_k) { return 7 + (sparse_k ? spmm_chunks(nb) + 2 : 0); }
+int qmr_init_launches(int nb, bool sparse_k) { return 4 + (sparse_k ? 2 * spmm_chunks(nb) : 0); }
 
 cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,
                          long long L, int nc, const double* scale, cudaStream_t st) {

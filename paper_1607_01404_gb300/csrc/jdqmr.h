@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "kernels.h"
+
 namespace phsvds {
 
 // Per-column state of the block sQMR recurrences (device memory).
@@ -14,17 +16,21 @@ struct QmrState {
 // Blocks are in the storage of mode prec (F32, DF64 or F64), row-major L x nb
 // with leading dimension nb (nb <= 8).  x: Ritz vectors (orthonormal columns),
 // b: right-hand sides (orthogonal to x), dinv: Jacobi diagonal K^-1 in the same
-// storage, or nullptr.  partial: >= 608 * 5 * nb * 8 bytes, dots: >= 5 * nb doubles.
-cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, void* kx, void* q,
-                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st);
+// storage, or nullptr; K: a sparse symmetric K^-1 (values in the mode's
+// format) applied by SpMM instead of dinv, with u an L x nb work block, or
+// nullptr.  partial: >= 608 * 5 * nb * 8 bytes, dots: >= 5 * nb doubles.
+cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, const CsrDev* K,
+                     void* u, void* kx, void* q, void* r, void* d, void* sol, QmrState* S, void* partial,
+                     double* dots, cudaStream_t st);
 // One inner step after w = op(q) (the caller applies the operator): updates r,
 // d, sol, q and the scalars; eta: per-column shifts (device doubles).  A column
 // stops when tau sqrt(k + 1) <= xi tau0 or after maxk steps.
 cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                     const double* eta, double xi, int maxk, void* q, void* r, void* d, void* sol, QmrState* S,
-                     void* partial, double* dots, cudaStream_t st);
-int qmr_step_launches();
-int qmr_init_launches();
+                     const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
+                     void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st);
+// kernel launches of one qmr_step / qmr_init call
+int qmr_step_launches(int nb, bool sparse_k);
+int qmr_init_launches(int nb, bool sparse_k);
 
 // dst[:, j] = scale[j] * src[:, j] with a mode conversion (scale: device doubles).
 cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,

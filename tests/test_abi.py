@@ -106,3 +106,44 @@ def test_create_rejects_bad_shapes_and_options():
     with pytest.raises(B.SvdsError) as e:
         B.svds_create(rp, ci, va, 2, 2, o)
     assert e.value.code == B.SVDS_ERR_ARG
+
+
+def test_gnn_init_is_seeded_and_scaled():
+    a = B.gnn_init(0)
+    b = B.gnn_init(0)
+    c = B.gnn_init(1)
+    assert a.dtype == np.float32 and a.shape == (B.gnn_num_params(),)
+    np.testing.assert_array_equal(a, b)
+    assert np.any(a != c)
+    # first-layer W1 (2 x 32): N(0, 2/34); bd = 0.5 is the last entry
+    w = B.gnn_init(7)[:64]
+    assert 0.1 < w.std() < 0.4
+    assert a[-1] == np.float32(0.5)
+
+
+def test_gnn_save_load_roundtrip_and_rejects_bad_files(tmp_path):
+    th = B.gnn_init(3)
+    p = tmp_path / "m.bin"
+    B.gnn_save(p, th)
+    np.testing.assert_array_equal(B.gnn_load(p), th)
+    raw = p.read_bytes()
+    for bad in (raw[:-4], b"XXXXXXXX" + raw[8:], raw[:8] + (5).to_bytes(4, "little") + raw[12:]):
+        q = tmp_path / "bad.bin"
+        q.write_bytes(bad)
+        with pytest.raises(B.SvdsError):
+            B.gnn_load(q)
+    with pytest.raises(B.SvdsError):
+        B.gnn_load(tmp_path / "missing.bin")
+
+
+def test_learned_precond_needs_parameters():
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 1], dtype=np.int32)
+    va = np.array([1.0, 2.0])
+    o = B.make_opts(precond=B.SVDS_PRECOND_LEARNED)
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 2, 2, o)
+    assert e.value.code == B.SVDS_ERR_ARG
+    o = B.make_opts(precond=7)
+    with pytest.raises(B.SvdsError):
+        B.svds_create(rp, ci, va, 2, 2, o)

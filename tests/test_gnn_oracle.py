@@ -11,11 +11,8 @@ def _small():
     A = wl.weighted_grid(6, 2, seed=3)
     g = G.Graph(A.to_scipy())
     rng = np.random.default_rng(0)
-    R = rng.standard_normal((g.n, 3))
-    T = rng.standard_normal((g.n, 3))
-    Y = rng.standard_normal((g.n, 2))
-    X = rng.standard_normal((g.n, 2))
-    return g, R, T, Y, X
+    T = rng.standard_normal((g.n, 5))
+    return g, g.C @ T, T
 
 
 def test_M_is_symmetric_spd_and_diagonally_dominant():
@@ -44,15 +41,12 @@ def test_graph_matches_definition():
     np.testing.assert_allclose(E, ref, atol=1e-12)
 
 
-@pytest.mark.parametrize("with_ritz", [False, True])
-def test_gradient_matches_central_differences(with_ritz):
-    g, R, T, Y, X = _small()
+def test_gradient_matches_central_differences():
+    g, R, T = _small()
     p = G.init_params(7)
+    p["bs"] = np.array(0.8)
     theta = G.flatten(p)
-    if with_ritz:
-        loss, grads = G.loss_and_grad(g, p, R, T, Y, X)
-    else:
-        loss, grads = G.loss_and_grad(g, p, R, T)
+    loss, grads = G.loss_and_grad(g, p, R, T)
     gflat = G.flatten(grads)
     rng = np.random.default_rng(1)
     idx = rng.choice(theta.size, size=40, replace=False)
@@ -62,19 +56,77 @@ def test_gradient_matches_central_differences(with_ritz):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fp = G.loss_and_grad(g, G.unflatten(tp), R, T, *( (Y, X) if with_ritz else ()))[0]
-        fm = G.loss_and_grad(g, G.unflatten(tm), R, T, *( (Y, X) if with_ritz else ()))[0]
-        fd = (fp - fm) / (2 * h)
+        fd = (G.loss_and_grad(g, G.unflatten(tp), R, T)[0] - G.loss_and_grad(g, G.unflatten(tm), R, T)[0]) / (2 * h)
         assert abs(fd - gflat[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (i, fd, gflat[i])
 
 
-def test_loss_is_scale_invariant():
-    g, R, T, _, _ = _small()
-    p = G.init_params(3)
-    l1 = G.loss_and_grad(g, p, R, T)[0]
-    l2 = G.loss_and_grad(g, p, R * 3.0, T * 0.5)[0]
-    assert abs(l1 - l2) < 1e-12
+def test_dm_matches_central_differences():
+    g, R, T = _small()
+    m = G.forward(g, G.init_params(2))
+    _, dm = G.loss_from_m(g, m, R, T)
+    rng = np.random.default_rng(3)
+    for k in rng.choice(m.size, size=25, replace=False):
+        h = 1e-4 * abs(m[k]) + 1e-12
+        mp, mm = m.copy(), m.copy()
+        mp[k] += h
+        mm[k] -= h
+        fd = (G.loss_from_m(g, mp, R, T)[0] - G.loss_from_m(g, mm, R, T)[0]) / (2 * h)
+        assert abs(fd - dm[k]) <= 1e-5 * abs(fd) + 1e-9 * np.abs(dm).max(), (k, fd, dm[k])
+
+
+def _identity_m(g):
+    return np.where(g.rows == g.indices, 1.0, 0.0)
+
+
+def test_loss_of_identity_on_eigenvectors():
+    # M = I and t_p eigenvectors of C (eigenvalue l_p): a_p = l_p, b_p = l_p^2, so
+    # L = 1 - (sum l)^2 / (P sum l^2), whatever the scale of each t_p
+    g, _, _ = _small()
+    lam, V = np.linalg.eigh(g.C.toarray())
+    sel = [0, 4, 9, 30]
+    T = V[:, sel] * np.array([1.0, -2.0, 0.5, 3.0])
+    L, _ = G.loss_from_m(g, _identity_m(g), g.C @ T, T)
+    l = lam[sel]
+    assert abs(L - (1 - l.sum() ** 2 / (len(l) * (l * l).sum()))) < 1e-13
+
+
+def test_loss_vanishes_for_the_exact_inverse_of_a_diagonal_C():
+    # C diagonal: M = C^-1 (representable on the pattern) gives M C t = t for every t
+    import scipy.sparse as sp
+
+    A = sp.diags([1.0, 2.0, 3.0, 0.5]).tocsr()
+    g = G.Graph(A)
+    m = 1.0 / g.cdiag[g.rows]
+    T = np.random.default_rng(4).standard_normal((4, 3))
+    L, dm = G.loss_from_m(g, m, g.C @ T, T)
+    assert abs(L) < 1e-15 and np.abs(dm).max() < 1e-13
+    L2, _ = G.loss_from_m(g, np.ones(4), g.C @ T, T)
+    assert L2 > 1e-3
+
+
+def test_loss_is_scale_invariant_and_bounded():
+    g, R, T = _small()
+    m = G.forward(g, G.init_params(3))
+    l1 = G.loss_from_m(g, m, R, T)[0]
+    s = np.array([3.0, 0.5, 1.0, 2.0, 7.0])
+    assert abs(G.loss_from_m(g, 2.5 * m, R * s, T * s)[0] - l1) < 1e-12
     assert 0.0 <= l1 <= 1.0
+
+
+def test_edge_weights_follow_the_coupling_strength():
+    g, _, _ = _small()
+    p = G.init_params(0)
+    for name in p:
+        p[name] = np.zeros_like(p[name])
+    p["bs"] = np.array(2.0)
+    p["bd"] = np.array(1.0)
+    m = G.forward(g, p)
+    off = g.offdiag
+    delta = np.log1p(np.e) / g.cdiag  # softplus(1) / c_ii
+    mu = np.minimum(delta[g.rows], delta[g.indices])
+    ref = 0.9 * np.tanh(2.0) * mu * np.abs(g.e) / np.maximum(g.wdeg[g.rows], g.wdeg[g.indices])
+    np.testing.assert_allclose(m[off], ref[off], rtol=1e-13)
+    np.testing.assert_allclose(m[~off], delta[g.rows[~off]], rtol=1e-13)
 
 
 def test_graph_keeps_cancelling_entries():

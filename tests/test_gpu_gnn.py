@@ -32,7 +32,7 @@ def _theta(seed):
     rng = np.random.default_rng(100 + seed)
     # non-zero biases so that every head term is exercised
     p["we"] = np.array(0.3)
-    p["bs"] = np.array(-0.2)
+    p["bs"] = np.array(0.7)
     for l in range(G.LAYERS):
         p[f"b_{l}"] = 0.1 * rng.standard_normal(G.WIDTH)
     th = G.flatten(p).astype(np.float32)
@@ -91,25 +91,24 @@ def test_loss_and_gradient_match_oracle(name, A):
     ref = G.Graph(A.to_scipy())
     rng = np.random.default_rng(11)
     n = ref.n
-    R, T = rng.standard_normal((n, 5)), rng.standard_normal((n, 5))
-    Y, X = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
-    th, p = _theta(2)
-    for with_q in (False, True):
-        args = (R, T, Y, X) if with_q else (R, T)
-        L, grad = g.loss_grad(th, *args)
-        Lr, gr = G.loss_and_grad(ref, p, *args)
+    lam, V = np.linalg.eigh(ref.C.toarray())
+    for T in (rng.standard_normal((n, 5)), np.hstack([V[:, :3], rng.standard_normal((n, 14))])):
+        th, p = _theta(2)
+        L, grad = g.loss_grad(th, ref.C @ T, T)
+        Lr, gr = G.loss_and_grad(ref, p, ref.C @ T, T)
         gr = G.flatten(gr)
         assert abs(L - Lr) < 1e-5 * max(1.0, abs(Lr)), (L, Lr)
         err = np.linalg.norm(grad - gr) / np.linalg.norm(gr)
-        assert err < G_TOL, (name, with_q, err)
+        assert err < G_TOL, (name, T.shape, err)
     g.close()
 
 
 def test_gradient_is_a_descent_direction_and_adam_steps():
     A = wl.weighted_grid(16, 2, seed=1)
     g = _gnn(A)
-    rng = np.random.default_rng(5)
-    R, T = rng.standard_normal((g.n, 4)), rng.standard_normal((g.n, 4))
+    R1, T1 = g.pairs(4, 0, 5)
+    R2, T2 = g.pairs(4, 40, 6)
+    R, T = np.hstack([R1, R2]), np.hstack([T1, T2])
     th, _ = _theta(4)
     L0, grad = g.loss_grad(th, R, T)
     m = np.zeros_like(th)
@@ -130,9 +129,83 @@ def test_rejects_bad_arguments():
     A = wl.weighted_grid(6, 2, seed=1)
     g = _gnn(A)
     th, _ = _theta(0)
-    R = np.zeros((g.n, 9))
+    R = np.ones((g.n, 33))
     with pytest.raises(B.SvdsError):
-        g.loss_grad(th, R, R)  # at most 8 pairs per call
+        g.loss_grad(th, R, R)  # at most 32 samples per call
+    Z = np.zeros((g.n, 2))
+    with pytest.raises(B.SvdsError) as e:
+        g.loss_grad(th, Z, np.ones((g.n, 2)))  # M R = 0
+    assert e.value.code == B.SVDS_ERR_NUMERIC
     with pytest.raises(ValueError):
         g.forward(th[:-1])
     g.close()
+
+
+def test_pairs_and_c_apply_match_the_graph():
+    A = wl.weighted_grid(18, 2, seed=4)
+    g = _gnn(A)
+    ref = G.Graph(A.to_scipy())
+    C = ref.C
+    normC = abs(C).sum(axis=1).max()
+    rq = []
+    for s in (0, 4, 32):
+        R, T = g.pairs(5, s, 9)
+        assert np.linalg.norm(R - C @ T) <= 1e-13 * normC * np.linalg.norm(T)
+        # damped Jacobi smoothing leaves the low end of the spectrum of C
+        rq.append(np.mean(np.sum(T * (C @ T), axis=0) / np.sum(T * T, axis=0)))
+    assert rq[0] > rq[1] > rq[2]
+    X = np.random.default_rng(2).standard_normal((g.n, 7))
+    Y = g.apply_c(X)
+    assert np.linalg.norm(Y - C @ X) <= 1e-13 * normC * np.linalg.norm(X)
+    g.close()
+
+
+def _dense_sigma(A, k):
+    s = np.linalg.svd(A.to_scipy().toarray(), compute_uv=False)
+    return np.sort(s)[:k]
+
+
+LEARNED_FORMS = [
+    dict(),  # GD+k, FP64-class
+    dict(stage1_precision=B.SVDS_FP32),
+    dict(method_stage1=B.SVDS_JDQMR, stage1_precision=B.SVDS_FP32),
+    dict(method_stage1=B.SVDS_JDQMR, innerPrecision=B.SVDS_FP64),
+    dict(method_stage1=B.SVDS_JDQMR, stage1_precision=B.SVDS_NATIVE_FP64),
+]
+
+
+@pytest.mark.parametrize("form", range(len(LEARNED_FORMS)))
+def test_solver_with_learned_preconditioner_is_correct(form):
+    A = wl.weighted_grid(24, 2, seed=12)
+    k = 5
+    th = B.gnn_init(0)
+    r = B.svds(A, k, "smallest", tol=1e-10, maxBlockSize=2, precond=B.SVDS_PRECOND_LEARNED, precondParams=th,
+               **LEARNED_FORMS[form])
+    assert r["nconv"] == k
+    sd = _dense_sigma(A, k)
+    np.testing.assert_allclose(r["sigma"], sd, rtol=1e-8, atol=1e-10 * np.linalg.norm(A.vals))
+    normA = np.linalg.svd(A.to_scipy().toarray(), compute_uv=False).max()
+    assert np.all(r["rnorm"] <= 1.0001e-10 * normA * 1.01)
+    assert r["stats"]["seconds_precond"] > 0
+
+
+def test_learned_preconditioner_from_model_file_and_largest_ignores_it(tmp_path):
+    A = wl.weighted_grid(16, 2, seed=3)
+    th = B.gnn_init(5)
+    p = tmp_path / "m.bin"
+    B.gnn_save(p, th)
+    r1 = B.svds(A, 3, "smallest", tol=1e-9, precond=B.SVDS_PRECOND_LEARNED, precondModel=str(p))
+    r2 = B.svds(A, 3, "smallest", tol=1e-9, precond=B.SVDS_PRECOND_LEARNED, precondParams=th)
+    np.testing.assert_array_equal(r1["sigma"], r2["sigma"])
+    r3 = B.svds(A, 3, "largest", tol=1e-9, precond=B.SVDS_PRECOND_LEARNED, precondParams=th)
+    assert r3["stats"]["seconds_precond"] == 0
+    np.testing.assert_allclose(r3["sigma"], np.sort(np.linalg.svd(A.to_scipy().toarray(), compute_uv=False))[::-1][:3],
+                               rtol=1e-9)
+
+
+def test_short_training_lowers_the_loss():
+    from paper_1607_01404_gb300 import gnn_train
+
+    theta, hist = gnn_train.train("wgrid2d", 20, seeds=range(3), epochs=12, lr=3e-3)
+    assert np.all(np.isfinite(theta))
+    assert hist[-1] < hist[0]
