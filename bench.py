@@ -4,14 +4,17 @@ One step = one complete solve of the workload through the C-ABI: handle
 creation from a device-resident CSR (transpose, value formats), the ||A||
 estimate, stage 1 and, if needed, stage 2, ending with the triplets and their
 residuals on the host.  The timed "chosen" form runs JDQMR in both stages with
-FP32 inner solves and an FP32 first phase of stage 1 (FP64-class outer
-iteration after it); beside it are timed the plain FP64-class form (the same
-JDQMR with FP64-class inner and outer iterations, no FP32 anywhere) and the
-plain FP64-class GD+k.
+FP32 inner solves, an FP32 first phase of stage 1 (FP64-class outer iteration
+after it) and the learned sparse-approximate-inverse preconditioner (3D model
+trained on 24^3 weighted grids; network inference inside the timed solve);
+beside it are timed the plain FP64-class form (the same JDQMR with FP64-class
+inner and outer iterations and the Jacobi preconditioner, no FP32 and no
+network) and the plain FP64-class GD+k with Jacobi.  A second report compares
+the Jacobi and learned preconditioners on held-out weighted grids (256^2,
+k = 10; 96^3, k = 20).
 
 Workload: the 3D grid-difference operator [D(x)I(x)I; I(x)D(x)I; I(x)I(x)D] on a
-128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4,
-Jacobi preconditioner.  Its working set is far larger than L2, so no flush is
+128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4.  Its working set is far larger than L2, so no flush is
 needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -35,7 +38,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "grid3d_N128"
 K, TARGET, BLOCK, TOL = 10, "smallest", 4, 1e-10
-METRIC = "sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner solves and FP32 stage-1 phase)"
+METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner solves, FP32 stage-1 phase, "
+          "learned preconditioner)")
+MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 UNIT = "s"
 # Products with A or A^T (per column) of a full GD+k FP64-class solve of this
 # workload, measured on a GB300 with this library (the plain GD+k line of the
@@ -222,7 +227,8 @@ def run_gpu(args, world, rank, local):
                   maxSeconds=600.0)
         if form == "chosen":
             kw.update(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
-                      innerPrecision=B.SVDS_FP32)
+                      innerPrecision=B.SVDS_FP32, precond=B.SVDS_PRECOND_LEARNED,
+                      precondModel=os.path.join(MODELS, "wgrid3d.bin"))
         elif form == "plain":
             kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_FP64)
@@ -283,6 +289,7 @@ def run_gpu(args, world, rank, local):
     t_e2e = time.perf_counter() - te0
     h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
     d2h = 8 * K * (A.m + A.n + 2)
+    gain = precond_gain(B, wl, sp)
     # roofline of the dominant kernel family (CSR SpMM, FP32 phase and FP64-class)
     roof32 = spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK)
     roofdf = spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK)
@@ -291,7 +298,31 @@ def run_gpu(args, world, rank, local):
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
                 t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
                 relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
-                roof32=roof32, roofdf=roofdf, ms_step=ms_step, A=A, e2e_nconv=oute[4])
+                roof32=roof32, roofdf=roofdf, ms_step=ms_step, A=A, e2e_nconv=oute[4], gain=gain)
+
+
+def precond_gain(B, wl, sp):
+    """Jacobi vs learned preconditioner (chosen JDQMR form) on held-out weighted grids."""
+    out = {}
+    for wname, model in (("wgrid2d_N256", "wgrid2d.bin"), ("wgrid3d_N96", "wgrid3d.bin")):
+        A, meta = wl.workload(wname)
+        row = {}
+        for name, pc in (("jacobi", B.SVDS_PRECOND_JACOBI), ("learned", B.SVDS_PRECOND_LEARNED)):
+            kw = dict(maxBlockSize=meta["b"], stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR,
+                      method_stage2=B.SVDS_JDQMR, precond=pc, seed=3, stream=sp, maxSeconds=120.0)
+            if pc == B.SVDS_PRECOND_LEARNED:
+                kw["precondModel"] = os.path.join(MODELS, model)
+            h = B.svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, B.make_opts(**kw))
+            try:
+                sig, _, _, rn, nconv, st, _ = B.svds_solve(h, meta["k"], B.SVDS_SMALLEST, TOL, want_vectors=False)
+            finally:
+                h.close()
+            row[name] = dict(seconds=round(st["seconds_total"], 4), matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
+                             inner_steps=int(st["inner_steps"]), seconds_precond=round(st["seconds_precond"], 5),
+                             numConverged=nconv)
+        row["speedup"] = round(row["jacobi"]["seconds"] / row["learned"]["seconds"], 3)
+        out[f"{wname} (held-out seed, k={meta['k']}, b={meta['b']})"] = row
+    return out
 
 
 def cpu_sample(A, seconds=15.0):
@@ -395,18 +426,21 @@ def main():
         ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype="f32+df64", data="synthetic",
         config=dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
-                    k=K, target=TARGET, block=BLOCK, tol=TOL, precond="jacobi",
-                    form="chosen: JDQMR (inner QMR solves in FP32), FP32 stage-1 phase, FP64-class outer polish/stage 2",
+                    k=K, target=TARGET, block=BLOCK, tol=TOL, precond="learned (gnn_models/wgrid3d.bin)",
+                    form="chosen: JDQMR (inner QMR solves in FP32), FP32 stage-1 phase, learned SPAI preconditioner, "
+                         "FP64-class outer polish/stage 2",
                     l2="working set >> L2 (no flush)", parallelism=f"replicas x{args.gpus}"),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
-        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT, form="JDQMR, FP64-class inner and outer",
+        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
+                        form="JDQMR, FP64-class inner and outer, Jacobi",
                         matvecs=mv_plain, max_rel_sigma_err=res["relerr_plain"]),
-        plain_fp64_gdk=dict(value=res["t_gdk"][0], unit=UNIT, form="GD+k, FP64-class",
+        plain_fp64_gdk=dict(value=res["t_gdk"][0], unit=UNIT, form="GD+k, FP64-class, Jacobi",
                             matvecs=int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"]),
                             max_rel_sigma_err=res["relerr_gdk"]),
         solve_stats=dict(matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
                          matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
-                         inner_steps=st["inner_steps"], stage2_used=st["stage2_used"], setup_s=st["seconds_setup"]),
+                         inner_steps=st["inner_steps"], stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
+                         precond_s=st["seconds_precond"]),
         roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
                       frac=achieved / peak, peak_kind=peak_kind, traffic=None,
                       all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
@@ -415,6 +449,7 @@ def main():
         cpu_baseline=cpu,
         e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
                  numConverged=res["e2e_nconv"]),
+        precond_gain=res["gain"],
         gpu_launches=launches,
         clocks=res["clocks"],
     )

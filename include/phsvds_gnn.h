@@ -14,13 +14,15 @@
  *   M       : m_ii = delta_i, m_ij = 0.9 s_ij min(delta_i, delta_j) |e_ij| / max(E_i, E_j)
  *             with E_i = sum_j |e_ij|; symmetric and strictly diagonally
  *             dominant with a positive diagonal, hence SPD;
- *   loss    : sparse-approximate-inverse residual with one shared scale over
- *             sampled directions t_p (R = C T):
- *             L = min_alpha mean_p |alpha M C t_p - t_p|^2 / |t_p|^2
- *               = 1 - (sum_p a_p)^2 / (P sum_p b_p),
- *             a_p = <M r_p, t_p> / |t_p|^2, b_p = |M r_p|^2 / |t_p|^2
- *             (the Frobenius objective of SPAI, Grote & Huckle 1997, on
- *             samples, invariant to the scale of M).
+ *   loss    : a condition-number proxy of the preconditioned operator M C,
+ *             which is self-adjoint in the C inner product with Rayleigh
+ *             quotient rho(t) = (C t)^T M (C t) / t^T C t.  From start blocks
+ *             T0 and X0: T = (M C)^ps T0 (power steps: top of the spectrum of
+ *             M C), X = (I - omega M C)^ss X0 with omega = 1 / max rho(T)
+ *             (smoothing steps: bottom of the spectrum), and
+ *             L = log mean_p rho(t_p) - log mean_q rho(x_q).
+ *             The samples follow the current M; the gradient holds them fixed
+ *             (at eigenvectors of M C the Rayleigh quotient is stationary).
  *
  * Parameters are a flat float array of phsvds_gnn_num_params() entries in the
  * order W1_0 (2x32), W2_0 (2x32), b_0 (32), W1_l, W2_l (32x32), b_l (32) for
@@ -61,11 +63,12 @@ int phsvds_gnn_pattern(const phsvds_gnn *g, int32_t *rowptr, int32_t *colidx);
 /* Forward pass: values of M on the pattern of C (host array of nnz floats). */
 int phsvds_gnn_forward(phsvds_gnn *g, const float *params, float *mvals);
 
-/* Loss and gradient for the samples T and R = C T (host FP64 column-major
- * n x P, 1 <= P <= 32).  grad: host doubles, phsvds_gnn_num_params();
- * SVDS_ERR_NUMERIC if M R vanishes. */
-int phsvds_gnn_loss_grad(phsvds_gnn *g, const float *params, const double *R, const double *T, int P,
-                         double *loss, double *grad);
+/* Loss and gradient from the start blocks T0 (n x P) and X0 (n x Q), host FP64
+ * column-major, 1 <= P, Q <= 8, 0 <= power_steps <= 100, 0 <= smooth_steps <=
+ * 1000.  grad: host doubles, phsvds_gnn_num_params(); SVDS_ERR_NUMERIC if a
+ * Rayleigh quotient is not positive (a start block in the null space of C). */
+int phsvds_gnn_loss_grad(phsvds_gnn *g, const float *params, const double *T0, int P, int power_steps,
+                         const double *X0, int Q, int smooth_steps, double *loss, double *grad);
 
 /* Training pairs on the graph: T = S^s Z, with S = I - (2/3) diag(C)^-1 C (s
  * steps of damped Jacobi smoothing of seeded N(0,1) columns Z, which leaves

@@ -20,17 +20,21 @@ kernels can be checked against it.  Every function is plain numpy/scipy.
   M is symmetric, strictly diagonally dominant with a positive diagonal,
   hence SPD (Gershgorin).  (With s_ij = const the off-diagonal part follows
   the coupling strength |e_ij|, as a truncated Neumann series of C^-1 does.)
-* Loss: sparse-approximate-inverse residual with one shared scale: for
-  samples t_p (columns of T, with R = C T),
-      L = min_alpha (1/P) sum_p ||alpha M C t_p - t_p||^2 / ||t_p||^2
-        = 1 - (sum_p a_p)^2 / (P sum_p b_p),
-      a_p = <M r_p, t_p> / ||t_p||^2,  b_p = ||M r_p||^2 / ||t_p||^2
-  (the Frobenius objective of SPAI, Grote & Huckle 1997, restricted to
-  sampled directions and made invariant to the scale of M).
+* Loss: a condition-number proxy of the preconditioned operator M C.  M C is
+  self-adjoint in the C inner product, with Rayleigh quotient
+      rho(t) = (C t)^T M (C t) / t^T C t,
+  whose extremes are the extreme eigenvalues of M C.  Samples follow the
+  current M: from start blocks T0 and X0,
+      T = (M C)^ps T0                       (power steps: top of the spectrum),
+      X = (I - omega M C)^ss X0, omega = 1 / max_p rho(t_p)   (smoothing: bottom),
+      L = log mean_p rho(t_p) - log mean_q rho(x_q).
+  The derivative holds T and X fixed (the Rayleigh quotient is stationary at
+  eigenvectors of M C, to which the samples are driven).
 
-Parity status: pinned by closed forms (M = I on eigenvector samples; M = C^-1
-on a diagonal C), central finite differences of the gradient, scale
-invariance and the SPD property.
+Parity status: pinned by closed forms (rho of an eigenvector of C; M = I on
+eigenvector samples; the power and smoothing samples converging to the
+extreme eigenvalues of C for M = I), central finite differences of the
+gradient with the samples fixed, scale invariance and the SPD property.
 """
 from __future__ import annotations
 
@@ -157,27 +161,49 @@ def M_matrix(G: Graph, m):
     return sp.csr_matrix((m, G.indices, G.indptr), shape=(G.n, G.n))
 
 
-def loss_from_m(G: Graph, m, R, T):
-    """Shared-scale SPAI loss of M on the samples T (R = C T) and dL/dm."""
+def rayleigh(G: Graph, m, T):
+    """rho_p = (C t_p)^T M (C t_p) / t_p^T C t_p and R = C T."""
     M = M_matrix(G, m)
-    Z = M @ R
-    P = T.shape[1]
-    tt = np.sum(T * T, axis=0)
-    a = np.sum(Z * T, axis=0) / tt
-    b = np.sum(Z * Z, axis=0) / tt
-    sa, sb = a.sum(), b.sum()
-    loss = float(1.0 - sa * sa / (P * sb))
-    # dL/dZ_p = -2 sa / (P sb) t_p / ||t_p||^2 + 2 sa^2 / (P sb^2) z_p / ||t_p||^2
-    dZ = (-2.0 * sa / (P * sb)) * T / tt + (2.0 * sa * sa / (P * sb * sb)) * Z / tt
-    dm = np.einsum("kp,kp->k", dZ[G.rows], R[G.indices])  # dZ_ip / dm_ij = r_jp
+    R = G.C @ T
+    return np.sum((M @ R) * R, axis=0) / np.sum(R * T, axis=0), R
+
+
+def samples(G: Graph, m, T0, X0, power_steps, smooth_steps):
+    """T = (M C)^ps T0 and X = (I - omega M C)^ss X0 with omega = 1 / max rho(T)."""
+    M = M_matrix(G, m)
+    T = np.array(T0, dtype=np.float64)
+    for _ in range(power_steps):
+        T = M @ (G.C @ T)
+    omega = 1.0 / rayleigh(G, m, T)[0].max()
+    X = np.array(X0, dtype=np.float64)
+    for _ in range(smooth_steps):
+        X = X - omega * (M @ (G.C @ X))
+    return T, X
+
+
+def loss_from_m(G: Graph, m, T, X):
+    """L = log mean rho(T) - log mean rho(X) for fixed samples, and dL/dm."""
+    ra, R = rayleigh(G, m, T)
+    rb, Y = rayleigh(G, m, X)
+    loss = float(np.log(ra.mean()) - np.log(rb.mean()))
+    # d rho_p / d m_ij = r_ip r_jp / t_p^T C t_p
+    ca = 1.0 / (ra.sum() * np.sum(R * T, axis=0))
+    cb = -1.0 / (rb.sum() * np.sum(Y * X, axis=0))
+    dm = np.einsum("kp,kp,p->k", R[G.rows], R[G.indices], ca) + np.einsum("kq,kq,q->k", Y[G.rows], Y[G.indices], cb)
     return loss, dm
 
 
-def loss_and_grad(G: Graph, params, R, T):
-    """Loss and gradient (dict like params) for the samples T (R = C T)."""
+def loss_and_grad(G: Graph, params, T0, X0, power_steps, smooth_steps):
+    """Loss and gradient (dict like params); the samples are taken at the current M."""
     m, cache = forward(G, params, keep=True)
-    loss, dm = loss_from_m(G, m, R, T)
+    T, X = samples(G, m, T0, X0, power_steps, smooth_steps)
+    loss, dm = loss_from_m(G, m, T, X)
     return loss, backward(G, params, cache, dm)
+
+
+def loss_fixed_samples(G: Graph, params, T, X):
+    """The loss as a function of the parameters with the samples fixed."""
+    return loss_from_m(G, forward(G, params), T, X)[0]
 
 
 def backward(G: Graph, params, cache, dm):

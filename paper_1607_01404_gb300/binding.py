@@ -113,8 +113,8 @@ _SIGS = {
     "phsvds_gnn_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "phsvds_gnn_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_gnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
-    "phsvds_gnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
-                                       C.POINTER(C.c_double), C.c_void_p]),
+    "phsvds_gnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "phsvds_gnn_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
     "phsvds_gnn_apply_c": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "phsvds_gnn_save": (C.c_int, [C.c_char_p, C.c_void_p]),
@@ -434,14 +434,14 @@ class Gnn:
         _check(lib().phsvds_gnn_forward(self.ptr, theta.ctypes.data, m.ctypes.data), "phsvds_gnn_forward")
         return m
 
-    def loss_grad(self, theta, R, T):
-        """Loss and gradient for the samples T (n x P, P <= 32) and R = C T."""
+    def loss_grad(self, theta, T0, X0, power_steps: int = 4, smooth_steps: int = 30):
+        """Loss and gradient from the start blocks T0 (n x P) and X0 (n x Q), P, Q <= 8."""
         theta = self._params(theta)
-        R, T = (np.asfortranarray(a, dtype=np.float64) for a in (R, T))
+        T0, X0 = (np.asfortranarray(a, dtype=np.float64) for a in (T0, X0))
         loss = C.c_double(0.0)
         grad = np.zeros(self.np)
-        rc = lib().phsvds_gnn_loss_grad(self.ptr, theta.ctypes.data, R.ctypes.data, T.ctypes.data, R.shape[1],
-                                        C.byref(loss), grad.ctypes.data)
+        rc = lib().phsvds_gnn_loss_grad(self.ptr, theta.ctypes.data, T0.ctypes.data, T0.shape[1], power_steps,
+                                        X0.ctypes.data, X0.shape[1], smooth_steps, C.byref(loss), grad.ctypes.data)
         _check(rc, "phsvds_gnn_loss_grad")
         return loss.value, grad
 

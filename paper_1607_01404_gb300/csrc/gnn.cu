@@ -247,27 +247,26 @@ __global__ void k_heads_edge(long long n, const int* __restrict__ cptr, const in
 }
 
 // ---- backward ---------------------------------------------------------------
-__global__ void k_lin_comb(long long total, const float* __restrict__ a, const float* __restrict__ b,
-                           const double* __restrict__ ca, const double* __restrict__ cb, int P,
-                           float* __restrict__ out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(e % P);
-    out[e] = (float)(ca[p] * (double)a[e] + cb[p] * (double)b[e]);
+// dm[k] (+)= sum_p c_p R[i, p] R[j, p] for entry k = (i, j) (R row-major n x P)
+__global__ void k_dm_outer(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                           const double* __restrict__ R, const double* __restrict__ c, int P, int accumulate,
+                           float* __restrict__ dm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double ri[8];
+    for (int p = 0; p < P; ++p) ri[p] = c[p] * R[i * P + p];
+    for (int k = cptr[i]; k < cptr[i + 1]; ++k) {
+      const long long j = cidx[k];
+      double acc = 0.0;
+      for (int p = 0; p < P; ++p) acc += ri[p] * R[j * P + p];
+      dm[k] = accumulate ? dm[k] + (float)acc : (float)acc;
+    }
   }
 }
 
-// dm[k] (+)= scale * sum_p dZ[i, p] R[j, p] for entry k = (i, j)
-__global__ void k_dm(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
-                     const float* __restrict__ dZ, const float* __restrict__ R, int P, float scale, int accumulate,
-                     float* __restrict__ dm) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    for (int k = cptr[i]; k < cptr[i + 1]; ++k) {
-      const int j = cidx[k];
-      float acc = 0.f;
-      for (int p = 0; p < P; ++p) acc = fmaf(dZ[i * P + p], R[(long long)j * P + p], acc);
-      dm[k] = accumulate ? dm[k] + scale * acc : scale * acc;
-    }
-  }
+// x <- x - omega z (n x P row-major)
+__global__ void k_axpy_neg(long long total, double omega, const double* __restrict__ z, double* __restrict__ x) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    x[e] -= omega * z[e];
 }
 
 // heads backward per row: ddelta_i, du_i; per-entry da_k = dm_k rho mu w_ij (1 - s^2)
@@ -426,13 +425,12 @@ struct phsvds_gnn {
   float *u = nullptr, *gpre = nullptr, *delta = nullptr, *s = nullptr, *m = nullptr;
   float *dm = nullptr, *da = nullptr, *dae = nullptr, *ddelta = nullptr, *du = nullptr, *gu = nullptr;
   float *dh = nullptr, *dz = nullptr, *tmp = nullptr, *tmp2 = nullptr, *ones = nullptr;
-  float *R = nullptr, *T = nullptr, *Z = nullptr, *dZ = nullptr;
+  double* kb[6] = {};  // n x 8 FP64 blocks of the loss (samples and products)
   double *dcoef = nullptr, *dG = nullptr, *dstage = nullptr, *grad = nullptr;
   float *am = nullptr, *av = nullptr;
   double* m64 = nullptr;  // FP64 copy of M for the FP64 solver mode
   double *w0 = nullptr, *w1 = nullptr, *w2 = nullptr;  // n x 8 FP64 work blocks (pairs, C products)
   void* partial = nullptr;
-  int cap_pairs = 0;
   bool train = false;
   long long launches = 0;
   Offsets off;
@@ -474,6 +472,14 @@ CsrDev Ecsr(const phsvds_gnn* g, const float* vals) {
   c.v32 = vals;
   return c;
 }
+
+// C = A^T A on its pattern (FP64 values)
+CsrDev Ccsr(const phsvds_gnn* g) {
+  CsrDev c = Ecsr(g, nullptr);
+  c.v64 = g->cval;
+  return c;
+}
+
 
 // G (p x q row-major, host) = P^T Q over all rows (FP64-class accumulation)
 int gram_host(phsvds_gnn* g, const float* P, int p, const float* Q, int ldq, int q0, int q, std::vector<double>& out) {
@@ -518,66 +524,89 @@ int forward_impl(phsvds_gnn* g, const float* params_host) {
   return 0;
 }
 
-int ensure_pairs(phsvds_gnn* g, int P) {
-  if (P <= g->cap_pairs) return 0;
-  int rc;
-  const size_t cnt = (size_t)g->n * P;
-  if ((rc = galloc(g, &g->R, cnt)) || (rc = galloc(g, &g->T, cnt)) || (rc = galloc(g, &g->Z, cnt)) ||
-      (rc = galloc(g, &g->dZ, cnt)))
-    return rc;
-  g->cap_pairs = P;
+CsrDev Mcsr64(const phsvds_gnn* g) {
+  CsrDev c = Ecsr(g, nullptr);
+  c.v64 = g->m64;
+  return c;
+}
+
+// diag of P^T Q for row-major n x q FP64 blocks (host result)
+int gram_diag64(phsvds_gnn* g, const double* P, const double* Q, int q, std::vector<double>& out) {
+  SegV Ps{P, q, q}, Qs{Q, q, q};
+  int nb = 0;
+  GK(launch_gram(kF64, 0, g->n, &Ps, 1, Qs, g->partial, gram_default_blocks(), &nb, g->st));
+  GK(launch_gram_reduce(kF64, g->partial, nb, q * q, g->dG, g->st));
+  std::vector<double> h((size_t)q * q);
+  GK(cudaMemcpyAsync(h.data(), g->dG, sizeof(double) * q * q, cudaMemcpyDeviceToHost, g->st));
+  GK(cudaStreamSynchronize(g->st));
+  out.resize(q);
+  for (int p = 0; p < q; ++p) out[p] = h[(size_t)p * q + p];
   return 0;
 }
 
-// Shared-scale SPAI loss over P <= 32 samples (host FP64 column-major R = C T
-// and T), in chunks of 8 columns: a_p = <M r_p, t_p> / |t_p|^2,
-// b_p = |M r_p|^2 / |t_p|^2, L = 1 - (sum a)^2 / (P sum b); writes dL/dm.
-int spai_term(phsvds_gnn* g, const double* Rh, const double* Th, int P, double* loss) {
+// rho_p = <M C t_p, C t_p> / <C t_p, t_p> for the columns of the device block T;
+// leaves R = C T in Rb.
+int rayleigh_dev(phsvds_gnn* g, const double* T, int q, double* Rb, double* Zb, std::vector<double>& rho,
+                 std::vector<double>& rt) {
+  GK(launch_spmm(kF64, Ccsr(g), T, q, Rb, q, q, g->st));
+  GK(launch_spmm(kF64, Mcsr64(g), Rb, q, Zb, q, q, g->st));
+  std::vector<double> zr;
+  int rc;
+  if ((rc = gram_diag64(g, Zb, Rb, q, zr)) || (rc = gram_diag64(g, Rb, T, q, rt))) return rc;
+  rho.resize(q);
+  for (int p = 0; p < q; ++p) rho[p] = zr[p] / rt[p];
+  return 0;
+}
+
+// Condition-number loss of M C from start blocks T0 (n x P) and X0 (n x Q)
+// (host FP64 column-major): T = (M C)^ps T0, X = (I - omega M C)^ss X0 with
+// omega = 1 / max rho(T); L = log mean rho(T) - log mean rho(X).  dL/dm with
+// the samples held fixed is written to g->dm.
+int kappa_term(phsvds_gnn* g, const double* T0, int P, int ps, const double* X0, int Q, int ss, double* loss) {
   const long long n = g->n;
-  const int nch = (P + 7) / 8;
-  std::vector<double> a(P), b(P), tt(P);
-  for (int c = 0; c < nch; ++c) {
-    const int c0 = 8 * c, w = P - c0 < 8 ? P - c0 : 8;
-    float *R = g->R + n * c0, *T = g->T + n * c0, *Z = g->Z + n * c0;
-    GK(cudaMemcpyAsync(g->dstage, Rh + n * c0, sizeof(double) * n * w, cudaMemcpyHostToDevice, g->st));
-    GK(launch_from_f64_colmajor(kF32, n, w, g->dstage, n, R, w, 1.0, g->st));
-    GK(cudaMemcpyAsync(g->dstage, Th + n * c0, sizeof(double) * n * w, cudaMemcpyHostToDevice, g->st));
-    GK(launch_from_f64_colmajor(kF32, n, w, g->dstage, n, T, w, 1.0, g->st));
-    GK(launch_spmm(kF32, Ecsr(g, g->m), R, w, Z, w, w, g->st));
-    std::vector<double> zt, zz, t2;
-    int rc;
-    if ((rc = gram_host(g, Z, w, T, w, 0, w, zt)) || (rc = gram_host(g, Z, w, Z, w, 0, w, zz)) ||
-        (rc = gram_host(g, T, w, T, w, 0, w, t2)))
-      return rc;
-    for (int p = 0; p < w; ++p) {
-      tt[c0 + p] = t2[(size_t)p * w + p];
-      a[c0 + p] = zt[(size_t)p * w + p] / tt[c0 + p];
-      b[c0 + p] = zz[(size_t)p * w + p] / tt[c0 + p];
-    }
+  double *T = g->kb[0], *X = g->kb[1], *W = g->kb[2], *Z = g->kb[3], *R = g->kb[4], *Y = g->kb[5];
+  k_to_f64<<<grid1(g->nnz), kT, 0, g->st>>>(g->nnz, g->m, g->m64);
+  GK(cudaMemcpyAsync(W, T0, sizeof(double) * n * P, cudaMemcpyHostToDevice, g->st));
+  GK(launch_from_f64_colmajor(kF64, n, P, W, n, T, P, 1.0, g->st));
+  for (int s = 0; s < ps; ++s) {
+    GK(launch_spmm(kF64, Ccsr(g), T, P, W, P, P, g->st));
+    GK(launch_spmm(kF64, Mcsr64(g), W, P, T, P, P, g->st));
   }
-  double sa = 0.0, sb = 0.0;
-  for (int p = 0; p < P; ++p) {
-    sa += a[p];
-    sb += b[p];
+  std::vector<double> ra, rta, rb, rtb;
+  int rc;
+  if ((rc = rayleigh_dev(g, T, P, R, Z, ra, rta))) return rc;
+  double amax = 0.0, sa = 0.0;
+  for (double v : ra) {
+    amax = std::max(amax, v);
+    sa += v;
   }
-  if (!(sb > 0) || !std::isfinite(sa) || !std::isfinite(sb)) {
+  if (!(amax > 0) || !std::isfinite(sa)) {
     phsvds::set_last_error("phsvds_gnn_loss_grad: M C T vanishes or is not finite");
     return SVDS_ERR_NUMERIC;
   }
-  *loss = 1.0 - sa * sa / (P * sb);
-  // dL/dZ_p = (-2 sa / (P sb) t_p + 2 sa^2 / (P sb^2) z_p) / |t_p|^2
-  std::vector<double> cc(2 * 32, 0.0);
-  for (int p = 0; p < P; ++p) {
-    cc[p] = -2.0 * sa / (P * sb) / tt[p];
-    cc[32 + p] = 2.0 * sa * sa / (P * sb * sb) / tt[p];
+  const double omega = 1.0 / amax;
+  GK(cudaMemcpyAsync(W, X0, sizeof(double) * n * Q, cudaMemcpyHostToDevice, g->st));
+  GK(launch_from_f64_colmajor(kF64, n, Q, W, n, X, Q, 1.0, g->st));
+  for (int s = 0; s < ss; ++s) {
+    GK(launch_spmm(kF64, Ccsr(g), X, Q, W, Q, Q, g->st));
+    GK(launch_spmm(kF64, Mcsr64(g), W, Q, Z, Q, Q, g->st));
+    k_axpy_neg<<<grid1(n * Q), kT, 0, g->st>>>(n * Q, omega, Z, X);
   }
-  GK(cudaMemcpyAsync(g->dcoef, cc.data(), sizeof(double) * 64, cudaMemcpyHostToDevice, g->st));
-  for (int c = 0; c < nch; ++c) {
-    const int c0 = 8 * c, w = P - c0 < 8 ? P - c0 : 8;
-    k_lin_comb<<<grid1(n * w), kT, 0, g->st>>>(n * w, g->T + n * c0, g->Z + n * c0, g->dcoef + c0,
-                                                 g->dcoef + 32 + c0, w, g->dZ + n * c0);
-    k_dm<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, g->dZ + n * c0, g->R + n * c0, w, 1.0f, c > 0, g->dm);
+  if ((rc = rayleigh_dev(g, X, Q, Y, Z, rb, rtb))) return rc;
+  double sb = 0.0;
+  for (double v : rb) sb += v;
+  if (!(sb > 0) || !std::isfinite(sb)) {
+    phsvds::set_last_error("phsvds_gnn_loss_grad: M C X vanishes or is not finite");
+    return SVDS_ERR_NUMERIC;
   }
+  *loss = std::log(sa / P) - std::log(sb / Q);
+  // d rho_p / d m_ij = r_ip r_jp / <r_p, t_p>
+  std::vector<double> cc(16, 0.0);
+  for (int p = 0; p < P; ++p) cc[p] = 1.0 / (sa * rta[p]);
+  for (int q = 0; q < Q; ++q) cc[8 + q] = -1.0 / (sb * rtb[q]);
+  GK(cudaMemcpyAsync(g->dcoef, cc.data(), sizeof(double) * 16, cudaMemcpyHostToDevice, g->st));
+  k_dm_outer<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, R, g->dcoef, P, 0, g->dm);
+  k_dm_outer<<<grid1(n), kT, 0, g->st>>>(n, g->cptr, g->cidx, Y, g->dcoef + 8, Q, 1, g->dm);
   GK(cudaGetLastError());
   GK(cudaStreamSynchronize(g->st));  // cc is read by the copy above
   return 0;
@@ -797,17 +826,21 @@ int phsvds_gnn_forward(phsvds_gnn* g, const float* params, float* mvals) {
   return SVDS_OK;
 }
 
-int phsvds_gnn_loss_grad(phsvds_gnn* g, const float* params, const double* R, const double* T, int P,
-                         double* loss, double* grad) {
-  if (!g || !g->train || !params || !R || !T || P < 1 || P > 32 || !loss || !grad) return SVDS_ERR_ARG;
+int phsvds_gnn_loss_grad(phsvds_gnn* g, const float* params, const double* T0, int P, int power_steps,
+                         const double* X0, int Q, int smooth_steps, double* loss, double* grad) {
+  if (!g || !g->train || !params || !T0 || !X0 || P < 1 || P > 8 || Q < 1 || Q > 8 || power_steps < 0 ||
+      power_steps > 100 || smooth_steps < 0 || smooth_steps > 1000 || !loss || !grad)
+    return SVDS_ERR_ARG;
   const Offsets& o = g->off;
   const long long n = g->n;
   const int gr = grid1(n);
   int rc = forward_impl(g, params);
   if (rc) return rc;
-  if ((rc = ensure_pairs(g, P))) return rc;
+  if (!g->m64 && (rc = galloc(g, &g->m64, g->nnz))) return rc;
+  for (int i = 0; i < 6; ++i)
+    if (!g->kb[i] && (rc = galloc(g, &g->kb[i], g->n * 8))) return rc;
   double L = 0.0;
-  if ((rc = spai_term(g, R, T, P, &L))) return rc;
+  if ((rc = kappa_term(g, T0, P, power_steps, X0, Q, smooth_steps, &L))) return rc;
   std::vector<double> gr_h(o.total, 0.0);
   // heads
   k_heads_bwd<<<gr, kT, 0, g->st>>>(n, g->cptr, g->cidx, g->tpos, g->dm, g->s, g->delta, g->wdeg, g->e, g->ddelta,
@@ -873,12 +906,6 @@ int ensure_work(phsvds_gnn* g) {
                  (rc = galloc(g, &g->w2, g->n * 8))))
     return rc;
   return 0;
-}
-
-CsrDev Ccsr(const phsvds_gnn* g) {
-  CsrDev c = Ecsr(g, nullptr);
-  c.v64 = g->cval;
-  return c;
 }
 
 // device row-major n x q (ld q) -> host column-major

@@ -1,15 +1,15 @@
 """Training driver of the learned preconditioner (initialisation, forward,
 backward and Adam run in libphsvds.so; this module only schedules them).
 
-Data, per training matrix A (a seeded weighted-grid operator), for the
-shared-scale SPAI loss min_alpha mean |alpha M C t - t|^2 / |t|^2 over sampled
-directions t that cover the spectrum of C = A^T A:
-* 4 seeded N(0,1) columns (mostly the top of the spectrum),
-* 4 + 4 columns after 8 and 64 damped-Jacobi smoothing steps (middle and low
-  end, where a diagonal preconditioner is weakest),
-* up to 4 right singular vectors of the smallest singular values of A
-  (computed by the solver itself);
-and R = C T.
+Loss: the condition-number proxy of phsvds_gnn.h, log mean rho(t) - log
+mean rho(x), with rho the Rayleigh quotient of M C in the C inner product, t
+driven to the top of the spectrum of M C by power steps and x to the bottom by
+smoothing steps, both with the current M.  Start blocks per training matrix
+(a seeded weighted-grid operator) and step:
+* T0: 8 seeded N(0,1) columns;
+* X0: 4 right singular vectors of the smallest singular values of A (Ritz
+  vectors harvested from a solve with the plain Jacobi solver) and 4 seeded
+  N(0,1) columns.
 
 Usage: python -m paper_1607_01404_gb300.gnn_train --out model.bin
 """
@@ -30,30 +30,22 @@ def training_matrix(family: str, N: int, seed: int) -> wl.CSR:
     return wl.weighted_grid(N, 2 if family == "wgrid2d" else 3, seed=seed)
 
 
-def harvest(A: wl.CSR, g: B.Gnn, seed: int, k: int = 4):
-    """Samples of one matrix: (R, T) with 12 smoothed random columns and k <= 4 singular vectors."""
-    Rs, Ts = [], []
-    for i, s in enumerate((0, 8, 64)):
-        R, T = g.pairs(4, s, 1000 * seed + i)
-        Rs.append(R)
-        Ts.append(T)
+def harvest(A: wl.CSR, seed: int, k: int = 4):
+    """Ritz vectors of one training matrix (smallest singular values, plain Jacobi solver)."""
     res = B.svds(A, k, "smallest", tol=1e-6, maxBlockSize=4, method_stage1=B.SVDS_JDQMR,
                  stage1_precision=B.SVDS_FP32, seed=seed + 1)
-    X = np.asfortranarray(res["V"][:, : min(k, 4)])
-    Rs.append(g.apply_c(X))
-    Ts.append(X)
-    return np.hstack(Rs), np.hstack(Ts)
+    return np.asfortranarray(res["V"][:, :k])
 
 
 def train(family: str = "wgrid2d", N: int = 64, seeds=range(0, 32), epochs: int = 40, lr: float = 3e-3,
-          init_seed: int = 0, log=None):
+          init_seed: int = 0, power_steps: int = 4, smooth_steps: int = 30, log=None):
     """Adam on the training matrices in turn; returns (theta, history of mean losses per epoch)."""
     build()
     data = []
     for s in seeds:
         A = training_matrix(family, N, s)
         g = B.Gnn(A.rowptr, A.colidx, A.vals, A.m, A.n)
-        data.append((g, harvest(A, g, s)))
+        data.append((g, harvest(A, s), np.random.default_rng(7919 * s + 1)))
     theta = B.gnn_init(init_seed)
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
@@ -61,15 +53,17 @@ def train(family: str = "wgrid2d", N: int = 64, seeds=range(0, 32), epochs: int 
     step = 0
     for ep in range(epochs):
         tot = 0.0
-        for g, (R, T) in data:
-            loss, grad = g.loss_grad(theta, R, T)
+        for g, ritz, rng in data:
+            T0 = rng.standard_normal((g.n, 8))
+            X0 = np.hstack([ritz, rng.standard_normal((g.n, 8 - ritz.shape[1]))])
+            loss, grad = g.loss_grad(theta, T0, X0, power_steps, smooth_steps)
             step += 1
             g.adam(theta, grad, m, v, step, lr)
             tot += loss
         hist.append(tot / len(data))
         if log:
             log(f"epoch {ep} mean loss {hist[-1]:.5f}")
-    for g, _ in data:
+    for g, _, _ in data:
         g.close()
     return theta, hist
 

@@ -11,8 +11,7 @@ def _small():
     A = wl.weighted_grid(6, 2, seed=3)
     g = G.Graph(A.to_scipy())
     rng = np.random.default_rng(0)
-    T = rng.standard_normal((g.n, 5))
-    return g, g.C @ T, T
+    return g, rng.standard_normal((g.n, 5)), rng.standard_normal((g.n, 4))
 
 
 def test_M_is_symmetric_spd_and_diagonally_dominant():
@@ -42,11 +41,13 @@ def test_graph_matches_definition():
 
 
 def test_gradient_matches_central_differences():
-    g, R, T = _small()
+    g, T0, X0 = _small()
     p = G.init_params(7)
     p["bs"] = np.array(0.8)
     theta = G.flatten(p)
-    loss, grads = G.loss_and_grad(g, p, R, T)
+    loss, grads = G.loss_and_grad(g, p, T0, X0, 3, 20)
+    T, X = G.samples(g, G.forward(g, p), T0, X0, 3, 20)
+    assert abs(G.loss_fixed_samples(g, p, T, X) - loss) < 1e-14
     gflat = G.flatten(grads)
     rng = np.random.default_rng(1)
     idx = rng.choice(theta.size, size=40, replace=False)
@@ -56,21 +57,21 @@ def test_gradient_matches_central_differences():
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (G.loss_and_grad(g, G.unflatten(tp), R, T)[0] - G.loss_and_grad(g, G.unflatten(tm), R, T)[0]) / (2 * h)
+        fd = (G.loss_fixed_samples(g, G.unflatten(tp), T, X) - G.loss_fixed_samples(g, G.unflatten(tm), T, X)) / (2 * h)
         assert abs(fd - gflat[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (i, fd, gflat[i])
 
 
 def test_dm_matches_central_differences():
-    g, R, T = _small()
+    g, T, X = _small()
     m = G.forward(g, G.init_params(2))
-    _, dm = G.loss_from_m(g, m, R, T)
+    _, dm = G.loss_from_m(g, m, T, X)
     rng = np.random.default_rng(3)
     for k in rng.choice(m.size, size=25, replace=False):
         h = 1e-4 * abs(m[k]) + 1e-12
         mp, mm = m.copy(), m.copy()
         mp[k] += h
         mm[k] -= h
-        fd = (G.loss_from_m(g, mp, R, T)[0] - G.loss_from_m(g, mm, R, T)[0]) / (2 * h)
+        fd = (G.loss_from_m(g, mp, T, X)[0] - G.loss_from_m(g, mm, T, X)[0]) / (2 * h)
         assert abs(fd - dm[k]) <= 1e-5 * abs(fd) + 1e-9 * np.abs(dm).max(), (k, fd, dm[k])
 
 
@@ -78,39 +79,47 @@ def _identity_m(g):
     return np.where(g.rows == g.indices, 1.0, 0.0)
 
 
-def test_loss_of_identity_on_eigenvectors():
-    # M = I and t_p eigenvectors of C (eigenvalue l_p): a_p = l_p, b_p = l_p^2, so
-    # L = 1 - (sum l)^2 / (P sum l^2), whatever the scale of each t_p
+def test_rayleigh_quotient_of_an_eigenvector():
+    # x eigenvector of C with eigenvalue lam: rho(x) = lam x^T M x / x^T x
     g, _, _ = _small()
     lam, V = np.linalg.eigh(g.C.toarray())
-    sel = [0, 4, 9, 30]
-    T = V[:, sel] * np.array([1.0, -2.0, 0.5, 3.0])
-    L, _ = G.loss_from_m(g, _identity_m(g), g.C @ T, T)
-    l = lam[sel]
-    assert abs(L - (1 - l.sum() ** 2 / (len(l) * (l * l).sum()))) < 1e-13
+    m = G.forward(g, G.init_params(4))
+    M = G.M_matrix(g, m).toarray()
+    X = V[:, [0, 3, 10]]
+    rho, _ = G.rayleigh(g, m, X)
+    np.testing.assert_allclose(rho, lam[[0, 3, 10]] * np.sum(X * (M @ X), axis=0), rtol=1e-10)
 
 
-def test_loss_vanishes_for_the_exact_inverse_of_a_diagonal_C():
-    # C diagonal: M = C^-1 (representable on the pattern) gives M C t = t for every t
-    import scipy.sparse as sp
-
-    A = sp.diags([1.0, 2.0, 3.0, 0.5]).tocsr()
-    g = G.Graph(A)
-    m = 1.0 / g.cdiag[g.rows]
-    T = np.random.default_rng(4).standard_normal((4, 3))
-    L, dm = G.loss_from_m(g, m, g.C @ T, T)
-    assert abs(L) < 1e-15 and np.abs(dm).max() < 1e-13
-    L2, _ = G.loss_from_m(g, np.ones(4), g.C @ T, T)
-    assert L2 > 1e-3
+def test_loss_of_identity_on_eigenvectors_is_log_of_mean_eigenvalues():
+    g, _, _ = _small()
+    lam, V = np.linalg.eigh(g.C.toarray())
+    hi, lo = [20, 25, 30, 35], [0, 1, 2]
+    T, X = V[:, hi] * np.array([1.0, -2.0, 0.5, 3.0]), V[:, lo]
+    L, _ = G.loss_from_m(g, _identity_m(g), T, X)
+    assert abs(L - (np.log(lam[hi].mean()) - np.log(lam[lo].mean()))) < 1e-12
 
 
-def test_loss_is_scale_invariant_and_bounded():
-    g, R, T = _small()
-    m = G.forward(g, G.init_params(3))
-    l1 = G.loss_from_m(g, m, R, T)[0]
-    s = np.array([3.0, 0.5, 1.0, 2.0, 7.0])
-    assert abs(G.loss_from_m(g, 2.5 * m, R * s, T * s)[0] - l1) < 1e-12
-    assert 0.0 <= l1 <= 1.0
+def test_samples_reach_the_extreme_eigenvalues_for_identity():
+    # M = I: power steps converge to the top of the spectrum of C, smoothing
+    # steps with omega = 1 / lam_max to the bottom
+    g, T0, X0 = _small()
+    lam = np.linalg.eigvalsh(g.C.toarray())
+    m = _identity_m(g) / lam[-1]  # M C with spectrum in (0, 1]: no overflow over many power steps
+    lam = lam / lam[-1]
+    T, X = G.samples(g, m, T0[:, :1], X0[:, :1], 400, 4000)
+    assert abs(G.rayleigh(g, m, T)[0][0] - lam[-1]) < 1e-6 * lam[-1]
+    assert abs(G.rayleigh(g, m, X)[0][0] - lam[0]) < 1e-3 * lam[0]
+
+
+def test_loss_is_scale_invariant():
+    g, T0, X0 = _small()
+    p = G.init_params(3)
+    m = G.forward(g, p)
+    T, X = G.samples(g, m, T0, X0, 3, 20)
+    l1 = G.loss_from_m(g, m, T, X)[0]
+    T2, X2 = G.samples(g, 2.5 * m, 3.0 * T0, 0.5 * X0, 3, 20)
+    assert abs(G.loss_from_m(g, 2.5 * m, T2, X2)[0] - l1) < 1e-12
+    assert l1 > 0
 
 
 def test_edge_weights_follow_the_coupling_strength():

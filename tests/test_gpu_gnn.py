@@ -92,25 +92,25 @@ def test_loss_and_gradient_match_oracle(name, A):
     rng = np.random.default_rng(11)
     n = ref.n
     lam, V = np.linalg.eigh(ref.C.toarray())
-    for T in (rng.standard_normal((n, 5)), np.hstack([V[:, :3], rng.standard_normal((n, 14))])):
+    for T0, X0, ps, ss in ((rng.standard_normal((n, 5)), rng.standard_normal((n, 3)), 0, 0),
+                           (rng.standard_normal((n, 8)), np.hstack([V[:, :4], rng.standard_normal((n, 4))]), 4, 30)):
         th, p = _theta(2)
-        L, grad = g.loss_grad(th, ref.C @ T, T)
-        Lr, gr = G.loss_and_grad(ref, p, ref.C @ T, T)
+        L, grad = g.loss_grad(th, T0, X0, ps, ss)
+        Lr, gr = G.loss_and_grad(ref, p, T0, X0, ps, ss)
         gr = G.flatten(gr)
-        assert abs(L - Lr) < 1e-5 * max(1.0, abs(Lr)), (L, Lr)
+        assert abs(L - Lr) < 1e-4 * max(1.0, abs(Lr)), (L, Lr)
         err = np.linalg.norm(grad - gr) / np.linalg.norm(gr)
-        assert err < G_TOL, (name, T.shape, err)
+        assert err < G_TOL, (name, ps, ss, err)
     g.close()
 
 
 def test_gradient_is_a_descent_direction_and_adam_steps():
     A = wl.weighted_grid(16, 2, seed=1)
     g = _gnn(A)
-    R1, T1 = g.pairs(4, 0, 5)
-    R2, T2 = g.pairs(4, 40, 6)
-    R, T = np.hstack([R1, R2]), np.hstack([T1, T2])
-    th, _ = _theta(4)
-    L0, grad = g.loss_grad(th, R, T)
+    rng = np.random.default_rng(5)
+    T0, X0 = rng.standard_normal((g.n, 8)), rng.standard_normal((g.n, 8))
+    th, p = _theta(4)
+    L0, grad = g.loss_grad(th, T0, X0)
     m = np.zeros_like(th)
     v = np.zeros_like(th)
     th1 = th.copy()
@@ -120,8 +120,10 @@ def test_gradient_is_a_descent_direction_and_adam_steps():
     vh = (0.001 * grad * grad) / 0.001
     ref = th.astype(np.float64) - 1e-3 * mh / (np.sqrt(vh) + 1e-8)
     np.testing.assert_allclose(th1, ref, rtol=1e-5, atol=1e-7)
-    L1, _ = g.loss_grad(th1, R, T)
-    assert L1 < L0
+    # with the samples of th held fixed the loss decreases along the step
+    gref = G.Graph(A.to_scipy())
+    T, X = G.samples(gref, G.forward(gref, p), T0, X0, 4, 30)
+    assert G.loss_fixed_samples(gref, G.unflatten(th1.astype(np.float64)), T, X) < L0
     g.close()
 
 
@@ -129,12 +131,12 @@ def test_rejects_bad_arguments():
     A = wl.weighted_grid(6, 2, seed=1)
     g = _gnn(A)
     th, _ = _theta(0)
-    R = np.ones((g.n, 33))
+    R = np.ones((g.n, 9))
     with pytest.raises(B.SvdsError):
-        g.loss_grad(th, R, R)  # at most 32 samples per call
+        g.loss_grad(th, R, R[:, :2])  # at most 8 columns per block
     Z = np.zeros((g.n, 2))
     with pytest.raises(B.SvdsError) as e:
-        g.loss_grad(th, Z, np.ones((g.n, 2)))  # M R = 0
+        g.loss_grad(th, Z, np.ones((g.n, 2)))  # Rayleigh quotient 0 / 0
     assert e.value.code == B.SVDS_ERR_NUMERIC
     with pytest.raises(ValueError):
         g.forward(th[:-1])
@@ -209,3 +211,24 @@ def test_short_training_lowers_the_loss():
     theta, hist = gnn_train.train("wgrid2d", 20, seeds=range(3), epochs=12, lr=3e-3)
     assert np.all(np.isfinite(theta))
     assert hist[-1] < hist[0]
+
+
+@pytest.mark.parametrize("family,N,model", [("wgrid2d", 128, "wgrid2d.bin"), ("wgrid3d", 40, "wgrid3d.bin")])
+def test_trained_models_gain_over_jacobi(family, N, model):
+    """The committed trained networks on a held-out seed: fewer products with A
+    (deterministic counts) than the Jacobi solver, the same triplets."""
+    import os
+
+    from paper_1607_01404_gb300 import gnn_train
+
+    A = gnn_train.training_matrix(family, N, 10042)
+    path = os.path.join(os.path.dirname(B.__file__), "gnn_models", model)
+    out = {}
+    for name, kw in (("jacobi", dict(precond=B.SVDS_PRECOND_JACOBI)),
+                     ("learned", dict(precond=B.SVDS_PRECOND_LEARNED, precondModel=path))):
+        r = B.svds(A, 8, "smallest", tol=1e-10, maxBlockSize=4, stage1_precision=B.SVDS_FP32, **kw)
+        assert r["nconv"] == 8
+        out[name] = r
+    mv = {k: v["stats"]["matvecs_stage1"] + v["stats"]["matvecs_stage2"] for k, v in out.items()}
+    assert mv["learned"] < 0.85 * mv["jacobi"], mv
+    np.testing.assert_allclose(out["learned"]["sigma"], out["jacobi"]["sigma"], rtol=1e-9)
