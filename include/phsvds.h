@@ -46,6 +46,11 @@ extern "C" {
 #define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
 #define SVDS_NATIVE_FP64 4 /* native FP64 arithmetic everywhere (check mode; slow on GB300) */
 
+#define SVDS_NORMAL_AUTO 0     /* C = A^T A applied as an explicit sparse matrix when that moves
+                                  fewer bytes than A then A^T (estimated from the patterns) */
+#define SVDS_NORMAL_TWOPASS 1  /* always A then A^T (Sec. 3.3) */
+#define SVDS_NORMAL_EXPLICIT 2 /* always the explicit C (when its pattern can be formed) */
+
 #define SVDS_PRECOND_NONE 0
 #define SVDS_PRECOND_JACOBI 1
 #define SVDS_PRECOND_LEARNED 2 /* sparse approximate inverse on the pattern of A^T A from the
@@ -94,6 +99,7 @@ typedef struct {
                                  network parameters (copied by svds_create), or NULL */
   const char *precondModel;   /* SVDS_PRECOND_LEARNED without precondParams: path of a
                                  parameter file written by phsvds_gnn_save */
+  int normalOperator;         /* SVDS_NORMAL_AUTO (default), _TWOPASS or _EXPLICIT */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -113,6 +119,7 @@ typedef struct {
   int64_t host_syncs;         /* device-to-host round trips */
   int64_t inner_steps;        /* JDQMR inner sQMR steps (each applies the operator to the block) */
   double seconds_precond;     /* learned preconditioner: graph of A^T A and network inference */
+  int64_t normal_nnz;         /* nonzeros of the explicit C = A^T A, 0 when A then A^T is used */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

@@ -31,6 +31,9 @@ SVDS_JDQMR = 1
 SVDS_FP32 = 1
 SVDS_FP64 = 3
 SVDS_NATIVE_FP64 = 4
+SVDS_NORMAL_AUTO = 0
+SVDS_NORMAL_TWOPASS = 1
+SVDS_NORMAL_EXPLICIT = 2
 SVDS_PRECOND_NONE = 0
 SVDS_PRECOND_JACOBI = 1
 SVDS_PRECOND_LEARNED = 2
@@ -51,7 +54,8 @@ class svds_opts(C.Structure):
                 ("maxMatvecs", C.c_int64), ("maxSeconds", C.c_double), ("seed", C.c_uint64),
                 ("printLevel", C.c_int), ("initSize", C.c_int), ("initV", C.c_void_p),
                 ("stream", C.c_void_p), ("innerMaxIt", C.c_int), ("innerRelTol", C.c_double),
-                ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p)]
+                ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p),
+                ("normalOperator", C.c_int)]
 
 
 class svds_stats(C.Structure):
@@ -62,7 +66,7 @@ class svds_stats(C.Structure):
                 ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
                 ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
                 ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
-                ("inner_steps", C.c_int64), ("seconds_precond", C.c_double)]
+                ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

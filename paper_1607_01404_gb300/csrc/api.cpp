@@ -185,6 +185,9 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
   if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
   if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED)
     return SVDS_ERR_ARG;
+  if (o.normalOperator != SVDS_NORMAL_AUTO && o.normalOperator != SVDS_NORMAL_TWOPASS &&
+      o.normalOperator != SVDS_NORMAL_EXPLICIT)
+    return SVDS_ERR_ARG;
   std::vector<float> gnn_params;
   if (o.precond == SVDS_PRECOND_LEARNED) {
     gnn_params.resize(phsvds_gnn_num_params());

@@ -186,7 +186,10 @@ void apply_op(Ctx& c, int prec, int op, const void* X, long long ldx, void* Y, l
     const int w = std::min(tmp_cols, nb - c0);
     const void* Xc = off(X, c0, prec);
     void* Yc = off(Y, c0, prec);
-    if (op == OP_C) {
+    if (op == OP_C && A.nnzC > 0) {
+      CK(launch_spmm(prec, A.csrC(), Xc, ldx, Yc, ldy, w, c.st));
+      c.launches -= spmm_launches(w);
+    } else if (op == OP_C) {
       CK(launch_spmm(prec, A.csr(false), Xc, ldx, tmp, w, w, c.st));
       CK(launch_spmm(prec, A.csr(true), tmp, w, Yc, ldy, w, c.st));
     } else {
@@ -196,6 +199,85 @@ void apply_op(Ctx& c, int prec, int op, const void* X, long long ldx, void* Y, l
     c.launches += 2 * spmm_launches(w);
     c.mv += 2LL * w;
   }
+}
+
+// Decide (once per handle) whether C = A^T A is applied as an explicit CSR
+// matrix, and build it.  Bytes per C apply of a block of b FP32 columns:
+// two passes 2 nnz(A) (4 + 4) + 4 (m + n + 2) + 4 b (2 m + 2 n); explicit
+// nnz(C) (4 + 4) + 4 (n + 1) + 8 b n.  AUTO takes the explicit form below 0.8
+// of the two-pass bytes.
+void ensure_normal(svds_handle* h, cudaStream_t st, int mode, int b, long long& launches) {
+  DevMatrix& A = h->A;
+  if (A.nnzC >= 0) return;
+  A.nnzC = 0;
+  if (mode == SVDS_NORMAL_TWOPASS || A.n < 1) return;
+  const long long n = A.n, m = A.m;
+  std::vector<void*> tmp;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    tmp.push_back(p);
+    return p;
+  };
+  auto drop = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : tmp) cudaFree(p);
+    tmp.clear();
+  };
+  int* cnt = static_cast<int*>(take(sizeof(int) * (n + 1)));
+  int* err = static_cast<int*>(take(sizeof(int) * 4));
+  int* work = static_cast<int*>(take(sizeof(int) * scan_work_ints(n)));
+  int* rp = static_cast<int*>(take(sizeof(int) * (n + 1)));
+  if (!cnt || !err || !work || !rp) {
+    drop();
+    return;  // not enough memory: the two-pass form needs none
+  }
+  CK(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
+  CK(launch_normal_count(n, A.rowptrT, A.colidxT, A.rowptr, A.colidx, cnt, err, st));
+  CK(launch_exclusive_scan(n, cnt, rp, work, st));
+  int herr = 0, hnnz = 0;
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hnnz, rp + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  launches += 4;
+  const double two = 2.0 * A.nnz * 8 + 4.0 * (m + n + 2) + 4.0 * b * (2.0 * m + 2.0 * n);
+  const double one = (double)hnnz * 8 + 4.0 * (n + 1) + 8.0 * b * n;
+  if (herr || hnnz <= 0 || (mode == SVDS_NORMAL_AUTO && one > 0.8 * two)) {
+    drop();
+    return;
+  }
+  int* ci = static_cast<int*>(take(sizeof(int) * hnnz));
+  double* cv = static_cast<double*>(take(sizeof(double) * hnnz));
+  float* v32 = static_cast<float*>(take(sizeof(float) * hnnz));
+  float* v32lo = static_cast<float*>(take(sizeof(float) * hnnz));
+  double* v64 = static_cast<double*>(take(sizeof(double) * hnnz));
+  if (!ci || !cv || !v32 || !v32lo || !v64) {
+    drop();
+    return;
+  }
+  CK(launch_normal_fill(n, A.rowptrT, A.colidxT, A.v64T, A.rowptr, A.colidx, A.v64, 1.0, rp, ci, cv, st));
+  CK(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
+  CK(launch_csr_values(hnnz, cv, 1.0, v32, v32lo, v64, err, st));
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  launches += 2;
+  // keep the matrix with the handle, release the temporaries
+  for (void* p : {static_cast<void*>(rp), static_cast<void*>(ci), static_cast<void*>(v32), static_cast<void*>(v32lo),
+                  static_cast<void*>(v64)}) {
+    h->allocs.push_back(p);
+    tmp.erase(std::find(tmp.begin(), tmp.end(), p));
+  }
+  drop();
+  A.rowptrC = rp;
+  A.colidxC = ci;
+  A.v32C = v32;
+  A.v32loC = v32lo;
+  A.v64C = v64;
+  A.exactC = herr == 0;
+  A.nnzC = hnnz;
 }
 
 // small helpers on column-major host matrices
@@ -1065,6 +1147,9 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), c.st));
     B1.Xlock = nullptr;
 
+    // ---- C = A^T A as one sparse matrix when that moves fewer bytes ----
+    ensure_normal(h, c.st, o.normalOperator, b, c.launches);
+
     // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
     double normA = o.aNorm > 0 ? o.aNorm * A.scale : 0.0;
     if (normA <= 0) {
@@ -1437,6 +1522,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.seconds_sync_wait = c.t_sync;
     S.host_syncs = c.nsync;
     S.inner_steps = c.inner;
+    S.normal_nnz = A.nnzC > 0 ? A.nnzC : 0;
     if (stats) *stats = S;
     h->launches += c.launches;
     return SVDS_OK;

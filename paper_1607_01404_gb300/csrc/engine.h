@@ -28,6 +28,27 @@ struct DevMatrix {
   double* colsq = nullptr;  // diag(A^T A), n
   double* rowsq = nullptr;  // diag(A A^T), m
   bool exact32 = true;      // every scaled value is a float: DF64 SpMM skips the lo part
+  // explicit C = A^T A (n x n) of the scaled values, built on demand when one
+  // SpMM with it moves fewer bytes than the two passes A then A^T
+  long long nnzC = -1;      // -1 not decided yet, 0 not used
+  int* rowptrC = nullptr;
+  int* colidxC = nullptr;
+  float* v32C = nullptr;
+  float* v32loC = nullptr;
+  double* v64C = nullptr;
+  bool exactC = true;
+  CsrDev csrC() const {
+    CsrDev c;
+    c.rows = n;
+    c.cols = n;
+    c.nnz = nnzC;
+    c.rowptr = rowptrC;
+    c.colidx = colidxC;
+    c.v32 = v32C;
+    c.v32lo = exactC ? nullptr : v32loC;
+    c.v64 = v64C;
+    return c;
+  }
   CsrDev csr(bool t) const {
     CsrDev c;
     c.rows = t ? n : m;

@@ -26,7 +26,6 @@ constexpr int kW = 32;      // width
 constexpr int kLayers = 4;
 constexpr float kRho = 0.9f;
 constexpr int kT = 256;
-constexpr int kMaxMerge = 64;  // rows of A^T longer than this are not supported for the graph
 
 int grid1(long long n) {
   long long g = (n + kT - 1) / kT;
@@ -36,70 +35,6 @@ int grid1(long long n) {
 }
 
 // ---- graph of C = A^T A ----------------------------------------------------
-// Row j of C merges the sorted rows i of A with a_ij != 0 (the entries of row j
-// of A^T); count = number of distinct columns.
-__global__ void k_c_count(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
-                          const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ cnt,
-                          int* __restrict__ err) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
-    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
-    if (nl > kMaxMerge) {
-      atomicOr(err, 1);
-      cnt[j] = 0;
-      continue;
-    }
-    int cur[kMaxMerge], end[kMaxMerge];
-    for (int t = 0; t < nl; ++t) {
-      const int i = ciT[t0 + t];
-      cur[t] = rp[i];
-      end[t] = rp[i + 1];
-    }
-    int count = 0;
-    while (true) {
-      int mn = 0x7fffffff;
-      for (int t = 0; t < nl; ++t)
-        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
-      if (mn == 0x7fffffff) break;
-      ++count;
-      for (int t = 0; t < nl; ++t)
-        if (cur[t] < end[t] && ci[cur[t]] == mn) ++cur[t];
-    }
-    cnt[j] = count;
-  }
-}
-
-__global__ void k_c_fill(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
-                         const double* __restrict__ vT, const int* __restrict__ rp, const int* __restrict__ ci,
-                         const double* __restrict__ va, double unscale, const int* __restrict__ cptr,
-                         int* __restrict__ cidx, double* __restrict__ cval) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
-    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
-    if (nl > kMaxMerge) continue;
-    int cur[kMaxMerge], end[kMaxMerge];
-    for (int t = 0; t < nl; ++t) {
-      const int i = ciT[t0 + t];
-      cur[t] = rp[i];
-      end[t] = rp[i + 1];
-    }
-    int o = cptr[j];
-    while (true) {
-      int mn = 0x7fffffff;
-      for (int t = 0; t < nl; ++t)
-        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
-      if (mn == 0x7fffffff) break;
-      double v = 0.0;
-      for (int t = 0; t < nl; ++t)
-        if (cur[t] < end[t] && ci[cur[t]] == mn) {
-          v += vT[t0 + t] * va[cur[t]];  // a_{i j} a_{i mn}
-          ++cur[t];
-        }
-      cidx[o] = mn;
-      cval[o] = v * unscale;
-      ++o;
-    }
-  }
-}
-
 __global__ void k_diag_deg(long long n, const int* __restrict__ cptr, const int* __restrict__ cidx,
                            const double* __restrict__ cval, double* __restrict__ cdiag, float* __restrict__ deg,
                            int* __restrict__ degmax) {
@@ -643,14 +578,15 @@ int gnn_build(phsvds_gnn** out, const DevMatrix& D, bool user_orientation, bool 
   if (cudaMemsetAsync(err, 0, 4 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(dmax, 0, 4 * sizeof(int), st) != cudaSuccess)
     return fail(gfail(cudaGetLastError(), "memset"));
-  k_c_count<<<grid1(n), kT, 0, st>>>(n, rpT, ciT, rp, ci, cnt, err);
+  if (launch_normal_count(n, rpT, ciT, rp, ci, cnt, err, st) != cudaSuccess)
+    return fail(gfail(cudaGetLastError(), "normal count"));
   if (launch_exclusive_scan(n, cnt, g->cptr, work, st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "scan"));
   int herr = 0, hnnz = 0;
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&hnnz, g->cptr + n, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(gfail(cudaGetLastError(), "graph count"));
   if (herr) {
-    phsvds::set_last_error("phsvds_gnn_create: a column of A has more than 64 nonzeros");
+    phsvds::set_last_error("phsvds_gnn_create: a column of A has more nonzeros than the merge supports");
     return fail(SVDS_ERR_SHAPE);
   }
   g->nnz = hnnz;
@@ -684,8 +620,9 @@ int gnn_build(phsvds_gnn** out, const DevMatrix& D, bool user_orientation, bool 
       return fail(rc);
   }
   // device values are scale * A (a power of two): C in the user's units is exact
-  k_c_fill<<<grid1(n), kT, 0, st>>>(n, rpT, ciT, vT, rp, ci, va, 1.0 / (D.scale * D.scale), g->cptr, g->cidx,
-                                    g->cval);
+  if (launch_normal_fill(n, rpT, ciT, vT, rp, ci, va, 1.0 / (D.scale * D.scale), g->cptr, g->cidx, g->cval, st) !=
+      cudaSuccess)
+    return fail(gfail(cudaGetLastError(), "normal fill"));
   k_diag_deg<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->deg, dmax);
   k_edges<<<grid1(n), kT, 0, st>>>(n, g->cptr, g->cidx, g->cval, g->cdiag, g->e, g->wdeg, g->tpos, g->logc);
   k_fill1<<<grid1(n > nnz ? n : nnz), kT, 0, st>>>(n > nnz ? n : nnz, g->ones);

@@ -1240,6 +1240,93 @@ cudaError_t launch_exclusive_scan(long long n, const int* in, int* out, int* wor
 
 size_t scan_work_ints(long long n) { return (size_t)(2 * ((n + kScanChunk - 1) / kScanChunk) + 4); }
 
+// ---------------------------------------------------------------------------
+// C = A^T A in CSR: row j merges the sorted rows i of A listed in row j of A^T
+// (a k-way merge of at most kMergeMax lists per thread, deterministic order).
+// ---------------------------------------------------------------------------
+constexpr int kMergeMax = 64;
+
+// Row j of C merges the sorted rows i of A with a_ij != 0 (the entries of row j
+// of A^T); count = number of distinct columns.
+__global__ void k_c_count(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
+                          const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ cnt,
+                          int* __restrict__ err) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
+    if (nl > kMergeMax) {
+      atomicOr(err, 1);
+      cnt[j] = 0;
+      continue;
+    }
+    int cur[kMergeMax], end[kMergeMax];
+    for (int t = 0; t < nl; ++t) {
+      const int i = ciT[t0 + t];
+      cur[t] = rp[i];
+      end[t] = rp[i + 1];
+    }
+    int count = 0;
+    while (true) {
+      int mn = 0x7fffffff;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
+      if (mn == 0x7fffffff) break;
+      ++count;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] == mn) ++cur[t];
+    }
+    cnt[j] = count;
+  }
+}
+
+__global__ void k_c_fill(long long n, const int* __restrict__ rpT, const int* __restrict__ ciT,
+                         const double* __restrict__ vT, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const double* __restrict__ va, double scale, const int* __restrict__ cptr,
+                         int* __restrict__ cidx, double* __restrict__ cval) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const int t0 = rpT[j], nl = rpT[j + 1] - t0;
+    if (nl > kMergeMax) continue;
+    int cur[kMergeMax], end[kMergeMax];
+    for (int t = 0; t < nl; ++t) {
+      const int i = ciT[t0 + t];
+      cur[t] = rp[i];
+      end[t] = rp[i + 1];
+    }
+    int o = cptr[j];
+    while (true) {
+      int mn = 0x7fffffff;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] < mn) mn = ci[cur[t]];
+      if (mn == 0x7fffffff) break;
+      double v = 0.0;
+      for (int t = 0; t < nl; ++t)
+        if (cur[t] < end[t] && ci[cur[t]] == mn) {
+          v += vT[t0 + t] * va[cur[t]];  // a_{i j} a_{i mn}
+          ++cur[t];
+        }
+      cidx[o] = mn;
+      cval[o] = v * scale;
+      ++o;
+    }
+  }
+}
+
+cudaError_t launch_normal_count(long long n, const int* rpT, const int* ciT, const int* rp, const int* ci, int* cnt,
+                                int* err, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_c_count<<<persistent_grid(n, kThreads), kThreads, 0, st>>>(n, rpT, ciT, rp, ci, cnt, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, const double* vT, const int* rp,
+                               const int* ci, const double* va, double scale, const int* cptr, int* cidx,
+                               double* cval, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_c_fill<<<persistent_grid(n, kThreads), kThreads, 0, st>>>(n, rpT, ciT, vT, rp, ci, va, scale, cptr, cidx, cval);
+  return cudaGetLastError();
+}
+
+int normal_merge_max() { return kMergeMax; }
+
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   k_row_sumsq<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, rowptr, vals, out);

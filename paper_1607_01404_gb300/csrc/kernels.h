@@ -105,6 +105,17 @@ size_t transpose_work_ints(long long cols);
 // out[0] = 0, out[i + 1] = in[0] + ... + in[i] (int32), for n counts; work: scan_work_ints(n) ints.
 cudaError_t launch_exclusive_scan(long long n, const int* in, int* out, int* work, cudaStream_t st);
 size_t scan_work_ints(long long n);
+// C = A^T A (n x n) from A (rp, ci, va; sorted rows) and A^T (rpT, ciT, vT; n
+// rows): count pass cnt[j] = entries of row j of C (err[0] |= 1 when a row of
+// A^T has more than normal_merge_max() entries; its count is 0), then, after
+// an exclusive scan into cptr, the fill pass (sorted columns, values
+// scale * sum_i a_ij a_ik in FP64).
+cudaError_t launch_normal_count(long long n, const int* rpT, const int* ciT, const int* rp, const int* ci, int* cnt,
+                                int* err, cudaStream_t st);
+cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, const double* vT, const int* rp,
+                               const int* ci, const double* va, double scale, const int* cptr, int* cidx,
+                               double* cval, cudaStream_t st);
+int normal_merge_max();
 // out[i] = sum_k vals[k]^2 over row i (FP64).
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st);
 // Jacobi scale in storage format: d[r] = 1 / s[r] (1 where s[r] == 0), optionally sqrt'ed first.

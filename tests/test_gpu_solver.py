@@ -235,3 +235,35 @@ def test_jdqmr_fp64_inner_solves(target):
     r = B.svds(A, 4, target, 1e-10, maxBlockSize=4, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                innerPrecision=B.SVDS_FP64, maxMatvecs=600000)
     _compare_to_dense(A, r, target, 4, 1e-10)
+
+
+@pytest.mark.parametrize("form", [dict(), dict(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR),
+                                  dict(stage1_precision=B.SVDS_NATIVE_FP64)])
+def test_explicit_normal_matrix_matches_two_passes(form):
+    """C = A^T A as one explicit sparse matrix: same triplets as A then A^T."""
+    A = wl.weighted_grid(20, 2, seed=5)
+    out = {}
+    for name, mode in (("two", B.SVDS_NORMAL_TWOPASS), ("explicit", B.SVDS_NORMAL_EXPLICIT)):
+        r = B.svds(A, 5, "smallest", tol=1e-10, maxBlockSize=2, normalOperator=mode, **form)
+        assert r["nconv"] == 5
+        out[name] = r
+    assert out["two"]["stats"]["normal_nnz"] == 0
+    S = A.to_scipy()
+    C = (S.T @ S).tocsr()
+    assert out["explicit"]["stats"]["normal_nnz"] == C.nnz
+    np.testing.assert_allclose(out["explicit"]["sigma"], out["two"]["sigma"], rtol=1e-9)
+    sd = np.sort(np.linalg.svd(S.toarray(), compute_uv=False))[:5]
+    np.testing.assert_allclose(out["explicit"]["sigma"], sd, rtol=1e-9)
+    normA = np.linalg.norm(S.toarray(), 2)
+    assert np.all(out["explicit"]["rnorm"] <= 1.01e-10 * normA)
+
+
+def test_auto_normal_operator_choice():
+    """AUTO: explicit C for grid operators (few nonzeros per row of C), two passes
+    for a matrix whose C is much denser than A."""
+    g = wl.grid_difference(16, 3)
+    r = B.svds(g, 3, "smallest", tol=1e-8, maxBlockSize=2)
+    assert r["stats"]["normal_nnz"] > 0
+    d = wl.random_illconditioned(3000, 1500, per_col=16, seed=3)
+    r = B.svds(d, 3, "largest", tol=1e-8, maxBlockSize=2)
+    assert r["stats"]["normal_nnz"] == 0
