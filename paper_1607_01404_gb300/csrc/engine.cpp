@@ -598,11 +598,33 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
   CK(convert_cols(prec, B.Rb, B.b, pin, bv, nbk, L, nbk, d2, c.st));
   CK(qmr_init(pin, L, nbk, x, bv, cfg.jdinv, cfg.jdK, B.ju, kx, q, r, d, sol, B.jS, c.partial, B.jdots, c.st));
   c.launches += 2 + qmr_init_launches(nbk, cfg.jdK != nullptr);
+  const DevMatrix& Am = *c.A;
   for (int k = 0; k < cfg.jd_maxk; ++k) {
-    apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
-    CK(qmr_step(pin, L, nbk, x, w, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol, B.jS,
-                c.partial, B.jdots, c.st));
-    c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr);
+    // w = op(q), fused with the step's first dot products when op is C
+    bool fused = false;
+    if (cfg.op == OP_C) {
+      if (Am.nnzC > 0) {
+        CK(qmr_op_dots(pin, L, nbk, Am.csrC(), q, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
+      } else {
+        CK(launch_spmm(pin, Am.csr(false), q, nbk, B.jtmp, nbk, nbk, c.st));
+        CK(qmr_op_dots(pin, L, nbk, Am.csr(true), B.jtmp, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
+        if (fused) {
+          c.launches += spmm_launches(nbk);
+        } else {
+          CK(launch_spmm(pin, Am.csr(true), B.jtmp, nbk, w, nbk, nbk, c.st));
+          c.launches += 2 * spmm_launches(nbk);
+        }
+        c.mv += 2LL * nbk;
+      }
+      if (fused) {
+        c.launches += 2;
+        if (Am.nnzC > 0) c.mv += 2LL * nbk;
+      }
+    }
+    if (!fused && !(cfg.op == OP_C && Am.nnzC <= 0)) apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
+    CK(qmr_step(pin, L, nbk, x, w, fused, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol,
+                B.jS, c.partial, B.jdots, c.st));
+    c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr, fused);
     c.inner += 1;
     if ((k + 1) % 8 == 0 && k + 1 < cfg.jd_maxk) {
       CK(cudaMemcpyAsync(c.hG, B.jS, sizeof(QmrState) * nbk, cudaMemcpyDeviceToHost, c.st));

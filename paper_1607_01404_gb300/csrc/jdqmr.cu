@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "jdqmr.h"
 #include "kernels.h"
+#include "spmm_dev.cuh"
 
 namespace phsvds {
 
@@ -345,6 +346,92 @@ __global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const ty
   block_reduce_store<P, 2, NB>(acc, nb, partial);
 }
 
+// Fused Y = K X (CSR, rows L, Y row-major with ld NB) and the dot products
+// of Y with two row-major blocks E1, E2 (ld NB): d0 = E1^T Y, d1 = E2^T Y and,
+// for ND = 4, d2 = E1^T E2, d3 = E2^T E2 (per column, FP64-class partials).
+// With (E1, E2) = (x, q) these are the four dots of k_qmr_dots1 for w = op q;
+// with (E1, E2) = (r, x) the two dots of k_qmr_dots_u for u = K^-1 r.
+template <class P, int NB, int VMODE, bool VEC, int ND>
+__global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ colidx, const float* __restrict__ v32,
+                                                  const float* __restrict__ v32lo, const double* __restrict__ v64,
+                                                  const typename P::S* __restrict__ X, long long ldx,
+                                                  typename P::S* __restrict__ Y, const typename P::S* __restrict__ E1,
+                                                  const typename P::S* __restrict__ E2,
+                                                  typename P::G* __restrict__ partial) {
+  using G = typename P::G;
+  using A = typename P::A;
+  G acc[ND][NB];
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+  for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
+    A y[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) y[c] = P::zero();
+    row_product<P, NB, VMODE, VEC, spmm_unroll<P, NB>()>(__ldg(rowptr + row), __ldg(rowptr + row + 1), colidx, v32,
+                                                          v32lo, v64, X, ldx, y);
+    store_yrow<P, NB, VEC>(Y + row * NB, y);
+    A e1[NB], e2[NB];
+    ldrow<P, NB, VEC>(E1, row, NB, e1);
+    ldrow<P, NB, VEC>(E2, row, NB, e2);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc[0][j] = P::gfma(acc[0][j], e1[j], y[j]);
+      acc[1][j] = P::gfma(acc[1][j], e2[j], y[j]);
+      if constexpr (ND == 4) {
+        acc[2][j] = P::gfma(acc[2][j], e1[j], e2[j]);
+        acc[3][j] = P::gfma(acc[3][j], e2[j], e2[j]);
+      }
+    }
+  }
+  block_reduce_store<P, ND, NB>(acc, NB, partial);
+}
+
+// launch k_spmm_dots for the value format of K; false when nb has no fused form
+template <class P, int NB, int ND>
+bool spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
+                  const void* E2, void* partial, int grid, cudaStream_t st) {
+  using SS = typename P::S;
+  using GG = typename P::G;
+  constexpr bool vec = (NB * sizeof(SS)) % 16 == 0;
+  if (vec && ((ldx * sizeof(SS)) % 16 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0 ||
+              reinterpret_cast<uintptr_t>(Y) % 16 != 0 || reinterpret_cast<uintptr_t>(E1) % 16 != 0 ||
+              reinterpret_cast<uintptr_t>(E2) % 16 != 0))
+    return false;
+  const SS *x = (const SS*)X, *e1 = (const SS*)E1, *e2 = (const SS*)E2;
+  SS* y = (SS*)Y;
+  GG* pd = (GG*)partial;
+  if constexpr (P::id == kF32) {
+    k_spmm_dots<P, NB, 0, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, nullptr, nullptr, x, ldx, y, e1,
+                                                         e2, pd);
+  } else if constexpr (P::id == kDF64) {
+    if (K.v32lo == nullptr)
+      k_spmm_dots<P, NB, 1, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, nullptr, nullptr, x, ldx, y,
+                                                           e1, e2, pd);
+    else
+      k_spmm_dots<P, NB, 2, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, K.v32lo, nullptr, x, ldx, y,
+                                                           e1, e2, pd);
+  } else {
+    k_spmm_dots<P, NB, 3, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, nullptr, nullptr, K.v64, x, ldx, y, e1,
+                                                         e2, pd);
+  }
+  return true;
+}
+
+template <class P, int ND>
+bool spmm_dots_p(int nb, long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
+                 const void* E2, void* partial, int grid, cudaStream_t st) {
+  switch (nb) {
+    case 1: return spmm_dots_nb<P, 1, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
+    case 2: return spmm_dots_nb<P, 2, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
+    case 4: return spmm_dots_nb<P, 4, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
+    case 8: return spmm_dots_nb<P, 8, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
+  }
+  return false;
+}
+
 // QMR smoothing scalars, stopping test, next search-direction coefficients
 __global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
   const int j = threadIdx.x;
@@ -499,25 +586,29 @@ cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void
 }
 
 template <class P, int NB, bool VEC>
-cudaError_t step_nb(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                    const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
-                    void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+cudaError_t step_nb(long long L, int nb, const void* x, const void* w, bool dots_ready, const void* kx,
+                    const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
+                    void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
   const int g = qmr_grid(L);
   G* pd = reinterpret_cast<G*>(partial);
   if (K) dinv = nullptr;
-  k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
-  k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  if (!dots_ready) {
+    k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
+    k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  }
   k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
   k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
                                               (const SS*)dinv, eta, S, (SS*)r, pd);
   k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
   if (K) {
     // u = K^-1 r by SpMM; r^T u and x^T u replace dots 1 and 2
-    const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
-    if (e != cudaSuccess) return e;
-    k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
+    if (!spmm_dots_p<P, 2>(nb, L, *K, r, nb, u, r, x, pd, g, st)) {
+      const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
+      if (e != cudaSuccess) return e;
+      k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
+    }
     k_reduce_g<P><<<2 * nb, 128, 0, st>>>(pd, g, 2 * nb, dots + nb);
   }
   k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
@@ -527,14 +618,14 @@ cudaError_t step_nb(long long L, int nb, const void* x, const void* w, const voi
 }
 
 template <class P>
-cudaError_t step_p(long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
+cudaError_t step_p(long long L, int nb, const void* x, const void* w, bool dr, const void* kx, const void* dinv,
                    const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
                    void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   constexpr size_t es = sizeof(typename P::S);
 #define STEP(NBv)                                                                                                  \
   ((nb == NBv && (NBv * es) % 16 == 0)                                                                            \
-       ? step_nb<P, NBv, true>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st)    \
-       : step_nb<P, NBv, false>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
+       ? step_nb<P, NBv, true>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st) \
+       : step_nb<P, NBv, false>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
   if (nb <= 1) return STEP(1);
   if (nb <= 2) return STEP(2);
   if (nb <= 4) return STEP(4);
@@ -556,17 +647,18 @@ cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b
   return cudaErrorInvalidValue;
 }
 
-cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, const void* kx, const void* dinv,
-                     const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
-                     void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, bool dots_ready, const void* kx,
+                     const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
+                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   if (nb < 1 || nb > kMaxNb || (K && !u)) return cudaErrorInvalidValue;
+  const bool dr = dots_ready;
   switch (prec) {
     case kF32:
-      return step_p<PF32>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PF32>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
     case kDF64:
-      return step_p<PDF64>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PDF64>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
     case kF64:
-      return step_p<PF64>(L, nb, x, w, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PF64>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -582,7 +674,34 @@ int spmm_chunks(int b) {
 }
 }  // namespace
 
-int qmr_step_launches(int nb, bool sparse_k) { return 7 + (sparse_k ? spmm_chunks(nb) + 2 : 0); }
+int qmr_step_launches(int nb, bool sparse_k, bool dots_ready) {
+  const bool fused = nb == 1 || nb == 2 || nb == 4 || nb == 8;
+  return 7 - (dots_ready ? 2 : 0) + (sparse_k ? (fused ? 2 : spmm_chunks(nb) + 2) : 0);
+}
+
+cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const void* X, long long ldx, void* w,
+                        const void* x, const void* q, void* partial, double* dots, bool* done, cudaStream_t st) {
+  *done = false;
+  if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+  const int g = qmr_grid(L);
+  bool ok = false;
+  switch (prec) {
+    case kF32: ok = spmm_dots_p<PF32, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
+    case kDF64: ok = spmm_dots_p<PDF64, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
+    case kF64: ok = spmm_dots_p<PF64, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (!ok) return cudaSuccess;
+  switch (prec) {
+    case kF32: k_reduce_g<PF32><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PF32::G*>(partial), g, 4 * nb, dots); break;
+    case kDF64:
+      k_reduce_g<PDF64><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PDF64::G*>(partial), g, 4 * nb, dots);
+      break;
+    default: k_reduce_g<PF64><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PF64::G*>(partial), g, 4 * nb, dots); break;
+  }
+  *done = true;
+  return cudaGetLastError();
+}
 int qmr_init_launches(int nb, bool sparse_k) { return 4 + (sparse_k ? 2 * spmm_chunks(nb) : 0); }
 
 cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,

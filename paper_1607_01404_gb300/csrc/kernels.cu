@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "spmm_dev.cuh"
 #include "tiled.h"
 
 namespace phsvds {
@@ -56,33 +57,6 @@ __device__ __forceinline__ const S* seg_col(const SegArr& sa, int c, long long* 
 // ---------------------------------------------------------------------------
 // SpMM
 // ---------------------------------------------------------------------------
-// VMODE: 0 float values (F32), 1 float values into double-float (DF64, exact
-// values), 2 double-float values (DF64), 3 double values (F64).  VEC: the NB
-// entries of a row are 16-byte multiples and every row starts on a 16-byte
-// boundary, so gathers and stores use 16-byte vector accesses.
-template <class P, int NB, bool VEC>
-__device__ __forceinline__ void load_xrow(const typename P::S* __restrict__ xr, typename P::A (&v)[NB]) {
-  using S = typename P::S;
-  if constexpr (VEC) {
-    constexpr int W = (int)(NB * sizeof(S) / 16);
-    float buf[NB * sizeof(S) / 4];
-    const float4* q4 = reinterpret_cast<const float4*>(xr);
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-      const float4 t = __ldg(q4 + i);
-      buf[4 * i] = t.x;
-      buf[4 * i + 1] = t.y;
-      buf[4 * i + 2] = t.z;
-      buf[4 * i + 3] = t.w;
-    }
-#pragma unroll
-    for (int c = 0; c < NB; ++c) v[c] = P::load(reinterpret_cast<const S*>(buf) + c);
-  } else {
-#pragma unroll
-    for (int c = 0; c < NB; ++c) v[c] = P::load(xr + c);
-  }
-}
-
 template <class P, int NB, int VMODE, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __restrict__ rowptr,
                                                    const int* __restrict__ colidx, const float* __restrict__ v32,
@@ -90,92 +64,18 @@ __global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __
                                                    const typename P::S* __restrict__ X, long long ldx,
                                                    typename P::S* __restrict__ Y, long long ldy) {
   using A = typename P::A;
-  using S = typename P::S;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= rows) return;
   A acc[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c) acc[c] = P::zero();
-  const int k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
-  for (int k = k0; k < k1; ++k) {
-    const int j = __ldg(colidx + k);
-    A xv[NB];
-    load_xrow<P, NB, VEC>(X + (long long)j * ldx, xv);
-    if constexpr (VMODE == 0) {
-      const float a = __ldg(v32 + k);
-#pragma unroll
-      for (int c = 0; c < NB; ++c) acc[c] = fmaf(xv[c], a, acc[c]);
-    } else if constexpr (VMODE == 1) {
-      const float a = __ldg(v32 + k);
-#pragma unroll
-      for (int c = 0; c < NB; ++c) acc[c] = df_fma_f(acc[c], xv[c], a);
-    } else if constexpr (VMODE == 2) {
-      const df a = {__ldg(v32 + k), __ldg(v32lo + k)};
-#pragma unroll
-      for (int c = 0; c < NB; ++c) acc[c] = df_fma(acc[c], xv[c], a);
-    } else {
-      const double a = __ldg(v64 + k);
-#pragma unroll
-      for (int c = 0; c < NB; ++c) acc[c] = ::fma(xv[c], a, acc[c]);
-    }
-  }
-  S* yr = Y + i * ldy;
-  if constexpr (VEC) {
-    constexpr int W = (int)(NB * sizeof(S) / 16);
-    float buf[NB * sizeof(S) / 4];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) P::store(reinterpret_cast<S*>(buf) + c, acc[c]);
-    float4* q4 = reinterpret_cast<float4*>(yr);
-#pragma unroll
-    for (int t = 0; t < W; ++t) q4[t] = make_float4(buf[4 * t], buf[4 * t + 1], buf[4 * t + 2], buf[4 * t + 3]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < NB; ++c) P::store(yr + c, acc[c]);
-  }
+  row_product<P, NB, VMODE, VEC, spmm_unroll<P, NB>()>(__ldg(rowptr + i), __ldg(rowptr + i + 1), colidx, v32, v32lo,
+                                                        v64, X, ldx, acc);
+  store_yrow<P, NB, VEC>(Y + i * ldy, acc);
 }
 
 // Short rows (at most a few nonzeros): each thread handles two consecutive rows
 // and interleaves their gathers, doubling the loads in flight per thread.
-template <class P, int NB, int VMODE, bool VEC>
-__device__ __forceinline__ void spmm_accum(const int k, const float* __restrict__ v32, const float* __restrict__ v32lo,
-                                           const double* __restrict__ v64, const typename P::A (&xv)[NB],
-                                           typename P::A (&acc)[NB]) {
-  if constexpr (VMODE == 0) {
-    const float a = __ldg(v32 + k);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = fmaf(xv[c], a, acc[c]);
-  } else if constexpr (VMODE == 1) {
-    const float a = __ldg(v32 + k);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = df_fma_f(acc[c], xv[c], a);
-  } else if constexpr (VMODE == 2) {
-    const df a = {__ldg(v32 + k), __ldg(v32lo + k)};
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = df_fma(acc[c], xv[c], a);
-  } else {
-    const double a = __ldg(v64 + k);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = ::fma(xv[c], a, acc[c]);
-  }
-}
-
-template <class P, int NB, bool VEC>
-__device__ __forceinline__ void store_yrow(typename P::S* yr, const typename P::A (&acc)[NB]) {
-  using S = typename P::S;
-  if constexpr (VEC) {
-    constexpr int W = (int)(NB * sizeof(S) / 16);
-    float buf[NB * sizeof(S) / 4];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) P::store(reinterpret_cast<S*>(buf) + c, acc[c]);
-    float4* q4 = reinterpret_cast<float4*>(yr);
-#pragma unroll
-    for (int t = 0; t < W; ++t) q4[t] = make_float4(buf[4 * t], buf[4 * t + 1], buf[4 * t + 2], buf[4 * t + 3]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < NB; ++c) P::store(yr + c, acc[c]);
-  }
-}
-
 template <class P, int NB, int VMODE, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_spmm2(long long rows, const int* __restrict__ rowptr,
                                                     const int* __restrict__ colidx, const float* __restrict__ v32,
