@@ -16,7 +16,10 @@
 // needed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "jdqmr.h"
@@ -29,6 +32,62 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxNb = 8;
+
+// Persistent grids: every SM holds as many 256-thread CTAs of the kernel as
+// its register and shared-memory use allow (queried once per kernel), so
+// there is no tail wave; at most kMaxGrid CTAs (partial-sum storage).
+constexpr int kMaxGrid = 2048;
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 152;
+    }
+    sms = v;
+  }
+  return sms;
+}
+
+// resident 256-thread CTAs per SM of one kernel (cached by kernel address)
+template <class K>
+int blocks_per_sm(K kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  const void* key = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kT, 0) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 1;
+  }
+  cache[key] = v;
+  return v;
+}
+
+template <class K>
+int occ_grid(K kernel, long long work) {
+  long long g = (work + kT - 1) / kT;
+  const long long cap = std::min<long long>((long long)sm_count() * blocks_per_sm(kernel), kMaxGrid);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// grid of the plain elementwise kernels
+int qmr_grid(long long L) {
+  long long g = (L + kT - 1) / kT;
+  const long long cap = (long long)sm_count() * 4;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
 
 // conversion of a double scalar to the mode's coefficient type
 template <class P>
@@ -52,10 +111,28 @@ __device__ __forceinline__ df shfl_down(df v, int o) {
 }
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 
+// Per-thread accumulators of the dot products: plain FP32 in the FP32 inner
+// mode (its vectors are FP32 and a thread sums a few dozen rows; the block and
+// grid levels stay FP64-class), the mode's FP64-class type otherwise.
+template <class P>
+struct TAcc {
+  using T = typename P::G;
+  __device__ static T zero() { return P::gzero(); }
+  __device__ static T fma(T a, typename P::A x, typename P::A y) { return P::gfma(a, x, y); }
+  __device__ static typename P::G g(T a) { return a; }
+};
+template <>
+struct TAcc<PF32> {
+  using T = float;
+  __device__ static float zero() { return 0.f; }
+  __device__ static float fma(float a, float x, float y) { return fmaf(x, y, a); }
+  __device__ static df g(float a) { return df{a, 0.f}; }
+};
+
 // Per-CTA partial sums of ND dot products for each of the NW <= 8 columns
 // (FP64-class accumulation, fixed order), written to partial[blk][d * nb + j].
 template <class P, int ND, int NW>
-__device__ __forceinline__ void block_reduce_store(typename P::G (&acc)[ND][NW], int nb, typename P::G* partial) {
+__device__ __forceinline__ void block_reduce_store(typename TAcc<P>::T (&acc)[ND][NW], int nb, typename P::G* partial) {
   using G = typename P::G;
   __shared__ G red[kT / 32][ND * kMaxNb];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -63,7 +140,7 @@ __device__ __forceinline__ void block_reduce_store(typename P::G (&acc)[ND][NW],
   for (int d = 0; d < ND; ++d)
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
-      G v = acc[d][j];
+      G v = TAcc<P>::g(acc[d][j]);
       for (int o = 16; o > 0; o >>= 1) v = P::gadd(v, shfl_down(v, o));
       if (lane == 0) red[warp][d * kMaxNb + j] = v;
     }
@@ -150,11 +227,11 @@ __global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const type
                                                  const typename P::S* __restrict__ upre,
                                                  typename P::G* __restrict__ partial) {
   using G = typename P::G;
-  G acc[5][kMaxNb];
+  typename TAcc<P>::T acc[5][kMaxNb];
 #pragma unroll
   for (int d = 0; d < 5; ++d)
 #pragma unroll
-    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < kMaxNb; ++j) acc[d][j] = TAcc<P>::zero();
   for (long long r = blockIdx.x * (long long)kT + threadIdx.x; r < L; r += (long long)gridDim.x * kT) {
     const auto s = ld_or_one<P>(dinv, r);
 #pragma unroll
@@ -171,11 +248,11 @@ __global__ void __launch_bounds__(kT) k_qmr_init(long long L, int nb, const type
           uv = mul<P>(s, bv);
           P::store(kx + o, kv);
         }
-        acc[0][j] = P::gfma(acc[0][j], xv, kv);
-        acc[1][j] = P::gfma(acc[1][j], xv, uv);
-        acc[2][j] = P::gfma(acc[2][j], bv, bv);
-        acc[3][j] = P::gfma(acc[3][j], bv, uv);
-        acc[4][j] = P::gfma(acc[4][j], bv, kv);
+        acc[0][j] = TAcc<P>::fma(acc[0][j], xv, kv);
+        acc[1][j] = TAcc<P>::fma(acc[1][j], xv, uv);
+        acc[2][j] = TAcc<P>::fma(acc[2][j], bv, bv);
+        acc[3][j] = TAcc<P>::fma(acc[3][j], bv, uv);
+        acc[4][j] = TAcc<P>::fma(acc[4][j], bv, kv);
       }
   }
   block_reduce_store<P, 5, kMaxNb>(acc, nb, partial);
@@ -232,11 +309,11 @@ __global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typ
                                                   typename P::G* __restrict__ partial) {
   using G = typename P::G;
   using A = typename P::A;
-  G acc[4][NB];
+  typename TAcc<P>::T acc[4][NB];
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
-    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = TAcc<P>::zero();
   for (long long r = blockIdx.x * (long long)kT + threadIdx.x; r < L; r += (long long)gridDim.x * kT) {
     A xv[NB], qv[NB], wv[NB];
     ldrow<P, NB, VEC>(x, r, nb, xv);
@@ -244,10 +321,10 @@ __global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typ
     ldrow<P, NB, VEC>(w, r, nb, wv);
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      acc[0][j] = P::gfma(acc[0][j], xv[j], wv[j]);
-      acc[1][j] = P::gfma(acc[1][j], qv[j], wv[j]);
-      acc[2][j] = P::gfma(acc[2][j], xv[j], qv[j]);
-      acc[3][j] = P::gfma(acc[3][j], qv[j], qv[j]);
+      acc[0][j] = TAcc<P>::fma(acc[0][j], xv[j], wv[j]);
+      acc[1][j] = TAcc<P>::fma(acc[1][j], qv[j], wv[j]);
+      acc[2][j] = TAcc<P>::fma(acc[2][j], xv[j], qv[j]);
+      acc[3][j] = TAcc<P>::fma(acc[3][j], qv[j], qv[j]);
     }
   }
   block_reduce_store<P, 4, NB>(acc, nb, partial);
@@ -291,11 +368,11 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
     se[threadIdx.x] = to_c<P>(ok ? eta[threadIdx.x] : 0.0);
   }
   __syncthreads();
-  G acc[4][NB];
+  typename TAcc<P>::T acc[4][NB];
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
-    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = TAcc<P>::zero();
   for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
     const auto sv = ld_or_one<P>(dinv, row);
     A xv[NB], qv[NB], wv[NB], rv[NB], kv[NB];
@@ -309,10 +386,10 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
       const A t = P::sub(P::sub(wv[j], P::mulc(qv[j], se[j])), P::mulc(xv[j], sc[j]));
       rv[j] = P::sub(rv[j], P::mulc(t, sa[j]));
       const A uv = mul<P>(sv, rv[j]);
-      acc[0][j] = P::gfma(acc[0][j], rv[j], rv[j]);
-      acc[1][j] = P::gfma(acc[1][j], rv[j], uv);
-      acc[2][j] = P::gfma(acc[2][j], xv[j], uv);
-      acc[3][j] = P::gfma(acc[3][j], rv[j], kv[j]);
+      acc[0][j] = TAcc<P>::fma(acc[0][j], rv[j], rv[j]);
+      acc[1][j] = TAcc<P>::fma(acc[1][j], rv[j], uv);
+      acc[2][j] = TAcc<P>::fma(acc[2][j], xv[j], uv);
+      acc[3][j] = TAcc<P>::fma(acc[3][j], rv[j], kv[j]);
     }
     strow<P, NB, VEC>(r, row, nb, rv);
   }
@@ -327,11 +404,11 @@ __global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const ty
                                                    typename P::G* __restrict__ partial) {
   using G = typename P::G;
   using A = typename P::A;
-  G acc[2][NB];
+  typename TAcc<P>::T acc[2][NB];
 #pragma unroll
   for (int d = 0; d < 2; ++d)
 #pragma unroll
-    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = TAcc<P>::zero();
   for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
     A xv[NB], rv[NB], uv[NB];
     ldrow<P, NB, VEC>(x, row, nb, xv);
@@ -339,8 +416,8 @@ __global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const ty
     ldrow<P, NB, VEC>(u, row, nb, uv);
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      acc[0][j] = P::gfma(acc[0][j], rv[j], uv[j]);
-      acc[1][j] = P::gfma(acc[1][j], xv[j], uv[j]);
+      acc[0][j] = TAcc<P>::fma(acc[0][j], rv[j], uv[j]);
+      acc[1][j] = TAcc<P>::fma(acc[1][j], xv[j], uv[j]);
     }
   }
   block_reduce_store<P, 2, NB>(acc, nb, partial);
@@ -361,11 +438,11 @@ __global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __rest
                                                   typename P::G* __restrict__ partial) {
   using G = typename P::G;
   using A = typename P::A;
-  G acc[ND][NB];
+  typename TAcc<P>::T acc[ND][NB];
 #pragma unroll
   for (int d = 0; d < ND; ++d)
 #pragma unroll
-    for (int j = 0; j < NB; ++j) acc[d][j] = P::gzero();
+    for (int j = 0; j < NB; ++j) acc[d][j] = TAcc<P>::zero();
   for (long long row = blockIdx.x * (long long)kT + threadIdx.x; row < L; row += (long long)gridDim.x * kT) {
     A y[NB];
 #pragma unroll
@@ -378,58 +455,57 @@ __global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __rest
     ldrow<P, NB, VEC>(E2, row, NB, e2);
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      acc[0][j] = P::gfma(acc[0][j], e1[j], y[j]);
-      acc[1][j] = P::gfma(acc[1][j], e2[j], y[j]);
+      acc[0][j] = TAcc<P>::fma(acc[0][j], e1[j], y[j]);
+      acc[1][j] = TAcc<P>::fma(acc[1][j], e2[j], y[j]);
       if constexpr (ND == 4) {
-        acc[2][j] = P::gfma(acc[2][j], e1[j], e2[j]);
-        acc[3][j] = P::gfma(acc[3][j], e2[j], e2[j]);
+        acc[2][j] = TAcc<P>::fma(acc[2][j], e1[j], e2[j]);
+        acc[3][j] = TAcc<P>::fma(acc[3][j], e2[j], e2[j]);
       }
     }
   }
   block_reduce_store<P, ND, NB>(acc, NB, partial);
 }
 
-// launch k_spmm_dots for the value format of K; false when nb has no fused form
+// launch k_spmm_dots for the value format of K; returns its grid (the number
+// of partial sums), or 0 when nb or the alignment has no fused form
 template <class P, int NB, int ND>
-bool spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
-                  const void* E2, void* partial, int grid, cudaStream_t st) {
+int spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1, const void* E2,
+                 void* partial, cudaStream_t st) {
   using SS = typename P::S;
   using GG = typename P::G;
   constexpr bool vec = (NB * sizeof(SS)) % 16 == 0;
   if (vec && ((ldx * sizeof(SS)) % 16 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0 ||
               reinterpret_cast<uintptr_t>(Y) % 16 != 0 || reinterpret_cast<uintptr_t>(E1) % 16 != 0 ||
               reinterpret_cast<uintptr_t>(E2) % 16 != 0))
-    return false;
+    return 0;
   const SS *x = (const SS*)X, *e1 = (const SS*)E1, *e2 = (const SS*)E2;
   SS* y = (SS*)Y;
   GG* pd = (GG*)partial;
+  auto go = [&](auto kern, const float* a32, const float* a32lo, const double* a64) {
+    const int g = occ_grid(kern, L);
+    kern<<<g, kT, 0, st>>>(L, K.rowptr, K.colidx, a32, a32lo, a64, x, ldx, y, e1, e2, pd);
+    return g;
+  };
   if constexpr (P::id == kF32) {
-    k_spmm_dots<P, NB, 0, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, nullptr, nullptr, x, ldx, y, e1,
-                                                         e2, pd);
+    return go(k_spmm_dots<P, NB, 0, vec, ND>, K.v32, nullptr, nullptr);
   } else if constexpr (P::id == kDF64) {
-    if (K.v32lo == nullptr)
-      k_spmm_dots<P, NB, 1, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, nullptr, nullptr, x, ldx, y,
-                                                           e1, e2, pd);
-    else
-      k_spmm_dots<P, NB, 2, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, K.v32, K.v32lo, nullptr, x, ldx, y,
-                                                           e1, e2, pd);
+    if (K.v32lo == nullptr) return go(k_spmm_dots<P, NB, 1, vec, ND>, K.v32, nullptr, nullptr);
+    return go(k_spmm_dots<P, NB, 2, vec, ND>, K.v32, K.v32lo, nullptr);
   } else {
-    k_spmm_dots<P, NB, 3, vec, ND><<<grid, kT, 0, st>>>(L, K.rowptr, K.colidx, nullptr, nullptr, K.v64, x, ldx, y, e1,
-                                                         e2, pd);
+    return go(k_spmm_dots<P, NB, 3, vec, ND>, nullptr, nullptr, K.v64);
   }
-  return true;
 }
 
 template <class P, int ND>
-bool spmm_dots_p(int nb, long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
-                 const void* E2, void* partial, int grid, cudaStream_t st) {
+int spmm_dots_p(int nb, long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
+                const void* E2, void* partial, cudaStream_t st) {
   switch (nb) {
-    case 1: return spmm_dots_nb<P, 1, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
-    case 2: return spmm_dots_nb<P, 2, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
-    case 4: return spmm_dots_nb<P, 4, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
-    case 8: return spmm_dots_nb<P, 8, ND>(L, K, X, ldx, Y, E1, E2, partial, grid, st);
+    case 1: return spmm_dots_nb<P, 1, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
+    case 2: return spmm_dots_nb<P, 2, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
+    case 4: return spmm_dots_nb<P, 4, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
+    case 8: return spmm_dots_nb<P, 8, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
   }
-  return false;
+  return 0;
 }
 
 // QMR smoothing scalars, stopping test, next search-direction coefficients
@@ -512,15 +588,6 @@ __global__ void __launch_bounds__(kT) k_qmr_update2(long long L, int nb, const t
   }
 }
 
-// Persistent grid of three 256-thread CTAs per SM (the widest sQMR kernels hold
-// three per SM at their register counts, so there is no tail wave).
-int qmr_grid(long long L) {
-  long long g = (L + kT - 1) / kT;
-  if (g > 152 * 3) g = 152 * 3;
-  if (g < 1) g = 1;
-  return (int)g;
-}
-
 template <class P>
 __global__ void k_reduce_g(const typename P::G* __restrict__ partial, int nblocks, int n, double* __restrict__ out) {
   using G = typename P::G;
@@ -567,7 +634,7 @@ cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void
                    cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
-  const int g = qmr_grid(L);
+  const int g = occ_grid(k_qmr_init<P>, L);
   G* pd = reinterpret_cast<G*>(partial);
   const SS* upre = nullptr;
   if (K) {
@@ -591,29 +658,34 @@ cudaError_t step_nb(long long L, int nb, const void* x, const void* w, bool dots
                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
-  const int g = qmr_grid(L);
   G* pd = reinterpret_cast<G*>(partial);
   if (K) dinv = nullptr;
   if (!dots_ready) {
+    const int g = occ_grid(k_qmr_dots1<P, NB, VEC>, L);
     k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
     k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
   }
   k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
-  k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
-                                              (const SS*)dinv, eta, S, (SS*)r, pd);
-  k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  {
+    const int g = occ_grid(k_qmr_update1<P, NB, VEC>, L);
+    k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
+                                                (const SS*)dinv, eta, S, (SS*)r, pd);
+    k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+  }
   if (K) {
     // u = K^-1 r by SpMM; r^T u and x^T u replace dots 1 and 2
-    if (!spmm_dots_p<P, 2>(nb, L, *K, r, nb, u, r, x, pd, g, st)) {
+    int g = spmm_dots_p<P, 2>(nb, L, *K, r, nb, u, r, x, pd, st);
+    if (!g) {
       const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
       if (e != cudaSuccess) return e;
+      g = occ_grid(k_qmr_dots_u<P, NB, VEC>, L);
       k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
     }
     k_reduce_g<P><<<2 * nb, 128, 0, st>>>(pd, g, 2 * nb, dots + nb);
   }
   k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
-  k_qmr_update2<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv,
-                                              K ? (const SS*)u : nullptr, S, (SS*)q, (SS*)d, (SS*)sol);
+  k_qmr_update2<P, NB, VEC><<<occ_grid(k_qmr_update2<P, NB, VEC>, L), kT, 0, st>>>(
+      L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv, K ? (const SS*)u : nullptr, S, (SS*)q, (SS*)d, (SS*)sol);
   return cudaGetLastError();
 }
 
@@ -683,15 +755,14 @@ cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const vo
                         const void* x, const void* q, void* partial, double* dots, bool* done, cudaStream_t st) {
   *done = false;
   if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
-  const int g = qmr_grid(L);
-  bool ok = false;
+  int g = 0;
   switch (prec) {
-    case kF32: ok = spmm_dots_p<PF32, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
-    case kDF64: ok = spmm_dots_p<PDF64, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
-    case kF64: ok = spmm_dots_p<PF64, 4>(nb, L, K, X, ldx, w, x, q, partial, g, st); break;
+    case kF32: g = spmm_dots_p<PF32, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
+    case kDF64: g = spmm_dots_p<PDF64, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
+    case kF64: g = spmm_dots_p<PF64, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
     default: return cudaErrorInvalidValue;
   }
-  if (!ok) return cudaSuccess;
+  if (!g) return cudaSuccess;
   switch (prec) {
     case kF32: k_reduce_g<PF32><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PF32::G*>(partial), g, 4 * nb, dots); break;
     case kDF64:

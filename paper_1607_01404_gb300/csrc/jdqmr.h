@@ -18,7 +18,7 @@ struct QmrState {
 // b: right-hand sides (orthogonal to x), dinv: Jacobi diagonal K^-1 in the same
 // storage, or nullptr; K: a sparse symmetric K^-1 (values in the mode's
 // format) applied by SpMM instead of dinv, with u an L x nb work block, or
-// nullptr.  partial: >= 608 * 5 * nb * 8 bytes, dots: >= 5 * nb doubles.
+// nullptr.  partial: >= 2048 * 5 * nb * 8 bytes, dots: >= 5 * nb doubles.
 cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b, const void* dinv, const CsrDev* K,
                      void* u, void* kx, void* q, void* r, void* d, void* sol, QmrState* S, void* partial,
                      double* dots, cudaStream_t st);
