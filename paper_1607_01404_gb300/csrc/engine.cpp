@@ -1175,29 +1175,45 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
     double normA = o.aNorm > 0 ? o.aNorm * A.scale : 0.0;
     if (normA <= 0) {
-      RunCfg cn;
-      cn.op = OP_C;
-      cn.k = 1;
-      cn.b = 1;
-      cn.mb = 15;
-      cn.mr = 6;
-      cn.smallest = false;
-      cn.normop = 0;
-      cn.u = 0;
-      cn.name = "norm";
+      // Lanczos (Arnoldi with full reorthogonalisation) on C from a seeded
+      // random vector.  theta_max of the projected matrix is a lower bound of
+      // ||C||, so the stopping tolerance ||r|| <= tol ||A|| can only get
+      // stricter; it converges fast at the top of the spectrum.  Stop when it
+      // changed by at most 1e-5 relative in two consecutive steps, on an
+      // invariant subspace, or after 50 steps (a few 1e-4 relative at worst on
+      // strongly clustered tops, i.e. a tolerance stricter by that much).
       RunBufs& Bn = lowprec ? B1a : B1;
-      Bn.b = 1;
-      CK(launch_fill_normal(Bn.prec, n, Bn.Xb, 1, 1, o.seed ^ 0x5eedULL, c.st));
-      cn.V0 = Bn.Xb;
-      cn.ldv0 = 1;
-      cn.b0 = 1;
-      cn.conv = [](const double* th, const double* rn, int, int nc, char* ok) {
-        for (int j = 0; j < nc; ++j) ok[j] = rn[j] <= 1e-3 * std::fabs(th[j]);
-      };
-      void* Xn = lowprec ? X1a : X1;
-      RunOut rn = run_gdk_rr(c, Bn, cn, Xn, kk);
-      Bn.b = b;
-      normA = std::sqrt(std::fabs(rn.theta[0]));
+      const int pn = Bn.prec;
+      const int maxs = (int)std::min<long long>(50, Bn.ldv - 1);  // columns of the basis buffer
+      CK(launch_fill_normal(pn, n, Bn.V, Bn.ldv, 1, o.seed ^ 0x5eedULL, c.st));
+      c.launches += 1;
+      ortho(c, pn, n, {}, Bn.V, Bn.ldv, 1, nullptr, 0);
+      std::vector<double> H((size_t)(maxs + 1) * (maxs + 1), 0.0);  // column-major, ld maxs + 1
+      CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), c.st));
+      double theta = 0.0;
+      int calm = 0;
+      for (int j = 0; j < maxs; ++j) {
+        apply_op(c, pn, OP_C, off(Bn.V, j, pn), Bn.ldv, Bn.W, Bn.ldv, 1, Bn.tmp, Bn.b);
+        // h = V^T w in a Gram, then the device-side CGS2 + CholQR2 of w into
+        // the next basis column: one host round trip per step
+        gram_dev(c, pn, 0, n, {SegV{Bn.V, Bn.ldv, j + 1}}, SegV{Bn.W, Bn.ldv, 1}, c.dG);
+        if (j + 1 < maxs) ortho_dev(c, pn, n, SegV{Bn.V, Bn.ldv, j + 1}, Bn.W, Bn.ldv, 1, off(Bn.V, j + 1, pn), Bn.ldv);
+        CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c.st));
+        const bool breakdown = take_status(c) != 0;
+        for (int i = 0; i <= j; ++i) H[(size_t)j * (maxs + 1) + i] = c.hG[i];
+        const int g = j + 1;
+        // V^T C V from the upper triangle of the Arnoldi coefficients (C symmetric)
+        std::vector<double> Hs((size_t)g * g), w(g), Z((size_t)g * g);
+        for (int a = 0; a < g; ++a)
+          for (int bb = 0; bb < g; ++bb)
+            Hs[(size_t)bb * g + a] = H[(size_t)std::max(a, bb) * (maxs + 1) + std::min(a, bb)];
+        if (!hla::sym_eig(g, Hs.data(), w.data(), Z.data())) throw NumFail{"norm estimate eigenproblem failed"};
+        const double th = w[g - 1];
+        calm = (theta > 0 && std::fabs(th - theta) <= 1e-5 * std::fabs(th)) ? calm + 1 : 0;
+        theta = std::max(theta, th);
+        if (breakdown || calm >= 2) break;
+      }
+      normA = std::sqrt(std::fabs(theta));
     }
     const double normC = normA * normA;
     S.seconds_setup = c.elapsed();
@@ -1498,35 +1514,28 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int bb) { return smallest ? sig[a] < sig[bb] : sig[a] > sig[bb]; });
     double* dtmp = reinterpret_cast<double*>(dout);
-    CK(launch_to_f64_colmajor(p2, L2, k, Xres, kk, dtmp, L2, 1.0, c.st));
-    c.launches += 1;
-    std::vector<double> hX((size_t)L2 * k);
-    CK(cudaMemcpyAsync(hX.data(), dtmp, sizeof(double) * L2 * k, cudaMemcpyDeviceToHost, c.st));
-    c.sync();
-    int nconv = 0;
-    bool prefix = true;
     const long long mu = A.transposed ? n : m;  // user rows
     const long long nu = A.transposed ? m : n;  // user cols
+    const long long voff = A.transposed ? n : 0, uoff = A.transposed ? 0 : n;  // user v / u rows of x
+    if (Uout || Vout) {
+      // FP64 column-major copy, sign convention on the device (largest-|.|
+      // entry of each v positive), then one copy per returned column
+      CK(launch_to_f64_colmajor(p2, L2, k, Xres, kk, dtmp, L2, 1.0, c.st));
+      CK(launch_col_sign(L2, L2, k, voff, nu, dtmp, c.st));
+      c.launches += 2;
+      for (int jj = 0; jj < k; ++jj) {
+        const double* col = dtmp + (size_t)order[jj] * L2;
+        if (Vout)
+          CK(cudaMemcpyAsync(Vout + (size_t)jj * nu, col + voff, sizeof(double) * nu, cudaMemcpyDeviceToHost, c.st));
+        if (Uout)
+          CK(cudaMemcpyAsync(Uout + (size_t)jj * mu, col + uoff, sizeof(double) * mu, cudaMemcpyDeviceToHost, c.st));
+      }
+      c.sync();
+    }
+    int nconv = 0;
+    bool prefix = true;
     for (int jj = 0; jj < k; ++jj) {
       const int j = order[jj];
-      const double* xv = &hX[(size_t)j * L2];
-      const double* xu = xv + n;
-      long long imax = 0;
-      for (long long r = 1; r < n; ++r)
-        if (std::fabs(xv[r]) > std::fabs(xv[imax])) imax = r;
-      double sg = xv[imax] < 0 ? -1.0 : 1.0;
-      if (A.transposed) {  // user A = (device A)^T: swap the roles of u and v
-        imax = 0;
-        for (long long r = 1; r < m; ++r)
-          if (std::fabs(xu[r]) > std::fabs(xu[imax])) imax = r;
-        sg = xu[imax] < 0 ? -1.0 : 1.0;
-      }
-      const double* vsrc = A.transposed ? xu : xv;
-      const double* usrc = A.transposed ? xv : xu;
-      if (Vout)
-        for (long long r = 0; r < nu; ++r) Vout[(size_t)jj * nu + r] = sg * vsrc[r];
-      if (Uout)
-        for (long long r = 0; r < mu; ++r) Uout[(size_t)jj * mu + r] = sg * usrc[r];
       sigma[jj] = sig[j] / A.scale;
       if (rnorm) rnorm[jj] = res[j] / A.scale;
       if (prefix && res[j] < normA * tol)

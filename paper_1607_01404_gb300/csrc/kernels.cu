@@ -1227,6 +1227,51 @@ cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, cons
 
 int normal_merge_max() { return kMergeMax; }
 
+// ---------------------------------------------------------------------------
+// Output sign convention: per column j of a column-major block, the entry of
+// largest magnitude in rows [r0, r0 + len) (lowest index on ties) is made
+// positive by scaling the whole column (rows [0, rows)).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_col_sign(long long rows, long long ld, long long r0, long long len,
+                                                       double* __restrict__ X) {
+  __shared__ double sv[kThreads];
+  __shared__ long long si[kThreads];
+  double* col = X + blockIdx.x * ld;
+  double best = -1.0;
+  long long bi = -1;
+  for (long long r = threadIdx.x; r < len; r += kThreads) {
+    const double a = fabs(col[r0 + r]);
+    if (a > best) {  // strictly larger: the first index of a tie stays
+      best = a;
+      bi = r;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double a = sv[threadIdx.x + w];
+      const long long ia = si[threadIdx.x + w];
+      if (ia >= 0 && (a > sv[threadIdx.x] || (a == sv[threadIdx.x] && (si[threadIdx.x] < 0 || ia < si[threadIdx.x])))) {
+        sv[threadIdx.x] = a;
+        si[threadIdx.x] = ia;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = si[0] >= 0 && col[r0 + si[0]] < 0.0;
+  if (!flip) return;
+  for (long long r = threadIdx.x; r < rows; r += kThreads) col[r] = -col[r];
+}
+
+cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
+                            cudaStream_t st) {
+  if (k <= 0 || rows <= 0) return cudaSuccess;
+  k_col_sign<<<k, kThreads, 0, st>>>(rows, ld, r0, len, X);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   k_row_sumsq<<<persistent_grid(rows, kThreads), kThreads, 0, st>>>(rows, rowptr, vals, out);

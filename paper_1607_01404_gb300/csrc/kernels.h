@@ -116,6 +116,11 @@ cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, cons
                                const int* ci, const double* va, double scale, const int* cptr, int* cidx,
                                double* cval, cudaStream_t st);
 int normal_merge_max();
+// Sign convention of the returned vectors: column j of the column-major block
+// X (rows x k, ld) is negated when its largest-magnitude entry in rows
+// [r0, r0 + len) (lowest index on ties) is negative.
+cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
+                            cudaStream_t st);
 // out[i] = sum_k vals[k]^2 over row i (FP64).
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st);
 // Jacobi scale in storage format: d[r] = 1 / s[r] (1 where s[r] == 0), optionally sqrt'ed first.
