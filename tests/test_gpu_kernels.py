@@ -1,8 +1,8 @@
 """Per-kernel parity of the CUDA path against the oracle / FP64 definitions.
 
 Tolerances: FP64-class modes (DF64, F64) must agree normwise to 1e-13 relative
-to ||(|A| |X|)|| (the spec SpMM bar, read normwise because element-wise
-relative error is unbounded under cancellation); the F32 mode to a few units
+to ||(|A| |X|)|| (the FP64 SpMM accuracy bar of 1e-13, read normwise because
+element-wise relative error is unbounded under cancellation); the F32 mode to a few units
 of 2^-24 times the same normaliser.
 """
 import numpy as np
