@@ -45,6 +45,9 @@ extern "C" {
 #define SVDS_FP64 3  /* FP64-class stage 1 (double-float arithmetic on the GPU) */
 #define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
 #define SVDS_NATIVE_FP64 4 /* native FP64 arithmetic everywhere (check mode; slow on GB300) */
+#define SVDS_BF16 5  /* as SVDS_FP32, with the values of A (and of the explicit A^T A) stored in
+                        bfloat16 wherever the operator is applied in FP32 (FP32 vectors and
+                        accumulation); the FP64-class phases use the exact values */
 
 #define SVDS_NORMAL_AUTO 0     /* C = A^T A applied as an explicit sparse matrix when that moves
                                   fewer bytes than A then A^T (estimated from the patterns) */
@@ -78,7 +81,7 @@ typedef struct {
   int maxBlockSize;     /* 0 = 1 */
   int method_stage1;    /* SVDS_GDPK (default) or SVDS_JDQMR */
   int method_stage2;    /* SVDS_GDPK (default) or SVDS_JDQMR */
-  int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32 or SVDS_NATIVE_FP64 */
+  int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32, SVDS_BF16 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
                            to the paper's stage-1 criterion before stage 2 (default 1) */
   int precond;          /* SVDS_PRECOND_JACOBI (default), SVDS_PRECOND_NONE or SVDS_PRECOND_LEARNED */

@@ -34,6 +34,15 @@ int phsvds_spmm(int prec, int64_t rows, int64_t cols, int64_t nnz, const int32_t
                 const float *v32, const float *v32lo, const double *v64, const void *X, int64_t ldx, void *Y,
                 int64_t ldy, int b, void *stream);
 
+/* Y = A X in the FP32 mode with bfloat16 values of A (v16: the upper 16 bits
+ * of FP32 numbers; X, Y FP32 row-major as phsvds_spmm).  Not in the paper: the
+ * reduced-precision operator of the mixed-precision stage 1. */
+int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                     const uint16_t *v16, const float *X, int64_t ldx, float *Y, int64_t ldy, int b, void *stream);
+/* v16 = bfloat16(v32), round to nearest even, for nnz finite device values;
+ * flags[0] (device int) |= 1 when some value is not exactly representable. */
+int phsvds_to_bf16(int64_t nnz, const float *v32, uint16_t *v16, int *flags, void *stream);
+
 /* G (p x q row-major doubles, device) = P^T Q over rows [r0, r1) (the Table 3
  * inner products: Rayleigh-Ritz projection V^T W, Gram matrices of CGS and
  * CholQR).  Accumulation is FP64-class in every mode and the reduction order

@@ -60,6 +60,16 @@ def spmm(A, X):
     return _as_csr(A) @ X
 
 
+def round_bf16(x):
+    """bfloat16 rounding of FP32 values: keep the upper 16 bits of the IEEE
+    single encoding after rounding to nearest, ties to even (the storage format
+    of the reduced-precision operator; not in the paper).  Returns float32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32)
+
+
 def spmm_t(A, Y):
     """X = A^T Y (the user matvec of Sec. 3.4 with transpose != 0)."""
     return _as_csr(A).T @ Y

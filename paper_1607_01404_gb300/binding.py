@@ -31,6 +31,7 @@ SVDS_JDQMR = 1
 SVDS_FP32 = 1
 SVDS_FP64 = 3
 SVDS_NATIVE_FP64 = 4
+SVDS_BF16 = 5
 SVDS_NORMAL_AUTO = 0
 SVDS_NORMAL_TWOPASS = 1
 SVDS_NORMAL_EXPLICIT = 2
@@ -86,6 +87,9 @@ _SIGS = {
     "phsvds_spmm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,
                               C.c_void_p]),
+    "phsvds_spmm_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
+    "phsvds_to_bf16": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_gram": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                               C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "phsvds_gram_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
@@ -276,6 +280,18 @@ def spmm(prec, rows, cols, rowptr, colidx, v32, v32lo, v64, X, ldx, Y, ldy, b, s
     nnz = int(colidx.numel())
     _check(lib().phsvds_spmm(prec, rows, cols, nnz, ptr(rowptr), ptr(colidx), ptr(v32), ptr(v32lo), ptr(v64),
                              ptr(X), ldx, ptr(Y), ldy, b, _stream(stream)), "phsvds_spmm")
+
+
+def spmm_bf16(rows, cols, rowptr, colidx, v16, X, ldx, Y, ldy, b, stream=None):
+    """Y = A X (FP32 vectors) with bfloat16 values of A (torch CUDA tensors)."""
+    _check(lib().phsvds_spmm_bf16(rows, cols, int(colidx.numel()), rowptr.data_ptr(), colidx.data_ptr(),
+                                  v16.data_ptr(), X.data_ptr(), ldx, Y.data_ptr(), ldy, b, _stream(stream)),
+           "phsvds_spmm_bf16")
+
+
+def to_bf16(v32, v16, flags, stream=None):
+    _check(lib().phsvds_to_bf16(int(v32.numel()), v32.data_ptr(), v16.data_ptr(), flags.data_ptr(), _stream(stream)),
+           "phsvds_to_bf16")
 
 
 def gram(prec, r0, r1, P, ldp, p, Q, ldq, q, G, scratch, stream=None):

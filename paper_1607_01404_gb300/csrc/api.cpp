@@ -175,7 +175,8 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
     o = *opts;
   else
     svds_opts_default(&o);
-  if (o.stage1_precision != SVDS_FP64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_NATIVE_FP64)
+  if (o.stage1_precision != SVDS_FP64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_BF16 &&
+      o.stage1_precision != SVDS_NATIVE_FP64)
     return SVDS_ERR_ARG;
   if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
   if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR) ||
@@ -292,6 +293,28 @@ int phsvds_spmm(int prec, int64_t rows, int64_t cols, int64_t nnz, const int32_t
   A.v32lo = v32lo;
   A.v64 = v64;
   CKR(launch_spmm(prec, A, X, ldx, Y, ldy, b, reinterpret_cast<cudaStream_t>(stream)));
+  return 0;
+}
+
+int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                     const uint16_t* v16, const float* X, int64_t ldx, float* Y, int64_t ldy, int b, void* stream) {
+  if (rows < 0 || cols < 0 || nnz < 0 || b < 0 || ldx < b || ldy < b) return SVDS_ERR_ARG;
+  if (rows > 0 && (!rowptr || !Y)) return SVDS_ERR_ARG;
+  if (nnz > 0 && (!colidx || !X || !v16)) return SVDS_ERR_ARG;
+  CsrDev A;
+  A.rows = rows;
+  A.cols = cols;
+  A.nnz = nnz;
+  A.rowptr = rowptr;
+  A.colidx = colidx;
+  A.v16 = v16;
+  CKR(launch_spmm(kF32, A, X, ldx, Y, ldy, b, reinterpret_cast<cudaStream_t>(stream)));
+  return 0;
+}
+
+int phsvds_to_bf16(int64_t nnz, const float* v32, uint16_t* v16, int* flags, void* stream) {
+  if (nnz < 0 || (nnz > 0 && (!v32 || !v16 || !flags))) return SVDS_ERR_ARG;
+  CKR(launch_to_bf16(nnz, v32, v16, flags, reinterpret_cast<cudaStream_t>(stream)));
   return 0;
 }
 

@@ -86,6 +86,13 @@ struct Ctx {
   int* hstatus = nullptr;  // pinned copy
   bool device_ortho = true;
   long long inner = 0;     // JDQMR inner steps
+  bool bf16 = false;       // F32-mode operator applications use the bfloat16 values
+  // CSR of A (which 0), A^T (1) or the explicit C (2) in the value format of prec
+  CsrDev op(int prec, int which) const {
+    CsrDev m = which == 2 ? A->csrC() : A->csr(which == 1);
+    if (bf16 && prec == kF32) m.v16 = which == 2 ? A->v16C : (which == 1 ? A->v16T : A->v16);
+    return m;
+  }
 
   double t_sync = 0, t_eig = 0;
   long long nsync = 0;
@@ -187,14 +194,14 @@ void apply_op(Ctx& c, int prec, int op, const void* X, long long ldx, void* Y, l
     const void* Xc = off(X, c0, prec);
     void* Yc = off(Y, c0, prec);
     if (op == OP_C && A.nnzC > 0) {
-      CK(launch_spmm(prec, A.csrC(), Xc, ldx, Yc, ldy, w, c.st));
+      CK(launch_spmm(prec, c.op(prec, 2), Xc, ldx, Yc, ldy, w, c.st));
       c.launches -= spmm_launches(w);
     } else if (op == OP_C) {
-      CK(launch_spmm(prec, A.csr(false), Xc, ldx, tmp, w, w, c.st));
-      CK(launch_spmm(prec, A.csr(true), tmp, w, Yc, ldy, w, c.st));
+      CK(launch_spmm(prec, c.op(prec, 0), Xc, ldx, tmp, w, w, c.st));
+      CK(launch_spmm(prec, c.op(prec, 1), tmp, w, Yc, ldy, w, c.st));
     } else {
-      CK(launch_spmm(prec, A.csr(true), off(Xc, A.n * ldx, prec), ldx, Yc, ldy, w, c.st));
-      CK(launch_spmm(prec, A.csr(false), Xc, ldx, off(Yc, A.n * ldy, prec), ldy, w, c.st));
+      CK(launch_spmm(prec, c.op(prec, 1), off(Xc, A.n * ldx, prec), ldx, Yc, ldy, w, c.st));
+      CK(launch_spmm(prec, c.op(prec, 0), Xc, ldx, off(Yc, A.n * ldy, prec), ldy, w, c.st));
     }
     c.launches += 2 * spmm_launches(w);
     c.mv += 2LL * w;
@@ -278,6 +285,44 @@ void ensure_normal(svds_handle* h, cudaStream_t st, int mode, int b, long long& 
   A.v64C = v64;
   A.exactC = herr == 0;
   A.nnzC = hnnz;
+}
+
+// bfloat16 copies of the FP32 values of A, A^T and the explicit C (once per handle).
+void ensure_bf16(svds_handle* h, cudaStream_t st, long long& launches) {
+  DevMatrix& A = h->A;
+  if (A.v16 && (A.nnzC <= 0 || A.v16C)) return;
+  auto take = [&](long long count) -> uint16_t* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(uint16_t) * (count > 0 ? count : 1)) != cudaSuccess) {
+      cudaGetLastError();
+      throw CudaFail{cudaErrorMemoryAllocation, "bfloat16 values"};
+    }
+    h->allocs.push_back(p);
+    return static_cast<uint16_t*>(p);
+  };
+  int* flags = nullptr;
+  if (cudaMalloc(&flags, sizeof(int) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    throw CudaFail{cudaErrorMemoryAllocation, "bfloat16 flags"};
+  }
+  CK(cudaMemsetAsync(flags, 0, sizeof(int) * 4, st));
+  if (!A.v16) {
+    A.v16 = take(A.nnz);
+    A.v16T = take(A.nnz);
+    CK(launch_to_bf16(A.nnz, A.v32, A.v16, flags, st));
+    CK(launch_to_bf16(A.nnz, A.v32T, A.v16T, flags, st));
+    launches += 2;
+  }
+  if (A.nnzC > 0 && !A.v16C) {
+    A.v16C = take(A.nnzC);
+    CK(launch_to_bf16(A.nnzC, A.v32C, A.v16C, flags, st));
+    launches += 1;
+  }
+  int hf = 0;
+  CK(cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(flags);
+  A.exact16 = A.exact16 && hf == 0;
 }
 
 // small helpers on column-major host matrices
@@ -604,14 +649,14 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
     bool fused = false;
     if (cfg.op == OP_C) {
       if (Am.nnzC > 0) {
-        CK(qmr_op_dots(pin, L, nbk, Am.csrC(), q, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
+        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 2), q, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
       } else {
-        CK(launch_spmm(pin, Am.csr(false), q, nbk, B.jtmp, nbk, nbk, c.st));
-        CK(qmr_op_dots(pin, L, nbk, Am.csr(true), B.jtmp, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
+        CK(launch_spmm(pin, c.op(pin, 0), q, nbk, B.jtmp, nbk, nbk, c.st));
+        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 1), B.jtmp, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
         if (fused) {
           c.launches += spmm_launches(nbk);
         } else {
-          CK(launch_spmm(pin, Am.csr(true), B.jtmp, nbk, w, nbk, nbk, c.st));
+          CK(launch_spmm(pin, c.op(pin, 1), B.jtmp, nbk, w, nbk, nbk, c.st));
           c.launches += 2 * spmm_launches(nbk);
         }
         c.mv += 2LL * nbk;
@@ -1051,7 +1096,8 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
   if (o.maxBasisSize > 0) mb = o.maxBasisSize;
   if (o.minRestartSize > 0) mr = o.minRestartSize;
   if (mr < k + b - 1 || mb < mr + b || mb > 240) return SVDS_ERR_ARG;
-  const bool lowprec = o.stage1_precision == SVDS_FP32;
+  const bool bf16 = o.stage1_precision == SVDS_BF16;
+  const bool lowprec = o.stage1_precision == SVDS_FP32 || bf16;
   const int p2 = o.stage1_precision == SVDS_NATIVE_FP64 ? kF64 : kDF64;  // FP64-class mode
   const int p1a = lowprec ? kF32 : p2;
   const bool polish = !lowprec || o.stage1_polish;
@@ -1171,6 +1217,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
 
     // ---- C = A^T A as one sparse matrix when that moves fewer bytes ----
     ensure_normal(h, c.st, o.normalOperator, b, c.launches);
+    if (bf16) {
+      ensure_bf16(h, c.st, c.launches);
+      c.bf16 = true;
+    }
 
     // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
     double normA = o.aNorm > 0 ? o.aNorm * A.scale : 0.0;
@@ -1295,7 +1345,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.jdK = Kinner;
     if (lowprec) {
       init_block(kF32, X1a, kk, b0);
-      c1.u = unit_roundoff(kF32);
+      // bfloat16 values that round A (or C) perturb the operator by ~2^-8 relative:
+      // the FP32 phase then stops at that floor
+      const bool exact_vals = A.exact16 && (A.nnzC > 0 ? A.exactC : A.exact32);
+      c1.u = (bf16 && !exact_vals) ? std::ldexp(1.0, -8) : unit_roundoff(kF32);
       c1.conv = stage1_conv(c1.u);
       c1.dscale = jac ? d1a : nullptr;
       c1.K = learned ? &K32 : nullptr;

@@ -37,6 +37,11 @@ struct DevMatrix {
   float* v32loC = nullptr;
   double* v64C = nullptr;
   bool exactC = true;
+  // bfloat16 copies of the values (built on demand for SVDS_BF16)
+  uint16_t* v16 = nullptr;
+  uint16_t* v16T = nullptr;
+  uint16_t* v16C = nullptr;
+  bool exact16 = true;  // every value is a bfloat16 number
   CsrDev csrC() const {
     CsrDev c;
     c.rows = n;

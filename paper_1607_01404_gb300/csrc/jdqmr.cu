@@ -487,6 +487,7 @@ int spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, voi
     return g;
   };
   if constexpr (P::id == kF32) {
+    if (K.v16) return go(k_spmm_dots<P, NB, 4, vec, ND>, reinterpret_cast<const float*>(K.v16), nullptr, nullptr);
     return go(k_spmm_dots<P, NB, 0, vec, ND>, K.v32, nullptr, nullptr);
   } else if constexpr (P::id == kDF64) {
     if (K.v32lo == nullptr) return go(k_spmm_dots<P, NB, 1, vec, ND>, K.v32, nullptr, nullptr);

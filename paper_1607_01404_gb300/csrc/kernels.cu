@@ -114,8 +114,13 @@ cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, lon
     const S* x = reinterpret_cast<const S*>(X);
     S* y = reinterpret_cast<S*>(Y);
     if constexpr (P::id == kF32) {
-      k_spmm2<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
-                                                        ldy);
+      if (A.v16)
+        k_spmm2<P, NB, 4, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx,
+                                                          reinterpret_cast<const float*>(A.v16), nullptr, nullptr, x,
+                                                          ldx, y, ldy);
+      else
+        k_spmm2<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx,
+                                                          y, ldy);
     } else if constexpr (P::id == kDF64) {
       if (A.v32lo == nullptr)
         k_spmm2<P, NB, 1, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx,
@@ -134,8 +139,13 @@ cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, lon
   const S* x = reinterpret_cast<const S*>(X);
   S* y = reinterpret_cast<S*>(Y);
   if constexpr (P::id == kF32) {
-    k_spmm<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
-                                                     ldy);
+    if (A.v16)
+      k_spmm<P, NB, 4, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx,
+                                                       reinterpret_cast<const float*>(A.v16), nullptr, nullptr, x, ldx,
+                                                       y, ldy);
+    else
+      k_spmm<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
+                                                       ldy);
   } else if constexpr (P::id == kDF64) {
     if (A.v32lo == nullptr)
       k_spmm<P, NB, 1, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
@@ -1226,6 +1236,26 @@ cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, cons
 }
 
 int normal_merge_max() { return kMergeMax; }
+
+// FP32 -> bfloat16, round to nearest even (finite inputs); flags[0] |= 1 when
+// some value is not exactly representable.
+__global__ void k_to_bf16(long long n, const float* __restrict__ x, unsigned short* __restrict__ y,
+                          int* __restrict__ flags) {
+  int inexact = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned u = __float_as_uint(x[i]);
+    const unsigned r = (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+    y[i] = (unsigned short)r;
+    inexact |= (r << 16) != u;
+  }
+  if (inexact) atomicOr(flags, 1);
+}
+
+cudaError_t launch_to_bf16(long long n, const float* x, uint16_t* y, int* flags, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_to_bf16<<<persistent_grid(n, kThreads), kThreads, 0, st>>>(n, x, reinterpret_cast<unsigned short*>(y), flags);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Output sign convention: per column j of a column-major block, the entry of

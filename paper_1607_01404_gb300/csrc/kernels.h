@@ -31,6 +31,7 @@ struct CsrDev {
   const float* v32 = nullptr;     // F32 values (also the hi part of DF64)
   const float* v32lo = nullptr;   // DF64 lo part, nullptr when every value is a float
   const double* v64 = nullptr;    // F64 values
+  const uint16_t* v16 = nullptr;  // bfloat16 values: used instead of v32 by the F32 mode when set
 };
 
 // Y (rows x b, ldy) = A X (cols x b, ldx).
@@ -116,6 +117,9 @@ cudaError_t launch_normal_fill(long long n, const int* rpT, const int* ciT, cons
                                const int* ci, const double* va, double scale, const int* cptr, int* cidx,
                                double* cval, cudaStream_t st);
 int normal_merge_max();
+// FP32 -> bfloat16 (round to nearest even) of n finite values; flags[0] |= 1
+// when some value is not exactly representable.
+cudaError_t launch_to_bf16(long long n, const float* x, uint16_t* y, int* flags, cudaStream_t st);
 // Sign convention of the returned vectors: column j of the column-major block
 // X (rows x k, ld) is negated when its largest-magnitude entry in rows
 // [r0, r0 + len) (lowest index on ties) is negative.

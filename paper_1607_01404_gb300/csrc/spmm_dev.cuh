@@ -8,7 +8,8 @@
 
 namespace phsvds {
 
-// VMODE: 0 float values (F32), 1 float values into double-float (DF64, exact
+// VMODE: 0 float values (F32), 4 bfloat16 values (F32 vectors), 1 float values
+// into double-float (DF64, exact
 // values), 2 double-float values (DF64), 3 double values (F64).  VEC: the NB
 // entries of a row are 16-byte multiples and every row starts on a 16-byte
 // boundary, so gathers and stores use 16-byte vector accesses.
@@ -41,6 +42,13 @@ __device__ __forceinline__ void spmm_accum(const int k, const float* __restrict_
                                            typename P::A (&acc)[NB]) {
   if constexpr (VMODE == 0) {
     const float a = __ldg(v32 + k);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = fmaf(xv[c], a, acc[c]);
+  } else if constexpr (VMODE == 4) {
+    // bfloat16 values (the upper 16 bits of an FP32 number; the pointer of the
+    // float values carries the 16-bit array in this mode)
+    const unsigned short bits = __ldg(reinterpret_cast<const unsigned short*>(v32) + k);
+    const float a = __uint_as_float((unsigned)bits << 16);
 #pragma unroll
     for (int c = 0; c < NB; ++c) acc[c] = fmaf(xv[c], a, acc[c]);
   } else if constexpr (VMODE == 1) {

@@ -199,3 +199,33 @@ def test_ritz_residual(prec, aligned, g, nb):
     assert np.all(np.abs(R - Rr) <= 4 * TOL[prec] * (np.abs(Ws) @ np.abs(Y) + sx * np.abs(th)))
     nr = np.sum(R * R, axis=0)
     np.testing.assert_allclose(n2.cpu().numpy(), nr, rtol=1e-12)
+
+
+@pytest.mark.parametrize("b", [1, 2, 4, 8, 5])
+def test_spmm_bf16_values_match_oracle(b):
+    """bfloat16 values: bit-exact rounding against the oracle's definition, and
+    Y = bf16(A) X in FP32 against the FP64 product with the rounded values."""
+    from oracle.phsvds_fp64 import round_bf16
+
+    for A in _matrices():
+        d = csr_device(A)
+        v16 = torch.zeros(max(A.nnz, 1), dtype=torch.int16, device=d["v32"].device)
+        flags = torch.zeros(4, dtype=torch.int32, device=d["v32"].device)
+        B.to_bf16(d["v32"][: A.nnz], v16, flags)
+        torch.cuda.synchronize()
+        v32 = A.vals.astype(np.float32)
+        r16 = round_bf16(v32)
+        got = (v16[: A.nnz].cpu().numpy().astype(np.uint16).astype(np.uint32) << 16).view(np.float32)
+        np.testing.assert_array_equal(got, r16)
+        assert int(flags[0].item()) == int(np.any(r16 != v32))
+        X = wl.dense_block(A.n, b, seed=b).astype(np.float32).astype(np.float64)
+        Xd = torch.from_numpy(X.astype(np.float32).ravel()).to(d["v32"].device)
+        Yd = torch.zeros(A.m * b, dtype=torch.float32, device=d["v32"].device)
+        B.spmm_bf16(A.m, A.n, d["rp"], d["ci"], v16, Xd, b, Yd, b, b)
+        Y = Yd.cpu().numpy().astype(np.float64).reshape(A.m, b)
+        Ar = wl.CSR(A.m, A.n, A.rowptr, A.colidx, r16.astype(np.float64), A.name)
+        ref = oracle.spmm(Ar, X)
+        Aabs = Ar.to_scipy().copy()
+        Aabs.data = np.abs(Aabs.data)
+        norm = np.abs(Aabs @ np.abs(X)).max()
+        assert np.abs(Y - ref).max() / norm <= TOL[B.PREC_F32], A.name

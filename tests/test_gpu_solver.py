@@ -268,3 +268,30 @@ def test_auto_normal_operator_choice():
     d = wl.random_illconditioned(3000, 1500, per_col=16, seed=3)
     r = B.svds(d, 3, "largest", tol=1e-8, maxBlockSize=2)
     assert r["stats"]["normal_nnz"] == 0
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_bf16_stage1_values_give_the_same_triplets(target):
+    """Stage-1 operator with bfloat16 values (FP32 vectors), FP32 values and the
+    FP64-class path: every form returns the same triplets to the tolerance;
+    the per-triplet relative difference against the FP64-class form is checked."""
+    A = wl.random_illconditioned(1500, 500, 16, seed=21)
+    k = 4
+    out = {}
+    for name, prec in (("bf16", B.SVDS_BF16), ("fp32", B.SVDS_FP32), ("fp64", B.SVDS_FP64)):
+        r = B.svds(A, k, target, 1e-10, maxBlockSize=2, stage1_precision=prec, method_stage1=B.SVDS_JDQMR,
+                   initV=wl.start_block(A.n, 2, 3), maxMatvecs=600000)
+        assert r["nconv"] == k, name
+        _compare_to_dense(A, r, target, k, 1e-10)
+        out[name] = r
+    for name in ("bf16", "fp32"):
+        rel = np.abs(out[name]["sigma"] - out["fp64"]["sigma"]) / out["fp64"]["sigma"]
+        assert rel.max() <= 1e-9, (name, rel)
+
+
+def test_bf16_exact_values_on_a_grid():
+    """Grid operators have values +-1: bfloat16 is exact, the FP32 floor applies."""
+    A = wl.grid_difference(24, 2)
+    r = B.svds(A, 5, "smallest", 1e-10, maxBlockSize=2, stage1_precision=B.SVDS_BF16)
+    s = np.sort(np.linalg.svd(A.to_scipy().toarray(), compute_uv=False))[:5]
+    np.testing.assert_allclose(r["sigma"], s, rtol=1e-10)

@@ -235,3 +235,26 @@ def test_value_error_bound_eq_2_1():
     kappa = s[0] / s[::-1][:3]
     rel = np.abs(r["sigma1"] - s[::-1][:3]) / s[::-1][:3]
     assert np.all(rel <= 10 * O.FLOOR_C * kappa ** 2 * O.EPS + 1e-13)
+
+
+def test_round_bf16_definition():
+    """Round to nearest even on the 8-bit significand of bfloat16."""
+    from oracle.phsvds_fp64 import round_bf16
+
+    e = 2.0 ** -7  # spacing of bfloat16 numbers in [1, 2)
+    x = np.array([1.0, -2.5, 0.15625, 1 + e / 2, 1 + 3 * e / 2, 1 + e / 2 + 2.0 ** -20, -(1 + e / 2 + 2.0 ** -20),
+                  3.0e-39, 0.0], dtype=np.float64)
+    want = np.array([1.0, -2.5, 0.15625, 1.0, 1 + 2 * e, 1 + e, -(1 + e), None, 0.0], dtype=object)
+    got = round_bf16(x.astype(np.float32)).astype(np.float64)
+    for g, w in zip(got[:7], want[:7]):
+        assert g == w
+    assert got[8] == 0.0
+    # every result is a bfloat16 number, within half a spacing (at most 2^-8 relative)
+    rng = np.random.default_rng(0)
+    v = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-3, 3, 20000)).astype(np.float32)
+    r = round_bf16(v)
+    assert np.all((r.view(np.uint32) & 0xFFFF) == 0)
+    assert np.all(np.abs(r.astype(np.float64) - v) <= 2.0 ** -8 * np.abs(v.astype(np.float64)))
+    # monotone
+    s = np.sort(v)
+    assert np.all(np.diff(round_bf16(s).astype(np.float64)) >= 0)
