@@ -123,6 +123,7 @@ typedef struct {
   int64_t inner_steps;        /* JDQMR inner sQMR steps (each applies the operator to the block) */
   double seconds_precond;     /* learned preconditioner: graph of A^T A and network inference */
   int64_t normal_nnz;         /* nonzeros of the explicit C = A^T A, 0 when A then A^T is used */
+  double seconds_output;      /* returning the vectors: FP64 conversion, sign convention, copies to U, V */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

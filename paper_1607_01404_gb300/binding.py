@@ -67,7 +67,8 @@ class svds_stats(C.Structure):
                 ("seconds_stage1", C.c_double), ("seconds_stage2", C.c_double),
                 ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
                 ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
-                ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64)]
+                ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64),
+                ("seconds_output", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

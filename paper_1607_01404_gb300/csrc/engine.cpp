@@ -1171,6 +1171,8 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     if (lowprec) reqs.push_back({&d1a, (size_t)n * 4});
     reqs.push_back({&d1, (size_t)n * e2});
     reqs.push_back({&dout, (size_t)L2 * kk * 8});
+    void* dout2 = nullptr;  // the returned U and V blocks, contiguous, in output order
+    reqs.push_back({&dout2, (size_t)L2 * kk * 8 + sizeof(int) * kk + 256});
     c.maxblk = gram_default_blocks();
     c.gcap = 256 * 256;
     reqs.push_back({&c.partial, gram_partial_bytes(std::max(c.maxblk, 152 * 16), 256, 8)});
@@ -1562,6 +1564,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       S.seconds_stage2 = c.elapsed() - t2;
     }
     // ---- outputs ----
+    const double t_out = c.elapsed();
     std::vector<int> order(k);
     for (int j = 0; j < k; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(),
@@ -1576,14 +1579,25 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       CK(launch_to_f64_colmajor(p2, L2, k, Xres, kk, dtmp, L2, 1.0, c.st));
       CK(launch_col_sign(L2, L2, k, voff, nu, dtmp, c.st));
       c.launches += 2;
-      for (int jj = 0; jj < k; ++jj) {
-        const double* col = dtmp + (size_t)order[jj] * L2;
-        if (Vout)
-          CK(cudaMemcpyAsync(Vout + (size_t)jj * nu, col + voff, sizeof(double) * nu, cudaMemcpyDeviceToHost, c.st));
-        if (Uout)
-          CK(cudaMemcpyAsync(Uout + (size_t)jj * mu, col + uoff, sizeof(double) * mu, cudaMemcpyDeviceToHost, c.st));
+      if (c.print >= 2) {
+        c.sync();
+        std::fprintf(stderr, "[output] conversion and signs done at %.4f s\n", c.elapsed() - t_out);
       }
-      c.sync();
+      // gather the columns in output order so that U and V each leave in one
+      // copy (many small copies into fresh pageable memory are far slower)
+      int* dperm = reinterpret_cast<int*>(reinterpret_cast<char*>(dout2) + (size_t)L2 * k * 8);
+      {
+        std::vector<int> perm(order.begin(), order.end());
+        CK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * k, cudaMemcpyHostToDevice, c.st));
+        double* Vblk = reinterpret_cast<double*>(dout2);
+        double* Ublk = Vblk + (size_t)nu * k;
+        CK(launch_gather_cols(nu, k, dtmp, L2, voff, dperm, Vblk, c.st));
+        CK(launch_gather_cols(mu, k, dtmp, L2, uoff, dperm, Ublk, c.st));
+        c.launches += 2;
+        if (Vout) CK(cudaMemcpyAsync(Vout, Vblk, sizeof(double) * nu * k, cudaMemcpyDeviceToHost, c.st));
+        if (Uout) CK(cudaMemcpyAsync(Uout, Ublk, sizeof(double) * mu * k, cudaMemcpyDeviceToHost, c.st));
+        c.sync();  // perm stays alive until here
+      }
     }
     int nconv = 0;
     bool prefix = true;
@@ -1607,6 +1621,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.host_syncs = c.nsync;
     S.inner_steps = c.inner;
     S.normal_nnz = A.nnzC > 0 ? A.nnzC : 0;
+    S.seconds_output = c.elapsed() - t_out;
     if (stats) *stats = S;
     h->launches += c.launches;
     return SVDS_OK;

@@ -1295,6 +1295,25 @@ __global__ void __launch_bounds__(kThreads) k_col_sign(long long rows, long long
   for (long long r = threadIdx.x; r < rows; r += kThreads) col[r] = -col[r];
 }
 
+// Out[:, jj] = X[r0 : r0 + len, perm[jj]] for jj < k (column-major, ld len):
+// the returned block in the caller's column order, contiguous.
+__global__ void k_gather_cols(long long len, int k, const double* __restrict__ X, long long ldx, long long r0,
+                              const int* __restrict__ perm, double* __restrict__ Out) {
+  const long long total = len * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % len;
+    const int jj = (int)(e / len);
+    Out[e] = X[(long long)perm[jj] * ldx + r0 + r];
+  }
+}
+
+cudaError_t launch_gather_cols(long long len, int k, const double* X, long long ldx, long long r0, const int* perm,
+                               double* Out, cudaStream_t st) {
+  if (len <= 0 || k <= 0) return cudaSuccess;
+  k_gather_cols<<<persistent_grid(len * k, kThreads), kThreads, 0, st>>>(len, k, X, ldx, r0, perm, Out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
                             cudaStream_t st) {
   if (k <= 0 || rows <= 0) return cudaSuccess;

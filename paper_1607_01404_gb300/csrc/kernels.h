@@ -125,6 +125,10 @@ cudaError_t launch_to_bf16(long long n, const float* x, uint16_t* y, int* flags,
 // [r0, r0 + len) (lowest index on ties) is negative.
 cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
                             cudaStream_t st);
+// Out (len x k, column-major, contiguous) = rows [r0, r0 + len) of the columns
+// perm[0..k) of the column-major X (ld ldx); perm is a device int array.
+cudaError_t launch_gather_cols(long long len, int k, const double* X, long long ldx, long long r0, const int* perm,
+                               double* Out, cudaStream_t st);
 // out[i] = sum_k vals[k]^2 over row i (FP64).
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st);
 // Jacobi scale in storage format: d[r] = 1 / s[r] (1 where s[r] == 0), optionally sqrt'ed first.
