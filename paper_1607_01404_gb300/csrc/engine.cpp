@@ -488,6 +488,7 @@ struct RunBufs {
   void* jd[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* jtmp = nullptr;  // m x b (inner-mode C op)
   void* ju = nullptr;    // L x b (inner-mode K^-1 r for a sparse preconditioner)
+  unsigned* jtick = nullptr;  // tickets of the fused reduction tails (zeroed per correction)
   QmrState* jS = nullptr;
   double* jdots = nullptr;
 };
@@ -641,19 +642,22 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
        *w = B.jd[7];
   CK(convert_cols(prec, B.Xb, B.b, pin, x, nbk, L, nbk, d1, c.st));
   CK(convert_cols(prec, B.Rb, B.b, pin, bv, nbk, L, nbk, d2, c.st));
+  CK(cudaMemsetAsync(B.jtick, 0, 64, c.st));
   CK(qmr_init(pin, L, nbk, x, bv, cfg.jdinv, cfg.jdK, B.ju, kx, q, r, d, sol, B.jS, c.partial, B.jdots, c.st));
   c.launches += 2 + qmr_init_launches(nbk, cfg.jdK != nullptr);
   const DevMatrix& Am = *c.A;
   for (int k = 0; k < cfg.jd_maxk; ++k) {
     // w = op(q), fused with the step's first dot products when op is C
-    bool fused = false;
+    int ready = 0;
     if (cfg.op == OP_C) {
       if (Am.nnzC > 0) {
-        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 2), q, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
+        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 2), q, nbk, w, x, q, c.partial, B.jdots, B.jtick, de, B.jS, &ready,
+                       c.st));
       } else {
         CK(launch_spmm(pin, c.op(pin, 0), q, nbk, B.jtmp, nbk, nbk, c.st));
-        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 1), B.jtmp, nbk, w, x, q, c.partial, B.jdots, &fused, c.st));
-        if (fused) {
+        CK(qmr_op_dots(pin, L, nbk, c.op(pin, 1), B.jtmp, nbk, w, x, q, c.partial, B.jdots, B.jtick, de, B.jS,
+                       &ready, c.st));
+        if (ready) {
           c.launches += spmm_launches(nbk);
         } else {
           CK(launch_spmm(pin, c.op(pin, 1), B.jtmp, nbk, w, nbk, nbk, c.st));
@@ -661,15 +665,15 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
         }
         c.mv += 2LL * nbk;
       }
-      if (fused) {
-        c.launches += 2;
+      if (ready) {
+        c.launches += ready == 2 ? 1 : 2;
         if (Am.nnzC > 0) c.mv += 2LL * nbk;
       }
     }
-    if (!fused && !(cfg.op == OP_C && Am.nnzC <= 0)) apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
-    CK(qmr_step(pin, L, nbk, x, w, fused, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d, sol,
-                B.jS, c.partial, B.jdots, c.st));
-    c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr, fused);
+    if (!ready && !(cfg.op == OP_C && Am.nnzC <= 0)) apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
+    CK(qmr_step(pin, L, nbk, x, w, ready, B.jtick, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d,
+                sol, B.jS, c.partial, B.jdots, c.st));
+    c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr, ready, (nbk & (nbk - 1)) == 0);
     c.inner += 1;
     if ((k + 1) % 8 == 0 && k + 1 < cfg.jd_maxk) {
       CK(cudaMemcpyAsync(c.hG, B.jS, sizeof(QmrState) * nbk, cudaMemcpyDeviceToHost, c.st));
@@ -1142,6 +1146,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       if (jdrun) {
         for (int i = 0; i < 8; ++i) reqs.push_back({&R.jd[i], (size_t)L * b * 8});
         reqs.push_back({&R.ju, (size_t)L * b * 8});
+        reqs.push_back({(void**)&R.jtick, 64});
         reqs.push_back({&R.jtmp, (size_t)m * b * 8});
         reqs.push_back({(void**)&R.jS, sizeof(QmrState) * 8});
         reqs.push_back({(void**)&R.jdots, sizeof(double) * 64});

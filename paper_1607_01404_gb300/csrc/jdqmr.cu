@@ -153,6 +153,74 @@ __device__ __forceinline__ void block_reduce_store(typename TAcc<P>::T (&acc)[ND
   }
 }
 
+__device__ void qmr_scalars1(int j, int nb, const double* __restrict__ dots, const double* __restrict__ eta,
+                             QmrState* S);
+__device__ void qmr_scalars2(int j, int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S);
+
+// The last CTA of a grid to finish (counted with an atomic ticket after every
+// CTA has stored its partial sums) reduces the partials in a fixed order into
+// dots[0, n) and runs the scalar step: mode 1 = scalars1, 2 = none,
+// 3 = scalars2 (with the dots of the whole step), then rearms the ticket.
+// No CTA waits for another, so the tail cannot stall.
+struct Tail {
+  unsigned* tick = nullptr;
+  double* out = nullptr;   // reduced values go to out[0, n)
+  double* dots = nullptr;  // the step's dots (for the scalar step)
+  int mode = 0;
+  int nb = 0;
+  const double* eta = nullptr;
+  double xi = 0.0;
+  int maxk = 0;
+  QmrState* S = nullptr;
+};
+
+template <class P>
+__device__ void grid_tail(const typename P::G* partial, int n, const Tail& t) {
+  using G = typename P::G;
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(t.tick, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // kT / n threads per value (n divides kT): thread t sums the partials of
+  // value t % n of CTAs t / n, t / n + kT / n, ... (coalesced, four loads in
+  // flight), then a fixed tree over the threads of each value
+  __shared__ G red[kT];
+  const int per = kT / n, e = threadIdx.x % n;
+  const long long tot = (long long)gridDim.x * n;
+  auto ld = [&](long long i) -> G {
+    if constexpr (P::id != kF64) {
+      const float2 f = __ldcg(reinterpret_cast<const float2*>(partial + i));
+      return G{f.x, f.y};
+    } else {
+      return __ldcg(reinterpret_cast<const double*>(partial + i));
+    }
+  };
+  G v = P::gzero();
+  long long i = threadIdx.x;
+  for (; i + 3LL * kT < tot; i += 4LL * kT) {
+    const G a0 = ld(i), a1 = ld(i + kT), a2 = ld(i + 2LL * kT), a3 = ld(i + 3LL * kT);
+    v = P::gadd(P::gadd(P::gadd(P::gadd(v, a0), a1), a2), a3);
+  }
+  for (; i < tot; i += kT) v = P::gadd(v, ld(i));
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = per / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w * n) red[threadIdx.x] = P::gadd(red[threadIdx.x], red[threadIdx.x + w * n]);
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < n) t.out[threadIdx.x] = P::gval(red[threadIdx.x]);
+  (void)e;
+  __syncthreads();
+  if ((int)threadIdx.x < t.nb) {
+    if (t.mode == 1) qmr_scalars1(threadIdx.x, t.nb, t.dots, t.eta, t.S);
+    if (t.mode == 3) qmr_scalars2(threadIdx.x, t.nb, t.dots, t.xi, t.maxk, t.S);
+  }
+  if (threadIdx.x == 0) *t.tick = 0u;
+}
+
 template <class P>
 __device__ __forceinline__ typename P::A ld_or_one(const typename P::S* p, long long i) {
   if (p) return P::load(p + i);
@@ -331,10 +399,8 @@ __global__ void __launch_bounds__(kT) k_qmr_dots1(long long L, int nb, const typ
 }
 
 // sigma = q^T t with t = w - eta q - x (x^T w - eta x^T q); alpha = rho / sigma
-__global__ void k_qmr_scalars1(int nb, const double* __restrict__ dots, const double* __restrict__ eta,
-                               QmrState* S) {
-  const int j = threadIdx.x;
-  if (j >= nb) return;
+__device__ void qmr_scalars1(int j, int nb, const double* __restrict__ dots, const double* __restrict__ eta,
+                             QmrState* S) {
   QmrState s = S[j];
   const double xw = dots[0 * nb + j], qw = dots[1 * nb + j], xq = dots[2 * nb + j], qq = dots[3 * nb + j];
   s.c1 = xw - eta[j] * xq;
@@ -348,6 +414,11 @@ __global__ void k_qmr_scalars1(int nb, const double* __restrict__ dots, const do
   S[j] = s;
 }
 
+__global__ void k_qmr_scalars1(int nb, const double* __restrict__ dots, const double* __restrict__ eta,
+                               QmrState* S) {
+  if ((int)threadIdx.x < nb) qmr_scalars1(threadIdx.x, nb, dots, eta, S);
+}
+
 // t = w - eta q - x c1 ; r -= alpha t ; u = K^-1 r ; dots r^T r, r^T u, x^T u, r^T kx
 template <class P, int NB, bool VEC>
 __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const typename P::S* __restrict__ x,
@@ -356,7 +427,8 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
                                                     const typename P::S* __restrict__ kx,
                                                     const typename P::S* __restrict__ dinv,
                                                     const double* __restrict__ eta, const QmrState* __restrict__ S,
-                                                    typename P::S* __restrict__ r, typename P::G* __restrict__ partial) {
+                                                    typename P::S* __restrict__ r, typename P::G* __restrict__ partial,
+                                                    Tail tail) {
   using G = typename P::G;
   using C = typename P::C;
   using A = typename P::A;
@@ -394,6 +466,7 @@ __global__ void __launch_bounds__(kT) k_qmr_update1(long long L, int nb, const t
     strow<P, NB, VEC>(r, row, nb, rv);
   }
   block_reduce_store<P, 4, NB>(acc, nb, partial);
+  if (tail.tick) grid_tail<P>(partial, 4 * nb, tail);
 }
 
 // dots r^T u, x^T u for u = K^-1 r computed by SpMM (sparse K^-1)
@@ -435,7 +508,7 @@ __global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __rest
                                                   const typename P::S* __restrict__ X, long long ldx,
                                                   typename P::S* __restrict__ Y, const typename P::S* __restrict__ E1,
                                                   const typename P::S* __restrict__ E2,
-                                                  typename P::G* __restrict__ partial) {
+                                                  typename P::G* __restrict__ partial, Tail tail) {
   using G = typename P::G;
   using A = typename P::A;
   typename TAcc<P>::T acc[ND][NB];
@@ -464,13 +537,14 @@ __global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __rest
     }
   }
   block_reduce_store<P, ND, NB>(acc, NB, partial);
+  if (tail.tick) grid_tail<P>(partial, ND * NB, tail);
 }
 
 // launch k_spmm_dots for the value format of K; returns its grid (the number
 // of partial sums), or 0 when nb or the alignment has no fused form
 template <class P, int NB, int ND>
 int spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1, const void* E2,
-                 void* partial, cudaStream_t st) {
+                 void* partial, const Tail& tail, cudaStream_t st) {
   using SS = typename P::S;
   using GG = typename P::G;
   constexpr bool vec = (NB * sizeof(SS)) % 16 == 0;
@@ -483,7 +557,7 @@ int spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, voi
   GG* pd = (GG*)partial;
   auto go = [&](auto kern, const float* a32, const float* a32lo, const double* a64) {
     const int g = occ_grid(kern, L);
-    kern<<<g, kT, 0, st>>>(L, K.rowptr, K.colidx, a32, a32lo, a64, x, ldx, y, e1, e2, pd);
+    kern<<<g, kT, 0, st>>>(L, K.rowptr, K.colidx, a32, a32lo, a64, x, ldx, y, e1, e2, pd, tail);
     return g;
   };
   if constexpr (P::id == kF32) {
@@ -499,20 +573,18 @@ int spmm_dots_nb(long long L, const CsrDev& K, const void* X, long long ldx, voi
 
 template <class P, int ND>
 int spmm_dots_p(int nb, long long L, const CsrDev& K, const void* X, long long ldx, void* Y, const void* E1,
-                const void* E2, void* partial, cudaStream_t st) {
+                const void* E2, void* partial, const Tail& tail, cudaStream_t st) {
   switch (nb) {
-    case 1: return spmm_dots_nb<P, 1, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
-    case 2: return spmm_dots_nb<P, 2, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
-    case 4: return spmm_dots_nb<P, 4, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
-    case 8: return spmm_dots_nb<P, 8, ND>(L, K, X, ldx, Y, E1, E2, partial, st);
+    case 1: return spmm_dots_nb<P, 1, ND>(L, K, X, ldx, Y, E1, E2, partial, tail, st);
+    case 2: return spmm_dots_nb<P, 2, ND>(L, K, X, ldx, Y, E1, E2, partial, tail, st);
+    case 4: return spmm_dots_nb<P, 4, ND>(L, K, X, ldx, Y, E1, E2, partial, tail, st);
+    case 8: return spmm_dots_nb<P, 8, ND>(L, K, X, ldx, Y, E1, E2, partial, tail, st);
   }
   return 0;
 }
 
 // QMR smoothing scalars, stopping test, next search-direction coefficients
-__global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
-  const int j = threadIdx.x;
-  if (j >= nb) return;
+__device__ void qmr_scalars2(int j, int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
   QmrState s = S[j];
   s.coefd = 0.0;
   s.coefq = 0.0;
@@ -540,6 +612,11 @@ __global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double x
   }
   S[j] = s;
 }
+
+__global__ void k_qmr_scalars2(int nb, const double* __restrict__ dots, double xi, int maxk, QmrState* S) {
+  if ((int)threadIdx.x < nb) qmr_scalars2(threadIdx.x, nb, dots, xi, maxk, S);
+}
+
 
 // d = coefd d + coefq q ; sol += d ; q = (K^-1 r - kx gamma) + beta q   (active columns)
 template <class P, int NB, bool VEC>
@@ -654,51 +731,79 @@ cudaError_t init_p(long long L, int nb, const void* x, const void* b, const void
 }
 
 template <class P, int NB, bool VEC>
-cudaError_t step_nb(long long L, int nb, const void* x, const void* w, bool dots_ready, const void* kx,
+cudaError_t step_nb(long long L, int nb, const void* x, const void* w, int ready, unsigned* ticks, const void* kx,
                     const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   using SS = typename P::S;
   using G = typename P::G;
   G* pd = reinterpret_cast<G*>(partial);
   if (K) dinv = nullptr;
-  if (!dots_ready) {
+  if (nb & (nb - 1)) ticks = nullptr;  // the tail reduction needs 4 nb to divide the CTA size
+  if (ready < 1) {
     const int g = occ_grid(k_qmr_dots1<P, NB, VEC>, L);
     k_qmr_dots1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, pd);
     k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
   }
-  k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
+  if (ready < 2) k_qmr_scalars1<<<1, 32, 0, st>>>(nb, dots, eta, S);
+  // with tickets the reductions and scalar steps run in the tails of the
+  // producing kernels; otherwise as separate launches
+  Tail t1;
+  if (ticks) {
+    t1.tick = ticks + 1;
+    t1.out = dots;
+    t1.dots = dots;
+    t1.mode = K ? 2 : 3;
+    t1.nb = nb;
+    t1.xi = xi;
+    t1.maxk = maxk;
+    t1.S = S;
+  }
   {
     const int g = occ_grid(k_qmr_update1<P, NB, VEC>, L);
     k_qmr_update1<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)q, (const SS*)w, (const SS*)kx,
-                                                (const SS*)dinv, eta, S, (SS*)r, pd);
-    k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
+                                                (const SS*)dinv, eta, S, (SS*)r, pd, t1);
+    if (!ticks) k_reduce_g<P><<<4 * nb, 128, 0, st>>>(pd, g, 4 * nb, dots);
   }
+  bool scal2_done = ticks && !K;
   if (K) {
     // u = K^-1 r by SpMM; r^T u and x^T u replace dots 1 and 2
-    int g = spmm_dots_p<P, 2>(nb, L, *K, r, nb, u, r, x, pd, st);
-    if (!g) {
-      const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
-      if (e != cudaSuccess) return e;
-      g = occ_grid(k_qmr_dots_u<P, NB, VEC>, L);
-      k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
+    Tail t2;
+    if (ticks) {
+      t2 = t1;
+      t2.tick = ticks + 2;
+      t2.out = dots + nb;
+      t2.mode = 3;
     }
-    k_reduce_g<P><<<2 * nb, 128, 0, st>>>(pd, g, 2 * nb, dots + nb);
+    int g = spmm_dots_p<P, 2>(nb, L, *K, r, nb, u, r, x, pd, t2, st);
+    if (g && ticks) {
+      scal2_done = true;
+    } else {
+      if (!g) {
+        const cudaError_t e = launch_spmm(P::id, *K, r, nb, u, nb, nb, st);
+        if (e != cudaSuccess) return e;
+        g = occ_grid(k_qmr_dots_u<P, NB, VEC>, L);
+        k_qmr_dots_u<P, NB, VEC><<<g, kT, 0, st>>>(L, nb, (const SS*)x, (const SS*)r, (const SS*)u, pd);
+      }
+      k_reduce_g<P><<<2 * nb, 128, 0, st>>>(pd, g, 2 * nb, dots + nb);
+    }
   }
-  k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
+  if (!scal2_done) k_qmr_scalars2<<<1, 32, 0, st>>>(nb, dots, xi, maxk, S);
   k_qmr_update2<P, NB, VEC><<<occ_grid(k_qmr_update2<P, NB, VEC>, L), kT, 0, st>>>(
       L, nb, (const SS*)r, (const SS*)kx, (const SS*)dinv, K ? (const SS*)u : nullptr, S, (SS*)q, (SS*)d, (SS*)sol);
   return cudaGetLastError();
 }
 
 template <class P>
-cudaError_t step_p(long long L, int nb, const void* x, const void* w, bool dr, const void* kx, const void* dinv,
-                   const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q, void* r, void* d,
-                   void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
+cudaError_t step_p(long long L, int nb, const void* x, const void* w, int dr, unsigned* tk, const void* kx,
+                   const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
+                   void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
   constexpr size_t es = sizeof(typename P::S);
 #define STEP(NBv)                                                                                                  \
   ((nb == NBv && (NBv * es) % 16 == 0)                                                                            \
-       ? step_nb<P, NBv, true>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st) \
-       : step_nb<P, NBv, false>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st))
+       ? step_nb<P, NBv, true>(L, nb, x, w, dr, tk, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, \
+                               st)                                                                                \
+       : step_nb<P, NBv, false>(L, nb, x, w, dr, tk, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial,     \
+                                dots, st))
   if (nb <= 1) return STEP(1);
   if (nb <= 2) return STEP(2);
   if (nb <= 4) return STEP(4);
@@ -720,18 +825,20 @@ cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b
   return cudaErrorInvalidValue;
 }
 
-cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, bool dots_ready, const void* kx,
-                     const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
-                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st) {
-  if (nb < 1 || nb > kMaxNb || (K && !u)) return cudaErrorInvalidValue;
-  const bool dr = dots_ready;
+cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, int ready, unsigned* ticks,
+                     const void* kx, const void* dinv, const CsrDev* K, void* u, const double* eta, double xi,
+                     int maxk, void* q, void* r, void* d, void* sol, QmrState* S, void* partial, double* dots,
+                     cudaStream_t st) {
+  if (nb < 1 || nb > kMaxNb || (K && !u) || ready < 0 || ready > 2) return cudaErrorInvalidValue;
+  const int dr = ready;
+  unsigned* tk = ticks;
   switch (prec) {
     case kF32:
-      return step_p<PF32>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PF32>(L, nb, x, w, dr, tk, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
     case kDF64:
-      return step_p<PDF64>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PDF64>(L, nb, x, w, dr, tk, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
     case kF64:
-      return step_p<PF64>(L, nb, x, w, dr, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
+      return step_p<PF64>(L, nb, x, w, dr, tk, kx, dinv, K, u, eta, xi, maxk, q, r, d, sol, S, partial, dots, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -747,23 +854,44 @@ int spmm_chunks(int b) {
 }
 }  // namespace
 
-int qmr_step_launches(int nb, bool sparse_k, bool dots_ready) {
+int qmr_step_launches(int nb, bool sparse_k, int ready, bool ticks) {
   const bool fused = nb == 1 || nb == 2 || nb == 4 || nb == 8;
-  return 7 - (dots_ready ? 2 : 0) + (sparse_k ? (fused ? 2 : spmm_chunks(nb) + 2) : 0);
+  int n = 2;                                   // update1, update2
+  if (ready < 1) n += 2;                       // dots1 + reduce
+  if (ready < 2) n += 1;                       // scalars1
+  if (!ticks) n += 1;                          // reduce after update1
+  if (sparse_k) n += fused ? (ticks ? 1 : 2) : spmm_chunks(nb) + 2;
+  if (!(ticks && (!sparse_k || fused))) n += 1;  // scalars2
+  return n;
 }
 
 cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const void* X, long long ldx, void* w,
-                        const void* x, const void* q, void* partial, double* dots, bool* done, cudaStream_t st) {
-  *done = false;
+                        const void* x, const void* q, void* partial, double* dots, unsigned* ticks,
+                        const double* eta, QmrState* S, int* ready, cudaStream_t st) {
+  *ready = 0;
   if (nb < 1 || nb > kMaxNb) return cudaErrorInvalidValue;
+  Tail t;
+  if (ticks) {
+    t.tick = ticks;
+    t.out = dots;
+    t.dots = dots;
+    t.mode = 1;
+    t.nb = nb;
+    t.eta = eta;
+    t.S = S;
+  }
   int g = 0;
   switch (prec) {
-    case kF32: g = spmm_dots_p<PF32, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
-    case kDF64: g = spmm_dots_p<PDF64, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
-    case kF64: g = spmm_dots_p<PF64, 4>(nb, L, K, X, ldx, w, x, q, partial, st); break;
+    case kF32: g = spmm_dots_p<PF32, 4>(nb, L, K, X, ldx, w, x, q, partial, t, st); break;
+    case kDF64: g = spmm_dots_p<PDF64, 4>(nb, L, K, X, ldx, w, x, q, partial, t, st); break;
+    case kF64: g = spmm_dots_p<PF64, 4>(nb, L, K, X, ldx, w, x, q, partial, t, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (!g) return cudaSuccess;
+  if (ticks) {
+    *ready = 2;  // dots reduced and scalars1 done in the kernel's tail
+    return cudaGetLastError();
+  }
   switch (prec) {
     case kF32: k_reduce_g<PF32><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PF32::G*>(partial), g, 4 * nb, dots); break;
     case kDF64:
@@ -771,7 +899,7 @@ cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const vo
       break;
     default: k_reduce_g<PF64><<<4 * nb, 128, 0, st>>>(reinterpret_cast<const PF64::G*>(partial), g, 4 * nb, dots); break;
   }
-  *done = true;
+  *ready = 1;
   return cudaGetLastError();
 }
 int qmr_init_launches(int nb, bool sparse_k) { return 4 + (sparse_k ? 2 * spmm_chunks(nb) : 0); }

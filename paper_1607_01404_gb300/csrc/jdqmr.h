@@ -25,18 +25,24 @@ cudaError_t qmr_init(int prec, long long L, int nb, const void* x, const void* b
 // One inner step after w = op(q) (the caller applies the operator): updates r,
 // d, sol, q and the scalars; eta: per-column shifts (device doubles).  A column
 // stops when tau sqrt(k + 1) <= xi tau0 or after maxk steps.
-// dots_ready: the four dots of w = op(q) with x and q are already in `dots`
-// (qmr_op_dots); otherwise this step computes them.
-cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, bool dots_ready, const void* kx,
-                     const void* dinv, const CsrDev* K, void* u, const double* eta, double xi, int maxk, void* q,
-                     void* r, void* d, void* sol, QmrState* S, void* partial, double* dots, cudaStream_t st);
+// ready: 0 = this step computes the dots of w = op(q) with x and q; 1 = they
+// are in `dots` (qmr_op_dots); 2 = and the first scalar step is done too.
+// ticks: >= 3 zeroed device counters that let the producing kernels reduce
+// their partial sums and run the scalar steps in their tails (fewer
+// launches), or nullptr for separate reduction and scalar launches.
+cudaError_t qmr_step(int prec, long long L, int nb, const void* x, const void* w, int ready, unsigned* ticks,
+                     const void* kx, const void* dinv, const CsrDev* K, void* u, const double* eta, double xi,
+                     int maxk, void* q, void* r, void* d, void* sol, QmrState* S, void* partial, double* dots,
+                     cudaStream_t st);
 // w = K X for a single CSR operator (K: rows L, X: ld ldx) fused with the four
-// dots x^T w, q^T w, x^T q, q^T q of a step, reduced into `dots`; *done is
-// false (and nothing is launched) when nb or the alignment has no fused form.
+// dots x^T w, q^T w, x^T q, q^T q of a step, reduced into `dots`; with ticks
+// the first scalar step of the step (eta, S) runs in the kernel's tail.
+// *ready = 0 (nothing launched: nb or the alignment has no fused form), 1 or 2
+// as for qmr_step.
 cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const void* X, long long ldx, void* w,
-                        const void* x, const void* q, void* partial, double* dots, bool* done, cudaStream_t st);
-// kernel launches of one qmr_step / qmr_init call
-int qmr_step_launches(int nb, bool sparse_k, bool dots_ready);
+                        const void* x, const void* q, void* partial, double* dots, unsigned* ticks,
+                        const double* eta, QmrState* S, int* ready, cudaStream_t st);
+int qmr_step_launches(int nb, bool sparse_k, int ready, bool ticks);
 int qmr_init_launches(int nb, bool sparse_k);
 
 // dst[:, j] = scale[j] * src[:, j] with a mode conversion (scale: device doubles).
