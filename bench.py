@@ -41,6 +41,10 @@ K, TARGET, BLOCK, TOL = 10, "smallest", 4, 1e-10
 METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner solves, FP32 stage-1 phase, "
           "learned preconditioner)")
 MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
+# DRAM bytes (read + write) of one launch from ncu captures of these kernels on
+# this workload (profiles/k_spmm_C_f32_b4_grid3d_N128.md, profiles/k_spmm_f32_b4_grid3d_N128.md);
+# None where the kernel changed after the capture
+TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None}
 UNIT = "s"
 # Products with A or A^T (per column) of a full GD+k FP64-class solve of this
 # workload, measured on a GB300 with this library (the plain GD+k line of the
@@ -471,7 +475,7 @@ def main():
                          inner_steps=st["inner_steps"], stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
                          precond_s=st["seconds_precond"]),
         roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
-                      frac=achieved / peak, peak_kind=peak_kind, traffic=None,
+                      frac=achieved / peak, peak_kind=peak_kind, traffic=TRAFFIC.get(dom),
                       all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
                            {**{f"f32_{a}": b for a, b in res["roof32"].items()},
                             **{f"df64_{a}": b for a, b in res["roofdf"].items()}}.items()}),
