@@ -42,8 +42,8 @@ METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner
           "learned preconditioner)")
 MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
-# this workload (profiles/k_spmm_C_f32_b4_grid3d_N128.md, profiles/k_spmm_f32_b4_grid3d_N128.md);
-# None where the kernel changed after the capture
+# this workload (--set full, one warm launch each); None where the kernel
+# changed after its capture
 TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None}
 UNIT = "s"
 # Products with A or A^T (per column) of a full GD+k FP64-class solve of this
