@@ -43,6 +43,20 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t *row
  * flags[0] (device int) |= 1 when some value is not exactly representable. */
 int phsvds_to_bf16(int64_t nnz, const float *v32, uint16_t *v16, int *flags, void *stream);
 
+/* JDQMR inner solve (Sec. 3.4): for each of the nb columns j, block symmetric
+ * QMR on the correction equation
+ *     (I - x_j x_j^T)(K - eta_j I)(I - x_j x_j^T) t_j = b_j,   t_j orthogonal to x_j,
+ * with the projected preconditioner built from dinv (Jacobi diagonal in the
+ * mode's storage, or NULL), exactly as inside svds_solve.  K: CSR (n x n, the
+ * value arrays of the mode as in phsvds_spmm); X, Bv, T: row-major n x nb
+ * device blocks of mode prec (X orthonormal columns, Bv orthogonal to them);
+ * eta: host doubles.  Stops a column when its QMR residual bound falls below
+ * xi ||b_j|| or after maxit steps; *steps (host, may be NULL) receives the
+ * number of steps taken.  nb <= 8.  Allocates and frees its own scratch. */
+int phsvds_jd_solve(int prec, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                    const float *v32, const float *v32lo, const double *v64, int nb, const void *X, const void *Bv,
+                    const double *eta, const void *dinv, int maxit, double xi, void *T, int *steps, void *stream);
+
 /* G (p x q row-major doubles, device) = P^T Q over rows [r0, r1) (the Table 3
  * inner products: Rayleigh-Ritz projection V^T W, Gram matrices of CGS and
  * CholQR).  Accumulation is FP64-class in every mode and the reduction order

@@ -70,6 +70,24 @@ def round_bf16(x):
     return r.astype(np.uint32).view(np.float32)
 
 
+def jd_correction_exact(C, X, B, eta):
+    """Exact solution of the Jacobi-Davidson correction equation per column j
+    (Sec. 3.4, JDQMR's inner system):
+        (I - x_j x_j^T)(C - eta_j I)(I - x_j x_j^T) t_j = b_j,  t_j orthogonal to x_j,
+    for unit vectors x_j and b_j orthogonal to x_j: t_j = Q (Q^T (C - eta_j I) Q)^-1 Q^T b_j
+    with Q an orthonormal basis of the complement of x_j (dense; small n only)."""
+    Cd = C.toarray() if hasattr(C, "toarray") else np.asarray(C, dtype=np.float64)
+    n = Cd.shape[0]
+    T = np.zeros_like(B, dtype=np.float64)
+    for j in range(B.shape[1]):
+        x = X[:, j] / np.linalg.norm(X[:, j])
+        Qf, _ = np.linalg.qr(np.column_stack([x, np.eye(n)]))
+        Q = Qf[:, 1:n]
+        Mj = Q.T @ (Cd - eta[j] * np.eye(n)) @ Q
+        T[:, j] = Q @ np.linalg.solve(Mj, Q.T @ B[:, j])
+    return T
+
+
 def spmm_t(A, Y):
     """X = A^T Y (the user matvec of Sec. 3.4 with transpose != 0)."""
     return _as_csr(A).T @ Y

@@ -91,6 +91,9 @@ _SIGS = {
     "phsvds_spmm_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
     "phsvds_to_bf16": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_jd_solve": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.c_double, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
     "phsvds_gram": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                               C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "phsvds_gram_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
@@ -288,6 +291,17 @@ def spmm_bf16(rows, cols, rowptr, colidx, v16, X, ldx, Y, ldy, b, stream=None):
     _check(lib().phsvds_spmm_bf16(rows, cols, int(colidx.numel()), rowptr.data_ptr(), colidx.data_ptr(),
                                   v16.data_ptr(), X.data_ptr(), ldx, Y.data_ptr(), ldy, b, _stream(stream)),
            "phsvds_spmm_bf16")
+
+
+def jd_solve(prec, n, rowptr, colidx, v32, v32lo, v64, nb, X, Bv, eta, dinv, maxit, xi, T, stream=None):
+    """JDQMR inner solve on device blocks (torch CUDA tensors); returns the steps taken."""
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    steps = C.c_int(0)
+    _check(lib().phsvds_jd_solve(prec, n, int(colidx.numel()), ptr(rowptr), ptr(colidx), ptr(v32), ptr(v32lo),
+                                 ptr(v64), nb, ptr(X), ptr(Bv), eta.ctypes.data, ptr(dinv), maxit, xi, ptr(T),
+                                 C.byref(steps), _stream(stream)), "phsvds_jd_solve")
+    return steps.value
 
 
 def to_bf16(v32, v16, flags, stream=None):

@@ -12,6 +12,7 @@
 #include "../../include/phsvds_gnn.h"
 #include "../../include/phsvds_kernels.h"
 #include "engine.h"
+#include "jdqmr.h"
 #include "hostla.h"
 #include "kernels.h"
 
@@ -310,6 +311,30 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t* row
   A.v16 = v16;
   CKR(launch_spmm(kF32, A, X, ldx, Y, ldy, b, reinterpret_cast<cudaStream_t>(stream)));
   return 0;
+}
+
+int phsvds_jd_solve(int prec, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                    const float* v32, const float* v32lo, const double* v64, int nb, const void* X, const void* Bv,
+                    const double* eta, const void* dinv, int maxit, double xi, void* T, int* steps, void* stream) {
+  if (!prec_ok(prec) || n < 1 || nnz < 0 || nb < 1 || nb > 8 || maxit < 0 || !(xi >= 0) || !rowptr || !X || !Bv ||
+      !eta || !T)
+    return SVDS_ERR_ARG;
+  if (nnz > 0 && (!colidx || (prec == kF64 ? !v64 : !v32))) return SVDS_ERR_ARG;
+  CsrDev K;
+  K.rows = n;
+  K.cols = n;
+  K.nnz = nnz;
+  K.rowptr = rowptr;
+  K.colidx = colidx;
+  K.v32 = v32;
+  K.v32lo = v32lo;
+  K.v64 = v64;
+  const int rc = jd_solve(prec, K, nb, X, Bv, eta, dinv, maxit, xi, T, steps, reinterpret_cast<cudaStream_t>(stream));
+  if (rc == -6) {
+    phsvds::set_last_error("phsvds_jd_solve: CUDA error");
+    return SVDS_ERR_CUDA;
+  }
+  return rc == -5 ? SVDS_ERR_NOMEM : rc;
 }
 
 int phsvds_to_bf16(int64_t nnz, const float* v32, uint16_t* v16, int* flags, void* stream) {

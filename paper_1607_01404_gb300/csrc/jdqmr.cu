@@ -20,6 +20,7 @@
 #include <cmath>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
 #include "jdqmr.h"
@@ -903,6 +904,64 @@ cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const vo
   return cudaGetLastError();
 }
 int qmr_init_launches(int nb, bool sparse_k) { return 4 + (sparse_k ? 2 * spmm_chunks(nb) : 0); }
+
+int jd_solve(int prec, const CsrDev& K, int nb, const void* X, const void* Bv, const double* eta_host,
+             const void* dinv, int maxit, double xi, void* T, int* steps, cudaStream_t st) {
+  const long long n = K.rows;
+  const size_t es = prec == kF32 ? 4 : 8;
+  std::vector<void*> mem;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.push_back(p);
+    return p;
+  };
+  auto done = [&](int code) {
+    cudaStreamSynchronize(st);
+    for (void* p : mem) cudaFree(p);
+    return code;
+  };
+  const size_t blk = (size_t)n * nb * es;
+  void *kx = take(blk), *q = take(blk), *r = take(blk), *d = take(blk), *w = take(blk), *u = take(blk);
+  QmrState* S = static_cast<QmrState*>(take(sizeof(QmrState) * kMaxNb));
+  double* dots = static_cast<double*>(take(sizeof(double) * 64));
+  double* deta = static_cast<double*>(take(sizeof(double) * kMaxNb));
+  unsigned* ticks = static_cast<unsigned*>(take(64));
+  void* partial = take((size_t)kMaxGrid * 5 * kMaxNb * 8);
+  if (!kx || !q || !r || !d || !w || !u || !S || !dots || !deta || !ticks || !partial) return done(-5);
+  if (cudaMemsetAsync(ticks, 0, 64, st) != cudaSuccess ||
+      cudaMemcpyAsync(deta, eta_host, sizeof(double) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      qmr_init(prec, n, nb, X, Bv, dinv, nullptr, u, kx, q, r, d, T, S, partial, dots, st) != cudaSuccess)
+    return done(-6);
+  int k = 0;
+  for (; k < maxit; ++k) {
+    int ready = 0;
+    if (qmr_op_dots(prec, n, nb, K, q, nb, w, X, q, partial, dots, ticks, deta, S, &ready, st) != cudaSuccess)
+      return done(-6);
+    if (!ready && launch_spmm(prec, K, q, nb, w, nb, nb, st) != cudaSuccess) return done(-6);
+    if (qmr_step(prec, n, nb, X, w, ready, ticks, kx, dinv, nullptr, u, deta, xi, maxit, q, r, d, T, S, partial, dots,
+                 st) != cudaSuccess)
+      return done(-6);
+    if ((k + 1) % 8 == 0) {
+      QmrState hs[kMaxNb];
+      if (cudaMemcpyAsync(hs, S, sizeof(QmrState) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return done(-6);
+      bool any = false;
+      for (int j = 0; j < nb; ++j) any = any || hs[j].active;
+      if (!any) {
+        ++k;
+        break;
+      }
+    }
+  }
+  if (steps) *steps = k;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return done(-6);
+  return done(0);
+}
 
 cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,
                          long long L, int nc, const double* scale, cudaStream_t st) {

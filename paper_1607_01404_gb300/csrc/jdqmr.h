@@ -45,6 +45,11 @@ cudaError_t qmr_op_dots(int prec, long long L, int nb, const CsrDev& K, const vo
 int qmr_step_launches(int nb, bool sparse_k, int ready, bool ticks);
 int qmr_init_launches(int nb, bool sparse_k);
 
+// Complete inner solve with its own scratch (the kernel-level entry point):
+// see phsvds_jd_solve in phsvds_kernels.h.  Returns 0 or an SVDS_ERR_* code.
+int jd_solve(int prec, const CsrDev& K, int nb, const void* X, const void* Bv, const double* eta_host,
+             const void* dinv, int maxit, double xi, void* T, int* steps, cudaStream_t st);
+
 // dst[:, j] = scale[j] * src[:, j] with a mode conversion (scale: device doubles).
 cudaError_t convert_cols(int src_prec, const void* src, long long lds, int dst_prec, void* dst, long long ldd,
                          long long L, int nc, const double* scale, cudaStream_t st);

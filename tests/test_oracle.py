@@ -258,3 +258,30 @@ def test_round_bf16_definition():
     # monotone
     s = np.sort(v)
     assert np.all(np.diff(round_bf16(s).astype(np.float64)) >= 0)
+
+
+def test_jd_correction_exact_definition():
+    """Diagonal C and x = e_0: t = (C - eta)^-1 b on the other coordinates; in
+    general the projected equation holds and t is orthogonal to x."""
+    from oracle.phsvds_fp64 import jd_correction_exact
+
+    d = np.array([1.0, 2.0, 3.5, 5.0, 7.0])
+    C = np.diag(d)
+    X = np.eye(5)[:, :1]
+    b = np.array([[0.0], [1.0], [-2.0], [0.5], [3.0]])
+    t = jd_correction_exact(C, X, b, np.array([2.5]))
+    want = np.zeros(5)
+    want[1:] = b[1:, 0] / (d[1:] - 2.5)
+    np.testing.assert_allclose(t[:, 0], want, rtol=1e-13, atol=1e-15)
+    rng = np.random.default_rng(2)
+    M = rng.standard_normal((30, 30))
+    C = M @ M.T
+    X = np.linalg.qr(rng.standard_normal((30, 2)))[0]
+    B = rng.standard_normal((30, 2))
+    B -= X * np.sum(X * B, axis=0)
+    eta = np.array([1.3, 7.7])
+    T = jd_correction_exact(C, X, B, eta)
+    for j in range(2):
+        P = np.eye(30) - np.outer(X[:, j], X[:, j])
+        np.testing.assert_allclose(P @ (C - eta[j] * np.eye(30)) @ P @ T[:, j], B[:, j], atol=1e-10 * np.abs(B).max())
+        assert abs(X[:, j] @ T[:, j]) < 1e-12 * np.linalg.norm(T[:, j])
