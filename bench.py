@@ -227,6 +227,44 @@ def spmm_roofline(A, dev, torch, B, prec, b, reps=30):
     return res
 
 
+def ortho_roofline(dev, torch, B, prec, L, g, b, reps=20):
+    """The two kernels of the CGS2 + CholQR2 orthogonalisation at the workload's
+    sizes (basis of g columns, block of b): the Gram G = V^T T (algorithmic
+    bytes L (g + b) s) and the update T <- T - V C (L (g + 2 b) s), timed with
+    CUDA events on their stream."""
+    words = 1 if prec == B.PREC_F32 else 2
+    s = 4 if prec == B.PREC_F32 else 8
+    ldv = (g + 3) // 4 * 4
+    V = torch.randn(L * ldv * words, dtype=torch.float32, device=dev)
+    T = torch.randn(L * b * words, dtype=torch.float32, device=dev)
+    if words == 2:
+        V.view(-1, 2)[:, 1] = 0
+        T.view(-1, 2)[:, 1] = 0
+    G = torch.zeros(g * b, dtype=torch.float64, device=dev)
+    scratch = torch.zeros(B.gram_scratch_bytes(g, b), dtype=torch.uint8, device=dev)
+    coef = torch.from_numpy(B.coef_convert(prec, np.full((g, b), 1e-3))).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    res = {}
+    for name, fn, alg in (
+        ("gram", lambda: B.gram(prec, 0, L, V, ldv, g, T, b, b, G, scratch, stream=sp), L * (g + b) * s),
+        ("combine", lambda: B.combine(prec, L, V, ldv, g, coef, T, b, 1, T, b, b, stream=sp), L * (g + 2 * b) * s),
+    ):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9}
+    return res
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -319,12 +357,15 @@ def run_gpu(args, world, rank, local):
     # roofline of the dominant kernel family (CSR SpMM, FP32 phase and FP64-class)
     roof32 = spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK)
     roofdf = spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK)
+    # orthogonalisation kernels at the solve's sizes (basis 32 columns, block 4)
+    orth = {f"{nm}_{k}": v for nm, pr in (("f32", B.PREC_F32), ("df64", B.PREC_DF64))
+            for k, v in ortho_roofline(dev, torch, B, pr, A.n, 32, BLOCK).items()}
     ms_step = statistics.median(t_chosen) * 1e3
     ms_step = max_over_ranks(ms_step, world)
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
                 t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
                 relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
-                roof32=roof32, roofdf=roofdf, ms_step=ms_step, A=A, e2e_nconv=oute[4], gain=gain)
+                roof32=roof32, roofdf=roofdf, orth=orth, ms_step=ms_step, A=A, e2e_nconv=oute[4], gain=gain)
 
 
 def precond_gain(B, wl, sp):
@@ -393,7 +434,9 @@ def main():
         dev = torch.device("cuda", 0)
         B.lib()
         out = {"f32": spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK, reps=args.steps),
-               "df64": spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK, reps=args.steps)}
+               "df64": spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK, reps=args.steps),
+               "ortho_f32": ortho_roofline(dev, torch, B, B.PREC_F32, A.n, 32, BLOCK, reps=args.steps),
+               "ortho_df64": ortho_roofline(dev, torch, B, B.PREC_DF64, A.n, 32, BLOCK, reps=args.steps)}
         print(json.dumps(out))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -482,6 +525,8 @@ def main():
                       all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
                            {**{f"f32_{a}": b for a, b in res["roof32"].items()},
                             **{f"df64_{a}": b for a, b in res["roofdf"].items()}}.items()}),
+        ortho_roofline={k: dict(ms=round(v["ms"], 4), bytes=v["bytes"], gbs=round(v["gbs"], 1),
+                                frac=round(v["gbs"] / peak, 4)) for k, v in res["orth"].items()},
         cpu_baseline=cpu,
         e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
                  numConverged=res["e2e_nconv"]),

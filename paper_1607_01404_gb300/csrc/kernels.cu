@@ -925,6 +925,180 @@ static cudaError_t combine_p(long long L, const SegArr& sa, int p, const void* c
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Row combine: one thread per row streams its p inputs (16-byte loads when
+// every segment row is 16-byte aligned), keeps the q outputs in registers and
+// writes them after all reads, so Out may alias an input segment or In.  The
+// coefficients (and R^-1) sit in shared memory and are read as broadcasts.
+// ---------------------------------------------------------------------------
+constexpr int kRowCombP = 64;
+
+
+template <class P>
+__device__ __forceinline__ typename P::A shfl_a(typename P::A v, int lane) {
+  if constexpr (P::id == kDF64) {
+    return df{__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane)};
+  } else {
+    return __shfl_sync(0xffffffffu, v, lane);
+  }
+}
+
+// one 16-byte load of W = 16 / sizeof(S) consecutive elements (no local array)
+template <class P>
+__device__ __forceinline__ void load16(const typename P::S* p, typename P::A (&x)[16 / sizeof(typename P::S)]) {
+  if constexpr (P::id == kF32) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+  } else if constexpr (P::id == kDF64) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    x[0] = df{t.x, t.y};
+    x[1] = df{t.z, t.w};
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    x[0] = t.x;
+    x[1] = t.y;
+  }
+}
+
+// TPR consecutive lanes share a row; lane part computes outputs
+// [4 part, 4 part + 4) (the row's loads hit L1 after the first lane).
+template <class P, int TPR, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_combine_row(long long L, SegArr segs, int p, int q,
+                                                          const typename P::C* __restrict__ coef,
+                                                          const typename P::S* In, long long ldin, int alpha_one,
+                                                          typename P::S* Out, long long ldout,
+                                                          const typename P::C* __restrict__ Rinv,
+                                                          typename P::S* Out2, long long ldout2) {
+  using S = typename P::S;
+  using A = typename P::A;
+  using C = typename P::C;
+  constexpr int QT = 4, Q = QT * TPR;
+  __shared__ C cs[kRowCombP * Q];
+  __shared__ C rs[Q * Q];
+  for (int e = threadIdx.x; e < p * Q; e += kThreads) {
+    const int c = e / Q, j = e % Q;
+    cs[e] = j < q ? coef[(long long)c * q + j] : C{};
+  }
+  if (Rinv)
+    for (int e = threadIdx.x; e < Q * Q; e += kThreads) {
+      const int i = e / Q, j = e % Q;
+      rs[e] = (i < q && j < q) ? Rinv[i * q + j] : C{};
+    }
+  __syncthreads();
+  const int part = threadIdx.x % TPR;
+  const int j0 = part * QT;
+  const long long rows_per_pass = (long long)gridDim.x * (kThreads / TPR);
+  // every lane runs the same number of passes (the shuffles below need whole warps)
+  for (long long base = (long long)blockIdx.x * (kThreads / TPR); base < L; base += rows_per_pass) {
+    const long long r = base + threadIdx.x / TPR;
+    const bool live = r < L;
+    A acc[QT];
+#pragma unroll
+    for (int j = 0; j < QT; ++j) acc[j] = (live && alpha_one && j0 + j < q) ? P::load(In + r * ldin + j0 + j) : P::zero();
+    if (live) {
+      int c0 = 0;
+      for (int sg = 0; sg < segs.n; ++sg) {
+        const S* row = reinterpret_cast<const S*>(segs.p[sg]) + r * segs.ld[sg];
+        const int nc = segs.nc[sg];
+        if constexpr (VEC) {
+          constexpr int W = (int)(16 / sizeof(S));
+          for (int c = 0; c < nc; c += W) {
+            A xs[W];
+            load16<P>(row + c, xs);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              const C* cr = cs + (c0 + c + w) * Q + j0;
+#pragma unroll
+              for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], xs[w], cr[j]);
+            }
+          }
+        } else {
+          for (int c = 0; c < nc; ++c) {
+            const A x = P::load(row + c);
+            const C* cr = cs + (c0 + c) * Q + j0;
+#pragma unroll
+            for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], x, cr[j]);
+          }
+        }
+        c0 += nc;
+      }
+    }
+    if (Rinv) {
+      // out_j = sum_{i <= j} acc_i Rinv_ij, the acc_i of lower parts from the
+      // lanes of the same row
+      A o[QT];
+#pragma unroll
+      for (int j = 0; j < QT; ++j) o[j] = P::zero();
+      const int lane0 = (threadIdx.x & 31) - part;
+#pragma unroll
+      for (int pp = 0; pp < TPR; ++pp) {
+#pragma unroll
+        for (int i = 0; i < QT; ++i) {
+          A v;
+          if constexpr (TPR == 1) {
+            v = acc[i];
+          } else {
+            v = shfl_a<P>(acc[i], lane0 + pp);
+          }
+          const int ii = pp * QT + i;
+#pragma unroll
+          for (int j = 0; j < QT; ++j)
+            if (ii <= j0 + j) o[j] = P::fmac(o[j], v, rs[ii * Q + j0 + j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < QT; ++j) acc[j] = o[j];
+    }
+    // Out may alias an input row that other lanes of this row still read
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < QT; ++j)
+        if (j0 + j < q) {
+          P::store(Out + r * ldout + j0 + j, acc[j]);
+          if (Out2) P::store(Out2 + r * ldout2 + j0 + j, acc[j]);
+        }
+    }
+  }
+}
+
+template <class P>
+cudaError_t combine_row_p(long long L, const SegArr& sa, int p, const void* coef, const void* In, long long ldin,
+                          int alpha_one, void* Out, long long ldout, int q, const void* Rinv, void* Out2,
+                          long long ldout2, cudaStream_t st) {
+  using S = typename P::S;
+  using C = typename P::C;
+  constexpr int W = (int)(16 / sizeof(S));
+  bool vec = true;
+  for (int sg = 0; sg < sa.n; ++sg)
+    vec = vec && (reinterpret_cast<uintptr_t>(sa.p[sg]) % 16 == 0) && ((sa.ld[sg] * sizeof(S)) % 16 == 0) &&
+          (sa.nc[sg] % W == 0);
+  const C* cf = reinterpret_cast<const C*>(coef);
+  const C* ri = reinterpret_cast<const C*>(Rinv);
+  const S* in = reinterpret_cast<const S*>(In);
+  S* out = reinterpret_cast<S*>(Out);
+  S* out2 = reinterpret_cast<S*>(Out2);
+#define ROWC(TPRV)                                                                                                 \
+  {                                                                                                                \
+    const int grid = persistent_grid((L + kThreads / TPRV - 1) / (kThreads / TPRV), 1);                           \
+    if (vec)                                                                                                       \
+      k_combine_row<P, TPRV, true><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout, ri, \
+                                                              out2, ldout2);                                       \
+    else                                                                                                           \
+      k_combine_row<P, TPRV, false><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout,    \
+                                                               ri, out2, ldout2);                                  \
+    return cudaGetLastError();                                                                                     \
+  }
+  if (q <= 4) ROWC(1)
+  if (q <= 8) ROWC(2)
+  if (q <= 16) ROWC(4)
+#undef ROWC
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, const void* coef, const void* In,
                            long long ldin, int alpha_one, void* Out, long long ldout, int q, const void* Rinv,
                            void* Out2, long long ldout2, cudaStream_t st) {
@@ -932,6 +1106,10 @@ cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, cons
   int p;
   SegArr sa = make_segs(Pp, nseg, &p);
   if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
+  if (p <= kRowCombP && q <= 16) {
+    PHSVDS_DISPATCH(prec, combine_row_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2,
+                                           st))
+  }
   {
     TileDesc T;
     if (make_tiles(Pp, nseg, elem_bytes(prec), true, &T)) {
