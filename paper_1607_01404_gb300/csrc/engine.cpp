@@ -1582,8 +1582,9 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       // FP64 column-major copy, sign convention on the device (largest-|.|
       // entry of each v positive), then one copy per returned column
       CK(launch_to_f64_colmajor(p2, L2, k, Xres, kk, dtmp, L2, 1.0, c.st));
-      CK(launch_col_sign(L2, L2, k, voff, nu, dtmp, c.st));
-      c.launches += 2;
+      // (the gather buffer is free until the gather below: the sign search uses it)
+      CK(launch_col_sign(L2, L2, k, voff, nu, dtmp, reinterpret_cast<double*>(dout2), c.st));
+      c.launches += 4;
       if (c.print >= 2) {
         c.sync();
         std::fprintf(stderr, "[output] conversion and signs done at %.4f s\n", c.elapsed() - t_out);

@@ -15,6 +15,7 @@
 //                       A^T A, validation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -933,6 +934,24 @@ static cudaError_t combine_p(long long L, const SegArr& sa, int p, const void* c
 // ---------------------------------------------------------------------------
 constexpr int kRowCombP = 64;
 
+template <class P>
+__device__ __forceinline__ typename P::A mul_a(typename P::A a, typename P::A b) {
+  if constexpr (P::id == kDF64) {
+    return df_mul(a, b);
+  } else {
+    return a * b;
+  }
+}
+
+template <class P>
+__device__ __forceinline__ typename P::G shfl_down_gacc(typename P::G v, int o) {
+  if constexpr (P::id == kF64) {
+    return __shfl_down_sync(0xffffffffu, v, o);
+  } else {
+    return df{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+  }
+}
+
 
 template <class P>
 __device__ __forceinline__ typename P::A shfl_a(typename P::A v, int lane) {
@@ -1095,6 +1114,7 @@ cudaError_t combine_row_p(long long L, const SegArr& sa, int p, const void* coef
   if (q <= 4) ROWC(1)
   if (q <= 8) ROWC(2)
   if (q <= 16) ROWC(4)
+  if (q <= 32) ROWC(8)
 #undef ROWC
   return cudaErrorInvalidValue;
 }
@@ -1106,7 +1126,7 @@ cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, cons
   int p;
   SegArr sa = make_segs(Pp, nseg, &p);
   if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
-  if (p <= kRowCombP && q <= 16) {
+  if (p <= kRowCombP && q <= 32) {
     PHSVDS_DISPATCH(prec, combine_row_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2,
                                            st))
   }
@@ -1147,10 +1167,147 @@ static cudaError_t ritz_p(long long L, SegV V, SegV W, int g, const void* Y, con
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Row Ritz kernel: TPR lanes share a row (lane part owns the block columns
+// 4 part .. 4 part + 3); X = V Y and R = W Y - X diag(theta) from streamed rows
+// of V and W, optional T = diag(d) R, and FP64-class partial sums of R^2 per
+// column (fixed shuffle butterfly, then warps in order): partial[blk][j].
+// ---------------------------------------------------------------------------
+template <class P, int TPR, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_ritz_row(long long L, const typename P::S* __restrict__ V,
+                                                       const typename P::S* __restrict__ W, long long ldv, int g,
+                                                       const typename P::C* __restrict__ Y,
+                                                       const typename P::C* __restrict__ theta,
+                                                       typename P::S* __restrict__ X, typename P::S* __restrict__ R,
+                                                       long long ldb, int nb, const typename P::S* __restrict__ dscale,
+                                                       typename P::S* __restrict__ T, typename P::G* __restrict__ partial) {
+  using S = typename P::S;
+  using A = typename P::A;
+  using C = typename P::C;
+  using G = typename P::G;
+  constexpr int QT = 4, Q = QT * TPR;
+  __shared__ C ys[kRowCombP * Q];
+  __shared__ C th[Q];
+  for (int e = threadIdx.x; e < g * Q; e += kThreads) {
+    const int c = e / Q, j = e % Q;
+    ys[e] = j < nb ? Y[(long long)c * nb + j] : C{};
+  }
+  if (threadIdx.x < Q) th[threadIdx.x] = threadIdx.x < nb ? theta[threadIdx.x] : C{};
+  __syncthreads();
+  const int part = threadIdx.x % TPR, j0 = part * QT;
+  G nrm[QT];
+#pragma unroll
+  for (int j = 0; j < QT; ++j) nrm[j] = P::gzero();
+  const long long rows_per_pass = (long long)gridDim.x * (kThreads / TPR);
+  for (long long r = (long long)blockIdx.x * (kThreads / TPR) + threadIdx.x / TPR; r < L; r += rows_per_pass) {
+    A ax[QT], ar[QT];
+#pragma unroll
+    for (int j = 0; j < QT; ++j) ax[j] = ar[j] = P::zero();
+    const S* vr = V + r * ldv;
+    const S* wr = W + r * ldv;
+    if constexpr (VEC) {
+      constexpr int WW = (int)(16 / sizeof(S));
+      for (int c = 0; c < g; c += WW) {
+        A xv[WW], xw[WW];
+        load16<P>(vr + c, xv);
+        load16<P>(wr + c, xw);
+#pragma unroll
+        for (int w = 0; w < WW; ++w) {
+          const C* yr = ys + (c + w) * Q + j0;
+#pragma unroll
+          for (int j = 0; j < QT; ++j) {
+            ax[j] = P::fmac(ax[j], xv[w], yr[j]);
+            ar[j] = P::fmac(ar[j], xw[w], yr[j]);
+          }
+        }
+      }
+    } else {
+      for (int c = 0; c < g; ++c) {
+        const A xv = P::load(vr + c), xw = P::load(wr + c);
+        const C* yr = ys + c * Q + j0;
+#pragma unroll
+        for (int j = 0; j < QT; ++j) {
+          ax[j] = P::fmac(ax[j], xv, yr[j]);
+          ar[j] = P::fmac(ar[j], xw, yr[j]);
+        }
+      }
+    }
+    A dr = P::zero();
+    if (T) dr = P::load(dscale + r);
+#pragma unroll
+    for (int j = 0; j < QT; ++j)
+      if (j0 + j < nb) {
+        const A rj = P::sub(ar[j], P::mulc(ax[j], th[j0 + j]));
+        P::store(X + r * ldb + j0 + j, ax[j]);
+        P::store(R + r * ldb + j0 + j, rj);
+        if (T) P::store(T + r * ldb + j0 + j, mul_a<P>(dr, rj));
+        nrm[j] = P::gfma(nrm[j], rj, rj);
+      }
+  }
+  // lanes of the same part across the warp's rows, then the warps in order
+#pragma unroll
+  for (int j = 0; j < QT; ++j)
+    for (int o = 16; o >= TPR; o >>= 1) nrm[j] = P::gadd(nrm[j], shfl_down_gacc<P>(nrm[j], o));
+  __shared__ G red[kThreads / 32][Q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < TPR)
+#pragma unroll
+    for (int j = 0; j < QT; ++j) red[warp][lane * QT + j] = nrm[j];
+  __syncthreads();
+  if ((int)threadIdx.x < nb) {
+    G v = red[0][threadIdx.x];
+    for (int w = 1; w < kThreads / 32; ++w) v = P::gadd(v, red[w][threadIdx.x]);
+    partial[(long long)blockIdx.x * nb + threadIdx.x] = v;
+  }
+}
+
+template <class P>
+cudaError_t ritz_row_p(long long L, SegV V, SegV W, int g, const void* Y, const void* theta, void* X, void* R,
+                       long long ldb, int nb, const void* dscale, void* T, void* partial, int max_blocks,
+                       int* nblocks, cudaStream_t st) {
+  using S = typename P::S;
+  using C = typename P::C;
+  using G = typename P::G;
+  constexpr int WW = (int)(16 / sizeof(S));
+  const bool vec = reinterpret_cast<uintptr_t>(V.p) % 16 == 0 && reinterpret_cast<uintptr_t>(W.p) % 16 == 0 &&
+                   (V.ld * sizeof(S)) % 16 == 0 && g % WW == 0;
+  const S* vp = reinterpret_cast<const S*>(V.p);
+  const S* wp = reinterpret_cast<const S*>(W.p);
+  const C* yp = reinterpret_cast<const C*>(Y);
+  const C* tp = reinterpret_cast<const C*>(theta);
+  S* xp = reinterpret_cast<S*>(X);
+  S* rp = reinterpret_cast<S*>(R);
+  const S* dp = reinterpret_cast<const S*>(dscale);
+  S* tq = reinterpret_cast<S*>(T);
+  G* pd = reinterpret_cast<G*>(partial);
+#define RITZR(TPRV)                                                                                                \
+  {                                                                                                                \
+    long long grid = (L + kThreads / TPRV - 1) / (kThreads / TPRV);                                                \
+    if (grid > max_blocks) grid = max_blocks;                                                                      \
+    if (grid < 1) grid = 1;                                                                                        \
+    *nblocks = (int)grid;                                                                                          \
+    if (vec)                                                                                                       \
+      k_ritz_row<P, TPRV, true><<<(int)grid, kThreads, 0, st>>>(L, vp, wp, V.ld, g, yp, tp, xp, rp, ldb, nb, dp,   \
+                                                                 tq, pd);                                          \
+    else                                                                                                           \
+      k_ritz_row<P, TPRV, false><<<(int)grid, kThreads, 0, st>>>(L, vp, wp, V.ld, g, yp, tp, xp, rp, ldb, nb, dp,  \
+                                                                  tq, pd);                                         \
+    return cudaGetLastError();                                                                                     \
+  }
+  if (nb <= 4) RITZR(1)
+  if (nb <= 8) RITZR(2)
+#undef RITZR
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_ritz_residual(int prec, long long L, SegV V, SegV W, int g, const void* Y, const void* theta,
                                  void* X, void* R, long long ldb, int nb, const void* dscale, void* T,
                                  void* norm_partial, int max_blocks, int* nblocks, cudaStream_t st) {
   if (g < 1 || nb < 1) return cudaErrorInvalidValue;
+  if (g <= kRowCombP && nb <= 8 && V.ld == W.ld) {
+    PHSVDS_DISPATCH(prec, ritz_row_p<P>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial, max_blocks,
+                                        nblocks, st))
+  }
   {
     SegV vw[2] = {SegV{V.p, V.ld, g}, SegV{W.p, W.ld, g}};
     TileDesc TD;
@@ -1440,39 +1597,6 @@ cudaError_t launch_to_bf16(long long n, const float* x, uint16_t* y, int* flags,
 // largest magnitude in rows [r0, r0 + len) (lowest index on ties) is made
 // positive by scaling the whole column (rows [0, rows)).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_col_sign(long long rows, long long ld, long long r0, long long len,
-                                                       double* __restrict__ X) {
-  __shared__ double sv[kThreads];
-  __shared__ long long si[kThreads];
-  double* col = X + blockIdx.x * ld;
-  double best = -1.0;
-  long long bi = -1;
-  for (long long r = threadIdx.x; r < len; r += kThreads) {
-    const double a = fabs(col[r0 + r]);
-    if (a > best) {  // strictly larger: the first index of a tie stays
-      best = a;
-      bi = r;
-    }
-  }
-  sv[threadIdx.x] = best;
-  si[threadIdx.x] = bi;
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      const double a = sv[threadIdx.x + w];
-      const long long ia = si[threadIdx.x + w];
-      if (ia >= 0 && (a > sv[threadIdx.x] || (a == sv[threadIdx.x] && (si[threadIdx.x] < 0 || ia < si[threadIdx.x])))) {
-        sv[threadIdx.x] = a;
-        si[threadIdx.x] = ia;
-      }
-    }
-    __syncthreads();
-  }
-  const bool flip = si[0] >= 0 && col[r0 + si[0]] < 0.0;
-  if (!flip) return;
-  for (long long r = threadIdx.x; r < rows; r += kThreads) col[r] = -col[r];
-}
-
 // Out[:, jj] = X[r0 : r0 + len, perm[jj]] for jj < k (column-major, ld len):
 // the returned block in the caller's column order, contiguous.
 __global__ void k_gather_cols(long long len, int k, const double* __restrict__ X, long long ldx, long long r0,
@@ -1492,11 +1616,89 @@ cudaError_t launch_gather_cols(long long len, int k, const double* X, long long 
   return cudaGetLastError();
 }
 
-cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
+// phase 1: per (row chunk, column) the largest |x| and its lowest index
+__global__ void __launch_bounds__(kThreads) k_col_absmax(long long ld, long long r0, long long len, int chunks,
+                                                         const double* __restrict__ X, double* __restrict__ pv,
+                                                         long long* __restrict__ pi) {
+  __shared__ double sv[kThreads];
+  __shared__ long long si[kThreads];
+  const int j = blockIdx.y, c = blockIdx.x;
+  const long long per = (len + chunks - 1) / chunks;
+  const long long a = (long long)c * per, b = a + per < len ? a + per : len;
+  const double* col = X + j * ld + r0;
+  double best = -1.0;
+  long long bi = -1;
+  for (long long r = a + threadIdx.x; r < b; r += kThreads) {
+    const double v = fabs(col[r]);
+    if (v > best) {  // strictly larger: the first index of a tie stays
+      best = v;
+      bi = r;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double v = sv[threadIdx.x + w];
+      const long long iv = si[threadIdx.x + w];
+      if (iv >= 0 && (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && (si[threadIdx.x] < 0 || iv < si[threadIdx.x])))) {
+        sv[threadIdx.x] = v;
+        si[threadIdx.x] = iv;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[(long long)j * chunks + c] = sv[0];
+    pi[(long long)j * chunks + c] = si[0];
+  }
+}
+
+// phase 2: chunks in order (a later chunk wins only when strictly larger), sign
+__global__ void k_col_sign_pick(long long ld, long long r0, int k, int chunks, const double* __restrict__ X,
+                                const double* __restrict__ pv, const long long* __restrict__ pi,
+                                double* __restrict__ sign) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double best = -1.0;
+  long long bi = -1;
+  for (int c = 0; c < chunks; ++c) {
+    const long long i = pi[(long long)j * chunks + c];
+    if (i >= 0 && pv[(long long)j * chunks + c] > best) {
+      best = pv[(long long)j * chunks + c];
+      bi = i;
+    }
+  }
+  sign[j] = (bi >= 0 && X[j * ld + r0 + bi] < 0.0) ? -1.0 : 1.0;
+}
+
+// phase 3: X[:, j] *= sign[j]
+__global__ void k_col_flip(long long rows, long long ld, int k, const double* __restrict__ sign, double* __restrict__ X) {
+  const long long total = rows * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / rows);
+    const long long r = e % rows;
+    if (sign[j] < 0.0) X[j * ld + r] = -X[j * ld + r];
+  }
+}
+
+cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X, double* work,
                             cudaStream_t st) {
   if (k <= 0 || rows <= 0) return cudaSuccess;
-  k_col_sign<<<k, kThreads, 0, st>>>(rows, ld, r0, len, X);
+  const int chunks = (int)std::max<long long>(1, std::min<long long>(256, (len + 65535) / 65536));
+  double* pv = work;
+  long long* pi = reinterpret_cast<long long*>(work + (size_t)k * chunks);
+  double* sign = work + (size_t)2 * k * chunks;
+  k_col_absmax<<<dim3(chunks, k), kThreads, 0, st>>>(ld, r0, len, chunks, X, pv, pi);
+  k_col_sign_pick<<<(k + 127) / 128, 128, 0, st>>>(ld, r0, k, chunks, X, pv, pi, sign);
+  k_col_flip<<<persistent_grid(rows * k, kThreads), kThreads, 0, st>>>(rows, ld, k, sign, X);
   return cudaGetLastError();
+}
+
+size_t col_sign_work_doubles(int k, long long len) {
+  const int chunks = (int)std::max<long long>(1, std::min<long long>(256, (len + 65535) / 65536));
+  return (size_t)2 * k * chunks + k;
 }
 
 cudaError_t launch_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out, cudaStream_t st) {

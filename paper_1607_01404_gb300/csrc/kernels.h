@@ -123,8 +123,10 @@ cudaError_t launch_to_bf16(long long n, const float* x, uint16_t* y, int* flags,
 // Sign convention of the returned vectors: column j of the column-major block
 // X (rows x k, ld) is negated when its largest-magnitude entry in rows
 // [r0, r0 + len) (lowest index on ties) is negative.
-cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X,
+cudaError_t launch_col_sign(long long rows, long long ld, int k, long long r0, long long len, double* X, double* work,
                             cudaStream_t st);
+// doubles of `work` that launch_col_sign needs
+size_t col_sign_work_doubles(int k, long long len);
 // Out (len x k, column-major, contiguous) = rows [r0, r0 + len) of the columns
 // perm[0..k) of the column-major X (ld ldx); perm is a device int array.
 cudaError_t launch_gather_cols(long long len, int k, const double* X, long long ldx, long long r0, const int* perm,
