@@ -295,3 +295,17 @@ def test_bf16_exact_values_on_a_grid():
     r = B.svds(A, 5, "smallest", 1e-10, maxBlockSize=2, stage1_precision=B.SVDS_BF16)
     s = np.sort(np.linalg.svd(A.to_scipy().toarray(), compute_uv=False))[:5]
     np.testing.assert_allclose(r["sigma"], s, rtol=1e-10)
+
+
+@pytest.mark.parametrize("method", [B.SVDS_GDPK, B.SVDS_JDQMR])
+def test_many_triplets(method):
+    """A larger k (basis sizes grow with k + b): the 40 smallest triplets of a 2D
+    grid against the closed form."""
+    A = wl.grid_difference(24, 2)
+    s = _grid_sigma(24, 2)
+    r = B.svds(A, 40, "smallest", 1e-10, maxBlockSize=4, method_stage1=method, stage1_precision=B.SVDS_FP32,
+               maxMatvecs=2000000)
+    assert r["nconv"] == 40
+    np.testing.assert_allclose(r["sigma"], s[:40], rtol=1e-9)
+    normA = s[-1]
+    assert np.all(r["rnorm"] <= 1.0001e-10 * normA)
