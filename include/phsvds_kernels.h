@@ -43,6 +43,16 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t *row
  * flags[0] (device int) |= 1 when some value is not exactly representable. */
 int phsvds_to_bf16(int64_t nnz, const float *v32, uint16_t *v16, int *flags, void *stream);
 
+/* Orthonormalise the block T (L x nb, ld ldt, in place) against the orthonormal
+ * basis V (L x g, ld ldv) by the solver's device-side CGS2 + CholQR2 (Sec. 3.2,
+ * Sec. 4.4): T <- (I - V V^T)^2 T, then Cholesky-QR twice, the small Cholesky
+ * and triangular steps on the device (FP64).  Blocks in the storage of mode
+ * prec; 1 <= nb <= 8, 1 <= g, g + nb <= 256.  *status (host, may be NULL) is 0,
+ * or nonzero when a Cholesky factor broke down (rank-deficient block; the
+ * solver then replaces columns on the host path).  Allocates its own scratch. */
+int phsvds_ortho(int prec, int64_t L, const void *V, int64_t ldv, int g, void *T, int64_t ldt, int nb, int *status,
+                 void *stream);
+
 /* JDQMR inner solve (Sec. 3.4): for each of the nb columns j, block symmetric
  * QMR on the correction equation
  *     (I - x_j x_j^T)(K - eta_j I)(I - x_j x_j^T) t_j = b_j,   t_j orthogonal to x_j,

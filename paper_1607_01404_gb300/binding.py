@@ -91,6 +91,8 @@ _SIGS = {
     "phsvds_spmm_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
     "phsvds_to_bf16": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_ortho": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                               C.POINTER(C.c_int), C.c_void_p]),
     "phsvds_jd_solve": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                   C.c_double, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
@@ -291,6 +293,14 @@ def spmm_bf16(rows, cols, rowptr, colidx, v16, X, ldx, Y, ldy, b, stream=None):
     _check(lib().phsvds_spmm_bf16(rows, cols, int(colidx.numel()), rowptr.data_ptr(), colidx.data_ptr(),
                                   v16.data_ptr(), X.data_ptr(), ldx, Y.data_ptr(), ldy, b, _stream(stream)),
            "phsvds_spmm_bf16")
+
+
+def ortho(prec, L, V, ldv, g, T, ldt, nb, stream=None):
+    """In-place CGS2 + CholQR2 of T against V (device blocks); returns the breakdown status."""
+    status = C.c_int(0)
+    _check(lib().phsvds_ortho(prec, L, V.data_ptr(), ldv, g, T.data_ptr(), ldt, nb, C.byref(status), _stream(stream)),
+           "phsvds_ortho")
+    return status.value
 
 
 def jd_solve(prec, n, rowptr, colidx, v32, v32lo, v64, nb, X, Bv, eta, dinv, maxit, xi, T, stream=None):

@@ -313,6 +313,13 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t* row
   return 0;
 }
 
+int phsvds_ortho(int prec, int64_t L, const void* V, int64_t ldv, int g, void* T, int64_t ldt, int nb, int* status,
+                 void* stream) {
+  if (!prec_ok(prec) || L < 1 || !V || !T || g < 1 || nb < 1 || nb > 8 || g + nb > 256 || ldv < g || ldt < nb)
+    return SVDS_ERR_ARG;
+  return ortho_block(prec, L, V, ldv, g, T, ldt, nb, status, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int phsvds_jd_solve(int prec, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
                     const float* v32, const float* v32lo, const double* v64, int nb, const void* X, const void* Bv,
                     const double* eta, const void* dinv, int maxit, double xi, void* T, int* steps, void* stream) {

@@ -1087,6 +1087,53 @@ const char* last_error_cstr() { return g_last_error.c_str(); }
 // ===========================================================================
 // Algorithm 1
 // ===========================================================================
+// The device-side CGS2 + CholQR2 of the solver on caller buffers, with its own
+// scratch (the kernel-level entry point phsvds_ortho).
+int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void* T, long long ldt, int nb,
+                int* status, cudaStream_t st) {
+  Ctx c;
+  c.st = st;
+  c.maxblk = gram_default_blocks();
+  std::vector<void*> mem;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.push_back(p);
+    return p;
+  };
+  auto done = [&](int code) {
+    cudaStreamSynchronize(st);
+    for (void* p : mem) cudaFree(p);
+    return code;
+  };
+  c.partial = take(gram_partial_bytes(c.maxblk, 256, 8));
+  c.dGo = static_cast<double*>(take(sizeof(double) * 264 * 8));
+  c.dwork = static_cast<double*>(take(sizeof(double) * 128));
+  for (int i = 0; i < 4; ++i) c.dco[i] = take(sizeof(double) * 264 * 8);
+  c.dstatus = static_cast<int*>(take(256));
+  if (!c.partial || !c.dGo || !c.dwork || !c.dco[0] || !c.dco[1] || !c.dco[2] || !c.dco[3] || !c.dstatus)
+    return done(SVDS_ERR_NOMEM);
+  try {
+    CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), st));
+    ortho_dev(c, prec, L, SegV{V, ldv, g}, T, ldt, nb, nullptr, 0);
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, c.dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status) *status = hs;
+  } catch (const CudaFail& f) {
+    set_last_error(std::string(cudaGetErrorString(f.e)) + " at " + f.where);
+    cudaGetLastError();
+    return done(SVDS_ERR_CUDA);
+  } catch (const NumFail& f) {
+    set_last_error(f.what);
+    return done(SVDS_ERR_NUMERIC);
+  }
+  return done(SVDS_OK);
+}
+
 int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* Uout, double* Vout, double* rnorm,
           int* numConverged, svds_stats* stats) {
   const auto tstart = Clock::now();

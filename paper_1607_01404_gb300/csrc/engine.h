@@ -104,4 +104,6 @@ namespace phsvds {
 int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* U, double* V, double* rnorm,
           int* numConverged, svds_stats* stats);
 void set_last_error(const std::string& s);
+int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void* T, long long ldt, int nb,
+                int* status, cudaStream_t st);
 }  // namespace phsvds

@@ -229,3 +229,25 @@ def test_spmm_bf16_values_match_oracle(b):
         Aabs.data = np.abs(Aabs.data)
         norm = np.abs(Aabs @ np.abs(X)).max()
         assert np.abs(Y - ref).max() / norm <= TOL[B.PREC_F32], A.name
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("g,nb", [(7, 4), (33, 4), (20, 1), (12, 8)])
+def test_device_ortho_matches_oracle(prec, g, nb):
+    """Device CGS2 + CholQR2 of a block against an orthonormal basis: the unique
+    Q of T = V C + Q R (R with positive diagonal), as the oracle computes it."""
+    L = 30011
+    rng = np.random.default_rng(g * 10 + nb)
+    V = np.linalg.qr(rng.standard_normal((L, g)))[0]
+    T = rng.standard_normal((L, nb)) + V @ rng.standard_normal((g, nb))  # with components along V
+    ldv, ldt = _ld(g, True), _ld(nb, True)
+    Vd, Td = to_device(prec, V, ld=ldv), to_device(prec, T, ld=ldt)
+    Vs, Ts = to_host(prec, Vd, L, ldv)[:, :g], to_host(prec, Td, L, ldt)[:, :nb]
+    status = B.ortho(prec, L, Vd, ldv, g, Td, ldt, nb)
+    Q = to_host(prec, Td, L, ldt)[:, :nb]
+    ref = oracle.orthonormalize(Ts, Vs)
+    tol = 2e-5 if prec == B.PREC_F32 else 1e-11
+    assert status == 0
+    assert np.abs(Q - ref).max() <= tol, np.abs(Q - ref).max()
+    assert np.abs(Q.T @ Q - np.eye(nb)).max() <= tol
+    assert np.abs(Vs.T @ Q).max() <= tol
