@@ -43,6 +43,19 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t *row
  * flags[0] (device int) |= 1 when some value is not exactly representable. */
 int phsvds_to_bf16(int64_t nnz, const float *v32, uint16_t *v16, int *flags, void *stream);
 
+/* The operator apply of a JDQMR inner step fused with its dot products: for a
+ * square CSR K (n x n, value arrays as phsvds_spmm), W = K X (X: ld ldx) and,
+ * per column j < nb, dots = [x_j^T w_j, q_j^T w_j, x_j^T q_j, q_j^T q_j] with
+ * x = E1, q = E2 (row-major n x nb blocks, ld nb); dots: device doubles laid
+ * out [4][nb].  nb in {1, 2, 4, 8}; W, E1, E2 and X 16-byte aligned with 16-byte
+ * rows when nb * element >= 16 (SVDS_ERR_ARG otherwise).  scratch: device,
+ * phsvds_spmm_dots_scratch_bytes(nb) bytes. */
+int phsvds_spmm_dots(int prec, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                     const float *v32, const float *v32lo, const double *v64, int nb, const void *X, int64_t ldx,
+                     void *W, const void *E1, const void *E2, double *dots, void *scratch, size_t scratch_bytes,
+                     void *stream);
+size_t phsvds_spmm_dots_scratch_bytes(int nb);
+
 /* Orthonormalise the block T (L x nb, ld ldt, in place) against the orthonormal
  * basis V (L x g, ld ldv) by the solver's device-side CGS2 + CholQR2 (Sec. 3.2,
  * Sec. 4.4): T <- (I - V V^T)^2 T, then Cholesky-QR twice, the small Cholesky

@@ -91,6 +91,10 @@ _SIGS = {
     "phsvds_spmm_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
     "phsvds_to_bf16": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phsvds_spmm_dots": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "phsvds_spmm_dots_scratch_bytes": (C.c_size_t, [C.c_int]),
     "phsvds_ortho": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                C.POINTER(C.c_int), C.c_void_p]),
     "phsvds_jd_solve": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -293,6 +297,18 @@ def spmm_bf16(rows, cols, rowptr, colidx, v16, X, ldx, Y, ldy, b, stream=None):
     _check(lib().phsvds_spmm_bf16(rows, cols, int(colidx.numel()), rowptr.data_ptr(), colidx.data_ptr(),
                                   v16.data_ptr(), X.data_ptr(), ldx, Y.data_ptr(), ldy, b, _stream(stream)),
            "phsvds_spmm_bf16")
+
+
+def spmm_dots_scratch_bytes(nb):
+    return int(lib().phsvds_spmm_dots_scratch_bytes(nb))
+
+
+def spmm_dots(prec, n, rowptr, colidx, v32, v32lo, v64, nb, X, ldx, W, E1, E2, dots, scratch, stream=None):
+    """W = K X fused with the four dot products of a JDQMR step (torch CUDA tensors)."""
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    _check(lib().phsvds_spmm_dots(prec, n, int(colidx.numel()), ptr(rowptr), ptr(colidx), ptr(v32), ptr(v32lo),
+                                  ptr(v64), nb, ptr(X), ldx, ptr(W), ptr(E1), ptr(E2), ptr(dots), ptr(scratch),
+                                  scratch.numel() * scratch.element_size(), _stream(stream)), "phsvds_spmm_dots")
 
 
 def ortho(prec, L, V, ldv, g, T, ldt, nb, stream=None):

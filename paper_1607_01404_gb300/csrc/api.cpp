@@ -313,6 +313,31 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t* row
   return 0;
 }
 
+size_t phsvds_spmm_dots_scratch_bytes(int nb) { return (size_t)2048 * 4 * (nb > 0 ? nb : 1) * 8; }
+
+int phsvds_spmm_dots(int prec, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                     const float* v32, const float* v32lo, const double* v64, int nb, const void* X, int64_t ldx,
+                     void* W, const void* E1, const void* E2, double* dots, void* scratch, size_t scratch_bytes,
+                     void* stream) {
+  if (!prec_ok(prec) || n < 1 || nnz < 0 || !(nb == 1 || nb == 2 || nb == 4 || nb == 8) || !rowptr || !X || !W ||
+      !E1 || !E2 || !dots || !scratch || scratch_bytes < phsvds_spmm_dots_scratch_bytes(nb) || ldx < nb)
+    return SVDS_ERR_ARG;
+  if (nnz > 0 && (!colidx || (prec == kF64 ? !v64 : !v32))) return SVDS_ERR_ARG;
+  CsrDev K;
+  K.rows = n;
+  K.cols = n;
+  K.nnz = nnz;
+  K.rowptr = rowptr;
+  K.colidx = colidx;
+  K.v32 = v32;
+  K.v32lo = v32lo;
+  K.v64 = v64;
+  int ready = 0;
+  CKR(qmr_op_dots(prec, n, nb, K, X, ldx, W, E1, E2, scratch, dots, nullptr, nullptr, nullptr, &ready,
+                  reinterpret_cast<cudaStream_t>(stream)));
+  return ready ? SVDS_OK : SVDS_ERR_ARG;
+}
+
 int phsvds_ortho(int prec, int64_t L, const void* V, int64_t ldv, int g, void* T, int64_t ldt, int nb, int* status,
                  void* stream) {
   if (!prec_ok(prec) || L < 1 || !V || !T || g < 1 || nb < 1 || nb > 8 || g + nb > 256 || ldv < g || ldt < nb)

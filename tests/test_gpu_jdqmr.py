@@ -67,3 +67,43 @@ def test_inner_solve_stops_on_the_relative_tolerance():
     s_tight = B.jd_solve(B.PREC_DF64, n, d["rp"], d["ci"], d["v32"], lo, d["v64"], 4, Xd, Bd, eta, None, 600, 1e-10,
                          Td)
     assert 0 < s_loose < s_tight <= 600
+
+
+@pytest.mark.parametrize("prec", [B.PREC_F32, B.PREC_DF64, B.PREC_F64])
+@pytest.mark.parametrize("nb", [1, 2, 4, 8])
+@pytest.mark.parametrize("wide", [False, True])
+def test_fused_operator_and_dots_match_fp64(prec, nb, wide):
+    """W = K X with the four dot products of one inner step, E1 = x, E2 = q:
+    [x^T w, q^T w, x^T q, q^T q] per column, against FP64 on the stored inputs."""
+    torch, dev = torch_dev()
+    A = wl.weighted_grid(41, 2, seed=nb)  # n = 1681: several CTAs and a ragged last one
+    S = A.to_scipy()
+    C = (S.T @ S).tocsr()
+    C.sort_indices()
+    n = C.shape[0]
+    K = wl.CSR(n, n, C.indptr.astype(np.int32), C.indices.astype(np.int32), C.data, "C")
+    d = csr_device(K)
+    rng = np.random.default_rng(nb + 10 * wide)
+    ldx = 2 * nb if wide else nb
+    Xd = to_device(prec, rng.standard_normal((n, ldx)))
+    E1d = to_device(prec, rng.standard_normal((n, nb)))
+    E2d = to_device(prec, rng.standard_normal((n, nb)))
+    X = to_host(prec, Xd, n, ldx)[:, :nb]
+    E1, E2 = to_host(prec, E1d, n, nb), to_host(prec, E2d, n, nb)
+    Wd = to_device(prec, np.zeros((n, nb)))
+    dots = torch.zeros(4 * nb, dtype=torch.float64, device=dev)
+    scratch = torch.zeros(B.spmm_dots_scratch_bytes(nb), dtype=torch.uint8, device=dev)
+    B.spmm_dots(prec, n, d["rp"], d["ci"], d["v32"], None if d["exact"] else d["v32lo"], d["v64"], nb, Xd, ldx,
+                Wd, E1d, E2d, dots, scratch)
+    W = to_host(prec, Wd, n, nb)
+    ref = C @ X
+    norm = np.abs(abs(C) @ np.abs(X)).max()
+    tw = 2e-6 if prec == B.PREC_F32 else 1e-13
+    assert np.abs(W - ref).max() <= tw * norm
+    got = dots.cpu().numpy().reshape(4, nb)
+    Ws = W  # the dots use the stored W
+    want = np.array([np.sum(E1 * Ws, 0), np.sum(E2 * Ws, 0), np.sum(E1 * E2, 0), np.sum(E2 * E2, 0)])
+    scale = np.array([np.sum(np.abs(E1 * Ws), 0), np.sum(np.abs(E2 * Ws), 0), np.sum(np.abs(E1 * E2), 0),
+                      np.sum(E2 * E2, 0)])
+    td = 2e-5 if prec == B.PREC_F32 else 1e-13
+    assert np.all(np.abs(got - want) <= td * scale), np.abs(got - want) / scale
