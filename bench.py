@@ -285,10 +285,12 @@ def run_gpu(args, world, rank, local):
     def opts(form, seed):
         kw = dict(maxBlockSize=BLOCK, stage1_polish=1, precond=B.SVDS_PRECOND_JACOBI, seed=seed, stream=sp,
                   maxSeconds=600.0)
-        if form == "chosen":
+        if form in ("chosen", "dynamic"):
             kw.update(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_FP32, precond=B.SVDS_PRECOND_LEARNED,
                       precondModel=os.path.join(MODELS, "wgrid3d.bin"))
+            if form == "dynamic":
+                kw.update(method_stage1=B.SVDS_DYNAMIC)
         elif form == "plain":
             kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_FP64)
@@ -345,6 +347,10 @@ def run_gpu(args, world, rank, local):
     relerr_p = float(np.max(np.abs(lastp[0] - exact) / exact))
     t_gdk, st_gdk, lastg = timed("gdk", 1, 700 + 1000 * rank)
     relerr_g = float(np.max(np.abs(lastg[0] - exact) / exact))
+    # DYNAMIC stage-1 method in the chosen form (switches GD+k / JDQMR by measured rates)
+    t_dyn, st_dyn, lastd = timed("dynamic", 1, 800 + 1000 * rank)
+    relerr_d = float(np.max(np.abs(lastd[0] - exact) / exact))
+    cond = condest_runs(B, torch, stream, rp, ci, va, A, sp)
     # end to end through host buffers
     torch.cuda.synchronize()
     te0 = time.perf_counter()
@@ -364,8 +370,39 @@ def run_gpu(args, world, rank, local):
     ms_step = max_over_ranks(ms_step, world)
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
                 t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
-                relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h,
+                relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h, t_dyn=t_dyn, st_dyn=st_dyn,
+                relerr_dyn=relerr_d, cond=cond,
                 roof32=roof32, roofdf=roofdf, orth=orth, ms_step=ms_step, A=A, e2e_nconv=oute[4], gain=gain)
+
+
+def condest_runs(B, torch, stream, rp, ci, va, A, sp):
+    """Condition-number estimate (Sec. 5: one largest and one smallest value,
+    block 1, ||r^C|| <= 0.1 |lambda|) on the bench matrix, device-resident CSR,
+    stage 1 with GD+k corrections and an FP32 first phase; kappa of the 128^3
+    grid in closed form."""
+    t = 4 * np.sin(np.array([1, 128]) * np.pi / 258) ** 2
+    kappa = float(np.sqrt(3 * t[1]) / np.sqrt(3 * t[0]))
+    out = {"kappa_exact": kappa}
+    for name, m in (("gdk", B.SVDS_GDPK),):
+        o = B.make_opts(stage1_precision=B.SVDS_FP32, method_stage1=m, precond=B.SVDS_PRECOND_JACOBI, stream=sp,
+                        maxSeconds=300.0)
+        h = B.svds_create(rp, ci, va, A.m, A.n, o, on_device=True)
+        try:
+            smax, smin, kap = B.C.c_double(), B.C.c_double(), B.C.c_double()
+            st = (B.svds_stats * 2)()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = B.lib().svds_condest(h.ptr, 0.1, B.C.byref(smax), B.C.byref(smin), B.C.byref(kap), st)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            h.close()
+        out[name] = dict(seconds=round(e0.elapsed_time(e1) / 1e3, 4), rc=rc, kappa=kap.value,
+                         rel_err=round(abs(kap.value / kappa - 1), 5),
+                         matvecs=int(st[0].matvecs_stage1 + st[1].matvecs_stage1))
+    return out
 
 
 def precond_gain(B, wl, sp):
@@ -531,6 +568,12 @@ def main():
         e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
                  numConverged=res["e2e_nconv"]),
         precond_gain=res["gain"],
+        dynamic=dict(value=res["t_dyn"][0], unit=UNIT, form="chosen form with the DYNAMIC stage-1 method",
+                     outer1=int(res["st_dyn"][0]["outer_stage1"]),
+                     outer1_jdqmr=int(res["st_dyn"][0]["outer_stage1_jdqmr"]),
+                     matvecs=int(res["st_dyn"][0]["matvecs_stage1"] + res["st_dyn"][0]["matvecs_stage2"]),
+                     max_rel_sigma_err=res["relerr_dyn"]),
+        condest=res["cond"],
         gpu_launches=launches,
         clocks=res["clocks"],
     )

@@ -41,6 +41,9 @@ extern "C" {
 #define SVDS_GDPK 0  /* GD+k (generalised Davidson with +k restarting) */
 #define SVDS_JDQMR 1 /* JDQMR: GD+k outer basis, corrections from symmetric QMR on the
                         Jacobi-Davidson correction equation (FP32 inner solves) */
+#define SVDS_DYNAMIC 2 /* stage 1 only: GD+k or JDQMR correction chosen per outer iteration
+                          from the measured reduction of log ||r|| per second of each
+                          (Sec. 3.4: the paper's stage-1 default switches to minimise time) */
 
 #define SVDS_FP64 3  /* FP64-class stage 1 (double-float arithmetic on the GPU) */
 #define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
@@ -79,7 +82,7 @@ typedef struct {
   int maxBasisSize;     /* 0 = default */
   int minRestartSize;   /* 0 = default */
   int maxBlockSize;     /* 0 = 1 */
-  int method_stage1;    /* SVDS_GDPK (default) or SVDS_JDQMR */
+  int method_stage1;    /* SVDS_GDPK (default), SVDS_JDQMR or SVDS_DYNAMIC */
   int method_stage2;    /* SVDS_GDPK (default) or SVDS_JDQMR */
   int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32, SVDS_BF16 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
@@ -103,6 +106,12 @@ typedef struct {
   const char *precondModel;   /* SVDS_PRECOND_LEARNED without precondParams: path of a
                                  parameter file written by phsvds_gnn_save */
   int normalOperator;         /* SVDS_NORMAL_AUTO (default), _TWOPASS or _EXPLICIT */
+  double relTol;              /* > 0: low-accuracy mode of the condition-number estimate (Sec. 5):
+                                 stage 1 stops when ||r^C|| <= relTol |lambda| (or at the floor
+                                 10 u ||C||), stage 2 is not run, and numConverged counts the
+                                 triplets that meet that relative rule; tol is then unused.
+                                 Stage 1 uses GD+k corrections in this mode whatever
+                                 method_stage1 says.  0 (default) = the rules of Algorithm 1 */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -124,6 +133,7 @@ typedef struct {
   double seconds_precond;     /* learned preconditioner: graph of A^T A and network inference */
   int64_t normal_nnz;         /* nonzeros of the explicit C = A^T A, 0 when A then A^T is used */
   double seconds_output;      /* returning the vectors: FP64 conversion, sign convention, copies to U, V */
+  int64_t outer_stage1_jdqmr; /* stage-1 outer iterations whose correction came from JDQMR */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;
@@ -145,12 +155,25 @@ int svds_create(svds_handle **h, const svds_csr *A, const svds_opts *opts);
 int svds_solve(svds_handle *h, int k, int target, double tol, double *sigma, double *U, double *V,
                double *rnorm, int *numConverged, svds_stats *stats);
 
+/* Condition-number estimate (Sec. 5): one largest and one smallest singular
+ * value, block size 1, each stage-1 solve stopped when ||r^C|| <= relTol
+ * |lambda| (relTol = 0.1 in the paper's experiments: a 10% relative error of
+ * the smallest value); the smallest solve uses the largest value as ||A||.
+ * Rayleigh-Ritz values bound the spectrum from inside, so *sigma_max <=
+ * sigma_1, *sigma_min >= sigma_n and *kappa = *sigma_max / *sigma_min never
+ * exceeds the true condition number.  stats: NULL or an array of two (largest,
+ * smallest).  The handle's precision and preconditioner apply; both solves
+ * use GD+k (see relTol) and block size 1.  Returns the
+ * first non-zero status of the two solves (SVDS_ERR_MAXIT: budget exhausted). */
+int svds_condest(svds_handle *h, double relTol, double *sigma_max, double *sigma_min, double *kappa,
+                 svds_stats *stats);
+
 /* Release the handle and its device memory (NULL is accepted). */
 void svds_destroy(svds_handle *h);
 
 /* Static message for an error code. */
 const char *svds_strerror(int code);
-/* Message of the last SVDS_ERR_CUDA in this thread (empty if none). */
+/* Message of the last SVDS_ERR_CUDA or SVDS_ERR_NUMERIC in this thread (empty if none). */
 const char *svds_last_error(void);
 
 #ifdef __cplusplus

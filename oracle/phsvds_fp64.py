@@ -602,3 +602,50 @@ def _finish(A, sig, U, V, out):
     out.update(sigma=np.asarray(sig, dtype=np.float64), U=U, V=V,
                rnorm=triplet_residuals(A, sig, U, V))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Condition-number estimate (Sec. 5)
+# ----------------------------------------------------------------------------
+def condest(A, rel_tol: float = 0.1, *, precond="jacobi", seed=0, max_matvecs=10**9):
+    """Estimate kappa(A) = sigma_max / sigma_min as in the paper's condition-number
+    experiment (Sec. 5): one largest and one smallest singular value, block size
+    one, stage 1 on C stopped as soon as ||r^C|| <= rel_tol |theta| (the paper
+    uses rel_tol = 0.1), no stage 2.  The largest value is found first and then
+    serves as ||A|| for the smallest (reading: the floor of Algorithm 1 line 2
+    becomes 10 eps max(||C||, |theta|), with ||C|| unknown, i.e. |theta|, during
+    the largest solve).  Each solve ends with the Rayleigh-Ritz of Algorithm 1
+    line 4 on its returned vector.  Returns a dict with sigma_max, sigma_min,
+    kappa, the final residual norms ||C v - lambda v|| (rC_max, rC_min) and the
+    two solves' Stats."""
+    A = _as_csr(A)
+    if A.shape[0] < A.shape[1]:
+        A = A.T.tocsr()  # same singular values (Sec. 2.1)
+    n = A.shape[1]
+    rng = np.random.default_rng(seed)
+    opC = lambda Z: apply_C(A, Z)  # noqa: E731
+
+    def solve(target, normC, prec):
+        def conv(theta, x, wx, rn):
+            lam = abs(theta)
+            return rn <= max(rel_tol * lam, FLOOR_C * EPS * max(normC, lam))
+
+        mb, mr = default_sizes(1, 1, target, 1)
+        st = Stats()
+        _, X, st = gdk_rr(opC, n, 1, 1, target, mb, mr, rng.standard_normal((n, 1)), prec, conv, normC, EPS,
+                          max_matvecs, 2, rng, st)
+        x = X[:, :1] / np.linalg.norm(X[:, :1])
+        cx = apply_C(A, x)
+        lam = float(x[:, 0] @ cx[:, 0])
+        return math.sqrt(abs(lam)), float(np.linalg.norm(cx[:, 0] - lam * x[:, 0])), st
+
+    s_max, r_max, st_max = solve("largest", 0.0, lambda R: R.copy())
+    colsq = np.asarray(A.multiply(A).sum(axis=0)).ravel()
+    if precond == "jacobi":
+        dinv = 1.0 / np.where(colsq > 0, colsq, 1.0)
+        prec = lambda R: R * dinv[:, None]  # noqa: E731
+    else:
+        prec = lambda R: R.copy()  # noqa: E731
+    s_min, r_min, st_min = solve("smallest", s_max * s_max, prec)
+    return dict(sigma_max=s_max, sigma_min=s_min, kappa=s_max / s_min if s_min > 0 else math.inf,
+                rC_max=r_max, rC_min=r_min, stats_largest=st_max, stats_smallest=st_min)

@@ -28,6 +28,7 @@ SVDS_LARGEST = 0
 SVDS_SMALLEST = 1
 SVDS_GDPK = 0
 SVDS_JDQMR = 1
+SVDS_DYNAMIC = 2
 SVDS_FP32 = 1
 SVDS_FP64 = 3
 SVDS_NATIVE_FP64 = 4
@@ -56,7 +57,8 @@ class svds_opts(C.Structure):
                 ("printLevel", C.c_int), ("initSize", C.c_int), ("initV", C.c_void_p),
                 ("stream", C.c_void_p), ("innerMaxIt", C.c_int), ("innerRelTol", C.c_double),
                 ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p),
-                ("normalOperator", C.c_int)]
+                ("normalOperator", C.c_int),
+                ("relTol", C.c_double)]
 
 
 class svds_stats(C.Structure):
@@ -68,7 +70,8 @@ class svds_stats(C.Structure):
                 ("seconds_total", C.c_double), ("kernel_launches", C.c_int64),
                 ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
                 ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64),
-                ("seconds_output", C.c_double)]
+                ("seconds_output", C.c_double),
+                ("outer_stage1_jdqmr", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,6 +86,7 @@ _SIGS = {
     "svds_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.POINTER(C.c_int), C.POINTER(svds_stats)]),
     "svds_destroy": (None, [C.c_void_p]),
+    "svds_condest": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "svds_strerror": (C.c_char_p, [C.c_int]),
     "svds_last_error": (C.c_char_p, []),
     "phsvds_spmm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -164,7 +168,7 @@ def exported_symbols() -> list[str]:
 class SvdsError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = lib().svds_strerror(code).decode()
-        extra = lib().svds_last_error().decode() if code == SVDS_ERR_CUDA else ""
+        extra = lib().svds_last_error().decode() if code in (SVDS_ERR_CUDA, SVDS_ERR_NUMERIC) else ""
         super().__init__(f"{where}: {msg} ({code}) {extra}".strip())
         self.code = code
 
@@ -266,6 +270,22 @@ def svds_solve(h: Handle, k: int, target: int, tol: float, want_vectors: bool = 
 
 def svds_destroy(h: Handle):
     h.close()
+
+
+def condest(A, rel_tol: float = 0.1, **opts):
+    """Condition-number estimate (svds_condest): dict with sigma_max, sigma_min,
+    kappa, rc and the stats of the largest and the smallest solve."""
+    o = make_opts(**opts)
+    h = svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, o)
+    try:
+        smax, smin, kap = C.c_double(), C.c_double(), C.c_double()
+        st = (svds_stats * 2)()
+        rc = lib().svds_condest(h.ptr, rel_tol, C.byref(smax), C.byref(smin), C.byref(kap), st)
+        _check(rc, "svds_condest", allow_maxit=True)
+    finally:
+        h.close()
+    return dict(sigma_max=smax.value, sigma_min=smin.value, kappa=kap.value, rc=rc,
+                stats_largest=st[0].as_dict(), stats_smallest=st[1].as_dict())
 
 
 def svds(A, k: int, target: str = "largest", tol: float = 1e-10, **opts):

@@ -180,7 +180,7 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
       o.stage1_precision != SVDS_NATIVE_FP64)
     return SVDS_ERR_ARG;
   if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
-  if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR) ||
+  if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR && o.method_stage1 != SVDS_DYNAMIC) ||
       (o.method_stage2 != SVDS_GDPK && o.method_stage2 != SVDS_JDQMR) || o.innerMaxIt < 0 || o.innerRelTol < 0)
     return SVDS_ERR_ARG;
   if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_FP64) return SVDS_ERR_ARG;
@@ -190,6 +190,7 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
   if (o.normalOperator != SVDS_NORMAL_AUTO && o.normalOperator != SVDS_NORMAL_TWOPASS &&
       o.normalOperator != SVDS_NORMAL_EXPLICIT)
     return SVDS_ERR_ARG;
+  if (!(o.relTol >= 0) || !std::isfinite(o.relTol)) return SVDS_ERR_ARG;
   std::vector<float> gnn_params;
   if (o.precond == SVDS_PRECOND_LEARNED) {
     gnn_params.resize(phsvds_gnn_num_params());
@@ -245,6 +246,35 @@ int svds_solve(svds_handle* h, int k, int target, double tol, double* sigma, dou
   if (h->opts.initSize > 0 && h->A.transposed) return SVDS_ERR_ARG;  // guesses are right vectors of the tall matrix
   cudaSetDevice(h->device);
   return phsvds::solve(h, k, target, tol, sigma, U, V, rnorm, numConverged, stats);
+}
+
+int svds_condest(svds_handle* h, double relTol, double* sigma_max, double* sigma_min, double* kappa,
+                 svds_stats* stats) {
+  if (!h || !sigma_max || !sigma_min || !kappa || !(relTol > 0) || !std::isfinite(relTol)) return SVDS_ERR_ARG;
+  if (h->opts.initSize > 0) return SVDS_ERR_ARG;  // guesses belong to k-triplet solves
+  const svds_opts saved = h->opts;
+  h->opts.relTol = relTol;
+  h->opts.maxBlockSize = 1;
+  h->opts.maxBasisSize = 0;
+  h->opts.minRestartSize = 0;
+  h->opts.aNorm = 0.0;
+  double smax = 0.0, smin = 0.0;
+  int nc = 0;
+  svds_stats st[2] = {};
+  int rc = svds_solve(h, 1, SVDS_LARGEST, relTol, &smax, nullptr, nullptr, nullptr, &nc, &st[0]);
+  if (rc == SVDS_OK) {
+    h->opts.aNorm = smax;
+    rc = svds_solve(h, 1, SVDS_SMALLEST, relTol, &smin, nullptr, nullptr, nullptr, &nc, &st[1]);
+  }
+  h->opts = saved;
+  if (stats) {
+    stats[0] = st[0];
+    stats[1] = st[1];
+  }
+  *sigma_max = smax;
+  *sigma_min = smin;
+  *kappa = smin > 0 ? smax / smin : INFINITY;
+  return rc;
 }
 
 void svds_destroy(svds_handle* h) {

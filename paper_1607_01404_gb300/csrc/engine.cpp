@@ -514,11 +514,107 @@ struct RunCfg {
   const CsrDev* jdK = nullptr;   // the same in the inner mode
   int jd_maxk = 30;
   double jd_xi = 0.1;
+  // DYNAMIC: choose between the two corrections per outer iteration
+  bool dyn = false;
 };
 
 struct RunOut {
   std::vector<double> theta;
   long long outer = 0;
+  long long outer_jd = 0;  // outer iterations whose correction came from JDQMR
+};
+
+// DYNAMIC method of stage 1 (Sec. 3.4: switch between GD+k and JDQMR so as to
+// minimise time).  The paper gives no rule; this one measures.  Progress of
+// an outer iteration is the decrease of log ||r|| summed over the Ritz
+// indices whose residual was computed both at that iteration and at the one
+// before, and it is charged, with the wall time between the two, to the
+// method that made the correction in between.  Schedule: a JDQMR trial of 2
+// outer iterations, a GD+k trial of at least 3 iterations and at least the
+// JDQMR trial's time, then the method with the higher rate for 4 times the
+// trials' time, a re-trial of the other method (its minimum iterations and its
+// last trial time), the better one again for a window twice as long, and so
+// on.  Every iteration stays a valid GD+k iteration, so the choice only
+// affects time, never the returned triplets.
+struct DynState {
+  int cur = 1;    // method of the next correction: 0 GD+k, 1 JDQMR
+  int stage = 0;  // 0 JDQMR trial, 1 GD+k trial, 2 exploit, 3 re-trial
+  int its = 0;
+  double t_win = 0, prog_win = 0;
+  double rate[2] = {0, 0}, trial_t[2] = {0, 0};
+  double exploit_len = 0;
+  double t_last = -1;
+  std::vector<std::pair<int, double>> last;
+  // the window closed by the last choose(), for the iteration log
+  bool closed = false;
+  int closed_m = 0, closed_its = 0;
+  double closed_t = 0;
+
+  void drop() {
+    t_last = -1;
+    last.clear();
+  }
+  void observe(double now, const std::vector<std::pair<int, double>>& res) {
+    if (t_last >= 0) {
+      double prog = 0;
+      for (const auto& a : res)
+        for (const auto& b : last)
+          if (a.first == b.first && a.second > 0 && b.second > 0) prog += std::log(b.second / a.second);
+      t_win += now - t_last;
+      prog_win += prog;
+      ++its;
+    }
+    last = res;
+    t_last = now;
+  }
+  static int min_its(int m) { return m == 1 ? 2 : 3; }
+  int best() const { return rate[0] > rate[1] ? 0 : 1; }
+  void close(int next) {
+    closed = true;
+    closed_m = cur;
+    closed_its = its;
+    closed_t = t_win;
+    rate[cur] = t_win > 0 ? prog_win / t_win : 0.0;
+    cur = next;
+    its = 0;
+    t_win = prog_win = 0;
+  }
+  int choose() {
+    closed = false;
+    switch (stage) {
+      case 0:
+        if (its >= 2) {
+          trial_t[1] = t_win;
+          close(0);
+          stage = 1;
+        }
+        break;
+      case 1:
+        if ((its >= 3 && t_win >= trial_t[1]) || its >= 200) {
+          trial_t[0] = t_win;
+          exploit_len = 4.0 * (trial_t[0] + trial_t[1]);
+          close(0);
+          cur = best();
+          stage = 2;
+        }
+        break;
+      case 2:
+        if (t_win >= exploit_len && its >= min_its(cur)) {
+          close(1 - cur);
+          stage = 3;
+        }
+        break;
+      default:
+        if (its >= min_its(cur) && t_win >= trial_t[cur]) {
+          trial_t[cur] = t_win;
+          close(cur);
+          cur = best();
+          exploit_len *= 2.0;
+          stage = 2;
+        }
+    }
+    return cur;
+  }
 };
 
 void put_block_rm(std::vector<double>& dst, int g, const double* Ycm, int ldy, const std::vector<int>& cols) {
@@ -703,6 +799,8 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
   int nprev = 0;
   int rsr = 0;
   std::vector<double> w, Z;
+  DynState dyn;
+  std::vector<std::pair<int, double>> tested;  // (Ritz index, residual) of this iteration
   while (true) {
     c.budget();
     ++out.outer;
@@ -727,6 +825,7 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       if (!flags[j]) cand.push_back(j);
     size_t ci = 0;
     int nbk = 0;
+    tested.clear();
     auto test_and_compact = [&](const std::vector<int>& take, const std::vector<double>& rn) {
       std::vector<double> th(take.size());
       for (size_t t = 0; t < take.size(); ++t) th[t] = theta[take[t]];
@@ -754,6 +853,7 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       std::vector<int> take;
       while (ci < cand.size() && (int)take.size() < b - nbk) take.push_back(cand[ci++]);
       std::vector<double> rn = ritz_cols(c, B, g, Y, theta, take, nbk);
+      for (size_t t = 0; t < take.size(); ++t) tested.emplace_back(take[t], rn[t]);
       test_and_compact(take, rn);
     }
     bool allflag = ncand == k;
@@ -805,6 +905,15 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       std::fprintf(stderr, "[%s] it %lld g %d conv %d/%d theta0 %.10e minres %.3e mv %lld\n", cfg.name, out.outer, g,
                    nf, k, theta[0], mn, c.mv);
     }
+    bool use_jd = cfg.jd;
+    if (cfg.dyn) {
+      dyn.observe(c.elapsed(), tested);
+      use_jd = dyn.choose() == 1;
+      if (dyn.closed && c.print >= 2)
+        std::fprintf(stderr, "[%s] dynamic: %s window of %d its, %.4f s; rates GD+k %.4g, JDQMR %.4g /s -> %s\n",
+                     cfg.name, dyn.closed_m ? "JDQMR" : "GD+k", dyn.closed_its, dyn.closed_t, dyn.rate[0],
+                     dyn.rate[1], use_jd ? "JDQMR" : "GD+k");
+    }
     // reset of V and W (Sec. 3.2)
     double rmin = 1e300;
     for (double r : rnb) rmin = std::min(rmin, r);
@@ -813,11 +922,13 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       rsr = 0;
       nprev = 0;
       Yprev.clear();
+      dyn.drop();
       continue;
     }
     // correction: JDQMR, or T = M R (learned sparse M, or Jacobi), or T = R
     void* T = B.Rb;
-    if (cfg.jd) {
+    if (use_jd) {
+      ++out.outer_jd;
       std::vector<double> eta(nbk);
       for (int j = 0; j < nbk; ++j) eta[j] = theta[block[j]];
       jd_correction(c, B, cfg, nbk, eta, rnb);
@@ -1204,7 +1315,8 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
         reqs.push_back({&R.Xlock, (size_t)L * k * e});
       }
     };
-    const bool jd1 = o.method_stage1 == SVDS_JDQMR, jd2 = o.method_stage2 == SVDS_JDQMR;
+    const bool dyn1 = o.method_stage1 == SVDS_DYNAMIC;
+    const bool jd1 = o.method_stage1 == SVDS_JDQMR || dyn1, jd2 = o.method_stage2 == SVDS_JDQMR;
     if (lowprec) plan_run(B1a, kF32, n, false, jd1);
     plan_run(B1, p2, n, false, jd1);
     plan_run(B2, p2, L2, smallest, jd2);
@@ -1234,7 +1346,9 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     for (int i = 0; i < 4; ++i) reqs.push_back({&c.dco[i], sizeof(double) * 264 * 8});
     reqs.push_back({(void**)&c.dstatus, 256});
     c.nslots = 64;
-    c.slot_bytes = (size_t)2 * 256 * 256 * 8 / 8;
+    // one slot holds the largest coefficient block: a basis-by-basis restart
+    // matrix of the widest basis (8-byte coefficients)
+    c.slot_bytes = std::max<size_t>((size_t)2 * 256 * 256, ((size_t)(ldv + 8) * (ldv + 8) * 8 + 255) & ~size_t(255));
     reqs.push_back({(void**)&c.dstage, (size_t)c.nslots * c.slot_bytes});
     size_t total = 0;
     for (auto& r : reqs) total += (r.bytes + 255) & ~size_t(255);
@@ -1278,7 +1392,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
 
     // ---- ||A|| (reading: estimate when not given; raised by later Ritz values) ----
     double normA = o.aNorm > 0 ? o.aNorm * A.scale : 0.0;
-    if (normA <= 0) {
+    // relative mode (condition-number estimate, Sec. 5) for the largest value:
+    // no estimate needed, the Ritz value itself gives ||A|| at the end
+    const double relTol = o.relTol;
+    if (normA <= 0 && !(relTol > 0 && !smallest)) {
       // Lanczos (Arnoldi with full reorthogonalisation) on C from a seeded
       // random vector.  theta_max of the projected matrix is a lower bound of
       // ||C||, so the stopping tolerance ||r|| <= tol ||A|| can only get
@@ -1323,10 +1440,14 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.seconds_setup = c.elapsed();
 
     // ---- stage 1 on C (Algorithm 1 lines 1-3) ----
+    // relative mode: ||r^C|| <= relTol |lambda| (Sec. 5), floor 10 u max(||C||, |lambda|)
     auto stage1_conv = [&](double u) {
       return [=](const double* th, const double* rn, int, int nc, char* ok) {
-        for (int j = 0; j < nc; ++j)
-          ok[j] = rn[j] <= std::max(std::sqrt(std::fabs(th[j]) * normC) * tol, 10.0 * u * normC);
+        for (int j = 0; j < nc; ++j) {
+          const double lam = std::fabs(th[j]);
+          ok[j] = relTol > 0 ? rn[j] <= std::max(relTol * lam, 10.0 * u * std::max(normC, lam))
+                             : rn[j] <= std::max(std::sqrt(lam * normC) * tol, 10.0 * u * normC);
+        }
       };
     };
     const bool jac = smallest && o.precond == SVDS_PRECOND_JACOBI;
@@ -1391,7 +1512,11 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.smallest = smallest;
     c1.normop = normC;
     c1.b0 = b0;
-    c1.jd = jd1;
+    // the relative mode (block 1, loose stop) keeps GD+k corrections: JDQMR
+    // corrections there can settle on an interior eigenvalue (Sec. 5 notes the
+    // risk of missing the extreme pair at low accuracy)
+    c1.jd = jd1 && !dyn1 && !(relTol > 0);
+    c1.dyn = dyn1 && !(relTol > 0);
     c1.jd_prec = jd_prec;
     c1.jdinv = jac ? (jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1)) : nullptr;
     c1.jd_maxk = jd_maxk;
@@ -1411,6 +1536,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c1.name = "stage1-fp32";
       RunOut ra = run_gdk_rr(c, B1a, c1, X1a, kk);
       S.outer_stage1 += ra.outer;
+      S.outer_stage1_jdqmr += ra.outer_jd;
       S.matvecs_stage1_lowprec = c.mv - mv0;
       // hand the FP32 Ritz vectors to the FP64-class phase
       double* dtmp = reinterpret_cast<double*>(dout);
@@ -1432,6 +1558,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c1.name = "stage1";
       RunOut r1 = run_gdk_rr(c, B1, c1, X1, kk);
       S.outer_stage1 += r1.outer;
+      S.outer_stage1_jdqmr += r1.outer_jd;
       lam = r1.theta;
     }
     // ---- Algorithm 1 lines 4-5: Rayleigh-Ritz on the returned vectors ----
@@ -1448,22 +1575,25 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       lk[j] = wk[src];
       std::memcpy(&Yk[(size_t)j * k], &Zk[(size_t)src * k], sizeof(double) * k);
     }
-    std::vector<double> Ykr = rowmajor(k, k, Yk.data(), k);
-    const void* dY = c.upload(p2, Ykr.data(), Ykr.size());
-    const void* dth = c.upload(p2, lk.data(), lk.size());
-    int nbl = 0;
-    // v = x (top n rows of Xfin), r^C = C x - lambda x
-    CK(launch_ritz_residual(p2, n, SegV{X1, kk, k}, SegV{CX, kk, k}, k, dY, dth, Xfin, R2, kk, k, nullptr, nullptr,
-                            c.partial, c.maxblk, &nbl, c.st));
-    CK(launch_gram_reduce(p2, c.partial, nbl, k, c.dG, c.st));
-    c.launches += 2;
-    CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * k, cudaMemcpyDeviceToHost, c.st));
-    c.sync();
     std::vector<double> rC(k), sig(k);
-    for (int j = 0; j < k; ++j) {
-      rC[j] = std::sqrt(std::max(c.hG[j], 0.0));
-      sig[j] = std::sqrt(std::fabs(lk[j]));
+    // v = x (top n rows of Xfin), r^C = C x - lambda x, in blocks of up to 8 Ritz vectors
+    for (int c0 = 0; c0 < k; c0 += 8) {
+      const int w = std::min(8, k - c0);
+      std::vector<double> Ych((size_t)k * w);  // rows of Yk, columns c0 .. c0 + w (row-major)
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < w; ++j) Ych[(size_t)i * w + j] = Yk[(size_t)(c0 + j) * k + i];
+      const void* dY = c.upload(p2, Ych.data(), Ych.size());
+      const void* dth = c.upload(p2, lk.data() + c0, w);
+      int nbl = 0;
+      CK(launch_ritz_residual(p2, n, SegV{X1, kk, k}, SegV{CX, kk, k}, k, dY, dth, off(Xfin, c0, p2), off(R2, c0, p2),
+                              kk, w, nullptr, nullptr, c.partial, c.maxblk, &nbl, c.st));
+      CK(launch_gram_reduce(p2, c.partial, nbl, w, c.dG, c.st));
+      c.launches += 2;
+      CK(cudaMemcpyAsync(c.hG, c.dG, sizeof(double) * w, cudaMemcpyDeviceToHost, c.st));
+      c.sync();
+      for (int j = 0; j < w; ++j) rC[c0 + j] = std::sqrt(std::max(c.hG[j], 0.0));
     }
+    for (int j = 0; j < k; ++j) sig[j] = std::sqrt(std::fabs(lk[j]));
     for (int j = 0; j < k; ++j) normA = std::max(normA, smallest ? 0.0 : sig[j]);
     // u = A v / sigma (bottom m rows of Xfin)
     void* Ufin = off(Xfin, n * kk, p2);
@@ -1512,6 +1642,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.seconds_stage1 = c.elapsed() - t1;
     bool all_ok = true;
     for (int j = 0; j < k; ++j) all_ok = all_ok && res[j] < normA * tol;
+    if (relTol > 0) all_ok = true;  // the relative mode stops after stage 1
     void* Xres = Xfin;
     if (!all_ok) {
       // ---- stage 2 on B (Algorithm 1 lines 9-20) ----
@@ -1658,7 +1789,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       const int j = order[jj];
       sigma[jj] = sig[j] / A.scale;
       if (rnorm) rnorm[jj] = res[j] / A.scale;
-      if (prefix && res[j] < normA * tol)
+      const bool ok = relTol > 0 ? rC[j] <= std::max(relTol * std::fabs(lk[j]),
+                                                      10.0 * unit_roundoff(p2) * std::max(normA * normA, std::fabs(lk[j])))
+                                 : res[j] < normA * tol;
+      if (prefix && ok)
         ++nconv;
       else
         prefix = false;

@@ -502,8 +502,29 @@ __global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const ty
 // for ND = 4, d2 = E1^T E2, d3 = E2^T E2 (per column, FP64-class partials).
 // With (E1, E2) = (x, q) these are the four dots of k_qmr_dots1 for w = op q;
 // with (E1, E2) = (r, x) the two dots of k_qmr_dots_u for u = K^-1 r.
+// Tuning of k_spmm_dots: CTAs per SM the register allocation must allow
+// (0 = no bound), and the number of row gathers a thread keeps in flight (0 =
+// spmm_unroll).  The gathers are latency-bound: 6 CTAs of 256 threads per SM
+// (at most 40 registers, a few spilled) with 2 gathers in flight beat 4 CTAs
+// with 4 gathers on the 7-nonzero rows of a 3D-grid A^T A.
+#ifndef PHSVDS_DOTS_MINB
+#define PHSVDS_DOTS_MINB 6
+#endif
+#if PHSVDS_DOTS_MINB > 0
+#define PHSVDS_DOTS_BOUNDS __launch_bounds__(kT, PHSVDS_DOTS_MINB)
+#else
+#define PHSVDS_DOTS_BOUNDS __launch_bounds__(kT)
+#endif
+#ifndef PHSVDS_DOTS_U
+#define PHSVDS_DOTS_U 2
+#endif
+template <class P, int NB>
+__host__ __device__ constexpr int dots_unroll() {
+  return PHSVDS_DOTS_U > 0 ? PHSVDS_DOTS_U : spmm_unroll<P, NB>();
+}
+
 template <class P, int NB, int VMODE, bool VEC, int ND>
-__global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __restrict__ rowptr,
+__global__ void PHSVDS_DOTS_BOUNDS k_spmm_dots(long long L, const int* __restrict__ rowptr,
                                                   const int* __restrict__ colidx, const float* __restrict__ v32,
                                                   const float* __restrict__ v32lo, const double* __restrict__ v64,
                                                   const typename P::S* __restrict__ X, long long ldx,
@@ -521,7 +542,7 @@ __global__ void __launch_bounds__(kT) k_spmm_dots(long long L, const int* __rest
     A y[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) y[c] = P::zero();
-    row_product<P, NB, VMODE, VEC, spmm_unroll<P, NB>()>(__ldg(rowptr + row), __ldg(rowptr + row + 1), colidx, v32,
+    row_product<P, NB, VMODE, VEC, dots_unroll<P, NB>()>(__ldg(rowptr + row), __ldg(rowptr + row + 1), colidx, v32,
                                                           v32lo, v64, X, ldx, y);
     store_yrow<P, NB, VEC>(Y + row * NB, y);
     A e1[NB], e2[NB];

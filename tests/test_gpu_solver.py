@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import phsvds_fp64 as O
 from paper_1607_01404_gb300 import binding as B
 from paper_1607_01404_gb300 import build as BLD
 from paper_1607_01404_gb300 import workloads as wl
@@ -309,3 +310,111 @@ def test_many_triplets(method):
     np.testing.assert_allclose(r["sigma"], s[:40], rtol=1e-9)
     normA = s[-1]
     assert np.all(r["rnorm"] <= 1.0001e-10 * normA)
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_many_triplets_120(target):
+    """The many-triplet regime (k = 120, basis 132 columns: tiled kernels beyond
+    the 64-column row kernels) against the closed form of a 2D grid."""
+    A = wl.grid_difference(40, 2)
+    s = _grid_sigma(40, 2)
+    ref = s[:120] if target == "smallest" else s[::-1][:120]
+    r = B.svds(A, 120, target, 1e-10, maxBlockSize=4, method_stage1=B.SVDS_JDQMR, stage1_precision=B.SVDS_FP32,
+               maxMatvecs=5000000)
+    assert r["nconv"] == 120
+    np.testing.assert_allclose(r["sigma"], ref, rtol=1e-9)
+    assert np.all(r["rnorm"] <= 1.0001e-10 * s[-1])
+    assert np.abs(r["V"].T @ r["V"] - np.eye(120)).max() < 1e-8
+
+
+def _wide(A):
+    At = A.to_scipy().T.tocsr()
+    At.sort_indices()
+    return wl.CSR(At.shape[0], At.shape[1], At.indptr.astype(np.int32), At.indices.astype(np.int32), At.data, "wide")
+
+
+def _dense_kappa(A):
+    s = np.linalg.svd(A.to_scipy().toarray(), compute_uv=False)
+    return s[0], s[-1]
+
+
+@pytest.mark.parametrize("prec", [B.SVDS_FP64, B.SVDS_FP32])
+@pytest.mark.parametrize("method", [B.SVDS_GDPK, B.SVDS_JDQMR])
+@pytest.mark.parametrize("name", ["grid3d", "random", "wide"])
+def test_condest_within_the_relative_bound(prec, method, name):
+    """svds_condest (Sec. 5, rel_tol 0.1).  Always: Ritz values lie inside the
+    spectrum, so sigma_max is not overestimated, sigma_min not underestimated
+    and the estimate never exceeds kappa.  Where the extreme values are well
+    separated (3D grid, the wide random matrix) the relative rule at both ends
+    puts it in [kappa sqrt(0.9 / 1.1), kappa], as the oracle's estimate on the
+    same matrix; on the square random matrix, whose smallest values are
+    clustered, a block-1 low-accuracy solve may stop at an interior value (the
+    paper's caveat), so only the bounds are asserted.  With a tiny rel_tol the
+    estimate is kappa to 1e-8.  The relative mode runs GD+k corrections for
+    either stage-1 method (block-1 JDQMR with a loose stop can settle on an
+    interior value)."""
+    A = {"grid3d": lambda: wl.grid_difference(14, 3),
+         "random": lambda: wl.random_illconditioned(3001, 1203, 16, seed=3),
+         "wide": lambda: _wide(wl.random_illconditioned(1500, 600, 16, seed=5))}[name]()
+    smax, smin = _dense_kappa(A)
+    kappa = smax / smin
+    r = B.condest(A, 0.1, stage1_precision=prec, method_stage1=method)
+    assert r["rc"] == 0
+    assert r["sigma_max"] <= smax * (1 + 1e-12) and r["sigma_min"] >= smin * (1 - 1e-12)
+    assert r["kappa"] <= kappa * (1 + 1e-12)
+    assert r["stats_largest"]["stage2_used"] == 0 and r["stats_smallest"]["stage2_used"] == 0
+    if name != "random":
+        assert kappa * np.sqrt(0.9 / 1.1) <= r["kappa"], (r["kappa"], kappa)
+        o = O.condest(A.to_scipy(), 0.1)
+        assert kappa * np.sqrt(0.9 / 1.1) <= o["kappa"] <= kappa * (1 + 1e-12)
+    tight = B.condest(A, 1e-9, stage1_precision=prec, method_stage1=method)
+    assert abs(tight["kappa"] / kappa - 1) < 1e-8, (tight["kappa"], kappa)
+
+
+def test_relative_mode_counts_the_relative_rule():
+    """svds_solve with relTol: the returned pairs meet ||C v - sigma^2 v|| <=
+    relTol sigma^2 (checked in FP64 on the host), numConverged counts them."""
+    A = wl.grid_difference(16, 3)
+    for target in ("largest", "smallest"):
+        r = B.svds(A, 3, target, 1e-10, maxBlockSize=1, relTol=0.05)
+        S = A.to_scipy()
+        V = r["V"]
+        CV = S.T @ (S @ V)
+        lam = np.sum(V * CV, axis=0)
+        res = np.linalg.norm(CV - V * lam, axis=0)
+        assert r["nconv"] == 3
+        assert np.all(res <= 0.05 * lam * (1 + 1e-9) + 1e-12), (res, lam)
+        np.testing.assert_allclose(r["sigma"] ** 2, lam, rtol=1e-12)
+
+
+@pytest.mark.parametrize("target", ["smallest", "largest"])
+def test_dynamic_method_closed_form(target):
+    """DYNAMIC stage 1 (Sec. 3.4): the same triplets as the fixed methods (closed
+    form of a 3D grid), and the switching uses both corrections."""
+    A = wl.grid_difference(24, 3)
+    s = _grid_sigma(24, 3)
+    ref = s[:10] if target == "smallest" else s[::-1][:10]
+    r = B.svds(A, 10, target, 1e-10, maxBlockSize=4, method_stage1=B.SVDS_DYNAMIC, stage1_precision=B.SVDS_FP32,
+               maxMatvecs=5000000)
+    assert r["nconv"] == 10
+    np.testing.assert_allclose(r["sigma"], ref, rtol=1e-9)
+    assert np.all(r["rnorm"] <= 1.0001e-10 * s[-1])
+    st = r["stats"]
+    assert 0 < st["outer_stage1_jdqmr"] < st["outer_stage1"], st
+
+
+def test_dynamic_method_is_near_the_faster_fixed_method():
+    """On a 64^3 grid (smallest, Jacobi) JDQMR is several times faster than GD+k;
+    DYNAMIC spends most outer iterations' time in it and stays within 1.6x of
+    the faster fixed method (minimum of two runs each)."""
+    A = wl.grid_difference(64, 3)
+    kw = dict(maxBlockSize=4, stage1_precision=B.SVDS_FP32, maxMatvecs=20000000)
+    t = {}
+    for name, m in (("gdk", B.SVDS_GDPK), ("jdqmr", B.SVDS_JDQMR), ("dynamic", B.SVDS_DYNAMIC)):
+        best = None
+        for _ in range(2):
+            r = B.svds(A, 10, "smallest", 1e-10, method_stage1=m, **kw)
+            assert r["nconv"] == 10
+            best = min(best or 1e30, r["stats"]["seconds_total"])
+        t[name] = best
+    assert t["dynamic"] <= 1.6 * min(t["gdk"], t["jdqmr"]), t

@@ -285,3 +285,27 @@ def test_jd_correction_exact_definition():
         P = np.eye(30) - np.outer(X[:, j], X[:, j])
         np.testing.assert_allclose(P @ (C - eta[j] * np.eye(30)) @ P @ T[:, j], B[:, j], atol=1e-10 * np.abs(B).max())
         assert abs(X[:, j] @ T[:, j]) < 1e-12 * np.linalg.norm(T[:, j])
+
+
+def test_condest_bounds_and_limit():
+    """Condition-number estimate (Sec. 5): Ritz values lie inside the spectrum,
+    so the estimate never exceeds kappa; with ||r^C|| <= 0.1 lambda at both ends
+    (and convergence to the extremes) it is within sqrt(1.1 / 0.9) of kappa;
+    as rel_tol -> 0 it reduces to the exact kappa of a dense SVD."""
+    for A in (wl.grid_difference(12, 3).to_scipy(), wl.random_illconditioned(900, 300, 16, seed=4).to_scipy()):
+        s = np.linalg.svd(A.toarray(), compute_uv=False)
+        kappa = s[0] / s[-1]
+        r = O.condest(A, 0.1)
+        assert r["sigma_max"] <= s[0] * (1 + 1e-12) and r["sigma_min"] >= s[-1] * (1 - 1e-12)
+        assert kappa * math.sqrt(0.9 / 1.1) <= r["kappa"] <= kappa * (1 + 1e-12), (r["kappa"], kappa)
+        assert r["rC_max"] <= 0.1 * r["sigma_max"] ** 2 * (1 + 1e-12)
+        assert r["rC_min"] <= 0.1 * r["sigma_min"] ** 2 * (1 + 1e-12)
+        tight = O.condest(A, 1e-12)
+        assert abs(tight["kappa"] / kappa - 1) < 1e-9, (tight["kappa"], kappa)
+
+
+def test_condest_wide_matrix_and_no_preconditioner():
+    A = wl.random_illconditioned(700, 250, 16, seed=8).to_scipy()
+    s = np.linalg.svd(A.toarray(), compute_uv=False)
+    r = O.condest(A.T.tocsr(), 1e-12, precond="none")  # 250 x 700: works on (A^T)^T = A
+    assert abs(r["kappa"] * s[-1] / s[0] - 1) < 1e-9
