@@ -406,12 +406,14 @@ def condest_runs(B, torch, stream, rp, ci, va, A, sp):
 
 
 def precond_gain(B, wl, sp):
-    """Jacobi vs learned preconditioner (chosen JDQMR form) on held-out weighted grids."""
+    """Jacobi vs learned vs block-Jacobi (blocks of 32 columns) preconditioner
+    (chosen JDQMR form) on held-out weighted grids."""
     out = {}
     for wname, model in (("wgrid2d_N256", "wgrid2d.bin"), ("wgrid3d_N96", "wgrid3d.bin")):
         A, meta = wl.workload(wname)
         row = {}
-        for name, pc in (("jacobi", B.SVDS_PRECOND_JACOBI), ("learned", B.SVDS_PRECOND_LEARNED)):
+        for name, pc in (("jacobi", B.SVDS_PRECOND_JACOBI), ("learned", B.SVDS_PRECOND_LEARNED),
+                         ("block_jacobi32", B.SVDS_PRECOND_BLOCKJACOBI)):
             kw = dict(maxBlockSize=meta["b"], stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR,
                       method_stage2=B.SVDS_JDQMR, precond=pc, seed=3, stream=sp, maxSeconds=120.0)
             if pc == B.SVDS_PRECOND_LEARNED:
@@ -425,6 +427,7 @@ def precond_gain(B, wl, sp):
                              inner_steps=int(st["inner_steps"]), seconds_precond=round(st["seconds_precond"], 5),
                              numConverged=nconv)
         row["speedup"] = round(row["jacobi"]["seconds"] / row["learned"]["seconds"], 3)
+        row["speedup_block_jacobi"] = round(row["jacobi"]["seconds"] / row["block_jacobi32"]["seconds"], 3)
         out[f"{wname} (held-out seed, k={meta['k']}, b={meta['b']})"] = row
     return out
 

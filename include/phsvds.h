@@ -61,6 +61,9 @@ extern "C" {
 #define SVDS_PRECOND_JACOBI 1
 #define SVDS_PRECOND_LEARNED 2 /* sparse approximate inverse on the pattern of A^T A from the
                                   graph network of phsvds_gnn.h (stage 1, smallest values) */
+#define SVDS_PRECOND_BLOCKJACOBI 3 /* block Jacobi on A^T A (Sec. 4): inverses of the diagonal
+                                      blocks of precondBlockSize consecutive columns (stage 1,
+                                      smallest values) */
 
 /* Sparse matrix in CSR form (0-based).  Column indices must be strictly
  * increasing inside each row and values finite.  When on_device is non-zero
@@ -87,7 +90,8 @@ typedef struct {
   int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32, SVDS_BF16 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
                            to the paper's stage-1 criterion before stage 2 (default 1) */
-  int precond;          /* SVDS_PRECOND_JACOBI (default), SVDS_PRECOND_NONE or SVDS_PRECOND_LEARNED */
+  int precond;          /* SVDS_PRECOND_JACOBI (default), SVDS_PRECOND_NONE, SVDS_PRECOND_LEARNED
+                           or SVDS_PRECOND_BLOCKJACOBI */
   double aNorm;         /* ||A||_2 if known, 0 = estimate */
   int64_t maxMatvecs;   /* budget in products with A or A^T (per column), 0 = unlimited */
   double maxSeconds;    /* wall-clock budget, 0 = unlimited */
@@ -112,6 +116,7 @@ typedef struct {
                                  triplets that meet that relative rule; tol is then unused.
                                  Stage 1 uses GD+k corrections in this mode whatever
                                  method_stage1 says.  0 (default) = the rules of Algorithm 1 */
+  int precondBlockSize;       /* SVDS_PRECOND_BLOCKJACOBI: columns per block, 1..64 (0 = 32) */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -130,7 +135,8 @@ typedef struct {
   double seconds_sync_wait;   /* host time blocked on the device (small results coming back) */
   int64_t host_syncs;         /* device-to-host round trips */
   int64_t inner_steps;        /* JDQMR inner sQMR steps (each applies the operator to the block) */
-  double seconds_precond;     /* learned preconditioner: graph of A^T A and network inference */
+  double seconds_precond;     /* building the learned (graph of A^T A and network inference) or
+                                 block-Jacobi preconditioner */
   int64_t normal_nnz;         /* nonzeros of the explicit C = A^T A, 0 when A then A^T is used */
   double seconds_output;      /* returning the vectors: FP64 conversion, sign convention, copies to U, V */
   int64_t outer_stage1_jdqmr; /* stage-1 outer iterations whose correction came from JDQMR */

@@ -56,6 +56,19 @@ int phsvds_spmm_dots(int prec, int64_t n, int64_t nnz, const int32_t *rowptr, co
                      void *stream);
 size_t phsvds_spmm_dots_scratch_bytes(int nb);
 
+/* Block-Jacobi preconditioner on C = A^T A (Sec. 4: block Jacobi on A^T A):
+ * M = blockdiag((C_II + delta_I I)^-1) over consecutive blocks I of bs columns
+ * (the last one ragged), C_II = A_I^T A_I, a zero diagonal entry (empty
+ * column) replaced by 1, delta_I = 1e-10 max_r (C_II)_rr; inverted in FP64,
+ * symmetrised.  Input: CSR of A^T (n rows = the columns of A, sorted column
+ * indices, FP64 values), device.  Output (device, caller-allocated): CSR of M
+ * with rowptr (n + 1 entries), colidx and the values in FP64 (v64) and / or
+ * FP32 (v32), phsvds_block_jacobi_nnz(n, bs) entries each; either value
+ * pointer may be NULL, not both.  1 <= bs <= 64, else SVDS_ERR_ARG. */
+int64_t phsvds_block_jacobi_nnz(int64_t n, int bs);
+int phsvds_block_jacobi(int64_t n, const int32_t *rowptrT, const int32_t *colidxT, const double *valsT, int bs,
+                        int32_t *rowptr, int32_t *colidx, double *v64, float *v32, void *stream);
+
 /* Orthonormalise the block T (L x nb, ld ldt, in place) against the orthonormal
  * basis V (L x g, ld ldv) by the solver's device-side CGS2 + CholQR2 (Sec. 3.2,
  * Sec. 4.4): T <- (I - V V^T)^2 T, then Cholesky-QR twice, the small Cholesky

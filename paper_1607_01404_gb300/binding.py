@@ -39,6 +39,7 @@ SVDS_NORMAL_EXPLICIT = 2
 SVDS_PRECOND_NONE = 0
 SVDS_PRECOND_JACOBI = 1
 SVDS_PRECOND_LEARNED = 2
+SVDS_PRECOND_BLOCKJACOBI = 3
 
 PREC_F32, PREC_DF64, PREC_F64 = 1, 2, 3
 
@@ -58,7 +59,8 @@ class svds_opts(C.Structure):
                 ("stream", C.c_void_p), ("innerMaxIt", C.c_int), ("innerRelTol", C.c_double),
                 ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p),
                 ("normalOperator", C.c_int),
-                ("relTol", C.c_double)]
+                ("relTol", C.c_double),
+                ("precondBlockSize", C.c_int)]
 
 
 class svds_stats(C.Structure):
@@ -99,6 +101,9 @@ _SIGS = {
                                    C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "phsvds_spmm_dots_scratch_bytes": (C.c_size_t, [C.c_int]),
+    "phsvds_block_jacobi_nnz": (C.c_int64, [C.c_int64, C.c_int]),
+    "phsvds_block_jacobi": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_ortho": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                C.POINTER(C.c_int), C.c_void_p]),
     "phsvds_jd_solve": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -329,6 +334,17 @@ def spmm_dots(prec, n, rowptr, colidx, v32, v32lo, v64, nb, X, ldx, W, E1, E2, d
     _check(lib().phsvds_spmm_dots(prec, n, int(colidx.numel()), ptr(rowptr), ptr(colidx), ptr(v32), ptr(v32lo),
                                   ptr(v64), nb, ptr(X), ldx, ptr(W), ptr(E1), ptr(E2), ptr(dots), ptr(scratch),
                                   scratch.numel() * scratch.element_size(), _stream(stream)), "phsvds_spmm_dots")
+
+
+def block_jacobi_nnz(n, bs):
+    return int(lib().phsvds_block_jacobi_nnz(n, bs))
+
+
+def block_jacobi(n, rowptrT, colidxT, valsT, bs, rowptr, colidx, v64=None, v32=None, stream=None):
+    """CSR of the block-Jacobi inverse of A^T A from the CSR of A^T (torch CUDA tensors)."""
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    _check(lib().phsvds_block_jacobi(n, ptr(rowptrT), ptr(colidxT), ptr(valsT), bs, ptr(rowptr), ptr(colidx),
+                                     ptr(v64), ptr(v32), _stream(stream)), "phsvds_block_jacobi")
 
 
 def ortho(prec, L, V, ldv, g, T, ldt, nb, stream=None):

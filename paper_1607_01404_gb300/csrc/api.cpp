@@ -12,6 +12,7 @@
 #include "../../include/phsvds_gnn.h"
 #include "../../include/phsvds_kernels.h"
 #include "engine.h"
+#include "bjacobi.h"
 #include "jdqmr.h"
 #include "hostla.h"
 #include "kernels.h"
@@ -185,12 +186,14 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
     return SVDS_ERR_ARG;
   if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_FP64) return SVDS_ERR_ARG;
   if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
-  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED)
+  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED &&
+      o.precond != SVDS_PRECOND_BLOCKJACOBI)
     return SVDS_ERR_ARG;
   if (o.normalOperator != SVDS_NORMAL_AUTO && o.normalOperator != SVDS_NORMAL_TWOPASS &&
       o.normalOperator != SVDS_NORMAL_EXPLICIT)
     return SVDS_ERR_ARG;
   if (!(o.relTol >= 0) || !std::isfinite(o.relTol)) return SVDS_ERR_ARG;
+  if (o.precondBlockSize < 0 || o.precondBlockSize > phsvds::kBjMaxBlock) return SVDS_ERR_ARG;
   std::vector<float> gnn_params;
   if (o.precond == SVDS_PRECOND_LEARNED) {
     gnn_params.resize(phsvds_gnn_num_params());
@@ -341,6 +344,19 @@ int phsvds_spmm_bf16(int64_t rows, int64_t cols, int64_t nnz, const int32_t* row
   A.v16 = v16;
   CKR(launch_spmm(kF32, A, X, ldx, Y, ldy, b, reinterpret_cast<cudaStream_t>(stream)));
   return 0;
+}
+
+int64_t phsvds_block_jacobi_nnz(int64_t n, int bs) {
+  return (bs < 1 || bs > phsvds::kBjMaxBlock) ? 0 : phsvds::bj_nnz(n, bs);
+}
+
+int phsvds_block_jacobi(int64_t n, const int32_t* rowptrT, const int32_t* colidxT, const double* valsT, int bs,
+                        int32_t* rowptr, int32_t* colidx, double* v64, float* v32, void* stream) {
+  if (n < 1 || bs < 1 || bs > phsvds::kBjMaxBlock || !rowptrT || !rowptr || !colidx || (!v64 && !v32))
+    return SVDS_ERR_ARG;
+  CKR(phsvds::launch_bj_build(n, bs, rowptrT, colidxT, valsT, rowptr, colidx, v32, v64,
+                              reinterpret_cast<cudaStream_t>(stream)));
+  return SVDS_OK;
 }
 
 size_t phsvds_spmm_dots_scratch_bytes(int nb) { return (size_t)2048 * 4 * (nb > 0 ? nb : 1) * 8; }

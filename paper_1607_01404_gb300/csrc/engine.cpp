@@ -18,6 +18,7 @@
 #include "../../include/phsvds_gnn.h"
 #include "gnn.h"
 #include "hostla.h"
+#include "bjacobi.h"
 #include "jdqmr.h"
 
 namespace phsvds {
@@ -1280,6 +1281,13 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     phsvds_gnn* g = nullptr;
     ~GnnGuard() { phsvds_gnn_destroy(g); }
   } gnn_guard;
+  struct BjGuard {  // device arrays of the block-Jacobi preconditioner
+    void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~BjGuard() {
+      for (void* q : p)
+        if (q) cudaFree(q);
+    }
+  } bj_guard;
   try {
     // ---- workspace ----
     struct Req {
@@ -1478,9 +1486,44 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c.sync();
       S.seconds_precond = c.elapsed() - tp;
     }
-    const CsrDev* Kouter = learned ? (p2 == kF64 ? &K64 : &K32) : nullptr;
+    // block Jacobi on C (Sec. 4), stage 1, smallest values: a CSR matrix with
+    // dense diagonal blocks, applied by the same SpMM kernels as the learned M
+    const bool bjac = smallest && o.precond == SVDS_PRECOND_BLOCKJACOBI;
+    if (bjac) {
+      const double tp = c.elapsed();
+      const int bs = o.precondBlockSize > 0 ? o.precondBlockSize : 32;
+      const long long nz = bj_nnz(n, bs);
+      const bool want64 = p2 == kF64;
+      const size_t sz[4] = {sizeof(int) * (size_t)(n + 1), sizeof(int) * (size_t)nz, sizeof(float) * (size_t)nz,
+                            want64 ? sizeof(double) * (size_t)nz : 0};
+      for (int i = 0; i < 4; ++i)
+        if (sz[i] && cudaMalloc(&bj_guard.p[i], sz[i]) != cudaSuccess) {
+          cudaGetLastError();
+          set_last_error("block-Jacobi allocation failed");
+          return SVDS_ERR_NOMEM;
+        }
+      int* brp = static_cast<int*>(bj_guard.p[0]);
+      int* bci = static_cast<int*>(bj_guard.p[1]);
+      float* b32 = static_cast<float*>(bj_guard.p[2]);
+      double* b64 = static_cast<double*>(bj_guard.p[3]);
+      CK(launch_bj_build(n, bs, A.rowptrT, A.colidxT, A.v64T, brp, bci, b32, b64, c.st));
+      c.launches += 1;
+      for (CsrDev* Kd : {&K32, &K64}) {
+        Kd->rows = n;
+        Kd->cols = n;
+        Kd->nnz = nz;
+        Kd->rowptr = brp;
+        Kd->colidx = bci;
+      }
+      K32.v32 = b32;
+      K64.v64 = b64;
+      c.sync();
+      S.seconds_precond = c.elapsed() - tp;
+    }
+    const bool sparseM = learned || bjac;
+    const CsrDev* Kouter = sparseM ? (p2 == kF64 ? &K64 : &K32) : nullptr;
     const int jd_prec = o.innerPrecision == SVDS_FP64 ? p2 : kF32;
-    const CsrDev* Kinner = learned ? (jd_prec == kF64 ? &K64 : &K32) : nullptr;
+    const CsrDev* Kinner = sparseM ? (jd_prec == kF64 ? &K64 : &K32) : nullptr;
     const int jd_maxk = o.innerMaxIt > 0 ? o.innerMaxIt : 30;
     const double jd_xi = o.innerRelTol > 0 ? o.innerRelTol : 0.1;
     // initial block: user guesses then seeded N(0,1) columns
@@ -1530,7 +1573,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       c1.u = (bf16 && !exact_vals) ? std::ldexp(1.0, -8) : unit_roundoff(kF32);
       c1.conv = stage1_conv(c1.u);
       c1.dscale = jac ? d1a : nullptr;
-      c1.K = learned ? &K32 : nullptr;
+      c1.K = sparseM ? &K32 : nullptr;
       c1.V0 = X1a;
       c1.ldv0 = kk;
       c1.name = "stage1-fp32";

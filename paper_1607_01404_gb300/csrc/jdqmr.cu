@@ -502,29 +502,32 @@ __global__ void __launch_bounds__(kT) k_qmr_dots_u(long long L, int nb, const ty
 // for ND = 4, d2 = E1^T E2, d3 = E2^T E2 (per column, FP64-class partials).
 // With (E1, E2) = (x, q) these are the four dots of k_qmr_dots1 for w = op q;
 // with (E1, E2) = (r, x) the two dots of k_qmr_dots_u for u = K^-1 r.
-// Tuning of k_spmm_dots: CTAs per SM the register allocation must allow
-// (0 = no bound), and the number of row gathers a thread keeps in flight (0 =
-// spmm_unroll).  The gathers are latency-bound: 6 CTAs of 256 threads per SM
-// (at most 40 registers, a few spilled) with 2 gathers in flight beat 4 CTAs
-// with 4 gathers on the 7-nonzero rows of a 3D-grid A^T A.
+// Tuning of k_spmm_dots in the F32 mode: CTAs per SM the register allocation
+// must allow, and the number of row gathers a thread keeps in flight.  The
+// gathers are latency-bound: 6 CTAs of 256 threads per SM (at most 40
+// registers, a few spilled) with 2 gathers in flight beat 4 CTAs with 4
+// gathers on the 7-nonzero rows of a 3D-grid A^T A.  Wider accumulators get
+// looser bounds so that nothing spills heavily: F32 blocks of 8 columns 3 CTAs
+// per SM (80 registers), double-float and FP64 blocks of up to 4 columns 3
+// CTAs (80 registers), of 8 columns 1 CTA (up to 168 registers); these keep the
+// default unroll.
 #ifndef PHSVDS_DOTS_MINB
 #define PHSVDS_DOTS_MINB 6
-#endif
-#if PHSVDS_DOTS_MINB > 0
-#define PHSVDS_DOTS_BOUNDS __launch_bounds__(kT, PHSVDS_DOTS_MINB)
-#else
-#define PHSVDS_DOTS_BOUNDS __launch_bounds__(kT)
 #endif
 #ifndef PHSVDS_DOTS_U
 #define PHSVDS_DOTS_U 2
 #endif
 template <class P, int NB>
+__host__ __device__ constexpr int dots_minb() {
+  return P::id == kF32 ? (NB >= 8 ? 3 : PHSVDS_DOTS_MINB) : (NB >= 8 ? 1 : 3);
+}
+template <class P, int NB>
 __host__ __device__ constexpr int dots_unroll() {
-  return PHSVDS_DOTS_U > 0 ? PHSVDS_DOTS_U : spmm_unroll<P, NB>();
+  return (P::id == kF32 && NB < 8 && PHSVDS_DOTS_U > 0) ? PHSVDS_DOTS_U : spmm_unroll<P, NB>();
 }
 
 template <class P, int NB, int VMODE, bool VEC, int ND>
-__global__ void PHSVDS_DOTS_BOUNDS k_spmm_dots(long long L, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(kT, dots_minb<P, NB>()) k_spmm_dots(long long L, const int* __restrict__ rowptr,
                                                   const int* __restrict__ colidx, const float* __restrict__ v32,
                                                   const float* __restrict__ v32lo, const double* __restrict__ v64,
                                                   const typename P::S* __restrict__ X, long long ldx,

@@ -251,3 +251,48 @@ def test_device_ortho_matches_oracle(prec, g, nb):
     assert np.abs(Q - ref).max() <= tol, np.abs(Q - ref).max()
     assert np.abs(Q.T @ Q - np.eye(nb)).max() <= tol
     assert np.abs(Vs.T @ Q).max() <= tol
+
+
+@pytest.mark.parametrize("bs", [1, 7, 32, 64])
+@pytest.mark.parametrize("name", ["random", "grid"])
+def test_block_jacobi_matches_oracle(bs, name):
+    """CSR of the block-Jacobi inverse of A^T A (ragged last block, an empty
+    column in the random matrix) against the oracle's dense block inverses."""
+    import scipy.sparse as sp
+
+    from oracle import phsvds_fp64 as O
+
+    if name == "random":
+        S = wl.random_illconditioned(2000, 701, 8, seed=bs).to_scipy().tolil()
+        S[:, 300] = 0.0
+        S = S.tocsr()
+    else:
+        S = wl.grid_difference(9, 3).to_scipy()
+    S.eliminate_zeros()
+    n = S.shape[1]
+    At = S.T.tocsr()
+    At.sort_indices()
+    dev = torch.device("cuda:0")
+    rpT = torch.from_numpy(At.indptr.astype(np.int32)).to(dev)
+    ciT = torch.from_numpy(At.indices.astype(np.int32)).to(dev)
+    vT = torch.from_numpy(At.data.astype(np.float64)).to(dev)
+    nz = B.block_jacobi_nnz(n, bs)
+    rp = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    ci = torch.zeros(nz, dtype=torch.int32, device=dev)
+    v64 = torch.zeros(nz, dtype=torch.float64, device=dev)
+    v32 = torch.zeros(nz, dtype=torch.float32, device=dev)
+    B.block_jacobi(n, rpT, ciT, vT, bs, rp, ci, v64=v64, v32=v32)
+    torch.cuda.synchronize()
+    M = sp.csr_matrix((v64.cpu().numpy(), ci.cpu().numpy(), rp.cpu().numpy()), shape=(n, n))
+    ref = O.block_jacobi(S, bs)
+    assert np.array_equal(M.indptr, ref.indptr) and np.array_equal(M.indices, ref.indices)
+    # FP64 Gauss-Jordan vs LAPACK inverse of each block: relative to the block's
+    # largest entry, scaled by the block's condition number
+    D = (M - ref).toarray()
+    R = ref.toarray()
+    for g0 in range(0, n, bs):
+        I = slice(g0, min(n, g0 + bs))
+        blk = R[I, I]
+        kappa = np.linalg.cond(blk)
+        assert np.abs(D[I, I]).max() <= 1e-14 * kappa * np.abs(blk).max() + 1e-300, (g0, kappa)
+    np.testing.assert_array_equal(v32.cpu().numpy(), v64.cpu().numpy().astype(np.float32))

@@ -418,3 +418,22 @@ def test_dynamic_method_is_near_the_faster_fixed_method():
             best = min(best or 1e30, r["stats"]["seconds_total"])
         t[name] = best
     assert t["dynamic"] <= 1.6 * min(t["gdk"], t["jdqmr"]), t
+
+
+@pytest.mark.parametrize("method", [B.SVDS_GDPK, B.SVDS_JDQMR])
+@pytest.mark.parametrize("prec", [B.SVDS_FP64, B.SVDS_FP32])
+def test_block_jacobi_preconditioner(method, prec):
+    """Block Jacobi on A^T A (Sec. 4) in both stage-1 methods and precisions:
+    the closed-form triplets of a 3D grid; fewer products than Jacobi."""
+    A = wl.grid_difference(20, 3)
+    s = _grid_sigma(20, 3)
+    out = {}
+    for pc in (B.SVDS_PRECOND_JACOBI, B.SVDS_PRECOND_BLOCKJACOBI):
+        r = B.svds(A, 6, "smallest", 1e-10, maxBlockSize=2, method_stage1=method, stage1_precision=prec,
+                   precond=pc, precondBlockSize=20, maxMatvecs=5000000)
+        assert r["nconv"] == 6
+        np.testing.assert_allclose(r["sigma"], s[:6], rtol=1e-9)
+        assert np.all(r["rnorm"] <= 1.0001e-10 * s[-1])
+        out[pc] = r["stats"]["matvecs_stage1"]
+    # blocks of 20 are whole grid lines: a stronger preconditioner than Jacobi
+    assert out[B.SVDS_PRECOND_BLOCKJACOBI] < out[B.SVDS_PRECOND_JACOBI], out

@@ -309,3 +309,49 @@ def test_condest_wide_matrix_and_no_preconditioner():
     s = np.linalg.svd(A.toarray(), compute_uv=False)
     r = O.condest(A.T.tocsr(), 1e-12, precond="none")  # 250 x 700: works on (A^T)^T = A
     assert abs(r["kappa"] * s[-1] / s[0] - 1) < 1e-9
+
+
+def test_block_jacobi_definition():
+    """Block Jacobi on A^T A: bs = 1 is Jacobi; a single block is the inverse
+    of (shifted) C; every diagonal block of M C is the identity up to the shift;
+    M is symmetric positive definite; an empty column gets the entry 1."""
+    A = wl.random_illconditioned(400, 90, 8, seed=6).to_scipy().tolil()
+    A[:, 17] = 0.0  # an empty column
+    A = A.tocsr()
+    C = (A.T @ A).toarray()
+    d = np.diag(C)
+    M1 = O.block_jacobi(A, 1).toarray()
+    # one column per block: delta = 1e-10 c_ii, and 1 for the empty column
+    np.testing.assert_allclose(np.diag(M1), np.where(d > 0, 1.0 / (np.where(d > 0, d, 1.0) * (1 + 1e-10)), 1.0),
+                               rtol=1e-14)
+    assert np.count_nonzero(M1 - np.diag(np.diag(M1))) == 0
+    Mall = O.block_jacobi(A, 90).toarray()
+    Cs = C.copy()
+    Cs[17, 17] = 1.0
+    Cs += 1e-10 * d.max() * np.eye(90)
+    np.testing.assert_allclose(Mall @ Cs, np.eye(90), atol=1e-9)
+    for bs in (7, 32):
+        M = O.block_jacobi(A, bs).toarray()
+        np.testing.assert_allclose(M, M.T, atol=0)
+        assert np.linalg.eigvalsh(M).min() > 0
+        for g0 in range(0, 90, bs):
+            I = slice(g0, min(90, g0 + bs))
+            CII = C[I, I].copy()
+            dI = np.diag(CII).copy()
+            delta = 1e-10 * dI.max()
+            dI[dI == 0] = 1.0
+            np.fill_diagonal(CII, dI + delta)
+            np.testing.assert_allclose(M[I, I] @ CII, np.eye(CII.shape[0]), atol=1e-9)
+            if g0 + bs < 90:
+                assert np.all(M[I, g0 + bs:] == 0)
+            if g0 <= 17 < g0 + bs:
+                # the empty column decouples: its entry is 1 / (1 + delta_I)
+                assert abs(M[17, 17] - 1.0 / (1.0 + delta)) < 1e-12
+
+
+def test_phsvds_block_jacobi_preconditioner_closed_form():
+    A = wl.grid_difference(8, 3)
+    t = 4.0 * np.sin(np.arange(1, 9) * np.pi / 18) ** 2
+    s = np.sort(np.sqrt((t[:, None, None] + t[None, :, None] + t[None, None, :]).ravel()))
+    r = O.phsvds(A.to_scipy(), 3, "smallest", 1e-10, b=2, precond="block_jacobi", bj_block=16)
+    np.testing.assert_allclose(r["sigma"], s[:3], rtol=1e-10)
