@@ -351,12 +351,26 @@ def run_gpu(args, world, rank, local):
     t_dyn, st_dyn, lastd = timed("dynamic", 1, 800 + 1000 * rank)
     relerr_d = float(np.max(np.abs(lastd[0] - exact) / exact))
     cond = condest_runs(B, torch, stream, rp, ci, va, A, sp)
-    # end to end through host buffers
-    torch.cuda.synchronize()
-    te0 = time.perf_counter()
-    oute = one_solve("chosen", 7 + 1000 * rank, host_inputs=True)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - te0
+    # end to end through the public API: the CSR of A in pinned host memory is
+    # copied in by svds_create, U, V, sigma and the residual norms come back
+    # into pinned host buffers (all allocated before the timed steps)
+    pin = dict(rp=torch.from_numpy(A.rowptr).pin_memory(), ci=torch.from_numpy(A.colidx).pin_memory(),
+               va=torch.from_numpy(A.vals).pin_memory(),
+               U=torch.empty((K, A.m), dtype=torch.float64).pin_memory(),
+               V=torch.empty((K, A.n), dtype=torch.float64).pin_memory())
+    t_e2e_all = []
+    for s_ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        o = opts("chosen", 7 + s_ + 1000 * rank)
+        h = B.svds_create(pin["rp"].numpy(), pin["ci"].numpy(), pin["va"].numpy(), A.m, A.n, o)
+        try:
+            oute = B.svds_solve(h, K, tgt, TOL, U=pin["U"].numpy().T, V=pin["V"].numpy().T)
+        finally:
+            h.close()
+        torch.cuda.synchronize()
+        t_e2e_all.append(time.perf_counter() - te0)
+    t_e2e = statistics.median(t_e2e_all)
     h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
     d2h = 8 * K * (A.m + A.n + 2)
     gain = precond_gain(B, wl, sp)

@@ -257,12 +257,18 @@ def svds_create(rowptr, colidx, vals, m: int, n: int, opts: svds_opts | None = N
     return Handle(h, m, n, keep)
 
 
-def svds_solve(h: Handle, k: int, target: int, tol: float, want_vectors: bool = True):
-    """Returns (sigma, U, V, rnorm, numConverged, stats dict, return code)."""
+def svds_solve(h: Handle, k: int, target: int, tol: float, want_vectors: bool = True, U=None, V=None):
+    """Returns (sigma, U, V, rnorm, numConverged, stats dict, return code).
+    U (m x k) and V (n x k) may be given as column-major float64 arrays (for
+    example views of pinned host buffers); otherwise they are allocated."""
     sigma = np.zeros(k)
     rnorm = np.zeros(k)
-    U = np.zeros((h.m, k), order="F") if want_vectors else None
-    V = np.zeros((h.n, k), order="F") if want_vectors else None
+    for X, rows in ((U, h.m), (V, h.n)):
+        if X is not None and (X.dtype != np.float64 or X.shape != (rows, k) or not X.flags.f_contiguous):
+            raise ValueError("output blocks must be float64, column-major, m x k and n x k")
+    if want_vectors:
+        U = np.zeros((h.m, k), order="F") if U is None else U
+        V = np.zeros((h.n, k), order="F") if V is None else V
     nconv = C.c_int(0)
     st = svds_stats()
     rc = lib().svds_solve(h.ptr, k, target, tol, sigma.ctypes.data,

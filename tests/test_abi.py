@@ -147,3 +147,27 @@ def test_learned_precond_needs_parameters():
     o = B.make_opts(precond=7)
     with pytest.raises(B.SvdsError):
         B.svds_create(rp, ci, va, 2, 2, o)
+
+
+@pytest.mark.parametrize("field,value", [("relTol", -0.1), ("relTol", float("nan")), ("precondBlockSize", 65),
+                                         ("precondBlockSize", -1), ("method_stage1", 3), ("method_stage2", 2)])
+def test_create_rejects_new_option_values(field, value):
+    """Option checks of the relative mode, block Jacobi and DYNAMIC (stage 1
+    only) run before any device work."""
+    rp, ci, va = _bad_csr("ok")
+    o = B.make_opts(**{field: value})
+    with pytest.raises(B.SvdsError) as e:
+        B.svds_create(rp, ci, va, 2, 2, o)
+    assert e.value.code == B.SVDS_ERR_ARG
+
+
+def test_condest_and_kernel_entry_argument_checks():
+    import ctypes as C
+
+    L = B.lib()
+    d = C.c_double()
+    assert L.svds_condest(None, 0.1, C.byref(d), C.byref(d), C.byref(d), None) == B.SVDS_ERR_ARG
+    assert B.block_jacobi_nnz(100, 32) == 3 * 32 * 32 + 4 * 4
+    assert B.block_jacobi_nnz(64, 64) == 64 * 64 and B.block_jacobi_nnz(10, 65) == 0
+    assert L.phsvds_block_jacobi(10, None, None, None, 4, None, None, None, None, None) == B.SVDS_ERR_ARG
+    assert B.spmm_dots_scratch_bytes(4) >= 2048 * 4 * 4 * 8
