@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "grid3d_N128"
 K, TARGET, BLOCK, TOL = 10, "smallest", 4, 1e-10
-METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: JDQMR with FP32 inner solves, FP32 stage-1 phase, "
-          "learned preconditioner)")
+METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: DYNAMIC GD+k/JDQMR stage 1 with FP32 inner solves, "
+          "FP32 stage-1 phase, learned preconditioner)")
 MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
 # this workload (--set full, one warm launch each); None where the kernel
@@ -285,12 +285,15 @@ def run_gpu(args, world, rank, local):
     def opts(form, seed):
         kw = dict(maxBlockSize=BLOCK, stage1_polish=1, precond=B.SVDS_PRECOND_JACOBI, seed=seed, stream=sp,
                   maxSeconds=600.0)
-        if form in ("chosen", "dynamic"):
-            kw.update(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+        if form in ("chosen", "jdqmr"):
+            # chosen: the paper's stage-1 default (DYNAMIC), FP32 first phase and
+            # inner solves, learned preconditioner; "jdqmr": the same with JDQMR
+            # corrections at every outer iteration
+            kw.update(stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_DYNAMIC, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_FP32, precond=B.SVDS_PRECOND_LEARNED,
                       precondModel=os.path.join(MODELS, "wgrid3d.bin"))
-            if form == "dynamic":
-                kw.update(method_stage1=B.SVDS_DYNAMIC)
+            if form == "jdqmr":
+                kw.update(method_stage1=B.SVDS_JDQMR)
         elif form == "plain":
             kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_FP64)
@@ -347,8 +350,9 @@ def run_gpu(args, world, rank, local):
     relerr_p = float(np.max(np.abs(lastp[0] - exact) / exact))
     t_gdk, st_gdk, lastg = timed("gdk", 1, 700 + 1000 * rank)
     relerr_g = float(np.max(np.abs(lastg[0] - exact) / exact))
-    # DYNAMIC stage-1 method in the chosen form (switches GD+k / JDQMR by measured rates)
-    t_dyn, st_dyn, lastd = timed("dynamic", 1, 800 + 1000 * rank)
+    # the chosen form with JDQMR corrections at every outer iteration
+    one_solve("jdqmr", 799 + 1000 * rank)  # warm-up of that form
+    t_dyn, st_dyn, lastd = timed("jdqmr", max(1, min(args.steps, 2)), 800 + 1000 * rank)
     relerr_d = float(np.max(np.abs(lastd[0] - exact) / exact))
     cond = condest_runs(B, torch, stream, rp, ci, va, A, sp)
     # end to end through the public API: the CSR of A in pinned host memory is
@@ -560,7 +564,8 @@ def main():
         dtype="f32+df64", data="synthetic",
         config=dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
                     k=K, target=TARGET, block=BLOCK, tol=TOL, precond="learned (gnn_models/wgrid3d.bin)",
-                    form="chosen: JDQMR (inner QMR solves in FP32), FP32 stage-1 phase, learned SPAI preconditioner, "
+                    form="chosen: DYNAMIC stage 1 (GD+k or JDQMR correction per outer iteration by measured "
+                         "rates; JDQMR inner QMR solves in FP32), FP32 stage-1 phase, learned SPAI preconditioner, "
                          "FP64-class outer polish/stage 2",
                     l2="working set >> L2 (no flush)", parallelism=f"replicas x{args.gpus}"),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
@@ -572,7 +577,8 @@ def main():
                             max_rel_sigma_err=res["relerr_gdk"]),
         solve_stats=dict(matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
                          matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
-                         inner_steps=st["inner_steps"], stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
+                         inner_steps=st["inner_steps"], outer1_jdqmr=st["outer_stage1_jdqmr"],
+                         stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
                          precond_s=st["seconds_precond"]),
         roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
                       frac=achieved / peak, peak_kind=peak_kind, traffic=TRAFFIC.get(dom),
@@ -585,11 +591,11 @@ def main():
         e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
                  numConverged=res["e2e_nconv"]),
         precond_gain=res["gain"],
-        dynamic=dict(value=res["t_dyn"][0], unit=UNIT, form="chosen form with the DYNAMIC stage-1 method",
-                     outer1=int(res["st_dyn"][0]["outer_stage1"]),
-                     outer1_jdqmr=int(res["st_dyn"][0]["outer_stage1_jdqmr"]),
-                     matvecs=int(res["st_dyn"][0]["matvecs_stage1"] + res["st_dyn"][0]["matvecs_stage2"]),
-                     max_rel_sigma_err=res["relerr_dyn"]),
+        chosen_jdqmr=dict(value=statistics.median(res["t_dyn"]), unit=UNIT,
+                          form="chosen form with JDQMR corrections at every stage-1 outer iteration",
+                          outer1=int(res["st_dyn"][-1]["outer_stage1"]),
+                          matvecs=int(res["st_dyn"][-1]["matvecs_stage1"] + res["st_dyn"][-1]["matvecs_stage2"]),
+                          max_rel_sigma_err=res["relerr_dyn"]),
         condest=res["cond"],
         gpu_launches=launches,
         clocks=res["clocks"],
