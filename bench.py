@@ -46,6 +46,12 @@ MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # changed after its capture
 TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None}
 UNIT = "s"
+# FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x the maximum SM clock
+# (one FADD, FMUL or FFMA per lane per cycle); the Gram's FP64-class (Dot2)
+# accumulation costs 10 such operations per product (exact product 2, TwoSum 6,
+# error accumulation 2)
+FP32_LANES = 152 * 128
+DOT2_OPS = 10
 # Products with A or A^T (per column) of a full GD+k FP64-class solve of this
 # workload, measured on a GB300 with this library (the plain GD+k line of the
 # bench reports it live); the CPU oracle runs the same GD+k algorithm, so its
@@ -558,6 +564,22 @@ def main():
     except Exception as e:  # the baseline is reported, never required
         cpu = dict(value=None, unit=UNIT, cores=os.cpu_count(), kind="oracle", sample=f"failed: {e}")
     value = res["ms_step"] / 1e3
+    # dominant kernel of the chosen solve (launch list): the FP32 Gram of the
+    # projections, FP32-issue-bound; measured at 32 x 4 columns on the workload's
+    # rows, achieved = DOT2_OPS x products / CUDA-event time per launch
+    g32 = res["orth"]["f32_gram"]
+    gprod = A.n * 32 * BLOCK
+    g_ach = DOT2_OPS * gprod / (g32["ms"] * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        sm_mhz = 2070.0
+    g_peak = FP32_LANES * sm_mhz * 1e6 / 1e12
+    gram_roof = dict(bound="alu", kernel=f"k_gram_row (FP32, Gram {32} x {BLOCK} columns, FP64-class Dot2)",
+                     achieved=g_ach, peak=g_peak, unit="T FP32 op/s", frac=g_ach / g_peak,
+                     peak_kind="derived: 152 SMs x 128 FP32 lanes x max SM clock",
+                     traffic=None, hbm_frac=g32["gbs"] / peak)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
@@ -580,7 +602,8 @@ def main():
                          inner_steps=st["inner_steps"], outer1_jdqmr=st["outer_stage1_jdqmr"],
                          stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
                          precond_s=st["seconds_precond"]),
-        roofline=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
+        roofline=gram_roof,
+        roofline_spmm=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
                       frac=achieved / peak, peak_kind=peak_kind, traffic=TRAFFIC.get(dom),
                       all={k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
                            {**{f"f32_{a}": b for a, b in res["roof32"].items()},

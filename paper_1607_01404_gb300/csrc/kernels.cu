@@ -862,6 +862,186 @@ cudaError_t launch_spmm(int prec, const CsrDev& A, const void* X, long long ldx,
   PHSVDS_DISPATCH(prec, spmm_p<P>(A, X, ldx, Y, ldy, b, st))
 }
 
+// ---------------------------------------------------------------------------
+// Row Gram: partial[blk] = P^T Q over rows [r0, r1) for P of at most
+// kRowGramP columns (up to 3 segments) and Q of at most 8.  TPR lanes share a
+// row: lane `part` owns the columns part + TPR k (k < KP) of P and all
+// columns of Q, so the loads of a row are coalesced across its lanes and nothing is
+// staged in shared memory.  Products are accumulated FP64-class as in the
+// tiled Gram (Dot2: exact product, TwoSum into hi, the rounding errors into
+// lo, renormalised every 2 rows); the rows of a CTA are reduced in a fixed
+// order (shuffles within a warp, then the warps in turn), so results are
+// deterministic.
+// ---------------------------------------------------------------------------
+constexpr int kRowGramP = 64;
+
+template <class P>
+struct RAcc;
+template <>
+struct RAcc<PF32> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x, float y) {
+    const df p = two_prod(x, y);
+    const df s = two_sum(hi, p.hi);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, p.lo));
+  }
+  __device__ __forceinline__ void norm() {
+    const df s = fast_two_sum(hi, lo);
+    hi = s.hi;
+    lo = s.lo;
+  }
+  __device__ __forceinline__ df get() const { return fast_two_sum(hi, lo); }
+};
+template <>
+struct RAcc<PDF64> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(df x, df y) {
+    const df p = two_prod(x.hi, y.hi);
+    const float pl = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+    const df s = two_sum(hi, p.hi);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, pl));
+  }
+  __device__ __forceinline__ void norm() {
+    const df s = fast_two_sum(hi, lo);
+    hi = s.hi;
+    lo = s.lo;
+  }
+  __device__ __forceinline__ df get() const { return fast_two_sum(hi, lo); }
+};
+template <>
+struct RAcc<PF64> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { v = fma(x, y, v); }
+  __device__ __forceinline__ void norm() {}
+  __device__ __forceinline__ double get() const { return v; }
+};
+
+template <class P>
+__device__ __forceinline__ typename P::G shfl_down_g(typename P::G v, int delta) {
+  if constexpr (P::id == kF64) {
+    return __shfl_down_sync(0xffffffffu, v, delta);
+  } else {
+    return df{__shfl_down_sync(0xffffffffu, v.hi, delta), __shfl_down_sync(0xffffffffu, v.lo, delta)};
+  }
+}
+
+template <class P, int TPR, int KP, int NQ>
+__global__ void __launch_bounds__(kThreads) k_gram_row(long long r0, long long r1, SegArr segs, int p,
+                                                       const typename P::S* __restrict__ Q, long long ldq, int q,
+                                                       typename P::G* __restrict__ partial) {
+  using S = typename P::S;
+  using A = typename P::A;
+  using G = typename P::G;
+  constexpr int RPC = kThreads / TPR;  // rows of a CTA pass
+  constexpr int NW = kThreads / 32;
+  __shared__ G red[NW * kRowGramP * 8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int part = lane % TPR;
+  // the P columns of this lane: base pointer and row stride, resolved once
+  const S* cb[KP];
+  long long cl[KP];
+  bool cv[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    int c = part + TPR * k;
+    cv[k] = c < p;
+    int s = 0;
+    while (s < segs.n - 1 && c >= segs.nc[s]) {
+      c -= segs.nc[s];
+      ++s;
+    }
+    cb[k] = cv[k] ? reinterpret_cast<const S*>(segs.p[s]) + c : nullptr;
+    cl[k] = cv[k] ? segs.ld[s] : 0;
+  }
+  RAcc<P> acc[KP][NQ];
+  const long long stride = (long long)gridDim.x * RPC;
+  // two rows per iteration (loads of both issued before the products), then
+  // the accumulators are renormalised
+  for (long long ra = r0 + (long long)blockIdx.x * RPC + threadIdx.x / TPR; ra < r1; ra += 2 * stride) {
+    const long long rb = ra + stride;
+    const bool hb = rb < r1;
+    A xa[KP], xb[KP], ya[NQ], yb[NQ];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      xa[k] = cv[k] ? P::load(cb[k] + ra * cl[k]) : P::zero();
+      xb[k] = (cv[k] && hb) ? P::load(cb[k] + rb * cl[k]) : P::zero();
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      ya[j] = j < q ? P::load(Q + ra * ldq + j) : P::zero();
+      yb[j] = (j < q && hb) ? P::load(Q + rb * ldq + j) : P::zero();
+    }
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        acc[k][j].add(xa[k], ya[j]);
+        acc[k][j].add(xb[k], yb[j]);
+        acc[k][j].norm();
+      }
+  }
+  // lanes of equal `part` in a warp: tree of shuffles in a fixed order
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      G v = acc[k][j].get();
+#pragma unroll
+      for (int off = 16; off >= TPR; off >>= 1) v = P::gadd(v, shfl_down_g<P>(v, off));
+      const int c = part + TPR * k;
+      if (lane < TPR && c < p && j < q) red[(warp * p + c) * q + j] = v;
+    }
+  __syncthreads();
+  const int pq = p * q;
+  for (int e = threadIdx.x; e < pq; e += kThreads) {
+    G v = red[e];
+    for (int w = 1; w < NW; ++w) v = P::gadd(v, red[w * pq + e]);
+    partial[(long long)blockIdx.x * pq + e] = v;
+  }
+}
+
+template <class P>
+cudaError_t gram_row_p(long long r0, long long r1, const SegArr& sa, int p, SegV Q, void* partial, int max_blocks,
+                       int* nblocks, cudaStream_t st) {
+  using S = typename P::S;
+  using G = typename P::G;
+  const S* q = reinterpret_cast<const S*>(Q.p);
+  G* out = reinterpret_cast<G*>(partial);
+  const long long rows = r1 > r0 ? r1 - r0 : 0;
+#define ROWG(TPRV, KPV, NQV)                                                                              \
+  {                                                                                                       \
+    int grid = persistent_grid((rows + kThreads / TPRV - 1) / (kThreads / TPRV), 1);                      \
+    if (grid > max_blocks) grid = max_blocks;                                                             \
+    if (grid < 1) grid = 1;                                                                               \
+    *nblocks = grid;                                                                                      \
+    k_gram_row<P, TPRV, KPV, NQV><<<grid, kThreads, 0, st>>>(r0, r1, sa, p, q, Q.ld, Q.nc, out);          \
+    return cudaGetLastError();                                                                            \
+  }
+#define ROWG_Q4(TPRV, KPV)           \
+  {                                  \
+    if (Q.nc <= 1) ROWG(TPRV, KPV, 1) \
+    if (Q.nc <= 2) ROWG(TPRV, KPV, 2) \
+    ROWG(TPRV, KPV, 4)               \
+  }
+#define ROWG_Q(TPRV, KPV)  \
+  {                        \
+    if (Q.nc <= 4) ROWG_Q4(TPRV, KPV) \
+    ROWG(TPRV, KPV, 8)     \
+  }
+  // lanes per row and P columns per lane: few idle lanes for p up to 64 at
+  // moderate register use (6 columns of 8 lanes when p <= 48 and q <= 4)
+  if (p <= 8) ROWG_Q(2, 4)
+  if (p <= 16) ROWG_Q(4, 4)
+  if (p <= 32) ROWG_Q(8, 4)
+  if (p <= 48 && Q.nc <= 4) ROWG_Q4(8, 6)
+  ROWG_Q(16, 4)
+#undef ROWG_Q
+#undef ROWG_Q4
+#undef ROWG
+}
+
 size_t gram_partial_bytes(int max_blocks, int p, int q) { return (size_t)max_blocks * p * q * 8; }
 int gram_default_blocks() { return 152 * 4; }
 
@@ -872,6 +1052,9 @@ cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* Pp, in
   if (p < 1 || p > kGramThreads || Q.nc < 1 || Q.nc > kGramQ || nseg < 1 || nseg > 3) return cudaErrorInvalidValue;
   if (r1 <= r0) {  // empty row range: one block of zeros
     r1 = r0;
+  }
+  if (p <= kRowGramP && Q.nc <= 8) {
+    PHSVDS_DISPATCH(prec, gram_row_p<P>(r0, r1, sa, p, Q, partial, max_blocks, nblocks, st))
   }
   {
     SegV all[4];
