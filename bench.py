@@ -44,7 +44,7 @@ MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
 # this workload (--set full, one warm launch each); None where the kernel
 # changed after its capture
-TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None}
+TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_row_f32_32x4": 315_316_480}
 UNIT = "s"
 # FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x the maximum SM clock
 # (one FADD, FMUL or FFMA per lane per cycle); the Gram's FP64-class (Dot2)
@@ -579,7 +579,7 @@ def main():
     gram_roof = dict(bound="alu", kernel=f"k_gram_row (FP32, Gram {32} x {BLOCK} columns, FP64-class Dot2)",
                      achieved=g_ach, peak=g_peak, unit="T FP32 op/s", frac=g_ach / g_peak,
                      peak_kind="derived: 152 SMs x 128 FP32 lanes x max SM clock",
-                     traffic=None, hbm_frac=g32["gbs"] / peak)
+                     traffic=TRAFFIC["gram_row_f32_32x4"], hbm_frac=g32["gbs"] / peak)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
