@@ -1205,9 +1205,11 @@ __global__ void __launch_bounds__(kThreads) k_combine_row(long long L, SegArr se
       for (int sg = 0; sg < segs.n; ++sg) {
         const S* row = reinterpret_cast<const S*>(segs.p[sg]) + r * segs.ld[sg];
         const int nc = segs.nc[sg];
+        int c1 = 0;  // first column of the scalar tail
         if constexpr (VEC) {
           constexpr int W = (int)(16 / sizeof(S));
-          for (int c = 0; c < nc; c += W) {
+          c1 = nc - nc % W;
+          for (int c = 0; c < c1; c += W) {
             A xs[W];
             load16<P>(row + c, xs);
 #pragma unroll
@@ -1217,8 +1219,9 @@ __global__ void __launch_bounds__(kThreads) k_combine_row(long long L, SegArr se
               for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], xs[w], cr[j]);
             }
           }
-        } else {
-          for (int c = 0; c < nc; ++c) {
+        }
+        {
+          for (int c = c1; c < nc; ++c) {
             const A x = P::load(row + c);
             const C* cr = cs + (c0 + c) * Q + j0;
 #pragma unroll
@@ -1273,11 +1276,11 @@ cudaError_t combine_row_p(long long L, const SegArr& sa, int p, const void* coef
                           long long ldout2, cudaStream_t st) {
   using S = typename P::S;
   using C = typename P::C;
-  constexpr int W = (int)(16 / sizeof(S));
+  // 16-byte loads for the aligned bulk of each segment's row, scalar loads for
+  // its last columns (segment widths need not be multiples of 16 bytes)
   bool vec = true;
   for (int sg = 0; sg < sa.n; ++sg)
-    vec = vec && (reinterpret_cast<uintptr_t>(sa.p[sg]) % 16 == 0) && ((sa.ld[sg] * sizeof(S)) % 16 == 0) &&
-          (sa.nc[sg] % W == 0);
+    vec = vec && (reinterpret_cast<uintptr_t>(sa.p[sg]) % 16 == 0) && ((sa.ld[sg] * sizeof(S)) % 16 == 0);
   const C* cf = reinterpret_cast<const C*>(coef);
   const C* ri = reinterpret_cast<const C*>(Rinv);
   const S* in = reinterpret_cast<const S*>(In);
@@ -1388,9 +1391,11 @@ __global__ void __launch_bounds__(kThreads) k_ritz_row(long long L, const typena
     for (int j = 0; j < QT; ++j) ax[j] = ar[j] = P::zero();
     const S* vr = V + r * ldv;
     const S* wr = W + r * ldv;
+    int c1 = 0;  // first column of the scalar tail
     if constexpr (VEC) {
       constexpr int WW = (int)(16 / sizeof(S));
-      for (int c = 0; c < g; c += WW) {
+      c1 = g - g % WW;
+      for (int c = 0; c < c1; c += WW) {
         A xv[WW], xw[WW];
         load16<P>(vr + c, xv);
         load16<P>(wr + c, xw);
@@ -1404,8 +1409,9 @@ __global__ void __launch_bounds__(kThreads) k_ritz_row(long long L, const typena
           }
         }
       }
-    } else {
-      for (int c = 0; c < g; ++c) {
+    }
+    {
+      for (int c = c1; c < g; ++c) {
         const A xv = P::load(vr + c), xw = P::load(wr + c);
         const C* yr = ys + c * Q + j0;
 #pragma unroll
@@ -1451,9 +1457,9 @@ cudaError_t ritz_row_p(long long L, SegV V, SegV W, int g, const void* Y, const 
   using S = typename P::S;
   using C = typename P::C;
   using G = typename P::G;
-  constexpr int WW = (int)(16 / sizeof(S));
+  // 16-byte loads for the aligned bulk of each row, scalar loads for its last columns
   const bool vec = reinterpret_cast<uintptr_t>(V.p) % 16 == 0 && reinterpret_cast<uintptr_t>(W.p) % 16 == 0 &&
-                   (V.ld * sizeof(S)) % 16 == 0 && g % WW == 0;
+                   (V.ld * sizeof(S)) % 16 == 0;
   const S* vp = reinterpret_cast<const S*>(V.p);
   const S* wp = reinterpret_cast<const S*>(W.p);
   const C* yp = reinterpret_cast<const C*>(Y);
