@@ -456,6 +456,16 @@ def precond_gain(B, wl, sp):
     return out
 
 
+def bench_config(A, gpus):
+    """The workload and form of the timed solve (the same for both arms)."""
+    return dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
+                k=K, target=TARGET, block=BLOCK, tol=TOL, precond="learned (gnn_models/wgrid3d.bin)",
+                form="chosen: DYNAMIC stage 1 (GD+k or JDQMR correction per outer iteration by measured "
+                     "rates; JDQMR inner QMR solves in FP32), FP32 stage-1 phase, learned SPAI preconditioner, "
+                     "FP64-class outer polish/stage 2",
+                l2="working set >> L2 (no flush)", parallelism=f"replicas x{gpus}")
+
+
 def cpu_sample(A, seconds=15.0):
     """The oracle as it stands on a bounded sample: stage 1 (FP64, GD+k, Jacobi)
     on the same matrix, stopped after a matvec budget sized to ~`seconds`;
@@ -523,8 +533,8 @@ def main():
         line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                     warmup=args.warmup, ms_per_step=statistics.median(s for _, s in vals) * 1e3,
                     higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                    config=dict(workload=WORKLOAD, m=A.m, n=A.n, nnz=A.nnz, k=K, target=TARGET, block=BLOCK, tol=TOL),
-                    cpu_baseline=dict(value=value, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                    config=bench_config(A, args.gpus),
+                    cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
                                       sample=f"oracle stage-1 GD+k on the full matrix stopped after ~{vals[0][0]} "
                                              f"matvecs per step; seconds/matvec x {full} matvecs of a full solve"),
                     e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -584,12 +594,7 @@ def main():
         metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype="f32+df64", data="synthetic",
-        config=dict(workload=f"{WORKLOAD}: 3D grid-difference operator 128^3 ({A.m} x {A.n}, nnz {A.nnz})",
-                    k=K, target=TARGET, block=BLOCK, tol=TOL, precond="learned (gnn_models/wgrid3d.bin)",
-                    form="chosen: DYNAMIC stage 1 (GD+k or JDQMR correction per outer iteration by measured "
-                         "rates; JDQMR inner QMR solves in FP32), FP32 stage-1 phase, learned SPAI preconditioner, "
-                         "FP64-class outer polish/stage 2",
-                    l2="working set >> L2 (no flush)", parallelism=f"replicas x{args.gpus}"),
+        config=bench_config(A, args.gpus),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
         plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
                         form="JDQMR, FP64-class inner and outer, Jacobi",
