@@ -15,8 +15,12 @@
 // (Dekker 1971) and TwoProd via a fused multiply-add.  The primitives use the
 // _rn intrinsics so that the compiler cannot contract or reassociate them.
 #pragma once
-#include <cstdint>
 #include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace phsvds {
 
@@ -143,5 +147,20 @@ struct PF64 {
   __device__ static G gadd(G a, G b) { return a + b; }
   __device__ static double gval(G a) { return a; }
 };
+
+// Allow `kernel` up to `bytes` of dynamic shared memory on the current device.
+// The attribute is per device and per kernel (every template instance is its
+// own kernel), so it is set once per (device, kernel); thread safe.
+inline cudaError_t smem_optin(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, kernel})) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({dev, kernel});
+  return e;
+}
 
 }  // namespace phsvds

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -40,17 +41,18 @@ constexpr int kMaxNb = 8;
 constexpr int kMaxGrid = 2048;
 
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0, v = 0;
+  static std::atomic<int> sms{0};
+  int v = sms.load(std::memory_order_relaxed);
+  if (!v) {
+    int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
       cudaGetLastError();
       v = 152;
     }
-    sms = v;
+    sms.store(v, std::memory_order_relaxed);
   }
-  return sms;
+  return v;
 }
 
 // resident 256-thread CTAs per SM of one kernel (cached by kernel address)

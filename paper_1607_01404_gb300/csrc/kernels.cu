@@ -1097,10 +1097,9 @@ static cudaError_t combine_p(long long L, const SegArr& sa, int p, const void* c
   using C = typename P::C;
   const size_t sm = combine_smem<P>(p, q, Rinv != nullptr);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr_set[4] = {false, false, false, false};
-  if (!attr_set[P::id]) {
-    cudaFuncSetAttribute(k_combine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_combine<P>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   const int grid = persistent_grid((L + kCmbRows - 1) / kCmbRows, 1);
   k_combine<P><<<grid, kCmbThreads, sm, st>>>(L, sa, p, reinterpret_cast<const C*>(coef), reinterpret_cast<const S*>(In),
@@ -1337,10 +1336,9 @@ static cudaError_t ritz_p(long long L, SegV V, SegV W, int g, const void* Y, con
   const size_t sm = sizeof(A) * 2 * (size_t)kCmbRows * (g + 1) + sizeof(C) * ((size_t)g * nb + nb) +
                     sizeof(G) * (size_t)kCmbRows * nb + 16;
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr_set[4] = {false, false, false, false};
-  if (!attr_set[P::id]) {
-    cudaFuncSetAttribute(k_ritz_residual<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_ritz_residual<P>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   int grid = persistent_grid((L + kCmbRows - 1) / kCmbRows, 1);
   if (grid > max_blocks) grid = max_blocks;

@@ -774,16 +774,13 @@ static cudaError_t gram_tp(const TileDesc& T, long long r0, long long r1, int p,
   size_t smem = sizeof(float) * 2 * kRows * T.rowwords;
   const size_t red = sizeof(typename P::G) * (size_t)NG * p * q;
   if (red > smem) smem = red;
-  static bool attr[4][4] = {};
   using G = typename P::G;
   G* out = reinterpret_cast<G*>(partial);
-#define GRAM_LAUNCH(NQv, idx)                                                                      \
-  do {                                                                                             \
-    if (!attr[P::id][idx]) {                                                                       \
-      cudaFuncSetAttribute(k_gram_t<P, NQv>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-      attr[P::id][idx] = true;                                                                     \
-    }                                                                                              \
-    k_gram_t<P, NQv><<<grid, kT, smem, st>>>(T, r0, r1, p, q, out);                                \
+#define GRAM_LAUNCH(NQv, idx)                                                               \
+  do {                                                                                   \
+    const cudaError_t e_ = smem_optin(reinterpret_cast<const void*>(k_gram_t<P, NQv>), 200 * 1024); \
+    if (e_ != cudaSuccess) return e_;                                                   \
+    k_gram_t<P, NQv><<<grid, kT, smem, st>>>(T, r0, r1, p, q, out);                               \
   } while (0)
   if (q <= 1)
     GRAM_LAUNCH(1, 0);
@@ -818,16 +815,13 @@ static cudaError_t gram_bp(const TileDesc& T, long long r0, long long r1, int p,
   const size_t red = sizeof(typename P::G) * (size_t)NG * p * q;
   if (red > smem) smem = red;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr[4][4] = {};
   using G = typename P::G;
   G* out = reinterpret_cast<G*>(partial);
-#define GRAMB_LAUNCH(NQv, idx)                                                                        \
-  do {                                                                                                \
-    if (!attr[P::id][idx]) {                                                                          \
-      cudaFuncSetAttribute(k_gram_b<P, NQv, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-      attr[P::id][idx] = true;                                                                        \
-    }                                                                                                 \
-    k_gram_b<P, NQv, S><<<grid, kT, smem, st>>>(T, r0, r1, p, q, out);                                \
+#define GRAMB_LAUNCH(NQv, idx)                                                               \
+  do {                                                                                   \
+    const cudaError_t e_ = smem_optin(reinterpret_cast<const void*>(k_gram_b<P, NQv, S>), 200 * 1024); \
+    if (e_ != cudaSuccess) return e_;                                                   \
+    k_gram_b<P, NQv, S><<<grid, kT, smem, st>>>(T, r0, r1, p, q, out);                               \
   } while (0)
   if (q <= 1)
     GRAMB_LAUNCH(1, 0);
@@ -886,10 +880,9 @@ static cudaError_t combine_tp(const TileDesc& T, long long L, int p, const void*
   const size_t smem = sizeof(float) * 2 * kRows * T.rowwords + sizeof(C) * ((size_t)p * q + (Rinv ? (size_t)q * q : 0)) +
                       (Rinv ? sizeof(A) * (size_t)kRows * q : 0);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr[4] = {};
-  if (!attr[P::id]) {
-    cudaFuncSetAttribute(k_combine_t<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_combine_t<P>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   const long long ntiles = (L + kRows - 1) / kRows;
   k_combine_t<P><<<tiled_grid(ntiles), kT, smem, st>>>(
@@ -909,10 +902,9 @@ static cudaError_t combine_rp(const TileDesc& T, long long L, int p, const void*
   const int RG = ((T.g16tot + 7) / 8) * 8;
   const size_t smem = (size_t)S * RT * RG * 16 + sizeof(C) * ((size_t)p * q + (Rinv ? (size_t)q * q : 0));
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr[4] = {};
-  if (!attr[P::id]) {
-    cudaFuncSetAttribute(k_combine_rows<P, 8 / TPR, TPR, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_combine_rows<P, 8 / TPR, TPR, S>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   const long long ntiles = (L + RT - 1) / RT;
   long long grid = ntiles < 152LL * 8 ? ntiles : 152LL * 8;
@@ -960,10 +952,9 @@ static cudaError_t ritz_tp(const TileDesc& T, long long L, int g, const void* Y,
   const size_t red = sizeof(G) * 16 * kRows;
   if (red > smem) smem = red;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr[4] = {};
-  if (!attr[P::id]) {
-    cudaFuncSetAttribute(k_ritz_t<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_ritz_t<P>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   const long long ntiles = (L + kRows - 1) / kRows;
   int grid = tiled_grid(ntiles);
@@ -990,10 +981,9 @@ static cudaError_t ritz_rp(const TileDesc& T, long long L, int g, const void* Y,
   const size_t red = sizeof(G) * (size_t)NB * RT;
   if (red > smem) smem = red;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr[4] = {};
-  if (!attr[P::id]) {
-    cudaFuncSetAttribute(k_ritz_rows<P, NB, TPR, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr[P::id] = true;
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_ritz_rows<P, NB, TPR, S>), 200 * 1024);
+    if (e != cudaSuccess) return e;
   }
   const long long ntiles = (L + RT - 1) / RT;
   long long grid = ntiles < 152LL * 8 ? ntiles : 152LL * 8;
