@@ -34,7 +34,11 @@ kernels can be checked against it.  Every function is plain numpy/scipy.
 Parity status: pinned by closed forms (rho of an eigenvector of C; M = I on
 eigenvector samples; the power and smoothing samples converging to the
 extreme eigenvalues of C for M = I), central finite differences of the
-gradient with the samples fixed, scale invariance and the SPD property.
+gradient with the samples fixed, scale invariance and the SPD property; the
+forward pass (graph, features, every message-passing layer, both heads and M)
+by a node-by-node loop restatement of the definition above on a small graph
+with non-zero parameters, which separates an E/C swap, a dropped bias, a
+misplaced ReLU or swapped W1/W2.
 """
 from __future__ import annotations
 

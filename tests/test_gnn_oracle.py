@@ -155,3 +155,104 @@ def test_num_params_matches_library():
 
     BLD.build()
     assert B.gnn_num_params() == G.n_params()
+
+
+# ---------------------------------------------------------------------------
+# Pin of the message-passing layers and heads: the network recomputed node by
+# node with plain Python loops from the definition (graph of A^T A, features,
+# h' = relu(h W1 + (E h) W2 + b) for 4 layers, node and edge heads, M), with
+# non-zero parameters so that every term reaches the output.
+# ---------------------------------------------------------------------------
+def _forward_by_loops(Ad, params):
+    """Ad: small dense A (list of rows).  Returns (list of h^l, {(i, j): m_ij})."""
+    import math
+
+    mrows, n = len(Ad), len(Ad[0])
+    C = [[sum(Ad[r][i] * Ad[r][j] for r in range(mrows)) for j in range(n)] for i in range(n)]
+    pat = [[any(Ad[r][i] != 0 and Ad[r][j] != 0 for r in range(mrows)) for j in range(n)] for i in range(n)]
+    cd = [C[i][i] if C[i][i] > 0 else 1.0 for i in range(n)]
+    e = [[C[i][j] / math.sqrt(cd[i] * cd[j]) if (pat[i][j] and i != j) else 0.0 for j in range(n)] for i in range(n)]
+    deg = [sum(1 for j in range(n) if pat[i][j] and j != i) for i in range(n)]
+    wdeg = [sum(abs(e[i][j]) for j in range(n)) for i in range(n)]
+    logc = [math.log(cd[i]) for i in range(n)]
+    mean_log = sum(logc) / n
+    dmax = max(max(deg), 1)
+    h = [[logc[i] - mean_log, deg[i] / dmax] for i in range(n)]
+    hs = [h]
+    for layer in range(4):
+        W1, W2, bb = params[f"W1_{layer}"], params[f"W2_{layer}"], params[f"b_{layer}"]
+        fin, width = len(W1), len(W1[0])
+        nb = [[sum(e[i][j] * h[j][f] for j in range(n)) for f in range(fin)] for i in range(n)]
+        z = [[sum(h[i][f] * W1[f][o] for f in range(fin)) + sum(nb[i][f] * W2[f][o] for f in range(fin)) + bb[o]
+              for o in range(width)] for i in range(n)]
+        h = [[max(v, 0.0) for v in row] for row in z]
+        hs.append(h)
+    width = len(h[0])
+    u = [sum(h[i][f] * params["ws"][f] for f in range(width)) for i in range(n)]
+    d = [math.log1p(math.exp(sum(h[i][f] * params["wd"][f] for f in range(width)) + float(params["bd"])))
+         for i in range(n)]
+    delta = [d[i] / cd[i] for i in range(n)]
+    m = {}
+    for i in range(n):
+        for j in range(n):
+            if not pat[i][j]:
+                continue
+            if i == j:
+                m[(i, j)] = delta[i]
+            else:
+                s = math.tanh(u[i] + u[j] + float(params["we"]) * e[i][j] + float(params["bs"]))
+                m[(i, j)] = 0.9 * s * min(delta[i], delta[j]) * abs(e[i][j]) / max(wdeg[i], wdeg[j])
+    return hs, m
+
+
+def _pin_case():
+    A = wl.weighted_grid(3, 2, seed=11)  # 12 x 9, every column coupled to its neighbours
+    Ad = A.to_scipy().toarray()
+    rng = np.random.default_rng(42)
+    p = {}
+    for name, shp in G.param_shapes():
+        p[name] = rng.standard_normal(shp) * (0.6 if len(shp) == 2 else 0.3)
+    p["bd"] = np.array(0.4)
+    p["we"] = np.array(1.3)
+    p["bs"] = np.array(-0.2)
+    return A, Ad, p
+
+
+def test_forward_layers_and_heads_match_loops_over_the_definition():
+    A, Ad, p = _pin_case()
+    g = G.Graph(A.to_scipy())
+    m, cache = G.forward(g, p, keep=True)
+    hs, mref = _forward_by_loops(Ad.tolist(), {k: v.tolist() for k, v in p.items()})
+    for layer in range(5):
+        np.testing.assert_allclose(cache["h"][layer], np.array(hs[layer]), rtol=1e-12, atol=1e-13)
+    for layer in range(1, 5):  # every layer has active and inactive units, so the relu matters
+        z = cache["z"][layer - 1]
+        assert (z > 0).any() and (z < 0).any()
+    rows, cols = g.rows, g.indices
+    assert len(mref) == m.size
+    ref = np.array([mref[(int(i), int(j))] for i, j in zip(rows, cols)])
+    np.testing.assert_allclose(m, ref, rtol=1e-12, atol=1e-15)
+    assert np.abs(ref[g.offdiag]).min() > 0  # the edge head reaches every off-diagonal entry
+
+
+def test_forward_pin_separates_plausible_slips():
+    # each slip of the layer stack changes M by far more than the pin's tolerance
+    A, Ad, p = _pin_case()
+    g = G.Graph(A.to_scipy())
+    _, mref = _forward_by_loops(Ad.tolist(), {k: v.tolist() for k, v in p.items()})
+    ref = np.array([mref[(int(i), int(j))] for i, j in zip(g.rows, g.indices)])
+
+    def far(m):
+        return np.max(np.abs(m - ref) / np.abs(ref)) > 1e-6
+
+    swapped = dict(p)
+    for layer in range(4):
+        swapped[f"W1_{layer}"], swapped[f"W2_{layer}"] = p[f"W2_{layer}"], p[f"W1_{layer}"]
+    assert far(G.forward(g, swapped))
+    nobias = dict(p)
+    for layer in range(4):
+        nobias[f"b_{layer}"] = np.zeros_like(p[f"b_{layer}"])
+    assert far(G.forward(g, nobias))
+    gc = G.Graph(A.to_scipy())
+    gc.E = gc.C.copy()  # messages weighted by c_ij instead of the normalised e_ij
+    assert far(G.forward(gc, p))
