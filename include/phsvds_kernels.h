@@ -79,6 +79,20 @@ int phsvds_block_jacobi(int64_t n, const int32_t *rowptrT, const int32_t *colidx
 int phsvds_ortho(int prec, int64_t L, const void *V, int64_t ldv, int g, void *T, int64_t ldt, int nb, int *status,
                  void *stream);
 
+/* phsvds_ortho followed, when the device steps report a breakdown (*status
+ * nonzero), by the solver's repair (Sec. 3.2 orthogonalisation; the replacement
+ * rule of the method's restatement): the block as given is orthonormalised
+ * again by host-driven CGS2 + CholQR2 in which a column that keeps at most
+ * 1e-10 of its norm after the projection on V, or whose Cholesky pivot within
+ * the block keeps at most max(1e-20, 64 u) of its squared norm (u = the mode's
+ * unit roundoff: a column that depends on the block's earlier columns), is
+ * replaced by a seeded N(0, 1) vector (seed) before the block is
+ * orthonormalised again.  On return T is orthonormal and orthogonal to V;
+ * *replaced (host, may be NULL) is 1 when columns were replaced.  Allocates
+ * its own device and pinned host scratch. */
+int phsvds_ortho_repair(int prec, int64_t L, const void *V, int64_t ldv, int g, void *T, int64_t ldt, int nb,
+                        uint64_t seed, int *status, int *replaced, void *stream);
+
 /* JDQMR inner solve (Sec. 3.4): for each of the nb columns j, block symmetric
  * QMR on the correction equation
  *     (I - x_j x_j^T)(K - eta_j I)(I - x_j x_j^T) t_j = b_j,   t_j orthogonal to x_j,
@@ -113,12 +127,13 @@ int phsvds_combine(int prec, int64_t L, const void *P, int64_t ldp, int p, const
  * an interface convenience of this library.  Its scratch is a fixed device
  * array inside the library (2,490,368 bytes, held on every GPU that loads the
  * library until the process exits), so it serves p <= 64 and q <= 8 and returns
- * SVDS_ERR_ARG beyond that.  It allocates nothing.  The first call on each
- * device (with that device current) resolves the array's device address;
- * make it before any stream capture.  All calls share the one array: calls
- * whose kernels overlap on the GPU (different streams, or different host
- * threads) race on it; serialise them.  Each call overwrites the part of the
- * array it uses, so the previous call's contents do not affect its result. */
+ * SVDS_ERR_ARG beyond that.  It allocates nothing.  Every call resolves the
+ * array's device address in the current context (cudaGetSymbolAddress); the
+ * first call in a context also loads the library's device code, so make it
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race on it; serialise them.  Each call overwrites the part of the array it
+ * uses, so the previous call's contents do not affect its result. */
 int phsvds_gram_noalloc(int prec, int64_t r0, int64_t r1, const void *P, int64_t ldp, int p, const void *Q,
                         int64_t ldq, int q, double *G, void *stream);
 

@@ -9,13 +9,15 @@
 //
 // The array lives in this translation unit; every GPU that loads the library
 // holds it until the process exits.  Host code cannot use the array's name as
-// a device address (it is a host-side stand-in), so the first call on each
-// device, with that device current, resolves the address with
-// cudaGetSymbolAddress and caches it.  Make that first call before any stream
-// capture.
+// a device address (it is a host-side stand-in), so every call resolves the
+// address in the current context with cudaGetSymbolAddress, which allocates
+// nothing.  Resolving per call (instead of caching one address per device)
+// stays correct after cudaDeviceReset or when the caller switches contexts.
+// The first call in a context also loads the library's device code into it:
+// make that first call before any stream capture.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <algorithm>
 #include <string>
 
 #include "../../include/phsvds.h"
@@ -26,32 +28,23 @@
 namespace {
 
 // Largest shapes the static scratch serves: P^T Q with p <= 64 and q <= 8
-// (the block widths of the solver); the partials of one launch take
-// gram_default_blocks() * p * q * 8 bytes = 608 * 64 * 8 * 8 = 2,490,368 bytes.
+// (the block widths of the solver).  One launch writes nblocks * p * q
+// accumulators of 8 bytes; the array holds kScratchBlocks of the largest
+// shape, and every launch bounds its grid by what the array holds for its own
+// shape, so no grid size can write past the end.
 constexpr int kMaxP = 64;
 constexpr int kMaxQ = 8;
-constexpr size_t kScratchBytes = (size_t)152 * 4 * kMaxP * kMaxQ * 8;
+constexpr int kScratchBlocks = 152 * 4;
+constexpr size_t kScratchBytes = (size_t)kScratchBlocks * kMaxP * kMaxQ * 8;  // 2,490,368 bytes
 
 static __device__ __align__(256) unsigned char g_gram_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up on first use).
+// Device address of the scratch array in the current context.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_gram_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_gram_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -76,9 +69,12 @@ extern "C" int phsvds_gram_noalloc(int prec, int64_t r0, int64_t r1, const void*
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SegV Ps{P, ldp, p};
   SegV Qs{Q, ldq, q};
+  // the grid is bounded by the blocks whose partials fit the array
+  const int fit = (int)(kScratchBytes / gram_partial_bytes(1, p, q));
+  const int max_blocks = std::min(gram_default_blocks(), fit);
   int nb = 0;
   // every CTA overwrites all of its p * q partials, so nothing needs clearing
-  e = launch_gram(prec, r0, r1, &Ps, 1, Qs, scratch, gram_default_blocks(), &nb, st);
+  e = launch_gram(prec, r0, r1, &Ps, 1, Qs, scratch, max_blocks, &nb, st);
   if (e == cudaSuccess) e = launch_gram_reduce(prec, scratch, nb, p * q, G, st);
   if (e != cudaSuccess) {
     set_last_error(std::string(cudaGetErrorString(e)) + " in phsvds_gram_noalloc");

@@ -43,7 +43,7 @@ def _case(prec, L, p, q, r0, r1, seed):
 
 
 def test_gram_noalloc_matches_gram_on_two_calls_in_a_row():
-    # first call: a large shape that fills most of the static scratch
+    # first call: a shape that fills about half of the static scratch
     G1, R1, n1 = _case(B.PREC_DF64, 200003, 35, 8, 0, 200003, 1)
     assert np.all(np.abs(G1 - R1) <= 1e-13 * n1 + 1e-300)
     # second call: another mode and a smaller shape; the scratch keeps the
@@ -52,9 +52,19 @@ def test_gram_noalloc_matches_gram_on_two_calls_in_a_row():
     assert np.all(np.abs(G2 - R2) <= 1e-13 * n2 + 1e-300)
 
 
+@pytest.mark.parametrize("prec", [B.PREC_F32, B.PREC_DF64, B.PREC_F64])
+def test_gram_noalloc_at_the_largest_shape(prec):
+    # p = 64, q = 8: the shape that sizes the array (every block's partials used)
+    G, R, nrm = _case(prec, 300007, 64, 8, 5, 300001, 7)
+    assert np.all(np.abs(G - R) <= 1e-13 * nrm + 1e-300)
+
+
 def test_gram_noalloc_rejects_shapes_beyond_its_scratch():
     x = torch.zeros(16 * 72, dtype=torch.float64, device="cuda:0")
-    G = torch.zeros(72 * 8, dtype=torch.float64, device="cuda:0")
+    G = torch.zeros(72 * 9, dtype=torch.float64, device="cuda:0")
     with pytest.raises(B.SvdsError) as e:
         B.gram_noalloc(B.PREC_F64, 0, 16, x, 72, 72, x, 72, 8, G)
+    assert e.value.code == B.SVDS_ERR_ARG
+    with pytest.raises(B.SvdsError) as e:  # q = 9 > 8
+        B.gram_noalloc(B.PREC_F64, 0, 16, x, 72, 16, x, 72, 9, G)
     assert e.value.code == B.SVDS_ERR_ARG
