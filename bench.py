@@ -301,10 +301,10 @@ def run_gpu(args, world, rank, local):
             if form == "jdqmr":
                 kw.update(method_stage1=B.SVDS_JDQMR)
         elif form == "plain":
-            kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
-                      innerPrecision=B.SVDS_FP64)
+            kw.update(stage1_precision=B.SVDS_DF64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+                      innerPrecision=B.SVDS_DF64)
         else:  # plain GD+k
-            kw.update(stage1_precision=B.SVDS_FP64, method_stage1=B.SVDS_GDPK, method_stage2=B.SVDS_GDPK)
+            kw.update(stage1_precision=B.SVDS_DF64, method_stage1=B.SVDS_GDPK, method_stage2=B.SVDS_GDPK)
         return B.make_opts(**kw)
 
     def one_solve(form, seed, host_inputs=False):

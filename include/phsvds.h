@@ -45,7 +45,13 @@ extern "C" {
                           from the measured reduction of log ||r|| per second of each
                           (Sec. 3.4: the paper's stage-1 default switches to minimise time) */
 
-#define SVDS_FP64 3  /* FP64-class stage 1 (double-float arithmetic on the GPU) */
+#define SVDS_DF64 3  /* FP64-class stage 1 in DOUBLE-FLOAT arithmetic: every long vector is a pair
+                        (hi, lo) of floats and every operation an error-free FP32 transformation,
+                        unit roundoff about 2^-48 (native FP64 is 2^-53) with the FP32 exponent
+                        range (A is scaled by a power of two).  Not IEEE binary64: use
+                        SVDS_NATIVE_FP64 for native FP64 arithmetic throughout. */
+#define SVDS_FP64 SVDS_DF64 /* older name of SVDS_DF64, kept for source compatibility: it selects
+                               DOUBLE-FLOAT arithmetic, not native FP64 */
 #define SVDS_FP32 1  /* FP32 first phase of stage 1 (see svds_opts.stage1_precision) */
 #define SVDS_NATIVE_FP64 4 /* native FP64 arithmetic everywhere (check mode; slow on GB300) */
 #define SVDS_BF16 5  /* as SVDS_FP32, with the values of A (and of the explicit A^T A) stored in
@@ -87,7 +93,7 @@ typedef struct {
   int maxBlockSize;     /* 0 = 1 */
   int method_stage1;    /* SVDS_GDPK (default), SVDS_JDQMR or SVDS_DYNAMIC */
   int method_stage2;    /* SVDS_GDPK (default) or SVDS_JDQMR */
-  int stage1_precision; /* SVDS_FP64 (default), SVDS_FP32, SVDS_BF16 or SVDS_NATIVE_FP64 */
+  int stage1_precision; /* SVDS_DF64 (default), SVDS_FP32, SVDS_BF16 or SVDS_NATIVE_FP64 */
   int stage1_polish;    /* with SVDS_FP32: 1 = continue stage 1 in FP64-class arithmetic
                            to the paper's stage-1 criterion before stage 2 (default 1) */
   int precond;          /* SVDS_PRECOND_JACOBI (default), SVDS_PRECOND_NONE, SVDS_PRECOND_LEARNED
@@ -103,7 +109,7 @@ typedef struct {
   int innerMaxIt;       /* JDQMR: inner steps per correction, 0 = 30 */
   double innerRelTol;   /* JDQMR: stop an inner solve when its QMR residual bound falls below
                            this fraction of the right-hand side, 0 = 0.1 */
-  int innerPrecision;   /* JDQMR inner solves: SVDS_FP32 (default) or SVDS_FP64 (the FP64-class
+  int innerPrecision;   /* JDQMR inner solves: SVDS_FP32 (default) or SVDS_DF64 (the FP64-class
                            mode of the outer iteration) */
   const float *precondParams; /* SVDS_PRECOND_LEARNED: host array of phsvds_gnn_num_params()
                                  network parameters (copied by svds_create), or NULL */
@@ -117,6 +123,12 @@ typedef struct {
                                  Stage 1 uses GD+k corrections in this mode whatever
                                  method_stage1 says.  0 (default) = the rules of Algorithm 1 */
   int precondBlockSize;       /* SVDS_PRECOND_BLOCKJACOBI: columns per block, 1..64 (0 = 32) */
+  int precondStallIts;        /* SVDS_PRECOND_LEARNED: the plain Jacobi preconditioner replaces the
+                                 learned M for the rest of stage 1 after this many outer iterations
+                                 in which the smallest residual of the corrected block did not fall
+                                 below 0.9 of its best since a pair last converged (0 = 20, < 0 =
+                                 never).  An M with a non-finite value or a non-positive diagonal is
+                                 replaced before the first iteration.  See svds_stats.precond_fallback */
 } svds_opts;
 
 /* Performance report (the paper's stats, Sec. 3.4; matvecs count products
@@ -140,6 +152,8 @@ typedef struct {
   int64_t normal_nnz;         /* nonzeros of the explicit C = A^T A, 0 when A then A^T is used */
   double seconds_output;      /* returning the vectors: FP64 conversion, sign convention, copies to U, V */
   int64_t outer_stage1_jdqmr; /* stage-1 outer iterations whose correction came from JDQMR */
+  int precond_fallback;       /* 0, or the learned preconditioner was replaced by Jacobi: 1 = M
+                                 rejected (non-finite value or non-positive diagonal), 2 = stall */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

@@ -30,7 +30,8 @@ SVDS_GDPK = 0
 SVDS_JDQMR = 1
 SVDS_DYNAMIC = 2
 SVDS_FP32 = 1
-SVDS_FP64 = 3
+SVDS_DF64 = 3  # double-float (FP64-class, u ~ 2^-48), not native FP64
+SVDS_FP64 = SVDS_DF64  # older name of SVDS_DF64
 SVDS_NATIVE_FP64 = 4
 SVDS_BF16 = 5
 SVDS_NORMAL_AUTO = 0
@@ -60,7 +61,8 @@ class svds_opts(C.Structure):
                 ("innerPrecision", C.c_int), ("precondParams", C.c_void_p), ("precondModel", C.c_char_p),
                 ("normalOperator", C.c_int),
                 ("relTol", C.c_double),
-                ("precondBlockSize", C.c_int)]
+                ("precondBlockSize", C.c_int),
+                ("precondStallIts", C.c_int)]
 
 
 class svds_stats(C.Structure):
@@ -73,7 +75,8 @@ class svds_stats(C.Structure):
                 ("seconds_host_eig", C.c_double), ("seconds_sync_wait", C.c_double), ("host_syncs", C.c_int64),
                 ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64),
                 ("seconds_output", C.c_double),
-                ("outer_stage1_jdqmr", C.c_int64)]
+                ("outer_stage1_jdqmr", C.c_int64),
+                ("precond_fallback", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -106,6 +109,8 @@ _SIGS = {
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phsvds_ortho": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                C.POINTER(C.c_int), C.c_void_p]),
+    "phsvds_ortho_repair": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                      C.c_int, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p]),
     "phsvds_jd_solve": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                   C.c_double, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
@@ -359,6 +364,14 @@ def ortho(prec, L, V, ldv, g, T, ldt, nb, stream=None):
     _check(lib().phsvds_ortho(prec, L, V.data_ptr(), ldv, g, T.data_ptr(), ldt, nb, C.byref(status), _stream(stream)),
            "phsvds_ortho")
     return status.value
+
+
+def ortho_repair(prec, L, V, ldv, g, T, ldt, nb, seed=1, stream=None):
+    """phsvds_ortho with the solver's repair of a breakdown; returns (status, replaced)."""
+    status, replaced = C.c_int(0), C.c_int(0)
+    _check(lib().phsvds_ortho_repair(prec, L, V.data_ptr(), ldv, g, T.data_ptr(), ldt, nb, seed, C.byref(status),
+                                     C.byref(replaced), _stream(stream)), "phsvds_ortho_repair")
+    return status.value, replaced.value
 
 
 def jd_solve(prec, n, rowptr, colidx, v32, v32lo, v64, nb, X, Bv, eta, dinv, maxit, xi, T, stream=None):

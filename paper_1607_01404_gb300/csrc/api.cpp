@@ -158,7 +158,7 @@ int svds_opts_default(svds_opts* o) {
   o->maxBlockSize = 1;
   o->method_stage1 = SVDS_GDPK;
   o->method_stage2 = SVDS_GDPK;
-  o->stage1_precision = SVDS_FP64;
+  o->stage1_precision = SVDS_DF64;
   o->stage1_polish = 1;
   o->precond = SVDS_PRECOND_JACOBI;
   o->seed = 1;
@@ -177,14 +177,14 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
     o = *opts;
   else
     svds_opts_default(&o);
-  if (o.stage1_precision != SVDS_FP64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_BF16 &&
+  if (o.stage1_precision != SVDS_DF64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_BF16 &&
       o.stage1_precision != SVDS_NATIVE_FP64)
     return SVDS_ERR_ARG;
   if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
   if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR && o.method_stage1 != SVDS_DYNAMIC) ||
       (o.method_stage2 != SVDS_GDPK && o.method_stage2 != SVDS_JDQMR) || o.innerMaxIt < 0 || o.innerRelTol < 0)
     return SVDS_ERR_ARG;
-  if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_FP64) return SVDS_ERR_ARG;
+  if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_DF64) return SVDS_ERR_ARG;
   if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
   if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED &&
       o.precond != SVDS_PRECOND_BLOCKJACOBI)
@@ -389,6 +389,14 @@ int phsvds_ortho(int prec, int64_t L, const void* V, int64_t ldv, int g, void* T
   if (!prec_ok(prec) || L < 1 || !V || !T || g < 1 || nb < 1 || nb > 8 || g + nb > 256 || ldv < g || ldt < nb)
     return SVDS_ERR_ARG;
   return ortho_block(prec, L, V, ldv, g, T, ldt, nb, status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int phsvds_ortho_repair(int prec, int64_t L, const void* V, int64_t ldv, int g, void* T, int64_t ldt, int nb,
+                        uint64_t seed, int* status, int* replaced, void* stream) {
+  if (!prec_ok(prec) || L < 1 || !V || !T || g < 1 || nb < 1 || nb > 8 || g + nb > 256 || ldv < g || ldt < nb)
+    return SVDS_ERR_ARG;
+  return ortho_block(prec, L, V, ldv, g, T, ldt, nb, status, reinterpret_cast<cudaStream_t>(stream), true, seed,
+                     replaced);
 }
 
 int phsvds_jd_solve(int prec, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,

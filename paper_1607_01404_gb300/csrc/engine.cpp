@@ -84,10 +84,14 @@ struct Ctx {
   double* dwork = nullptr;
   void* dco[4] = {nullptr, nullptr, nullptr, nullptr};
   int* dstatus = nullptr;  // breakdown flags raised by the device steps
+  int* dflag = nullptr;    // result of the learned preconditioner's check
   int* hstatus = nullptr;  // pinned copy
   bool device_ortho = true;
   long long inner = 0;     // JDQMR inner steps
   bool bf16 = false;       // F32-mode operator applications use the bfloat16 values
+  // the learned preconditioner was replaced by Jacobi: 1 = M failed its
+  // check (a non-finite value or a non-positive diagonal), 2 = stall
+  int precond_fallback = 0;
   // CSR of A (which 0), A^T (1) or the explicit C (2) in the value format of prec
   CsrDev op(int prec, int which) const {
     CsrDev m = which == 2 ? A->csrC() : A->csr(which == 1);
@@ -382,6 +386,32 @@ OrthoRes ortho(Ctx& c, int prec, long long L, const std::vector<SegV>& basis, vo
   std::vector<int> bad;
   for (int j = 0; j < nb; ++j)
     if (!(S[(size_t)j * nb + j] > 1e-20 * std::max(norms0[j], 1e-300))) bad.push_back(j);
+  if (bad.empty()) {
+    // numerical rank of the block itself: Cholesky of S in column order; a
+    // column whose pivot keeps at most tau of its squared norm depends on the
+    // earlier columns of the block (a duplicated correction, say) and is
+    // replaced in the same way.  tau is the drop rule's 1e-20 or, above it,
+    // the rounding level of the mode's storage (a duplicate's pivot is
+    // rounding noise, not zero)
+    const double tau = std::max(1e-20, 64.0 * unit_roundoff(prec));
+    std::vector<double> Lc((size_t)nb * nb, 0.0);  // lower factor, row-major; skipped columns stay 0
+    for (int j = 0; j < nb; ++j) {
+      const double sjj = S[(size_t)j * nb + j];
+      double d = sjj;
+      for (int l = 0; l < j; ++l) d -= Lc[(size_t)j * nb + l] * Lc[(size_t)j * nb + l];
+      if (!(d > tau * sjj)) {
+        bad.push_back(j);
+        continue;
+      }
+      const double ljj = std::sqrt(d);
+      Lc[(size_t)j * nb + j] = ljj;
+      for (int i = j + 1; i < nb; ++i) {
+        double v = 0.5 * (S[(size_t)i * nb + j] + S[(size_t)j * nb + i]);
+        for (int l = 0; l < j; ++l) v -= Lc[(size_t)i * nb + l] * Lc[(size_t)j * nb + l];
+        Lc[(size_t)i * nb + j] = v / ljj;
+      }
+    }
+  }
   if (!bad.empty()) {
     if (depth >= 3) throw NumFail{"orthogonalisation breakdown persists"};
     for (int j : bad) {
@@ -517,6 +547,13 @@ struct RunCfg {
   double jd_xi = 0.1;
   // DYNAMIC: choose between the two corrections per outer iteration
   bool dyn = false;
+  // fallback of a learned preconditioner (K / jdK) to Jacobi: after stall_its
+  // outer iterations in which the smallest residual of the corrected block
+  // did not fall below 0.9 of its best since the last newly converged pair
+  // (0 = never), K and jdK are dropped for the Jacobi scalings below
+  int stall_its = 0;
+  const void* fb_dscale = nullptr;  // Jacobi diagonal in the outer mode's storage
+  const void* fb_jdinv = nullptr;   // the same in the inner mode's storage
 };
 
 struct RunOut {
@@ -788,7 +825,8 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
 // ---------------------------------------------------------------------------
 // GD+k with Rayleigh-Ritz and soft locking (stage 1 on C; stage 2 largest on B)
 // ---------------------------------------------------------------------------
-RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long ldx) {
+RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg0, void* Xout, long long ldx) {
+  RunCfg cfg = cfg0;  // the preconditioner may fall back to Jacobi during the run
   const int prec = B.prec;
   const int k = cfg.k, b = cfg.b;
   RunOut out;
@@ -802,6 +840,9 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
   std::vector<double> w, Z;
   DynState dyn;
   std::vector<std::pair<int, double>> tested;  // (Ritz index, residual) of this iteration
+  // stall detector of a learned preconditioner
+  double stall_best = 1e300;
+  int stall_since = 0, stall_nconv = -1;
   while (true) {
     c.budget();
     ++out.outer;
@@ -905,6 +946,29 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg, void* Xout, long long l
       for (char f : flags) nf += f;
       std::fprintf(stderr, "[%s] it %lld g %d conv %d/%d theta0 %.10e minres %.3e mv %lld\n", cfg.name, out.outer, g,
                    nf, k, theta[0], mn, c.mv);
+    }
+    if (cfg.stall_its > 0 && (cfg.K || cfg.jdK)) {
+      int nf = 0;
+      for (char f : flags) nf += f;
+      double rmin = 1e300;
+      for (double r : rnb) rmin = std::min(rmin, r);
+      if (nf > stall_nconv) {
+        stall_nconv = nf;
+        stall_best = rmin;
+        stall_since = 0;
+      } else if (rmin < 0.9 * stall_best) {
+        stall_best = rmin;
+        stall_since = 0;
+      } else if (++stall_since >= cfg.stall_its) {
+        cfg.K = nullptr;
+        cfg.jdK = nullptr;
+        cfg.dscale = cfg.fb_dscale;
+        cfg.jdinv = cfg.fb_jdinv;
+        c.precond_fallback = 2;
+        if (c.print >= 1)
+          std::fprintf(stderr, "[%s] learned preconditioner stalled for %d outer iterations: Jacobi from here on\n",
+                       cfg.name, cfg.stall_its);
+      }
     }
     bool use_jd = cfg.jd;
     if (cfg.dyn) {
@@ -1202,11 +1266,13 @@ const char* last_error_cstr() { return g_last_error.c_str(); }
 // The device-side CGS2 + CholQR2 of the solver on caller buffers, with its own
 // scratch (the kernel-level entry point phsvds_ortho).
 int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void* T, long long ldt, int nb,
-                int* status, cudaStream_t st) {
+                int* status, cudaStream_t st, bool repair, unsigned long long seed, int* replaced) {
   Ctx c;
   c.st = st;
   c.maxblk = gram_default_blocks();
+  c.seed = seed;
   std::vector<void*> mem;
+  void* hpin = nullptr;
   auto take = [&](size_t bytes) -> void* {
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -1219,6 +1285,7 @@ int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void
   auto done = [&](int code) {
     cudaStreamSynchronize(st);
     for (void* p : mem) cudaFree(p);
+    if (hpin) cudaFreeHost(hpin);
     return code;
   };
   c.partial = take(gram_partial_bytes(c.maxblk, 256, 8));
@@ -1228,13 +1295,41 @@ int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void
   c.dstatus = static_cast<int*>(take(256));
   if (!c.partial || !c.dGo || !c.dwork || !c.dco[0] || !c.dco[1] || !c.dco[2] || !c.dco[3] || !c.dstatus)
     return done(SVDS_ERR_NOMEM);
+  // the host-driven repair needs a copy of the block, the Gram staging and
+  // coefficient slots (as in a solve)
+  void* T0 = nullptr;
+  if (repair) {
+    c.gcap = 264 * 8;
+    c.nslots = 8;
+    c.slot_bytes = 264 * 8 * 8;  // a (g + nb) x nb coefficient block
+    c.dG = static_cast<double*>(take(sizeof(double) * c.gcap));
+    c.dstage = static_cast<char*>(take((size_t)c.nslots * c.slot_bytes));
+    T0 = take((size_t)L * nb * elem_bytes(prec));
+    if (cudaMallocHost(&hpin, sizeof(double) * c.gcap + (size_t)c.nslots * c.slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      hpin = nullptr;
+    }
+    if (!c.dG || !c.dstage || !T0 || !hpin) return done(SVDS_ERR_NOMEM);
+    c.hG = static_cast<double*>(hpin);
+    c.hstage = static_cast<char*>(hpin) + sizeof(double) * c.gcap;
+    c.slot_epoch.assign(c.nslots, 0);
+  }
+  if (replaced) *replaced = 0;
   try {
     CK(cudaMemsetAsync(c.dstatus, 0, sizeof(int), st));
+    if (repair) CK(launch_copy_cols(prec, L, T, ldt, T0, nb, nb, st));
     ortho_dev(c, prec, L, SegV{V, ldv, g}, T, ldt, nb, nullptr, 0);
     int hs = 0;
     CK(cudaMemcpyAsync(&hs, c.dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (status) *status = hs;
+    if (repair && hs != 0) {
+      // the solver's breakdown path: the block as given, orthonormalised by the
+      // host-driven CGS2 + CholQR2 that replaces dependent columns
+      CK(launch_copy_cols(prec, L, T0, nb, T, ldt, nb, st));
+      OrthoRes r = ortho(c, prec, L, {SegV{V, ldv, g}}, T, ldt, nb, nullptr, 0);
+      if (replaced) *replaced = r.replaced ? 1 : 0;
+    }
   } catch (const CudaFail& f) {
     set_last_error(std::string(cudaGetErrorString(f.e)) + " at " + f.where);
     cudaGetLastError();
@@ -1353,6 +1448,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     reqs.push_back({(void**)&c.dwork, sizeof(double) * 128});
     for (int i = 0; i < 4; ++i) reqs.push_back({&c.dco[i], sizeof(double) * 264 * 8});
     reqs.push_back({(void**)&c.dstatus, 256});
+    reqs.push_back({(void**)&c.dflag, 256});
     c.nslots = 64;
     // one slot holds the largest coefficient block: a basis-by-basis restart
     // matrix of the widest basis (8-byte coefficients)
@@ -1459,7 +1555,12 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       };
     };
     const bool jac = smallest && o.precond == SVDS_PRECOND_JACOBI;
-    if (jac) {
+    // learned sparse approximate inverse on the pattern of C (stage 1 only,
+    // smallest values; its scale is immaterial to GD+k and to the sQMR
+    // iterates); the plain Jacobi preconditioner is its fallback, so the
+    // Jacobi scalings are built for it too
+    bool learned = smallest && o.precond == SVDS_PRECOND_LEARNED && !h->gnn_params.empty();
+    if (jac || learned) {
       if (lowprec) CK(launch_make_dscale(kF32, n, A.colsq, 0, d1a, c.st));
       CK(launch_make_dscale(p2, n, A.colsq, 0, d1, c.st));
       c.launches += lowprec ? 2 : 1;
@@ -1468,9 +1569,6 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
         c.launches += 1;
       }
     }
-    // learned sparse approximate inverse on the pattern of C (stage 1 only,
-    // smallest values; its scale is immaterial to GD+k and to the sQMR iterates)
-    const bool learned = smallest && o.precond == SVDS_PRECOND_LEARNED && !h->gnn_params.empty();
     CsrDev K32, K64;
     if (learned) {
       const double tp = c.elapsed();
@@ -1483,9 +1581,26 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       if (grc == SVDS_ERR_NOMEM) return SVDS_ERR_NOMEM;
       if (grc) throw CudaFail{cudaErrorUnknown, "learned preconditioner"};
       c.launches += gnn_launches(gg);
+      // M must be usable: finite values and a positive diagonal (its
+      // construction guarantees both for finite parameters unless the
+      // diagonal underflows); otherwise Jacobi replaces it for the whole solve
+      CK(cudaMemsetAsync(c.dflag, 0, sizeof(int), c.st));
+      CK(launch_precond_check(n, K32.rowptr, K32.colidx, K32.v32, nullptr, c.dflag, c.st));
+      if (p2 == kF64) CK(launch_precond_check(n, K64.rowptr, K64.colidx, nullptr, K64.v64, c.dflag, c.st));
+      c.launches += p2 == kF64 ? 2 : 1;
+      CK(cudaMemcpyAsync(c.hstatus + 1, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
       c.sync();
+      if (c.hstatus[1] != 0) {
+        learned = false;
+        c.precond_fallback = 1;
+        if (c.print >= 1)
+          std::fprintf(stderr, "[setup] learned preconditioner rejected (%s): Jacobi instead\n",
+                       (c.hstatus[1] & 1) ? "non-finite value" : "non-positive diagonal");
+      }
       S.seconds_precond = c.elapsed() - tp;
     }
+    // Jacobi where the learned preconditioner was asked for and rejected
+    const bool jac_fb = c.precond_fallback == 1;
     // block Jacobi on C (Sec. 4), stage 1, smallest values: a CSR matrix with
     // dense diagonal blocks, applied by the same SpMM kernels as the learned M
     const bool bjac = smallest && o.precond == SVDS_PRECOND_BLOCKJACOBI;
@@ -1522,7 +1637,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     }
     const bool sparseM = learned || bjac;
     const CsrDev* Kouter = sparseM ? (p2 == kF64 ? &K64 : &K32) : nullptr;
-    const int jd_prec = o.innerPrecision == SVDS_FP64 ? p2 : kF32;
+    const int jd_prec = o.innerPrecision == SVDS_DF64 ? p2 : kF32;
     const CsrDev* Kinner = sparseM ? (jd_prec == kF64 ? &K64 : &K32) : nullptr;
     const int jd_maxk = o.innerMaxIt > 0 ? o.innerMaxIt : 30;
     const double jd_xi = o.innerRelTol > 0 ? o.innerRelTol : 0.1;
@@ -1561,7 +1676,12 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.jd = jd1 && !dyn1 && !(relTol > 0);
     c1.dyn = dyn1 && !(relTol > 0);
     c1.jd_prec = jd_prec;
-    c1.jdinv = jac ? (jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1)) : nullptr;
+    const void* jd_jacobi = jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1);
+    c1.jdinv = (jac || jac_fb) ? jd_jacobi : nullptr;
+    if (learned) {
+      c1.stall_its = o.precondStallIts == 0 ? 20 : std::max(0, o.precondStallIts);
+      c1.fb_jdinv = jd_jacobi;
+    }
     c1.jd_maxk = jd_maxk;
     c1.jd_xi = jd_xi;
     c1.jdK = Kinner;
@@ -1572,7 +1692,8 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       const bool exact_vals = A.exact16 && (A.nnzC > 0 ? A.exactC : A.exact32);
       c1.u = (bf16 && !exact_vals) ? std::ldexp(1.0, -8) : unit_roundoff(kF32);
       c1.conv = stage1_conv(c1.u);
-      c1.dscale = jac ? d1a : nullptr;
+      c1.dscale = (jac || jac_fb) ? d1a : nullptr;
+      c1.fb_dscale = d1a;
       c1.K = sparseM ? &K32 : nullptr;
       c1.V0 = X1a;
       c1.ldv0 = kk;
@@ -1593,8 +1714,15 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     if (polish) {
       c1.u = unit_roundoff(p2);
       c1.conv = stage1_conv(c1.u);
-      c1.dscale = jac ? d1 : nullptr;
+      c1.dscale = (jac || jac_fb) ? d1 : nullptr;
+      c1.fb_dscale = d1;
       c1.K = Kouter;
+      if (c.precond_fallback == 2) {  // the FP32 phase stalled with the learned M
+        c1.dscale = d1;
+        c1.K = nullptr;
+        c1.jdK = nullptr;
+        c1.jdinv = jd_jacobi;
+      }
       c1.V0 = X1;
       c1.ldv0 = kk;
       c1.b0 = lowprec ? k : b0;
@@ -1852,6 +1980,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     S.inner_steps = c.inner;
     S.normal_nnz = A.nnzC > 0 ? A.nnzC : 0;
     S.seconds_output = c.elapsed() - t_out;
+    S.precond_fallback = c.precond_fallback;
     if (stats) *stats = S;
     h->launches += c.launches;
     return SVDS_OK;
@@ -1869,6 +1998,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     if (numConverged) *numConverged = 0;
     S.seconds_total = c.elapsed();
     S.kernel_launches = c.launches;
+    S.precond_fallback = c.precond_fallback;
     if (stats) *stats = S;
     return SVDS_ERR_MAXIT;
   }

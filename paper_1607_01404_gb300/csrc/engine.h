@@ -105,5 +105,6 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
           int* numConverged, svds_stats* stats);
 void set_last_error(const std::string& s);
 int ortho_block(int prec, long long L, const void* V, long long ldv, int g, void* T, long long ldt, int nb,
-                int* status, cudaStream_t st);
+                int* status, cudaStream_t st, bool repair = false, unsigned long long seed = 0,
+                int* replaced = nullptr);
 }  // namespace phsvds

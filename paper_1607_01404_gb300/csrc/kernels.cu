@@ -248,15 +248,6 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(long long r0, long long r
 }
 
 template <class P>
-__global__ void k_gram_reduce(const typename P::G* __restrict__ partial, int nblocks, int pq, double* __restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= pq) return;
-  typename P::G s = partial[e];
-  for (int b = 1; b < nblocks; ++b) s = P::gadd(s, partial[(long long)b * pq + e]);
-  G[e] = P::gval(s);
-}
-
-template <class P>
 cudaError_t gram_p(long long r0, long long r1, const SegArr& sa, int p, SegV Q, void* partial, int max_blocks,
                    int* nblocks, cudaStream_t st) {
   long long rows = r1 - r0;
@@ -692,6 +683,20 @@ __global__ void k_sort_segments(long long rowsT, const int* rowptrT, int* colidx
   }
 }
 
+__global__ void k_precond_check(long long n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                                const float* __restrict__ v32, const double* __restrict__ v64, int* flags) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    int f = 2;  // until a positive diagonal entry is seen
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const double v = v32 ? (double)v32[k] : v64[k];
+      if (!isfinite(v)) f |= 1;
+      if (colidx[k] == i && v > 0) f &= ~2;
+    }
+    if (f) atomicOr(flags, f);
+  }
+}
+
 __global__ void k_row_sumsq(long long rows, const int* rowptr, const double* vals, double* out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -1042,6 +1047,14 @@ cudaError_t gram_row_p(long long r0, long long r1, const SegArr& sa, int p, SegV
 #undef ROWG
 }
 
+cudaError_t launch_precond_check(long long n, const int* rowptr, const int* colidx, const float* v32,
+                                 const double* v64, int* flags, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (!v32 && !v64) return cudaErrorInvalidValue;
+  k_precond_check<<<std::min(grid_for(n, kThreads), 152 * 8), kThreads, 0, st>>>(n, rowptr, colidx, v32, v64, flags);
+  return cudaGetLastError();
+}
+
 size_t gram_partial_bytes(int max_blocks, int p, int q) { return (size_t)max_blocks * p * q * 8; }
 int gram_default_blocks() { return 152 * 4; }
 
@@ -1069,24 +1082,6 @@ cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* Pp, in
 
 cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st) {
   return tiled_reduce(prec, partial, nblocks, pq, G, st);
-}
-
-cudaError_t launch_gram_reduce_serial(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st) {
-  const int grid = grid_for(pq, kThreads);
-  switch (prec) {
-    case kF32:
-      k_gram_reduce<PF32><<<grid, kThreads, 0, st>>>(reinterpret_cast<const df*>(partial), nblocks, pq, G);
-      break;
-    case kDF64:
-      k_gram_reduce<PDF64><<<grid, kThreads, 0, st>>>(reinterpret_cast<const df*>(partial), nblocks, pq, G);
-      break;
-    case kF64:
-      k_gram_reduce<PF64><<<grid, kThreads, 0, st>>>(reinterpret_cast<const double*>(partial), nblocks, pq, G);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 template <class P>

@@ -139,6 +139,12 @@ cudaError_t launch_make_dscale(int prec, long long L, const double* s, int use_s
 cudaError_t launch_csr_validate(long long rows, long long cols, const int* rowptr, const int* colidx,
                                 const double* vals, int* flags, cudaStream_t st);
 
+// Check of a square sparse preconditioner (FP32 values v32, or FP64 v64 when
+// v32 is null): flags[0] |= 1 for a non-finite value, |= 2 for a row whose
+// diagonal entry is missing or not positive.
+cudaError_t launch_precond_check(long long n, const int* rowptr, const int* colidx, const float* v32,
+                                 const double* v64, int* flags, cudaStream_t st);
+
 // Small dense steps of the device-side CGS2 + CholQR2 (see kernels.cu).
 cudaError_t launch_ortho_small(int stage, int prec, int g, int nb, const double* G, double* work, void* coef,
                                void* rinv, int* status, double drop2, cudaStream_t st);

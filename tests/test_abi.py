@@ -40,7 +40,7 @@ def test_strerror_and_defaults():
     assert B.svds_strerror(0) == "success"
     assert "CSR" in B.svds_strerror(B.SVDS_ERR_CSR)
     o = B.svds_opts_default()
-    assert o.maxBlockSize == 1 and o.stage1_precision == B.SVDS_FP64 and o.precond == B.SVDS_PRECOND_JACOBI
+    assert o.maxBlockSize == 1 and o.stage1_precision == B.SVDS_DF64 and o.precond == B.SVDS_PRECOND_JACOBI
 
 
 def test_host_symeig_matches_lapack():

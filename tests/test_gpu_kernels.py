@@ -253,6 +253,39 @@ def test_device_ortho_matches_oracle(prec, g, nb):
     assert np.abs(Vs.T @ Q).max() <= tol
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_device_ortho_breakdown_is_reported_and_repaired(prec):
+    """A block with a column in span(V) and a duplicated column: the device
+    CGS2 + CholQR2 reports the breakdown (host-visible status), and the
+    solver's repair replaces the dependent columns by seeded random vectors
+    so that the result is orthonormal and orthogonal to V; the independent
+    column keeps its direction (it is the first column of Q up to sign)."""
+    L, g, nb = 20011, 9, 4
+    rng = np.random.default_rng(77)
+    V = np.linalg.qr(rng.standard_normal((L, g)))[0]
+    t = rng.standard_normal(L)
+    T = np.stack([t, V @ rng.standard_normal(g), t, rng.standard_normal(L)], axis=1)  # col 1 in span(V), col 2 = col 0
+    ldv, ldt = _ld(g, True), _ld(nb, True)
+    Vd = to_device(prec, V, ld=ldv)
+    Vs = to_host(prec, Vd, L, ldv)[:, :g]
+    Td = to_device(prec, T, ld=ldt)
+    assert B.ortho(prec, L, Vd, ldv, g, Td, ldt, nb) != 0
+    Td = to_device(prec, T, ld=ldt)
+    Ts = to_host(prec, Td, L, ldt)[:, :nb]
+    status, replaced = B.ortho_repair(prec, L, Vd, ldv, g, Td, ldt, nb, seed=5)
+    assert status != 0 and replaced == 1
+    Q = to_host(prec, Td, L, ldt)[:, :nb]
+    tol = 2e-5 if prec == B.PREC_F32 else 1e-11
+    assert np.abs(Q.T @ Q - np.eye(nb)).max() <= tol
+    assert np.abs(Vs.T @ Q).max() <= tol
+    t0 = Ts[:, 0] - Vs @ (Vs.T @ Ts[:, 0])
+    assert abs(abs(Q[:, 0] @ t0) / np.linalg.norm(t0) - 1) <= tol
+    # a regular block goes through unchanged by the repair path
+    Tr = rng.standard_normal((L, nb))
+    Td = to_device(prec, Tr, ld=ldt)
+    assert B.ortho_repair(prec, L, Vd, ldv, g, Td, ldt, nb) == (0, 0)
+
+
 @pytest.mark.parametrize("bs", [1, 7, 32, 64])
 @pytest.mark.parametrize("name", ["random", "grid"])
 def test_block_jacobi_matches_oracle(bs, name):

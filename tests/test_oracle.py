@@ -355,3 +355,26 @@ def test_phsvds_block_jacobi_preconditioner_closed_form():
     s = np.sort(np.sqrt((t[:, None, None] + t[None, :, None] + t[None, None, :]).ravel()))
     r = O.phsvds(A.to_scipy(), 3, "smallest", 1e-10, b=2, precond="block_jacobi", bj_block=16)
     np.testing.assert_allclose(r["sigma"], s[:3], rtol=1e-10)
+
+
+def test_subspace_helper_accepts_oracle_vectors_and_rejects_wrong_ones():
+    """The angle checks of the GPU tests (tests/subspace.py) on oracle results:
+    the closed-form and dense subspaces accept the oracle's vectors (config 1,
+    whose 5th smallest value is a double value cut at k = 5), and reject a
+    vector taken from another value's subspace."""
+    import pytest as _pt
+
+    from subspace import check_dense_vectors, check_grid_vectors
+
+    A = wl.grid_difference(32, 2)
+    small, large = _golden_grid2d()
+    r = oracle.phsvds(A, 5, "smallest", 1e-10, b=1, V0=wl.start_block(A.n, 1, 0), normA=large[0])
+    assert check_grid_vectors(A, 32, 2, r) < 1e-8
+    bad = dict(r, V=r["V"][:, [1, 0, 2, 3, 4]])
+    with _pt.raises(AssertionError):
+        check_grid_vectors(A, 32, 2, bad)
+    R = wl.random_illconditioned(600, 200, 16, seed=11)
+    rr = oracle.phsvds(R, 3, "largest", 1e-10, b=1)
+    assert check_dense_vectors(R, rr) < 1e-8
+    with _pt.raises(AssertionError):
+        check_dense_vectors(R, dict(rr, U=rr["U"][:, [0, 2, 1]]))
