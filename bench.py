@@ -46,18 +46,24 @@ MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # changed after its capture
 TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_row_f32_32x4": 315_316_480}
 UNIT = "s"
-# FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x the maximum SM clock
-# (one FADD, FMUL or FFMA per lane per cycle); the Gram's FP64-class (Dot2)
-# accumulation costs 10 such operations per product (exact product 2, TwoSum 6,
-# error accumulation 2)
-FP32_LANES = 152 * 128
-DOT2_OPS = 10
-# Products with A or A^T (per column) of a full GD+k FP64-class solve of this
-# workload, measured on a GB300 with this library (the plain GD+k line of the
-# bench reports it live); the CPU oracle runs the same GD+k algorithm, so its
-# full-solve time is extrapolated from its measured cost per matvec on a bounded
-# sample when the reference arm runs alone.
-FULL_SOLVE_MATVECS = 12292
+# FP32 operations per product of the anchored FP64-class Gram accumulation in
+# the FP32 mode (fma, subtract, fma, add)
+GRAM_OPS = 4
+# The oracle run to completion on this workload (python -m oracle.full_solve):
+# its own wall time and product count; the CPU baseline of every run scales the
+# oracle's measured cost per product on a bounded sample by that count
+ORACLE_RECORD_REL = "oracle/records/grid3d_N128_k10_smallest.json"
+ORACLE_RECORD = os.path.join(ROOT, ORACLE_RECORD_REL)
+
+
+def oracle_full_count():
+    """(products with A and A^T of the oracle's full solve, its record) or (None, None)."""
+    try:
+        with open(ORACLE_RECORD) as f:
+            rec = json.load(f)
+        return int(rec["matvecs_stage1"] + rec["matvecs_stage2"]), rec
+    except Exception:
+        return None, None
 
 
 def log(*a):
@@ -158,7 +164,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def spmm_roofline(A, dev, torch, B, prec, b, reps=30):
+def spmm_roofline(A, dev, torch, B, prec, b, reps=30, with_c=True):
     """Time the CSR SpMM kernels of one C = A^T A application on the workload
     with CUDA events on their stream; algorithmic bytes per launch:
     nnz (4 index + value bytes) + 4 (rows + 1) + s b (rows + cols)."""
@@ -196,27 +202,14 @@ def spmm_roofline(A, dev, torch, B, prec, b, reps=30):
     vbytes = 4 if (prec != B.PREC_F64) else 8
     if prec == B.PREC_DF64 and not exact:
         vbytes = 8
-    # the explicit C = A^T A (the operator of stage 1 when it is the cheaper form)
-    S = A.to_scipy()
-    Cs = (S.T @ S).tocsr()
-    Cs.sort_indices()
-    rpC = torch.from_numpy(Cs.indptr.astype(np.int32)).to(dev)
-    ciC = torch.from_numpy(Cs.indices.astype(np.int32)).to(dev)
-    vaC = torch.from_numpy(Cs.data).to(dev)
-    v32C = torch.empty(Cs.nnz, dtype=torch.float32, device=dev)
-    v32loC = torch.empty(Cs.nnz, dtype=torch.float32, device=dev)
-    v64C = torch.empty(Cs.nnz, dtype=torch.float64, device=dev)
-    flagsC = torch.zeros(4, dtype=torch.int32, device=dev)
-    B.csr_values(vaC, v32C, v32loC, v64C, flagsC)
-    loC = None if int(flagsC[0].item()) == 0 else v32loC
     res = {}
-    nnzs = {"spmm_A": nnz, "spmm_AT": nnz, "spmm_C": Cs.nnz}
-    for name, (rows, cols, r, c, vv, vl, src, dst) in {
-        "spmm_A": (A.m, A.n, rp, ci, v32, lo, X, Y),
-        "spmm_AT": (A.n, A.m, rpT, ciT, v32T, loT, Y, W),
-        "spmm_C": (A.n, A.n, rpC, ciC, v32C, loC, X, W),
-    }.items():
-        v64x = {"spmm_A": v64, "spmm_AT": v64T, "spmm_C": v64C}[name]
+    nnzs = {"spmm_A": nnz, "spmm_AT": nnz}
+    mats = {"spmm_A": (A.m, A.n, rp, ci, v32, lo, X, Y), "spmm_AT": (A.n, A.m, rpT, ciT, v32T, loT, Y, W)}
+    v64s = {"spmm_A": v64, "spmm_AT": v64T}
+    if with_c:
+        _explicit_c(A, dev, torch, B, X, W, nnzs, mats, v64s)
+    for name, (rows, cols, r, c, vv, vl, src, dst) in mats.items():
+        v64x = v64s[name]
         for _ in range(3):
             B.spmm(prec, rows, cols, r, c, vv, vl, v64x, src, b, dst, b, b, stream=sp)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -231,6 +224,25 @@ def spmm_roofline(A, dev, torch, B, prec, b, reps=30):
         alg = nnzs[name] * (4 + vbytes) + 4 * (rows + 1) + s * b * (rows + cols)
         res[name] = {"ms": ms, "bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9}
     return res
+
+
+def _explicit_c(A, dev, torch, B, X, W, nnzs, mats, v64s):
+    """The explicit C = A^T A (the operator of stage 1 when it is the cheaper form)."""
+    S = A.to_scipy()
+    Cs = (S.T @ S).tocsr()
+    Cs.sort_indices()
+    rpC = torch.from_numpy(Cs.indptr.astype(np.int32)).to(dev)
+    ciC = torch.from_numpy(Cs.indices.astype(np.int32)).to(dev)
+    vaC = torch.from_numpy(Cs.data).to(dev)
+    v32C = torch.empty(Cs.nnz, dtype=torch.float32, device=dev)
+    v32loC = torch.empty(Cs.nnz, dtype=torch.float32, device=dev)
+    v64C = torch.empty(Cs.nnz, dtype=torch.float64, device=dev)
+    flagsC = torch.zeros(4, dtype=torch.int32, device=dev)
+    B.csr_values(vaC, v32C, v32loC, v64C, flagsC)
+    loC = None if int(flagsC[0].item()) == 0 else v32loC
+    nnzs["spmm_C"] = Cs.nnz
+    mats["spmm_C"] = (A.n, A.n, rpC, ciC, v32C, loC, X, W)
+    v64s["spmm_C"] = v64C
 
 
 def ortho_roofline(dev, torch, B, prec, L, g, b, reps=20):
@@ -303,6 +315,11 @@ def run_gpu(args, world, rank, local):
         elif form == "plain":
             kw.update(stage1_precision=B.SVDS_DF64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
                       innerPrecision=B.SVDS_DF64)
+        elif form == "native":  # native FP64 arithmetic throughout (IEEE binary64 on the FP64 pipe)
+            kw.update(stage1_precision=B.SVDS_NATIVE_FP64, method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR,
+                      innerPrecision=B.SVDS_DF64)
+        elif form == "native_gdk":
+            kw.update(stage1_precision=B.SVDS_NATIVE_FP64, method_stage1=B.SVDS_GDPK, method_stage2=B.SVDS_GDPK)
         else:  # plain GD+k
             kw.update(stage1_precision=B.SVDS_DF64, method_stage1=B.SVDS_GDPK, method_stage2=B.SVDS_GDPK)
         return B.make_opts(**kw)
@@ -356,6 +373,12 @@ def run_gpu(args, world, rank, local):
     relerr_p = float(np.max(np.abs(lastp[0] - exact) / exact))
     t_gdk, st_gdk, lastg = timed("gdk", 1, 700 + 1000 * rank)
     relerr_g = float(np.max(np.abs(lastg[0] - exact) / exact))
+    # the plain solver in native FP64 (the FP64 pipe), JDQMR and GD+k
+    native = {}
+    for form in ("native", "native_gdk"):
+        tn, stn, lastn = timed(form, 1, 900 + 1000 * rank)
+        native[form] = dict(seconds=tn[0], stats=stn[0], sigma=lastn[0], rnorm=lastn[3], nconv=lastn[4],
+                            relerr=float(np.max(np.abs(lastn[0] - exact) / exact)))
     # the chosen form with JDQMR corrections at every outer iteration
     one_solve("jdqmr", 799 + 1000 * rank)  # warm-up of that form
     t_dyn, st_dyn, lastd = timed("jdqmr", max(1, min(args.steps, 2)), 800 + 1000 * rank)
@@ -383,7 +406,6 @@ def run_gpu(args, world, rank, local):
     t_e2e = statistics.median(t_e2e_all)
     h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
     d2h = 8 * K * (A.m + A.n + 2)
-    gain = precond_gain(B, wl, sp)
     # roofline of the dominant kernel family (CSR SpMM, FP32 phase and FP64-class)
     roof32 = spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK)
     roofdf = spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK)
@@ -392,11 +414,17 @@ def run_gpu(args, world, rank, local):
             for k, v in ortho_roofline(dev, torch, B, pr, A.n, 32, BLOCK).items()}
     ms_step = statistics.median(t_chosen) * 1e3
     ms_step = max_over_ranks(ms_step, world)
+    c1 = config1_report(B, wl, sp)
+    c3 = config3_report(B, wl, sp, dev, torch) if not args.skip_c3 else None
+    c4 = config4_report(B, wl, sp, args.c4_seeds)
+    c5 = config5_report(B, wl, sp)
+    fp32_peak = sgemm_peak(torch, dev)
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
+                native=native, c1=c1, c3=c3, c4=c4, c5=c5, fp32_peak=fp32_peak, sigma=sigma,
                 t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
                 relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h, t_dyn=t_dyn, st_dyn=st_dyn,
                 relerr_dyn=relerr_d, cond=cond,
-                roof32=roof32, roofdf=roofdf, orth=orth, ms_step=ms_step, A=A, e2e_nconv=oute[4], gain=gain)
+                roof32=roof32, roofdf=roofdf, orth=orth, ms_step=ms_step, A=A, e2e_nconv=oute[4])
 
 
 def condest_runs(B, torch, stream, rp, ci, va, A, sp):
@@ -429,31 +457,230 @@ def condest_runs(B, torch, stream, rp, ci, va, A, sp):
     return out
 
 
-def precond_gain(B, wl, sp):
-    """Jacobi vs learned vs block-Jacobi (blocks of 32 columns) preconditioner
-    (chosen JDQMR form) on held-out weighted grids."""
+def _host_residuals(S, sigma, U, V):
+    """Eq. (res) recomputed on the host in FP64 from the returned vectors."""
+    AV = S @ V
+    AtU = S.T @ U
+    return np.sqrt(np.sum((AV - U * sigma) ** 2, axis=0) + np.sum((AtU - V * sigma) ** 2, axis=0))
+
+
+def _grid2d_angles(N, sigma, V, rel=1e-9):
+    """sin of the angle between each returned v and the closed-form right
+    singular subspace of its value (Kronecker products of sine vectors)."""
+    t = 4.0 * np.sin(np.arange(1, N + 1) * np.pi / (2 * (N + 1))) ** 2
+    sv = np.sqrt(t[:, None] + t[None, :])
+    pts = np.arange(1, N + 1)
+    sines = np.array([np.sin(i * pts * np.pi / (N + 1)) for i in range(1, N + 1)])
+    sines /= np.linalg.norm(sines, axis=1, keepdims=True)
+    out = []
+    for j, s_ in enumerate(sigma):
+        ii, jj = np.nonzero(np.abs(sv - s_) <= rel * s_)
+        basis = np.stack([np.kron(sines[i], sines[k]) for i, k in zip(ii, jj)], axis=1)
+        x = V[:, j] / np.linalg.norm(V[:, j])
+        out.append(float(np.linalg.norm(x - basis @ (basis.T @ x))))
+    return out
+
+
+def _solve_timed(B, torch, A, k, target, stream, on_device=None, **kw):
+    """One solve (handle creation included) timed with CUDA events on its stream."""
+    o = B.make_opts(stream=stream.cuda_stream, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if on_device is not None:
+        h = B.svds_create(*on_device, A.m, A.n, o, on_device=True)
+    else:
+        h = B.svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, o)
+    try:
+        out = B.svds_solve(h, k, B.SVDS_SMALLEST if target == "smallest" else B.SVDS_LARGEST, TOL)
+    finally:
+        h.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def config1_report(B, wl, sp):
+    """The 2D grid-difference operator of 32^2 (2112 x 1024), the 5 smallest and
+    the 5 largest triplets with block 1 (the paper's default), plain FP64
+    (native and double-float GD+k, Jacobi): GPU times, sigma against the
+    closed form, sin angles to the closed-form subspaces (the 5th value of
+    each end is double and cut at k = 5, so its vector may lie anywhere in the
+    plane), and the oracle run to completion on the host cores."""
+    import torch
+
+    A = wl.grid_difference(32, 2)
+    S = A.to_scipy()
+    t = 4.0 * np.sin(np.arange(1, 33) * np.pi / 66) ** 2
+    sv = np.sort(np.sqrt(t[:, None] + t[None, :]).ravel())
+    stream = torch.cuda.Stream()
     out = {}
-    for wname, model in (("wgrid2d_N256", "wgrid2d.bin"), ("wgrid3d_N96", "wgrid3d.bin")):
-        A, meta = wl.workload(wname)
+    for target in ("smallest", "largest"):
+        ex = sv[:5] if target == "smallest" else sv[::-1][:5]
         row = {}
-        for name, pc in (("jacobi", B.SVDS_PRECOND_JACOBI), ("learned", B.SVDS_PRECOND_LEARNED),
-                         ("block_jacobi32", B.SVDS_PRECOND_BLOCKJACOBI)):
-            kw = dict(maxBlockSize=meta["b"], stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR,
+        for name, prec in (("native_fp64", B.SVDS_NATIVE_FP64), ("df64", B.SVDS_DF64)):
+            _solve_timed(B, torch, A, 5, target, stream, maxBlockSize=1, stage1_precision=prec,
+                         initV=wl.start_block(A.n, 1, 0))  # warm
+            secs, (sig, U, V, rn, nconv, st, rc) = _solve_timed(B, torch, A, 5, target, stream, maxBlockSize=1,
+                                                                  stage1_precision=prec,
+                                                                  initV=wl.start_block(A.n, 1, 0))
+            res = _host_residuals(S, sig, U, V)
+            row[name] = dict(seconds=round(secs, 5), numConverged=nconv,
+                             matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
+                             max_rel_sigma_err=float(np.max(np.abs(sig - ex) / ex)),
+                             max_res_over_normA=float(res.max() / sv[-1]),
+                             max_sin_angle=max(_grid2d_angles(32, sig, V)))
+        try:  # the oracle to completion on the host cores (FP64 numpy/scipy, same start vector)
+            import oracle
+
+            t0 = time.perf_counter()
+            o = oracle.phsvds(A, 5, target, TOL, b=1, V0=wl.start_block(A.n, 1, 0))
+            row["oracle_cpu"] = dict(seconds=round(time.perf_counter() - t0, 4), cores=os.cpu_count(),
+                                     matvecs=int(o["stats1"].matvecs + (o["stats2"].matvecs if o.get("stats2") else 0)),
+                                     max_rel_sigma_err=float(np.max(np.abs(o["sigma"] - ex) / ex)))
+        except Exception as e:  # reported, never required
+            row["oracle_cpu"] = dict(failed=str(e))
+        out[target] = row
+    return out
+
+
+def config3_report(B, wl, sp, dev, torch):
+    """The tall ill-conditioned random matrix (1,000,000 x 500,000, 16 distinct
+    rows per column, N(0,1) values, column j scaled by 10^u_j, u_j ~ U(-3, 0)),
+    standing in for the least-squares matrices of Table 4: the 10 largest and
+    the 10 smallest triplets (block 4, JDQMR in both stages) with stage 1 in
+    the FP64-class (double-float) mode, with an FP32 first phase, and with an
+    FP32 first phase on bfloat16 values; per-triplet relative sigma difference
+    against the double-float run, Eq. (res) recomputed in FP64 on the host,
+    and the bytes and time of the two SpMM passes (A then A^T) of one
+    stage-1 operator application."""
+    A, _ = wl.workload("randill_1e6x5e5")
+    S = A.to_scipy()
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colidx).to(dev)
+    va = torch.from_numpy(A.vals).to(dev)
+    stream = torch.cuda.Stream(dev)
+    out = dict(workload=f"randill_1e6x5e5 ({A.m} x {A.n}, nnz {A.nnz})")
+    normA = None
+    for target in ("largest", "smallest"):
+        runs = {}
+        for name, prec in (("df64", B.SVDS_DF64), ("fp32", B.SVDS_FP32), ("bf16", B.SVDS_BF16)):
+            kw = dict(maxBlockSize=4, stage1_precision=prec, method_stage1=B.SVDS_JDQMR,
+                      method_stage2=B.SVDS_JDQMR, precond=B.SVDS_PRECOND_JACOBI, seed=5, maxSeconds=300.0)
+            secs, (sig, U, V, rn, nconv, st, rc) = _solve_timed(B, torch, A, 10, target, stream,
+                                                                  on_device=(rp, ci, va), **kw)
+            normA = normA or st["aNorm"]
+            res = _host_residuals(S, sig, U, V)
+            runs[name] = dict(seconds=round(secs, 4), numConverged=nconv, rc=rc,
+                              matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
+                              matvecs_lowprec=int(st["matvecs_stage1_lowprec"]), stage2_used=st["stage2_used"],
+                              normal_nnz=int(st["normal_nnz"]), sigma=[float(x) for x in sig],
+                              max_res_over_normA=float(res.max() / st["aNorm"]))
+        ref = np.array(runs["df64"]["sigma"])
+        for name in ("fp32", "bf16"):
+            runs[name]["rel_sigma_diff_vs_df64"] = [float(x) for x in np.abs(np.array(runs[name]["sigma"]) - ref) / ref]
+        out[target] = runs
+    out["spmm_two_pass_f32"] = spmm_roofline(A, dev, torch, B, B.PREC_F32, 4, reps=10, with_c=False)
+    return out
+
+
+def config4_report(B, wl, sp, nseeds):
+    """Held-out weighted 2D grids (256^2, log-normal edge weights sigma 1.5,
+    seeds 10000 .. 10000 + nseeds - 1), the 10 smallest triplets, block 4, in
+    the JDQMR form with FP32 inner solves and FP32 first phase: no
+    preconditioner, Jacobi and the learned M (2D model); medians of the solve
+    time and of the products with A and A^T over the seeds, and the largest
+    relative sigma difference between the arms."""
+    model = os.path.join(MODELS, "wgrid2d.bin")
+    rows = {"none": [], "jacobi": [], "learned": []}
+    maxdiff = 0.0
+    for seed in range(10000, 10000 + nseeds):
+        A = wl.weighted_grid(256, 2, seed)
+        sig = {}
+        for name, pc in (("none", B.SVDS_PRECOND_NONE), ("jacobi", B.SVDS_PRECOND_JACOBI),
+                         ("learned", B.SVDS_PRECOND_LEARNED)):
+            kw = dict(maxBlockSize=4, stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_JDQMR,
                       method_stage2=B.SVDS_JDQMR, precond=pc, seed=3, stream=sp, maxSeconds=120.0)
             if pc == B.SVDS_PRECOND_LEARNED:
-                kw["precondModel"] = os.path.join(MODELS, model)
+                kw["precondModel"] = model
             h = B.svds_create(A.rowptr, A.colidx, A.vals, A.m, A.n, B.make_opts(**kw))
             try:
-                sig, _, _, rn, nconv, st, _ = B.svds_solve(h, meta["k"], B.SVDS_SMALLEST, TOL, want_vectors=False)
+                s_, _, _, rn, nconv, st, rc = B.svds_solve(h, 10, B.SVDS_SMALLEST, TOL, want_vectors=False)
             finally:
                 h.close()
-            row[name] = dict(seconds=round(st["seconds_total"], 4), matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
-                             inner_steps=int(st["inner_steps"]), seconds_precond=round(st["seconds_precond"], 5),
-                             numConverged=nconv)
-        row["speedup"] = round(row["jacobi"]["seconds"] / row["learned"]["seconds"], 3)
-        row["speedup_block_jacobi"] = round(row["jacobi"]["seconds"] / row["block_jacobi32"]["seconds"], 3)
-        out[f"{wname} (held-out seed, k={meta['k']}, b={meta['b']})"] = row
+            rows[name].append(dict(seconds=st["seconds_total"], matvecs=st["matvecs_stage1"] + st["matvecs_stage2"],
+                                   outer=st["outer_stage1"] + st["outer_stage2"], nconv=nconv,
+                                   fallback=st["precond_fallback"]))
+            sig[name] = s_
+        for name in ("none", "learned"):
+            maxdiff = max(maxdiff, float(np.max(np.abs(sig[name] - sig["jacobi"]) / sig["jacobi"])))
+    med = {k: dict(seconds=round(statistics.median(r["seconds"] for r in v), 4),
+                   matvecs=int(statistics.median(r["matvecs"] for r in v)),
+                   outer=int(statistics.median(r["outer"] for r in v)),
+                   all_converged=all(r["nconv"] == 10 for r in v),
+                   fallbacks=sum(1 for r in v if r["fallback"])) for k, v in rows.items()}
+    return dict(seeds=f"10000..{10000 + nseeds - 1} ({nseeds} held-out seeds)", k=10, block=4, median=med,
+                max_rel_sigma_diff_vs_jacobi=maxdiff,
+                speedup_learned_vs_jacobi=round(med["jacobi"]["seconds"] / med["learned"]["seconds"], 3),
+                speedup_learned_vs_none=round(med["none"]["seconds"] / med["learned"]["seconds"], 3))
+
+
+def config5_report(B, wl, sp):
+    """The weighted 3D grid of 96^3 (held-out seed 10000), the 20 smallest
+    triplets, block 8: the chosen form (DYNAMIC stage 1 with an FP32 first
+    phase and FP32 inner solves, learned M from the 3D model, double-float
+    polish and stage 2) against the plain solver with the Jacobi
+    preconditioner in double-float and in native FP64 (JDQMR in both stages)."""
+    import torch
+
+    A, meta = wl.workload("wgrid3d_N96")
+    stream = torch.cuda.Stream()
+    base = dict(maxBlockSize=8, precond=B.SVDS_PRECOND_JACOBI, seed=3, maxSeconds=300.0,
+                method_stage1=B.SVDS_JDQMR, method_stage2=B.SVDS_JDQMR)
+    forms = {
+        "chosen": dict(base, stage1_precision=B.SVDS_FP32, method_stage1=B.SVDS_DYNAMIC, innerPrecision=B.SVDS_FP32,
+                       precond=B.SVDS_PRECOND_LEARNED, precondModel=os.path.join(MODELS, "wgrid3d.bin")),
+        "plain_df64": dict(base, stage1_precision=B.SVDS_DF64, innerPrecision=B.SVDS_DF64),
+        "plain_native_fp64": dict(base, stage1_precision=B.SVDS_NATIVE_FP64, innerPrecision=B.SVDS_DF64),
+    }
+    out = dict(workload=f"wgrid3d_N96 seed 10000 ({A.m} x {A.n}, nnz {A.nnz})", k=20, block=8)
+    sig = {}
+    for name, kw in forms.items():
+        _solve_timed(B, torch, A, 20, "smallest", stream, **kw) if name == "chosen" else None  # warm
+        secs, (s_, U, V, rn, nconv, st, rc) = _solve_timed(B, torch, A, 20, "smallest", stream, **kw)
+        sig[name] = s_
+        out[name] = dict(seconds=round(secs, 4), numConverged=nconv, matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
+                         outer=int(st["outer_stage1"] + st["outer_stage2"]), fallback=st["precond_fallback"],
+                         max_rnorm_over_normA=float(np.max(rn) / st["aNorm"]))
+    for name in ("chosen", "plain_native_fp64"):
+        out[name]["max_rel_sigma_diff_vs_plain_df64"] = float(np.max(np.abs(sig[name] - sig["plain_df64"])
+                                                                     / sig["plain_df64"]))
+    out["speedup_chosen_vs_plain_df64"] = round(out["plain_df64"]["seconds"] / out["chosen"]["seconds"], 3)
+    out["speedup_chosen_vs_plain_native_fp64"] = round(out["plain_native_fp64"]["seconds"] / out["chosen"]["seconds"], 3)
     return out
+
+
+def sgemm_peak(torch, dev):
+    """FP32 SIMT throughput measured with cuBLAS SGEMM (TF32 off), 8192^3, best
+    of 5: the measured FP32-pipe denominator of the Gram's issue analysis."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(8192, 8192, device=dev)
+        b = torch.randn(8192, 8192, device=dev)
+        for _ in range(2):
+            torch.mm(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.mm(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return 2 * 8192 ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def bench_config(A, gpus):
@@ -493,6 +720,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--c4-seeds", type=int, default=10, help="held-out seeds of the 256^2 preconditioner report")
+    ap.add_argument("--skip-c3", action="store_true", help="skip the 1e6 x 5e5 random-matrix report")
     ap.add_argument("--solve-only", action="store_true",
                     help="run only the warm-up and timed chosen solves and print their times (for launch lists)")
     ap.add_argument("--kernels-only", action="store_true",
@@ -528,7 +757,7 @@ def main():
             vals.append((mv, secs))
         vals = vals[args.warmup:]
         per_mv = statistics.median(s / m for m, s in vals)
-        full = FULL_SOLVE_MATVECS or 0
+        full, rec = oracle_full_count()
         value = per_mv * full if full else None
         line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                     warmup=args.warmup, ms_per_step=statistics.median(s for _, s in vals) * 1e3,
@@ -536,7 +765,9 @@ def main():
                     config=bench_config(A, args.gpus),
                     cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
                                       sample=f"oracle stage-1 GD+k on the full matrix stopped after ~{vals[0][0]} "
-                                             f"matvecs per step; seconds/matvec x {full} matvecs of a full solve"),
+                                             f"matvecs per step; seconds/matvec x {full} matvecs of the oracle's "
+                                             f"own full solve ({ORACLE_RECORD_REL})",
+                                      oracle_full_solve=rec),
                     e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
         print(json.dumps(line))
         return 0
@@ -564,32 +795,33 @@ def main():
     mv_plain = int(res["st_plain"][-1]["matvecs_stage1"] + res["st_plain"][-1]["matvecs_stage2"])
     mv_gdk = int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"])
     cpu = None
+    full, rec = oracle_full_count()
     try:
         mv, secs, cores = cpu_sample(A, args.cpu_seconds)
         per_mv = secs / mv
-        cpu = dict(value=per_mv * mv_gdk, unit=UNIT, cores=cores, kind="oracle",
+        count, whose = (full, f"the oracle's own full solve, {ORACLE_RECORD_REL}") if full else \
+            (mv_gdk, "the GPU double-float GD+k count: no oracle record")
+        cpu = dict(value=per_mv * count, unit=UNIT, cores=cores, kind="oracle",
                    sample=f"oracle (FP64 numpy/scipy) stage-1 GD+k on the full matrix for {mv} matvecs "
-                          f"({secs:.1f} s); seconds/matvec x {mv_gdk} matvecs of the same GD+k algorithm's full "
-                          f"solve (GPU FP64-class GD+k count)")
+                          f"({secs:.1f} s); seconds/matvec x {count} matvecs of a full solve ({whose})",
+                   oracle_full_solve=rec, config1=res["c1"])
     except Exception as e:  # the baseline is reported, never required
         cpu = dict(value=None, unit=UNIT, cores=os.cpu_count(), kind="oracle", sample=f"failed: {e}")
     value = res["ms_step"] / 1e3
-    # dominant kernel of the chosen solve (launch list): the FP32 Gram of the
-    # projections, FP32-issue-bound; measured at 32 x 4 columns on the workload's
-    # rows, achieved = DOT2_OPS x products / CUDA-event time per launch
+    # dominant kernel of the chosen solve (launch list under profiles/): the
+    # FP32 Gram of the projections; algorithmic bytes L (g + b) s of one launch
+    # at the solve's shape (g = 32 basis columns, b = 4) over its CUDA-event time
     g32 = res["orth"]["f32_gram"]
     gprod = A.n * 32 * BLOCK
-    g_ach = DOT2_OPS * gprod / (g32["ms"] * 1e-3) / 1e12
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            sm_mhz = float(json.load(f)["sm_max_mhz"])
-    except Exception:
-        sm_mhz = 2070.0
-    g_peak = FP32_LANES * sm_mhz * 1e6 / 1e12
-    gram_roof = dict(bound="alu", kernel=f"k_gram_row (FP32, Gram {32} x {BLOCK} columns, FP64-class Dot2)",
-                     achieved=g_ach, peak=g_peak, unit="T FP32 op/s", frac=g_ach / g_peak,
-                     peak_kind="derived: 152 SMs x 128 FP32 lanes x max SM clock",
-                     traffic=TRAFFIC["gram_row_f32_32x4"], hbm_frac=g32["gbs"] / peak)
+    gram_roof = dict(bound="hbm", kernel=f"k_gram_anc (FP32, Gram 32 x {BLOCK} columns, FP64-class anchored "
+                                         f"accumulation)", achieved=g32["gbs"], peak=peak, unit="GB/s",
+                     frac=g32["gbs"] / peak, peak_kind=peak_kind, traffic=TRAFFIC.get("gram_anc_f32_32x4"),
+                     bytes_per_launch=g32["bytes"], ms_per_launch=round(g32["ms"], 5),
+                     fp32_issue=dict(ops_per_product=GRAM_OPS,
+                                     achieved_tops=GRAM_OPS * gprod / (g32["ms"] * 1e-3) / 1e12,
+                                     sgemm_measured_tflops=res["fp32_peak"],
+                                     note="FP32 operations of the accumulation per second against cuBLAS SGEMM "
+                                          "(TF32 off) measured in this run"))
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
@@ -597,8 +829,16 @@ def main():
         config=bench_config(A, args.gpus),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
         plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
-                        form="JDQMR, FP64-class inner and outer, Jacobi",
+                        form="JDQMR, double-float (FP64-class, u ~ 2^-48) inner and outer, Jacobi",
                         matvecs=mv_plain, max_rel_sigma_err=res["relerr_plain"]),
+        plain_native_fp64={k: dict(value=v["seconds"], unit=UNIT, numConverged=v["nconv"],
+                                   form=("JDQMR" if k == "native" else "GD+k") + ", native FP64, Jacobi",
+                                   matvecs=int(v["stats"]["matvecs_stage1"] + v["stats"]["matvecs_stage2"]),
+                                   max_rel_sigma_err=v["relerr"],
+                                   max_rel_sigma_diff_vs_chosen=float(np.max(np.abs(v["sigma"] - res["sigma"])
+                                                                             / v["sigma"])),
+                                   max_rnorm_over_normA=float(np.max(v["rnorm"]) / v["stats"]["aNorm"]))
+                           for k, v in res["native"].items()},
         plain_fp64_gdk=dict(value=res["t_gdk"][0], unit=UNIT, form="GD+k, FP64-class, Jacobi",
                             matvecs=int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"]),
                             max_rel_sigma_err=res["relerr_gdk"]),
@@ -618,7 +858,10 @@ def main():
         cpu_baseline=cpu,
         e2e=dict(value=res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"],
                  numConverged=res["e2e_nconv"]),
-        precond_gain=res["gain"],
+        config1_grid2d_N32=res["c1"],
+        config3_randill_1e6x5e5=res["c3"],
+        config4_wgrid2d_N256=res["c4"],
+        config5_wgrid3d_N96=res["c5"],
         chosen_jdqmr=dict(value=statistics.median(res["t_dyn"]), unit=UNIT,
                           form="chosen form with JDQMR corrections at every stage-1 outer iteration",
                           outer1=int(res["st_dyn"][-1]["outer_stage1"]),

@@ -126,7 +126,7 @@ typedef struct {
   int precondStallIts;        /* SVDS_PRECOND_LEARNED: the plain Jacobi preconditioner replaces the
                                  learned M for the rest of stage 1 after this many outer iterations
                                  in which the smallest residual of the corrected block did not fall
-                                 below 0.9 of its best since a pair last converged (0 = 20, < 0 =
+                                 below 0.99 of its best since a pair last converged (0 = 50, < 0 =
                                  never).  An M with a non-finite value or a non-positive diagonal is
                                  replaced before the first iteration.  See svds_stats.precond_fallback */
 } svds_opts;

@@ -84,8 +84,8 @@ int phsvds_ortho(int prec, int64_t L, const void *V, int64_t ldv, int g, void *T
  * rule of the method's restatement): the block as given is orthonormalised
  * again by host-driven CGS2 + CholQR2 in which a column that keeps at most
  * 1e-10 of its norm after the projection on V, or whose Cholesky pivot within
- * the block keeps at most max(1e-20, 64 u) of its squared norm (u = the mode's
- * unit roundoff: a column that depends on the block's earlier columns), is
+ * the block keeps at most 1e-14 of its squared norm (a column that depends on
+ * the block's earlier columns), is
  * replaced by a seeded N(0, 1) vector (seed) before the block is
  * orthonormalised again.  On return T is orthonormal and orthogonal to V;
  * *replaced (host, may be NULL) is 1 when columns were replaced.  Allocates

@@ -390,10 +390,11 @@ OrthoRes ortho(Ctx& c, int prec, long long L, const std::vector<SegV>& basis, vo
     // numerical rank of the block itself: Cholesky of S in column order; a
     // column whose pivot keeps at most tau of its squared norm depends on the
     // earlier columns of the block (a duplicated correction, say) and is
-    // replaced in the same way.  tau is the drop rule's 1e-20 or, above it,
-    // the rounding level of the mode's storage (a duplicate's pivot is
-    // rounding noise, not zero)
-    const double tau = std::max(1e-20, 64.0 * unit_roundoff(prec));
+    // replaced in the same way.  A duplicate's pivot is the FP64 rounding of
+    // this factorisation (about 1e-16 of the squared norm), not zero; tau
+    // stays well below the pivots of merely ill-conditioned blocks, which the
+    // shifted Cholesky-QR below handles
+    const double tau = 1e-14;
     std::vector<double> Lc((size_t)nb * nb, 0.0);  // lower factor, row-major; skipped columns stay 0
     for (int j = 0; j < nb; ++j) {
       const double sjj = S[(size_t)j * nb + j];
@@ -549,7 +550,7 @@ struct RunCfg {
   bool dyn = false;
   // fallback of a learned preconditioner (K / jdK) to Jacobi: after stall_its
   // outer iterations in which the smallest residual of the corrected block
-  // did not fall below 0.9 of its best since the last newly converged pair
+  // did not fall below 0.99 of its best since the last newly converged pair
   // (0 = never), K and jdK are dropped for the Jacobi scalings below
   int stall_its = 0;
   const void* fb_dscale = nullptr;  // Jacobi diagonal in the outer mode's storage
@@ -956,7 +957,7 @@ RunOut run_gdk_rr(Ctx& c, RunBufs& B, const RunCfg& cfg0, void* Xout, long long 
         stall_nconv = nf;
         stall_best = rmin;
         stall_since = 0;
-      } else if (rmin < 0.9 * stall_best) {
+      } else if (rmin < 0.99 * stall_best) {
         stall_best = rmin;
         stall_since = 0;
       } else if (++stall_since >= cfg.stall_its) {
@@ -1360,7 +1361,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
   const int p1a = lowprec ? kF32 : p2;
   const bool polish = !lowprec || o.stage1_polish;
   const long long ldv = (mb + 3) & ~3LL;
-  const int kk = std::max(std::max(k, b), std::min(std::max(o.initSize, 0), k));
+  // columns of the stage-1 blocks: k vectors, and with a reduced-precision
+  // first phase b more for the start of the FP64-class phase
+  const int kk = std::max(std::max(k, b), std::min(std::max(o.initSize, 0), k)) +
+                 ((o.stage1_precision == SVDS_FP32 || o.stage1_precision == SVDS_BF16) ? b : 0);
 
   Ctx c;
   c.h = h;
@@ -1679,7 +1683,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     const void* jd_jacobi = jd_prec == kF32 ? static_cast<const void*>(dj32) : static_cast<const void*>(d1);
     c1.jdinv = (jac || jac_fb) ? jd_jacobi : nullptr;
     if (learned) {
-      c1.stall_its = o.precondStallIts == 0 ? 20 : std::max(0, o.precondStallIts);
+      c1.stall_its = o.precondStallIts == 0 ? 50 : std::max(0, o.precondStallIts);
       c1.fb_jdinv = jd_jacobi;
     }
     c1.jd_maxk = jd_maxk;
@@ -1706,7 +1710,11 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       double* dtmp = reinterpret_cast<double*>(dout);
       CK(launch_to_f64_colmajor(kF32, n, k, X1a, kk, dtmp, n, 1.0, c.st));
       CK(launch_from_f64_colmajor(p2, n, k, dtmp, n, X1, kk, 1.0, c.st));
-      c.launches += 2;
+      // b seeded random columns beside them: a direction that the reduced-
+      // precision operator could not resolve (a value below its floor) can
+      // still enter the FP64-class basis
+      CK(launch_fill_normal(p2, n, off(X1, k, p2), kk, b, o.seed ^ 0xB0B0ULL));
+      c.launches += 3;
     } else {
       init_block(p2, X1, kk, b0);
     }
@@ -1725,7 +1733,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       }
       c1.V0 = X1;
       c1.ldv0 = kk;
-      c1.b0 = lowprec ? k : b0;
+      c1.b0 = lowprec ? k + b : b0;
       c1.name = "stage1";
       RunOut r1 = run_gdk_rr(c, B1, c1, X1, kk);
       S.outer_stage1 += r1.outer;

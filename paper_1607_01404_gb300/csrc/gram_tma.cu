@@ -1,0 +1,520 @@
+// TMA-fed row Gram G = [P0 P1 P2]^T Q (the Table 3 inner products: the
+// Rayleigh-Ritz projection V^T W and the Gram matrices of CGS and CholQR) for
+// the F32 and DF64 storage modes, p <= 64 and q <= 8.
+//
+// Memory side: row tiles of every segment are streamed into a ring of shared-
+// memory stages by the Tensor Memory Accelerator (cp.async.bulk.tensor.2d with
+// an mbarrier per stage, one 2D tensor map per segment: rows x the segment's
+// columns counted from the 16-byte boundary at or before its first column).
+// Each stage has an mbarrier that completes when its copies have landed; the
+// warps wait on it independently, and the last warp to finish a stage (an
+// arrival counter in shared memory) refills it with the CTA's next chunk, so
+// no CTA-wide barrier and no idle producer warp sit in the loop.  The bytes in
+// flight cost no registers: a CTA keeps kStages tiles in flight.
+// Rows past r1 and columns past the segment are outside the tensor maps and
+// arrive as zeros, so the ragged tail needs no masks.  Tile rows are padded so
+// that the lanes of a warp (TPR lanes per row, 32 / TPR rows) read distinct
+// shared-memory banks.
+//
+// Arithmetic side: the lane layout of the row Gram (lane `part` of a row owns
+// P columns part + TPR k and every Q column), FP64-class accumulation of
+// every product, and a fixed-order double-float reduction of the lanes
+// (deterministic).
+// * DF64 storage: Dot2 (Ogita, Rump and Oishi 2005): the exact product of the
+//   hi parts (TwoProd by FMA) plus the cross terms, TwoSum into hi, rounding
+//   errors into lo, renormalised every 2 rows; accurate to about 2^-48 of
+//   the products, as the double-float data.
+// * FP32 storage: anchored accumulation.  Pair (i, j) of a lane accumulates
+//   into s = sigma_ij + partial sum, sigma_ij = a_i b_j a power of two of at
+//   least 4 times the Cauchy-Schwarz bound sqrt(SP_i SQ_j) of the lane's
+//   partial sums (SP, SQ: running sums of squares), so that
+//       s' = fma(p, q, s),  z = s' - s  (exact: Sterbenz),  d = fma(p, q, -z)
+//   is the rounding error of the update to FP32 precision, summed in c:
+//   4 FP32 operations per product instead of Dot2's 10.  An outgrown anchor
+//   is raised with 4x headroom and its pairs move to it by an error-free
+//   FastTwoSum; every 8 rows c is folded into s.  The error of a product is
+//   about 2^-47 sigma_ij, i.e. 2^-43 of the Cauchy-Schwarz bound of the
+//   lane's rows: far below the 2^-24 of the FP32 data, but not the 2^-48 of
+//   double-float data, which therefore keeps Dot2.  Entries must be below
+//   2^50 in magnitude.
+//
+// Every mbarrier wait is bounded (about 2^31 SM cycles); a CTA whose wait
+// runs out writes NaN partial sums, waits (bounded) for its copies in flight
+// and returns, so the failure reaches the caller as a NaN Gram.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace phsvds {
+
+namespace {
+
+constexpr int kT = 256;       // threads per CTA
+constexpr int kStages = 4;    // tiles in flight per CTA
+constexpr int kMaxSeg = 4;    // up to 3 P segments and Q
+constexpr int kMaxP = 64;
+constexpr long long kWaitCycles = 1LL << 31;
+constexpr int kMaxSmem = 200 * 1024 + 128;  // largest dynamic shared memory of a plan
+constexpr int kBarBytes = kStages * 8 + kStages * 4 + 16;  // stage barriers, arrival counters, failure word
+constexpr int kRingTwoCtas = 110 * 1024;         // a plan at most this large lets two CTAs share an SM
+
+struct TmaSeg {
+  int soff;  // float offset of the segment's tile inside a stage
+  int bw;    // floats per tile row (box width)
+  int xoff;  // float offset of the segment's column 0 inside a tile row
+  int nc;    // columns (elements)
+};
+struct TmaPlan {
+  TmaSeg seg[kMaxSeg];  // [0, nP): P segments, [nP]: Q
+  int nP;
+  int stage_floats;  // a multiple of 32 (every tile starts on a 128-byte boundary)
+  int R;             // rows per stage
+  int bar_off;       // float offset of the stage barriers (after the ring and the reduction buffer)
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on one phase of a stage's barrier
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---- anchored accumulation (see the file header) ----
+__device__ __forceinline__ float hi_of(float x) { return x; }
+
+__device__ __forceinline__ void anc_add(float& s, float& c, float x, float y) {
+  const float t = s;
+  s = __fmaf_rn(x, y, t);
+  const float z = __fsub_rn(s, t);
+  c = __fadd_rn(c, __fmaf_rn(x, y, -z));
+}
+// Dot2 step for double-float values: hi + lo += x y
+__device__ __forceinline__ void dot2_add(float& hi, float& lo, df x, df y) {
+  const df p = two_prod(x.hi, y.hi);
+  const float pl = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  const df s = two_sum(hi, p.hi);
+  hi = s.hi;
+  lo = __fadd_rn(lo, __fadd_rn(s.lo, pl));
+}
+// smallest power of two a with a^2 >= 18 sp, at least 2^-58 (the floor keeps
+// the bound valid for entries whose squares underflow)
+__device__ __forceinline__ float anc_anchor(float sp) {
+  const unsigned u = __float_as_uint(18.0f * sp);
+  int e = (int)(u >> 23) - 127;
+  if (u & 0x7fffffu) ++e;
+  int ea = (e + 1) >> 1;
+  ea = max(ea, -58);
+  return __uint_as_float((unsigned)(ea + 127) << 23);
+}
+// moves pair (s, c) from anchor so to sn (|sn| >= 2 |so|): error-free
+__device__ __forceinline__ void anc_move(float& s, float& c, float so, float sn) {
+  const float v = __fsub_rn(s, so);
+  const float t = __fadd_rn(sn, v);
+  c = __fadd_rn(c, __fsub_rn(v, __fsub_rn(t, sn)));
+  s = t;
+}
+
+template <class P>
+__device__ __forceinline__ typename P::A lds(const float* p);
+template <>
+__device__ __forceinline__ float lds<PF32>(const float* p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ df lds<PDF64>(const float* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return df{v.x, v.y};
+}
+
+template <class P, int TPR, int KP, int NQ>
+__global__ void __launch_bounds__(kT, 2)
+    k_gram_tma(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
+               const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap m3, const TmaPlan plan,
+               long long r0, long long r1, int p, int q, df* __restrict__ partial) {
+  using A = typename P::A;
+  constexpr int E = P::id == kF32 ? 1 : 2;  // floats per element
+  constexpr int RPC = kT / TPR;              // rows the CTA covers at once
+  constexpr int NW = kT / 32;
+  constexpr float kFloor = 3.4694470e-18f;   // 2^-58
+  constexpr bool kAnchored = P::id == kF32;
+  extern __shared__ __align__(128) float smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + plan.bar_off);
+  int* arrived = reinterpret_cast<int*>(full + kStages);
+  int* fail = arrived + kStages;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int R = plan.R;
+  const long long nchunks = (r1 - r0 + R - 1) / R;
+  const int nseg = plan.nP + 1;
+  unsigned tx_bytes = 0;
+  for (int sg = 0; sg < nseg; ++sg) tx_bytes += (unsigned)(plan.seg[sg].bw * R * 4);
+  // copies of chunk ch into stage st (one thread)
+  auto issue = [&](long long ch, int st) {
+    const CUtensorMap* maps[kMaxSeg] = {&m0, &m1, &m2, &m3};
+    float* base = smem + (size_t)st * plan.stage_floats;
+    mbar_expect_tx(&full[st], tx_bytes);
+    const int y = (int)(r0 + ch * R);
+    for (int sg = 0; sg < nseg; ++sg) tma_load_2d(base + plan.seg[sg].soff, maps[sg], 0, y, &full[st]);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      arrived[st] = 0;
+    }
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int st = 0; st < kStages; ++st) {
+      const long long ch = blockIdx.x + (long long)st * gridDim.x;
+      if (ch < nchunks) issue(ch, st);
+    }
+  }
+  __syncthreads();
+
+  // ---- consumer warps ----
+  const int part = threadIdx.x % TPR;
+  int co[KP], cw[KP];
+  bool cv[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    int c = part + TPR * k;
+    cv[k] = c < p;
+    int sg = 0;
+    while (sg < plan.nP - 1 && c >= plan.seg[sg].nc) {
+      c -= plan.seg[sg].nc;
+      ++sg;
+    }
+    co[k] = cv[k] ? plan.seg[sg].soff + plan.seg[sg].xoff + c * E : 0;
+    cw[k] = cv[k] ? plan.seg[sg].bw : 0;
+  }
+  const TmaSeg qs = plan.seg[plan.nP];
+  const int qo = qs.soff + qs.xoff;
+
+  float sa[KP][NQ], ca[KP][NQ];
+  // anchors a_k, b_j (powers of two) and the running sums of squares; an
+  // anchor is raised when 4.5 x its sum of squares exceeds its square
+  float an[KP], bn[NQ], sp[KP], sq[NQ];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    an[k] = kFloor;
+    sp[k] = 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    bn[j] = kFloor;
+    sq[j] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      sa[k][j] = kAnchored ? kFloor * kFloor : 0.f;
+      ca[k][j] = 0.f;
+    }
+
+  const int row0 = threadIdx.x / TPR;
+  int it = 0, pairs = 0;
+  for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
+    const int stage = it % kStages;
+    if (atomicAdd(fail, 0) || !mbar_wait(&full[stage], (unsigned)((it / kStages) & 1))) {
+      atomicOr(fail, 1);
+      break;
+    }
+    const float* tile = smem + (size_t)stage * plan.stage_floats;
+    for (int ra = row0; ra < R; ra += 2 * RPC, ++pairs) {
+      const int rb = ra + RPC;
+      A xa[KP], xb[KP], ya[NQ], yb[NQ];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        xa[k] = cv[k] ? lds<P>(tile + co[k] + ra * cw[k]) : P::zero();
+        xb[k] = cv[k] ? lds<P>(tile + co[k] + rb * cw[k]) : P::zero();
+      }
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        ya[j] = j < q ? lds<P>(tile + qo + ra * qs.bw + j * E) : P::zero();
+        yb[j] = j < q ? lds<P>(tile + qo + rb * qs.bw + j * E) : P::zero();
+      }
+      if constexpr (kAnchored) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          sp[k] = __fmaf_rn(hi_of(xa[k]), hi_of(xa[k]), sp[k]);
+          sp[k] = __fmaf_rn(hi_of(xb[k]), hi_of(xb[k]), sp[k]);
+        }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+          sq[j] = __fmaf_rn(hi_of(ya[j]), hi_of(ya[j]), sq[j]);
+          sq[j] = __fmaf_rn(hi_of(yb[j]), hi_of(yb[j]), sq[j]);
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+          if (4.5f * sp[k] > an[k] * an[k]) {
+            const float a1 = anc_anchor(sp[k]);
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], a1 * bn[j]);
+            an[k] = a1;
+          }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j)
+          if (4.5f * sq[j] > bn[j] * bn[j]) {
+            const float b1 = anc_anchor(sq[j]);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], an[k] * b1);
+            bn[j] = b1;
+          }
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+#pragma unroll
+          for (int j = 0; j < NQ; ++j) {
+            anc_add(sa[k][j], ca[k][j], xa[k], ya[j]);
+            anc_add(sa[k][j], ca[k][j], xb[k], yb[j]);
+          }
+        if ((pairs & 3) == 3) {  // every 8 rows: fold c into s (|s| >= |c|)
+#pragma unroll
+          for (int k = 0; k < KP; ++k)
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+              const float t = __fadd_rn(sa[k][j], ca[k][j]);
+              ca[k][j] = __fsub_rn(ca[k][j], __fsub_rn(t, sa[k][j]));
+              sa[k][j] = t;
+            }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+#pragma unroll
+          for (int j = 0; j < NQ; ++j) {
+            dot2_add(sa[k][j], ca[k][j], xa[k], ya[j]);
+            dot2_add(sa[k][j], ca[k][j], xb[k], yb[j]);
+            const df t = fast_two_sum(sa[k][j], ca[k][j]);
+            sa[k][j] = t.hi;
+            ca[k][j] = t.lo;
+          }
+      }
+    }
+    // this warp is done with the stage; the last warp to finish refills it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&arrived[stage], 1) == NW - 1) {
+        arrived[stage] = 0;
+        const long long nx = ch + (long long)kStages * gridDim.x;
+        if (nx < nchunks) {
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(nx, stage);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int pq = p * q;
+  if (*fail) {
+    // copies still in flight land in this CTA's shared memory: wait for them
+    // (bounded) before leaving, then report NaN partial sums
+    if (threadIdx.x == 0)
+      for (int j = 0; j < kStages; ++j) {
+        const long long ch = blockIdx.x + (long long)(it + j) * gridDim.x;
+        if (ch < nchunks) mbar_wait(&full[(it + j) % kStages], (unsigned)(((it + j) / kStages) & 1));
+      }
+    __syncthreads();
+    for (int e = threadIdx.x; e < pq; e += kT) partial[(long long)blockIdx.x * pq + e] = df{__int_as_float(0x7fc00000), 0.f};
+    return;
+  }
+  df* red = reinterpret_cast<df*>(smem);
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      df g;
+      if constexpr (kAnchored) {
+        g = two_sum(__fsub_rn(sa[k][j], an[k] * bn[j]), ca[k][j]);  // s - sigma is exact
+      } else {
+        g = fast_two_sum(sa[k][j], ca[k][j]);
+      }
+#pragma unroll
+      for (int off = 16; off >= TPR; off >>= 1)
+        g = df_add(g, df{__shfl_down_sync(0xffffffffu, g.hi, off), __shfl_down_sync(0xffffffffu, g.lo, off)});
+      const int c = part + TPR * k;
+      if (lane < TPR && c < p && j < q) red[(warp * p + c) * q + j] = g;
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < pq; e += kT) {
+    df v = red[e];
+    for (int w = 1; w < NW; ++w) v = df_add(v, red[w * pq + e]);
+    partial[(long long)blockIdx.x * pq + e] = v;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// smallest w >= need, w a multiple of 4 floats, w = rho (mod 32) when rho > 0
+int padded_width(int need, int rho) {
+  int w = (need + 3) & ~3;
+  if (rho > 0)
+    while (w % 32 != rho) w += 4;
+  return w;
+}
+
+template <class P, int TPR, int KP, int NQ>
+cudaError_t run(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long long r0, long long r1, int p, int q,
+                void* partial, int max_blocks, int* nblocks, cudaStream_t st) {
+  auto kern = k_gram_tma<P, TPR, KP, NQ>;
+  const size_t sm = (size_t)plan.bar_off * 4 + kBarBytes;
+  // the opt-in is set once per kernel instance: to the largest plan allowed
+  cudaError_t e = smem_optin(reinterpret_cast<const void*>(kern), kMaxSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long nchunks = (r1 - r0 + plan.R - 1) / plan.R;
+  long long g = std::min<long long>((long long)std::max(per_sm, 1) * std::max(sms, 1), max_blocks);
+  g = std::max<long long>(1, std::min(g, nchunks));
+  *nblocks = (int)g;
+  kern<<<(int)g, kT, sm, st>>>(maps[0], maps[1], maps[2], maps[3], plan, r0, r1, p, q,
+                               reinterpret_cast<df*>(partial));
+  return cudaGetLastError();
+}
+
+template <class P, int TPR>
+cudaError_t run_q4(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long long r0, long long r1, int p, int q,
+                   void* partial, int max_blocks, int* nb, cudaStream_t st) {
+  if (q <= 1) return run<P, TPR, 4, 1>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (q <= 2) return run<P, TPR, 4, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  return run<P, TPR, 4, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+}
+
+template <class P>
+cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long long r1, int p, void* partial,
+                       int max_blocks, int* nb, cudaStream_t st) {
+  constexpr int E = P::id == kF32 ? 1 : 2;
+  const int q = Q.nc;
+  // lanes per row (tpr) and P columns per lane (kp) so that a lane owns at
+  // most 16 pairs: 4 columns for q <= 4, 2 for q <= 8
+  const int kp = q <= 4 ? 4 : 2;
+  int tpr = 2;
+  while (tpr * kp < p) tpr *= 2;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // bank padding: the 32 / tpr rows a warp reads at once start on distinct banks
+  const int rho = E == 1 ? std::max(tpr, 4) % 32 : (2 * tpr) % 32;
+  // rows per stage: four passes of the consumers (two when the ring would
+  // keep two CTAs from sharing an SM)
+  const int rpc = kT / tpr;
+  TmaPlan plan{};
+  CUtensorMap maps[kMaxSeg];
+  for (int R : {std::min(4 * rpc, 256), 2 * rpc}) {
+    plan = TmaPlan{};
+    plan.nP = nseg;
+    plan.R = R;
+    std::memset(maps, 0, sizeof(maps));
+    int soff = 0;
+    for (int s = 0; s <= nseg; ++s) {
+      const SegV& g = s < nseg ? segs[s] : Q;
+      const uintptr_t a = reinterpret_cast<uintptr_t>(g.p);
+      const uintptr_t base = a & ~uintptr_t(15);
+      const long long stride = g.ld * (long long)(4 * E);
+      if (stride % 16 != 0 || a % (4 * E) != 0) return cudaErrorNotSupported;
+      const int xoff = (int)((a - base) / 4);
+      const int need = xoff + g.nc * E;
+      const int bw = padded_width(need, rho);
+      if (bw > 256 || need * 4LL > stride) return cudaErrorNotSupported;
+      const cuuint64_t dims[2] = {(cuuint64_t)need, (cuuint64_t)r1};
+      const cuuint64_t strides[1] = {(cuuint64_t)stride};
+      const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)R};
+      const cuuint32_t estr[2] = {1, 1};
+      const CUresult cr = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, reinterpret_cast<void*>(base), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) return cudaErrorNotSupported;
+      plan.seg[s] = TmaSeg{soff, bw, xoff, g.nc};
+      soff += (bw * R + 31) & ~31;
+    }
+    plan.stage_floats = soff;
+    const int ring = kStages * soff;
+    const int red = (kT / 32) * p * q * (int)(sizeof(df) / 4);
+    plan.bar_off = (std::max(ring, red) + 31) & ~31;
+    if ((size_t)plan.bar_off * 4 + kBarBytes <= (size_t)kRingTwoCtas) break;
+  }
+  if ((size_t)plan.bar_off * 4 + kBarBytes > (size_t)kMaxSmem) return cudaErrorNotSupported;
+  for (int s = nseg + 1; s < kMaxSeg; ++s) maps[s] = maps[nseg];  // unused slots: any valid map
+  if (kp == 4) {
+    if (tpr == 2) return run_q4<P, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+    if (tpr == 4) return run_q4<P, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+    if (tpr == 8) return run_q4<P, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+    return run_q4<P, 16>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  }
+  if (tpr == 2) return run<P, 2, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (tpr == 4) return run<P, 4, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (tpr == 8) return run<P, 8, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (tpr == 16) return run<P, 16, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  return run<P, 32, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tma(int prec, long long r0, long long r1, const SegV* P, int nseg, SegV Q, void* partial,
+                            int max_blocks, int* nblocks, cudaStream_t st) {
+  int p = 0;
+  for (int s = 0; s < nseg; ++s) p += P[s].nc;
+  if (nseg < 1 || nseg > 3 || p < 1 || p > kMaxP || Q.nc < 1 || Q.nc > 8 || r1 <= r0 || r1 > 2147483647LL)
+    return cudaErrorNotSupported;
+  if (prec == kF32) return gram_tma_p<PF32>(P, nseg, Q, r0, r1, p, partial, max_blocks, nblocks, st);
+  if (prec == kDF64) return gram_tma_p<PDF64>(P, nseg, Q, r0, r1, p, partial, max_blocks, nblocks, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace phsvds

@@ -1007,6 +1007,194 @@ __global__ void __launch_bounds__(kThreads) k_gram_row(long long r0, long long r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Anchored row Gram (F32 storage): the row Gram's layout (TPR lanes
+// per row, lane `part` owns P columns part + TPR k and every Q column) with a
+// cheaper FP64-class accumulation.  Pair (i, j) of a lane accumulates into
+// s = sigma_ij + (partial sum), where sigma_ij = a_i b_j is a power of two of
+// at least 4 times the Cauchy-Schwarz bound sqrt(SP_i SQ_j) of every partial
+// sum of the lane (SP, SQ: running sums of squares of the lane's entries).
+// s then stays within a factor 2 of sigma at every step, so
+//     s' = fma(p, q, s),  z = s' - s  (exact: Sterbenz),  d = fma(p, q, -z)
+// is the rounding error of the update to FP32 precision, and d is summed in
+// c: 4 FP32 operations per product instead of the 10 of Dot2 (double-float
+// data keeps Dot2: this scheme's 2^-43 falls short of its 2^-48).  When a running sum of squares outgrows its anchor, the
+// anchor is raised with 4x headroom and the pairs concerned move to it by an
+// error-free FastTwoSum; every 8 rows c is folded into s (FastTwoSum), so |c|
+// stays within a few units of sigma's last place.  The error of a product is
+// about 2^-47 sigma_ij, i.e. 2^-43 of the Cauchy-Schwarz bound of the lane's
+// rows.  Lane results are reduced in double-float in a fixed order as in the
+// row Gram (deterministic).  Entries must be below 2^50 in magnitude (the
+// anchors and sums of squares stay finite); the solver's blocks are far inside.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float hi_part(float x) { return x; }
+__device__ __forceinline__ float hi_part(df x) { return x.hi; }
+
+__device__ __forceinline__ void anc_add(float& s, float& c, float x, float y) {
+  const float t = s;
+  s = __fmaf_rn(x, y, t);
+  const float z = __fsub_rn(s, t);
+  c = __fadd_rn(c, __fmaf_rn(x, y, -z));
+}
+
+// Smallest power of two a with a^2 >= 18 sp (4x headroom over a^2 >= 4.5 sp),
+// and at least 2^-58: the floor keeps the bound valid for entries whose
+// squares underflow (below 2^-75) over up to 2^32 rows.
+__device__ __forceinline__ float anc_anchor(float sp) {
+  const unsigned u = __float_as_uint(18.0f * sp);
+  int e = (int)(u >> 23) - 127;
+  if (u & 0x7fffffu) ++e;  // ceil(log2 x) (conservative for subnormal x)
+  int ea = (e + 1) >> 1;   // ceil(e / 2)
+  ea = max(ea, -58);
+  return __uint_as_float((unsigned)(ea + 127) << 23);
+}
+
+template <class P, int TPR, int KP, int NQ>
+__global__ void __launch_bounds__(kThreads) k_gram_anc(long long r0, long long r1, SegArr segs, int p,
+                                                       const typename P::S* __restrict__ Q, long long ldq, int q,
+                                                       df* __restrict__ partial) {
+  using S = typename P::S;
+  using A = typename P::A;
+  constexpr int RPC = kThreads / TPR;  // rows of a CTA pass
+  constexpr int NW = kThreads / 32;
+  constexpr float kFloor = 3.4694470e-18f;  // 2^-58
+  __shared__ df red[NW * kRowGramP * 8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int part = lane % TPR;
+  const S* cb[KP];
+  long long cl[KP];
+  bool cv[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    int c = part + TPR * k;
+    cv[k] = c < p;
+    int sg = 0;
+    while (sg < segs.n - 1 && c >= segs.nc[sg]) {
+      c -= segs.nc[sg];
+      ++sg;
+    }
+    cb[k] = cv[k] ? reinterpret_cast<const S*>(segs.p[sg]) + c : nullptr;
+    cl[k] = cv[k] ? segs.ld[sg] : 0;
+  }
+  float sa[KP][NQ], ca[KP][NQ];
+  float an[KP], bn[NQ], ta[KP], tb[NQ], sp[KP], sq[NQ];
+  const float thr0 = kFloor * kFloor * (1.0f / 4.5f);
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    an[k] = kFloor;
+    ta[k] = thr0;
+    sp[k] = 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    bn[j] = kFloor;
+    tb[j] = thr0;
+    sq[j] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      sa[k][j] = kFloor * kFloor;
+      ca[k][j] = 0.f;
+    }
+  const long long stride = (long long)gridDim.x * RPC;
+  int it = 0;
+  for (long long ra = r0 + (long long)blockIdx.x * RPC + threadIdx.x / TPR; ra < r1; ra += 2 * stride) {
+    const long long rb = ra + stride;
+    const bool hb = rb < r1;
+    A xa[KP], xb[KP], ya[NQ], yb[NQ];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      xa[k] = cv[k] ? P::load(cb[k] + ra * cl[k]) : P::zero();
+      xb[k] = (cv[k] && hb) ? P::load(cb[k] + rb * cl[k]) : P::zero();
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      ya[j] = j < q ? P::load(Q + ra * ldq + j) : P::zero();
+      yb[j] = (j < q && hb) ? P::load(Q + rb * ldq + j) : P::zero();
+    }
+    // running sums of squares, then raise the anchors that they outgrew
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      sp[k] = __fmaf_rn(hi_part(xa[k]), hi_part(xa[k]), sp[k]);
+      sp[k] = __fmaf_rn(hi_part(xb[k]), hi_part(xb[k]), sp[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      sq[j] = __fmaf_rn(hi_part(ya[j]), hi_part(ya[j]), sq[j]);
+      sq[j] = __fmaf_rn(hi_part(yb[j]), hi_part(yb[j]), sq[j]);
+    }
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+      if (sp[k] > ta[k]) {
+        const float a1 = anc_anchor(sp[k]);
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+          const float so = an[k] * bn[j], sn = a1 * bn[j];
+          const float v = __fsub_rn(sa[k][j], so);
+          const float t = __fadd_rn(sn, v);
+          ca[k][j] = __fadd_rn(ca[k][j], __fsub_rn(v, __fsub_rn(t, sn)));
+          sa[k][j] = t;
+        }
+        an[k] = a1;
+        ta[k] = a1 * a1 * (1.0f / 4.5f);
+      }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j)
+      if (sq[j] > tb[j]) {
+        const float b1 = anc_anchor(sq[j]);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          const float so = an[k] * bn[j], sn = an[k] * b1;
+          const float v = __fsub_rn(sa[k][j], so);
+          const float t = __fadd_rn(sn, v);
+          ca[k][j] = __fadd_rn(ca[k][j], __fsub_rn(v, __fsub_rn(t, sn)));
+          sa[k][j] = t;
+        }
+        bn[j] = b1;
+        tb[j] = b1 * b1 * (1.0f / 4.5f);
+      }
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        anc_add(sa[k][j], ca[k][j], xa[k], ya[j]);
+        anc_add(sa[k][j], ca[k][j], xb[k], yb[j]);
+      }
+    if ((++it & 3) == 0) {  // every 8 rows: fold c into s (|s| >= |c|)
+#pragma unroll
+      for (int k = 0; k < KP; ++k)
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+          const float t = __fadd_rn(sa[k][j], ca[k][j]);
+          ca[k][j] = __fsub_rn(ca[k][j], __fsub_rn(t, sa[k][j]));
+          sa[k][j] = t;
+        }
+    }
+  }
+  // lanes of equal `part` in a warp: tree of shuffles in a fixed order
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      const float v = __fsub_rn(sa[k][j], an[k] * bn[j]);  // exact
+      df g = two_sum(v, ca[k][j]);
+#pragma unroll
+      for (int off = 16; off >= TPR; off >>= 1)
+        g = df_add(g, df{__shfl_down_sync(0xffffffffu, g.hi, off), __shfl_down_sync(0xffffffffu, g.lo, off)});
+      const int c = part + TPR * k;
+      if (lane < TPR && c < p && j < q) red[(warp * p + c) * q + j] = g;
+    }
+  __syncthreads();
+  const int pq = p * q;
+  for (int e = threadIdx.x; e < pq; e += kThreads) {
+    df v = red[e];
+    for (int w = 1; w < NW; ++w) v = df_add(v, red[w * pq + e]);
+    partial[(long long)blockIdx.x * pq + e] = v;
+  }
+}
+
 template <class P>
 cudaError_t gram_row_p(long long r0, long long r1, const SegArr& sa, int p, SegV Q, void* partial, int max_blocks,
                        int* nblocks, cudaStream_t st) {
@@ -1021,7 +1209,11 @@ cudaError_t gram_row_p(long long r0, long long r1, const SegArr& sa, int p, SegV
     if (grid > max_blocks) grid = max_blocks;                                                             \
     if (grid < 1) grid = 1;                                                                               \
     *nblocks = grid;                                                                                      \
-    k_gram_row<P, TPRV, KPV, NQV><<<grid, kThreads, 0, st>>>(r0, r1, sa, p, q, Q.ld, Q.nc, out);          \
+    if constexpr (P::id != kF32) {                                                                        \
+      k_gram_row<P, TPRV, KPV, NQV><<<grid, kThreads, 0, st>>>(r0, r1, sa, p, q, Q.ld, Q.nc, out);        \
+    } else {                                                                                              \
+      k_gram_anc<P, TPRV, KPV, NQV><<<grid, kThreads, 0, st>>>(r0, r1, sa, p, q, Q.ld, Q.nc, out);        \
+    }                                                                                                     \
     return cudaGetLastError();                                                                            \
   }
 #define ROWG_Q4(TPRV, KPV)           \
@@ -1067,6 +1259,11 @@ cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* Pp, in
     r1 = r0;
   }
   if (p <= kRowGramP && Q.nc <= 8) {
+    if (prec != kF64) {
+      const cudaError_t e = launch_gram_tma(prec, r0, r1, Pp, nseg, Q, partial, max_blocks, nblocks, st);
+      if (e != cudaErrorNotSupported) return e;
+      cudaGetLastError();
+    }
     PHSVDS_DISPATCH(prec, gram_row_p<P>(r0, r1, sa, p, Q, partial, max_blocks, nblocks, st))
   }
   {
@@ -1159,10 +1356,13 @@ __device__ __forceinline__ void load16(const typename P::S* p, typename P::A (&x
   }
 }
 
-// TPR consecutive lanes share a row; lane part computes outputs
-// [4 part, 4 part + 4) (the row's loads hit L1 after the first lane).
-template <class P, int TPR, bool VEC>
-__global__ void __launch_bounds__(kThreads) k_combine_row(long long L, SegArr segs, int p, int q,
+// One thread per row: it streams the row's p inputs (16-byte loads for the
+// aligned bulk of each segment, scalar loads for the tail), keeps its QT >= q
+// outputs in registers and writes them after all reads, so Out may alias an
+// input segment or In.  The coefficients (and R^-1) sit in shared memory and
+// every lane of a warp reads the same address (a broadcast).
+template <class P, int QT, bool VEC>
+__global__ void __launch_bounds__(kThreads, 2) k_combine_row(long long L, SegArr segs, int p, int q,
                                                           const typename P::C* __restrict__ coef,
                                                           const typename P::S* In, long long ldin, int alpha_one,
                                                           typename P::S* Out, long long ldout,
@@ -1171,96 +1371,68 @@ __global__ void __launch_bounds__(kThreads) k_combine_row(long long L, SegArr se
   using S = typename P::S;
   using A = typename P::A;
   using C = typename P::C;
-  constexpr int QT = 4, Q = QT * TPR;
-  __shared__ C cs[kRowCombP * Q];
-  __shared__ C rs[Q * Q];
-  for (int e = threadIdx.x; e < p * Q; e += kThreads) {
-    const int c = e / Q, j = e % Q;
+  constexpr int QR = QT <= 8 ? QT : 1;  // R^-1 is applied for q <= 8 only
+  __shared__ C cs[kRowCombP * QT];
+  __shared__ C rs[QR * QR];
+  for (int e = threadIdx.x; e < p * QT; e += kThreads) {
+    const int c = e / QT, j = e % QT;
     cs[e] = j < q ? coef[(long long)c * q + j] : C{};
   }
-  if (Rinv)
-    for (int e = threadIdx.x; e < Q * Q; e += kThreads) {
-      const int i = e / Q, j = e % Q;
+  if (QT <= 8 && Rinv)
+    for (int e = threadIdx.x; e < QT * QT; e += kThreads) {
+      const int i = e / QT, j = e % QT;
       rs[e] = (i < q && j < q) ? Rinv[i * q + j] : C{};
     }
   __syncthreads();
-  const int part = threadIdx.x % TPR;
-  const int j0 = part * QT;
-  const long long rows_per_pass = (long long)gridDim.x * (kThreads / TPR);
-  // every lane runs the same number of passes (the shuffles below need whole warps)
-  for (long long base = (long long)blockIdx.x * (kThreads / TPR); base < L; base += rows_per_pass) {
-    const long long r = base + threadIdx.x / TPR;
-    const bool live = r < L;
+  const long long stride = (long long)gridDim.x * kThreads;
+  for (long long r = (long long)blockIdx.x * kThreads + threadIdx.x; r < L; r += stride) {
     A acc[QT];
 #pragma unroll
-    for (int j = 0; j < QT; ++j) acc[j] = (live && alpha_one && j0 + j < q) ? P::load(In + r * ldin + j0 + j) : P::zero();
-    if (live) {
-      int c0 = 0;
-      for (int sg = 0; sg < segs.n; ++sg) {
-        const S* row = reinterpret_cast<const S*>(segs.p[sg]) + r * segs.ld[sg];
-        const int nc = segs.nc[sg];
-        int c1 = 0;  // first column of the scalar tail
-        if constexpr (VEC) {
-          constexpr int W = (int)(16 / sizeof(S));
-          c1 = nc - nc % W;
-          for (int c = 0; c < c1; c += W) {
-            A xs[W];
-            load16<P>(row + c, xs);
+    for (int j = 0; j < QT; ++j) acc[j] = (alpha_one && j < q) ? P::load(In + r * ldin + j) : P::zero();
+    int c0 = 0;
+    for (int sg = 0; sg < segs.n; ++sg) {
+      const S* row = reinterpret_cast<const S*>(segs.p[sg]) + r * segs.ld[sg];
+      const int nc = segs.nc[sg];
+      int c1 = 0;  // first column of the scalar tail
+      if constexpr (VEC) {
+        constexpr int W = (int)(16 / sizeof(S));
+        c1 = nc - nc % W;
+        for (int c = 0; c < c1; c += W) {
+          A xs[W];
+          load16<P>(row + c, xs);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-              const C* cr = cs + (c0 + c + w) * Q + j0;
+          for (int w = 0; w < W; ++w) {
+            const C* cr = cs + (c0 + c + w) * QT;
 #pragma unroll
-              for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], xs[w], cr[j]);
-            }
+            for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], xs[w], cr[j]);
           }
-        }
-        {
-          for (int c = c1; c < nc; ++c) {
-            const A x = P::load(row + c);
-            const C* cr = cs + (c0 + c) * Q + j0;
-#pragma unroll
-            for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], x, cr[j]);
-          }
-        }
-        c0 += nc;
-      }
-    }
-    if (Rinv) {
-      // out_j = sum_{i <= j} acc_i Rinv_ij, the acc_i of lower parts from the
-      // lanes of the same row
-      A o[QT];
-#pragma unroll
-      for (int j = 0; j < QT; ++j) o[j] = P::zero();
-      const int lane0 = (threadIdx.x & 31) - part;
-#pragma unroll
-      for (int pp = 0; pp < TPR; ++pp) {
-#pragma unroll
-        for (int i = 0; i < QT; ++i) {
-          A v;
-          if constexpr (TPR == 1) {
-            v = acc[i];
-          } else {
-            v = shfl_a<P>(acc[i], lane0 + pp);
-          }
-          const int ii = pp * QT + i;
-#pragma unroll
-          for (int j = 0; j < QT; ++j)
-            if (ii <= j0 + j) o[j] = P::fmac(o[j], v, rs[ii * Q + j0 + j]);
         }
       }
+      for (int c = c1; c < nc; ++c) {
+        const A x = P::load(row + c);
+        const C* cr = cs + (c0 + c) * QT;
 #pragma unroll
-      for (int j = 0; j < QT; ++j) acc[j] = o[j];
+        for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], x, cr[j]);
+      }
+      c0 += nc;
     }
-    // Out may alias an input row that other lanes of this row still read
-    __syncwarp();
-    if (live) {
+    if constexpr (QT <= 8) {
+      if (Rinv) {  // acc_j <- sum_{i <= j} acc_i Rinv_ij, in place from the last column down
 #pragma unroll
-      for (int j = 0; j < QT; ++j)
-        if (j0 + j < q) {
-          P::store(Out + r * ldout + j0 + j, acc[j]);
-          if (Out2) P::store(Out2 + r * ldout2 + j0 + j, acc[j]);
+        for (int j = QT - 1; j >= 0; --j) {
+          A t = P::zero();
+#pragma unroll
+          for (int i = 0; i <= j; ++i) t = P::fmac(t, acc[i], rs[i * QT + j]);
+          acc[j] = t;
         }
+      }
     }
+#pragma unroll
+    for (int j = 0; j < QT; ++j)
+      if (j < q) {
+        P::store(Out + r * ldout + j, acc[j]);
+        if (Out2) P::store(Out2 + r * ldout2 + j, acc[j]);
+      }
   }
 }
 
@@ -1280,21 +1452,22 @@ cudaError_t combine_row_p(long long L, const SegArr& sa, int p, const void* coef
   const S* in = reinterpret_cast<const S*>(In);
   S* out = reinterpret_cast<S*>(Out);
   S* out2 = reinterpret_cast<S*>(Out2);
-#define ROWC(TPRV)                                                                                                 \
+#define ROWC(QTV)                                                                                                  \
   {                                                                                                                \
-    const int grid = persistent_grid((L + kThreads / TPRV - 1) / (kThreads / TPRV), 1);                           \
+    const int grid = persistent_grid((L + kThreads - 1) / kThreads, 1);                                           \
     if (vec)                                                                                                       \
-      k_combine_row<P, TPRV, true><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout, ri, \
-                                                              out2, ldout2);                                       \
+      k_combine_row<P, QTV, true><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout, ri,  \
+                                                             out2, ldout2);                                        \
     else                                                                                                           \
-      k_combine_row<P, TPRV, false><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout,    \
-                                                               ri, out2, ldout2);                                  \
+      k_combine_row<P, QTV, false><<<grid, kThreads, 0, st>>>(L, sa, p, q, cf, in, ldin, alpha_one, out, ldout, ri, \
+                                                              out2, ldout2);                                       \
     return cudaGetLastError();                                                                                     \
   }
-  if (q <= 4) ROWC(1)
-  if (q <= 8) ROWC(2)
-  if (q <= 16) ROWC(4)
-  if (q <= 32) ROWC(8)
+  if (q <= 4) ROWC(4)
+  if (q <= 8) ROWC(8)
+  if (q <= 16) ROWC(16)
+  if (q <= 24) ROWC(24)
+  if (q <= 32) ROWC(32)
 #undef ROWC
   return cudaErrorInvalidValue;
 }
@@ -1306,7 +1479,7 @@ cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, cons
   int p;
   SegArr sa = make_segs(Pp, nseg, &p);
   if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
-  if (p <= kRowCombP && q <= 32) {
+  if (p <= kRowCombP && q <= 32 && (!Rinv || q <= 8)) {
     PHSVDS_DISPATCH(prec, combine_row_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2,
                                            st))
   }

@@ -43,6 +43,11 @@ cudaError_t launch_spmm(int prec, const CsrDev& A, const void* X, long long ldx,
 // number of blocks used via *nblocks.  `max_blocks` bounds the grid.
 cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* P, int nseg, SegV Q,
                         void* partial, int max_blocks, int* nblocks, cudaStream_t st);
+// The TMA-fed Gram of gram_tma.cu (F32 and DF64, p <= 64, q <= 8, 16-byte row
+// strides): same contract as launch_gram; cudaErrorNotSupported when its
+// preconditions do not hold (the caller then uses the row kernels).
+cudaError_t launch_gram_tma(int prec, long long r0, long long r1, const SegV* P, int nseg, SegV Q, void* partial,
+                            int max_blocks, int* nblocks, cudaStream_t st);
 // Sum the partials in fixed order into G (p x q, row-major doubles, device).
 cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st);
 // Bytes of partial storage that launch_gram may use.

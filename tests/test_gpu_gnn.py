@@ -234,6 +234,7 @@ def test_trained_models_gain_over_jacobi(family, N, model):
         assert r["nconv"] == 8
         out[name] = r
     mv = {k: v["stats"]["matvecs_stage1"] + v["stats"]["matvecs_stage2"] for k, v in out.items()}
+    assert out["learned"]["stats"]["precond_fallback"] == 0
     assert mv["learned"] < 0.85 * mv["jacobi"], mv
     # both runs meet ||r|| <= 1e-10 ||A||; the values agree to 1e-10 (quadratic in ||r||)
     np.testing.assert_allclose(out["learned"]["sigma"], out["jacobi"]["sigma"], rtol=1e-10)
@@ -250,15 +251,17 @@ def _fallback_case():
 @pytest.mark.parametrize("bad", ["underflow", "nan"])
 def test_learned_preconditioner_rejected_falls_back_to_jacobi(bad):
     """An unusable M (a diagonal that underflows to zero: zero weights and a
-    node-head bias of -200; or a NaN parameter) is replaced by the Jacobi
-    preconditioner before the first iteration, with the same triplets."""
+    node-head bias of -200; or a NaN node-head bias, which reaches M's
+    diagonal: a NaN in a layer weight would be cleared by the ReLU) is
+    replaced by the Jacobi preconditioner before the first iteration, with
+    the same triplets."""
     A, kw, ref = _fallback_case()
     th = np.zeros(B.gnn_num_params(), dtype=np.float32)
     if bad == "underflow":
         th[-1] = -200.0  # bd: softplus(-200) is 0 in FP32
     else:
         th[:] = B.gnn_init(0)
-        th[5] = np.nan
+        th[-1] = np.nan  # bd
     r = B.svds(A, 4, "smallest", 1e-10, precond=B.SVDS_PRECOND_LEARNED, precondParams=th, **kw)
     assert r["nconv"] == 4
     assert r["stats"]["precond_fallback"] == 1
@@ -269,8 +272,8 @@ def test_learned_preconditioner_rejected_falls_back_to_jacobi(bad):
 def test_learned_preconditioner_stall_falls_back_to_jacobi():
     """A poor M (node-head weights that spread the diagonal over many orders of
     magnitude) in GD+k with a one-iteration stall window: the residual fails to
-    drop by 10% at some outer iteration, Jacobi takes over, and the triplets
-    are the Jacobi run's."""
+    reach a new minimum at some outer iteration, Jacobi takes over, and the
+    triplets are the Jacobi run's."""
     A, kw, ref = _fallback_case()
     kw = dict(kw, method_stage1=B.SVDS_GDPK)  # GD+k: many outer iterations, small steps
     th = B.gnn_init(3)
