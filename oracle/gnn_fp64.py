@@ -12,6 +12,10 @@ kernels can be checked against it.  Every function is plain numpy/scipy.
 * Node features: x_i = [log c_ii - mean_j log c_jj, deg_i / max_j deg_j].
 * Message passing, 4 layers of width 32:
       z^l = h^l W1_l + (E h^l) W2_l + b_l,  h^{l+1} = relu(z^l),  h^0 = x.
+  The network applies the layer weights W1_l, W2_l in bfloat16 (the FP32
+  master weights rounded to nearest even; see bf16_weights), biases and heads
+  in FP32; this module computes with whatever parameters it is given, so the
+  tests pass it bf16_weights(params).
 * Heads: u_i = h_i . ws,  d_i = softplus(h_i . wd + bd),  delta_i = d_i / c_ii,
       s_ij = tanh(u_i + u_j + we e_ij + bs)   (symmetric by construction).
 * M on the pattern of C:  m_ii = delta_i,
@@ -75,6 +79,18 @@ def unflatten(theta):
 
 def flatten(params):
     return np.concatenate([np.asarray(params[name], dtype=np.float64).ravel() for name, _ in param_shapes()])
+
+
+def bf16_weights(params):
+    """The parameters as the network applies them: W1_l and W2_l rounded to
+    bfloat16 (FP32 master values, round to nearest even), the rest unchanged."""
+    from .phsvds_fp64 import round_bf16
+
+    out = dict(params)
+    for name in params:
+        if name.startswith("W1_") or name.startswith("W2_"):
+            out[name] = round_bf16(np.asarray(params[name], dtype=np.float32)).astype(np.float64)
+    return out
 
 
 def init_params(seed=0):

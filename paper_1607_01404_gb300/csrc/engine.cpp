@@ -1713,7 +1713,7 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
       // b seeded random columns beside them: a direction that the reduced-
       // precision operator could not resolve (a value below its floor) can
       // still enter the FP64-class basis
-      CK(launch_fill_normal(p2, n, off(X1, k, p2), kk, b, o.seed ^ 0xB0B0ULL));
+      CK(launch_fill_normal(p2, n, off(X1, k, p2), kk, b, o.seed ^ 0xB0B0ULL, c.st));
       c.launches += 3;
     } else {
       init_block(p2, X1, kk, b0);

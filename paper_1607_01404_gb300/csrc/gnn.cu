@@ -97,32 +97,60 @@ __global__ void k_x0(long long n, const float* __restrict__ logc, const float* _
 }
 
 // ---- forward ----------------------------------------------------------------
-// z = h W1 + Eh W2 + b, hout = relu(z); one thread per row, weights in shared memory.
+// The layer weights W1, W2 are used in bfloat16 (round to nearest even of the
+// FP32 master copy; FP32 products and accumulation), in the forward pass and
+// in the backward pass alike; biases and heads stay FP32.
+__device__ __forceinline__ float bf16r(float x) {
+  const unsigned u = __float_as_uint(x);
+  return __uint_as_float(((u + 0x7fffu + ((u >> 16) & 1u)) >> 16) << 16);
+}
+
+// z = h W1 + Eh W2 + b, hout = relu(z).  A CTA takes tiles of 64 rows: h and
+// Eh of the tile are staged in shared memory with coalesced loads (rows
+// padded by one float against bank conflicts), thread t computes outputs
+// [8 (t mod 4), 8 (t mod 4) + 8) of row t / 4 with the weights from shared
+// memory, and z and hout leave as 32-byte row segments (a warp writes 8 whole
+// rows).
+constexpr int kLRows = 64;
 template <int FIN>
 __global__ void __launch_bounds__(kT) k_layer_fwd(long long n, const float* __restrict__ h,
                                                   const float* __restrict__ Eh, const float* __restrict__ W1,
                                                   const float* __restrict__ W2, const float* __restrict__ b,
                                                   float* __restrict__ z, float* __restrict__ hout) {
+  static_assert(kT == 4 * kLRows, "four threads per row");
   __shared__ float w1[FIN * kW], w2[FIN * kW], bb[kW];
+  __shared__ float hs[kLRows * (FIN + 1)], es[kLRows * (FIN + 1)];
   for (int e = threadIdx.x; e < FIN * kW; e += blockDim.x) {
-    w1[e] = W1[e];
-    w2[e] = W2[e];
+    w1[e] = bf16r(W1[e]);
+    w2[e] = bf16r(W2[e]);
   }
   if (threadIdx.x < kW) bb[threadIdx.x] = b[threadIdx.x];
-  __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    float acc[kW];
-#pragma unroll
-    for (int j = 0; j < kW; ++j) acc[j] = bb[j];
-    for (int c = 0; c < FIN; ++c) {
-      const float hv = h[i * FIN + c], ev = Eh[i * FIN + c];
-#pragma unroll
-      for (int j = 0; j < kW; ++j) acc[j] = fmaf(hv, w1[c * kW + j], fmaf(ev, w2[c * kW + j], acc[j]));
+  const int row = threadIdx.x >> 2, j0 = 8 * (threadIdx.x & 3);
+  for (long long r0 = (long long)blockIdx.x * kLRows; r0 < n; r0 += (long long)gridDim.x * kLRows) {
+    const int rows = (int)(n - r0 < kLRows ? n - r0 : kLRows);
+    __syncthreads();  // weights staged / previous tile consumed
+    for (int e = threadIdx.x; e < rows * FIN; e += kT) {
+      const int rr = e / FIN, c = e % FIN;
+      hs[rr * (FIN + 1) + c] = h[r0 * FIN + e];
+      es[rr * (FIN + 1) + c] = Eh[r0 * FIN + e];
     }
+    __syncthreads();
+    if (row < rows) {
+      float acc[8];
 #pragma unroll
-    for (int j = 0; j < kW; ++j) {
-      z[i * kW + j] = acc[j];
-      hout[i * kW + j] = fmaxf(acc[j], 0.f);
+      for (int j = 0; j < 8; ++j) acc[j] = bb[j0 + j];
+#pragma unroll 4
+      for (int c = 0; c < FIN; ++c) {
+        const float hv = hs[row * (FIN + 1) + c], ev = es[row * (FIN + 1) + c];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fmaf(hv, w1[c * kW + j0 + j], fmaf(ev, w2[c * kW + j0 + j], acc[j]));
+      }
+      float4* zo = reinterpret_cast<float4*>(z + (r0 + row) * kW + j0);
+      float4* ho = reinterpret_cast<float4*>(hout + (r0 + row) * kW + j0);
+      zo[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      zo[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      ho[0] = make_float4(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f), fmaxf(acc[2], 0.f), fmaxf(acc[3], 0.f));
+      ho[1] = make_float4(fmaxf(acc[4], 0.f), fmaxf(acc[5], 0.f), fmaxf(acc[6], 0.f), fmaxf(acc[7], 0.f));
     }
   }
 }
@@ -271,7 +299,7 @@ template <int FOUT>
 __global__ void __launch_bounds__(kT) k_rowmat_t(long long n, const float* __restrict__ dz, const float* __restrict__ W,
                                                  const float* __restrict__ add, float* __restrict__ out) {
   __shared__ float w[FOUT * kW];
-  for (int e = threadIdx.x; e < FOUT * kW; e += blockDim.x) w[e] = W[e];
+  for (int e = threadIdx.x; e < FOUT * kW; e += blockDim.x) w[e] = bf16r(W[e]);  // the forward's weights
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     float d[kW];

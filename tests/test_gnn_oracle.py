@@ -256,3 +256,18 @@ def test_forward_pin_separates_plausible_slips():
     gc = G.Graph(A.to_scipy())
     gc.E = gc.C.copy()  # messages weighted by c_ij instead of the normalised e_ij
     assert far(G.forward(gc, p))
+
+
+def test_bf16_weights_round_only_the_layer_weights():
+    # the network's layer weights in bfloat16: W1_l, W2_l rounded to nearest
+    # even (the pinned rounding of the oracle), biases and heads unchanged
+    from oracle.phsvds_fp64 import round_bf16
+
+    p = G.init_params(6)
+    q = G.bf16_weights(p)
+    for name in p:
+        if name.startswith(("W1_", "W2_")):
+            np.testing.assert_array_equal(q[name], round_bf16(p[name].astype(np.float32)).astype(np.float64))
+            assert np.abs(q[name] - p[name]).max() <= 2.0 ** -8 * np.abs(p[name]).max()
+        else:
+            np.testing.assert_array_equal(q[name], p[name])

@@ -38,7 +38,8 @@ def _theta(seed):
     for l in range(G.LAYERS):
         p[f"b_{l}"] = 0.1 * rng.standard_normal(G.WIDTH)
     th = G.flatten(p).astype(np.float32)
-    return th, G.unflatten(th.astype(np.float64))
+    # the network applies its layer weights in bfloat16
+    return th, G.bf16_weights(G.unflatten(th.astype(np.float64)))
 
 
 @pytest.mark.parametrize("name,A", _cases())
@@ -125,7 +126,7 @@ def test_gradient_is_a_descent_direction_and_adam_steps():
     # with the samples of th held fixed the loss decreases along the step
     gref = G.Graph(A.to_scipy())
     T, X = G.samples(gref, G.forward(gref, p), T0, X0, 4, 30)
-    assert G.loss_fixed_samples(gref, G.unflatten(th1.astype(np.float64)), T, X) < L0
+    assert G.loss_fixed_samples(gref, G.bf16_weights(G.unflatten(th1.astype(np.float64))), T, X) < L0
     g.close()
 
 
