@@ -726,6 +726,9 @@ def main():
                     help="run only the warm-up and timed chosen solves and print their times (for launch lists)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the SpMM kernels of the workload (no solver; used for ncu captures)")
+    ap.add_argument("--kernels-workload", default=WORKLOAD,
+                    help="workload of --kernels-only: grid3d_N128 (SpMM, Gram and combine) or randill_1e6x5e5 "
+                         "(the two SpMM passes of its operator)")
     args = ap.parse_args()
     if args.kernels_only:
         import torch
@@ -733,9 +736,14 @@ def main():
         from paper_1607_01404_gb300 import binding as B
         from paper_1607_01404_gb300 import workloads as wl
 
-        A, _ = wl.workload(WORKLOAD)
+        A, _ = wl.workload(args.kernels_workload)
         dev = torch.device("cuda", 0)
         B.lib()
+        if args.kernels_workload != WORKLOAD:
+            out = {"workload": args.kernels_workload,
+                   "f32": spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK, reps=args.steps, with_c=False)}
+            print(json.dumps(out))
+            return 0
         out = {"f32": spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK, reps=args.steps),
                "df64": spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK, reps=args.steps),
                "ortho_f32": ortho_roofline(dev, torch, B, B.PREC_F32, A.n, 32, BLOCK, reps=args.steps),

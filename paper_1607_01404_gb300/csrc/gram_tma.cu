@@ -62,6 +62,7 @@ constexpr int kStages = 4;    // tiles in flight per CTA
 constexpr int kMaxSeg = 4;    // up to 3 P segments and Q
 constexpr int kMaxP = 64;
 constexpr long long kWaitCycles = 1LL << 31;
+constexpr unsigned kSuspendNs = 20000;  // a waiting thread sleeps until the phase completes or 20 us pass
 constexpr int kMaxSmem = 200 * 1024 + 128;  // largest dynamic shared memory of a plan
 constexpr int kBarBytes = kStages * 8 + kStages * 4 + 16;  // stage barriers, arrival counters, failure word
 constexpr int kRingTwoCtas = 110 * 1024;         // a plan at most this large lets two CTAs share an SM
@@ -94,11 +95,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -228,18 +229,21 @@ __global__ void __launch_bounds__(kT, 2)
   const int qo = qs.soff + qs.xoff;
 
   float sa[KP][NQ], ca[KP][NQ];
-  // anchors a_k, b_j (powers of two) and the running sums of squares; an
-  // anchor is raised when 4.5 x its sum of squares exceeds its square
-  float an[KP], bn[NQ], sp[KP], sq[NQ];
+  // anchors a_k, b_j (powers of two), the running sums of squares and the
+  // thresholds a^2 / 4.5 above which an anchor is raised
+  float an[KP], bn[NQ], sp[KP], sq[NQ], ta[KP], tb[NQ];
+  const float thr0 = kFloor * kFloor * (1.0f / 4.5f);
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     an[k] = kFloor;
     sp[k] = 0.f;
+    ta[k] = thr0;
   }
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
     bn[j] = kFloor;
     sq[j] = 0.f;
+    tb[j] = thr0;
   }
 #pragma unroll
   for (int k = 0; k < KP; ++k)
@@ -284,19 +288,21 @@ __global__ void __launch_bounds__(kT, 2)
         }
 #pragma unroll
         for (int k = 0; k < KP; ++k)
-          if (4.5f * sp[k] > an[k] * an[k]) {
+          if (sp[k] > ta[k]) {
             const float a1 = anc_anchor(sp[k]);
 #pragma unroll
             for (int j = 0; j < NQ; ++j) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], a1 * bn[j]);
             an[k] = a1;
+            ta[k] = a1 * a1 * (1.0f / 4.5f);
           }
 #pragma unroll
         for (int j = 0; j < NQ; ++j)
-          if (4.5f * sq[j] > bn[j] * bn[j]) {
+          if (sq[j] > tb[j]) {
             const float b1 = anc_anchor(sq[j]);
 #pragma unroll
             for (int k = 0; k < KP; ++k) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], an[k] * b1);
             bn[j] = b1;
+            tb[j] = b1 * b1 * (1.0f / 4.5f);
           }
 #pragma unroll
         for (int k = 0; k < KP; ++k)
