@@ -209,21 +209,22 @@ __global__ void __launch_bounds__(kT, 2)
   }
   __syncthreads();
 
-  // ---- consumer warps ----
+  // ---- the P columns of this lane ----
+  // Columns p .. TPR KP - 1 fall past the end of the last segment, inside its
+  // tile rows (the planner widened that box) where the copies wrote zeros, so
+  // every lane loads all KP columns and all NQ Q columns without predicates.
   const int part = threadIdx.x % TPR;
   int co[KP], cw[KP];
-  bool cv[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     int c = part + TPR * k;
-    cv[k] = c < p;
     int sg = 0;
     while (sg < plan.nP - 1 && c >= plan.seg[sg].nc) {
       c -= plan.seg[sg].nc;
       ++sg;
     }
-    co[k] = cv[k] ? plan.seg[sg].soff + plan.seg[sg].xoff + c * E : 0;
-    cw[k] = cv[k] ? plan.seg[sg].bw : 0;
+    co[k] = plan.seg[sg].soff + plan.seg[sg].xoff + c * E;
+    cw[k] = plan.seg[sg].bw;
   }
   const TmaSeg qs = plan.seg[plan.nP];
   const int qo = qs.soff + qs.xoff;
@@ -267,13 +268,13 @@ __global__ void __launch_bounds__(kT, 2)
       A xa[KP], xb[KP], ya[NQ], yb[NQ];
 #pragma unroll
       for (int k = 0; k < KP; ++k) {
-        xa[k] = cv[k] ? lds<P>(tile + co[k] + ra * cw[k]) : P::zero();
-        xb[k] = cv[k] ? lds<P>(tile + co[k] + rb * cw[k]) : P::zero();
+        xa[k] = lds<P>(tile + co[k] + ra * cw[k]);
+        xb[k] = lds<P>(tile + co[k] + rb * cw[k]);
       }
 #pragma unroll
       for (int j = 0; j < NQ; ++j) {
-        ya[j] = j < q ? lds<P>(tile + qo + ra * qs.bw + j * E) : P::zero();
-        yb[j] = j < q ? lds<P>(tile + qo + rb * qs.bw + j * E) : P::zero();
+        ya[j] = lds<P>(tile + qo + ra * qs.bw + j * E);
+        yb[j] = lds<P>(tile + qo + rb * qs.bw + j * E);
       }
       if constexpr (kAnchored) {
 #pragma unroll
@@ -453,6 +454,7 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
   const int kp = q <= 4 ? 4 : 2;
   int tpr = 2;
   while (tpr * kp < p) tpr *= 2;
+  const int nq = q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : 8;  // Q columns of the kernel instance
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // bank padding: the 32 / tpr rows a warp reads at once start on distinct banks
@@ -476,7 +478,10 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
       if (stride % 16 != 0 || a % (4 * E) != 0) return cudaErrorNotSupported;
       const int xoff = (int)((a - base) / 4);
       const int need = xoff + g.nc * E;
-      const int bw = padded_width(need, rho);
+      // the tile also covers the columns that lanes read past the data (zeros):
+      // up to TPR KP columns of P in the last segment, NQ columns of Q
+      const int cover = s < nseg ? (s == nseg - 1 ? g.nc + (tpr * kp - p) : g.nc) : nq;
+      const int bw = padded_width(xoff + cover * E, rho);
       if (bw > 256 || need * 4LL > stride) return cudaErrorNotSupported;
       const cuuint64_t dims[2] = {(cuuint64_t)need, (cuuint64_t)r1};
       const cuuint64_t strides[1] = {(cuuint64_t)stride};

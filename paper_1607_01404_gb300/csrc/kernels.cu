@@ -1396,8 +1396,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_combine_row(long long L, SegArr
       int c1 = 0;  // first column of the scalar tail
       if constexpr (VEC) {
         constexpr int W = (int)(16 / sizeof(S));
+        constexpr int U = QT <= 8 ? 4 : 2;  // 16-byte loads in flight per thread
         c1 = nc - nc % W;
-        for (int c = 0; c < c1; c += W) {
+        int c = 0;
+        for (; c + U * W <= c1; c += U * W) {
+          A xs[U][W];
+#pragma unroll
+          for (int u = 0; u < U; ++u) load16<P>(row + c + u * W, xs[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              const C* cr = cs + (c0 + c + u * W + w) * QT;
+#pragma unroll
+              for (int j = 0; j < QT; ++j) acc[j] = P::fmac(acc[j], xs[u][w], cr[j]);
+            }
+        }
+        for (; c < c1; c += W) {
           A xs[W];
           load16<P>(row + c, xs);
 #pragma unroll
