@@ -3,19 +3,23 @@
 One step = one complete solve of the workload through the C-ABI: handle
 creation from a device-resident CSR (transpose, value formats), the ||A||
 estimate, stage 1 and, if needed, stage 2, ending with the triplets and their
-residuals on the host.  The timed "chosen" form runs JDQMR in both stages with
-FP32 inner solves, an FP32 first phase of stage 1 (FP64-class outer iteration
-after it) and the learned sparse-approximate-inverse preconditioner (3D model
-trained on 24^3 weighted grids; network inference inside the timed solve);
-beside it are timed the plain FP64-class form (the same JDQMR with FP64-class
-inner and outer iterations and the Jacobi preconditioner, no FP32 and no
-network) and the plain FP64-class GD+k with Jacobi.  A second report compares
-the Jacobi and learned preconditioners on held-out weighted grids (256^2,
-k = 10; 96^3, k = 20).
+residuals on the host.  The timed "chosen" form runs DYNAMIC stage 1 (GD+k or
+JDQMR correction per outer iteration, FP32 inner solves), an FP32 first phase of
+stage 1 with a double-float (FP64-class) polish, and the learned sparse-
+approximate-inverse preconditioner (network inference inside the timed solve).
 
 Workload: the 3D grid-difference operator [D(x)I(x)I; I(x)D(x)I; I(x)I(x)D] on a
-128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4.  Its working set is far larger than L2, so no flush is
-needed between steps.
+128^3 grid (6,340,608 x 2,097,152, 12,582,912 nnz), k = 10 smallest, block 4.
+Its working set is far larger than L2, so no flush is needed between steps.
+
+Beside the timed line the JSON reports: the plain solver with the Jacobi
+preconditioner in double-float and in native FP64 (JDQMR and GD+k); the end-to-
+end time from pinned host buffers; the rooflines of the dominant kernel (the
+FP32 Gram) and of the SpMM; the 32^2 grid with the oracle run to completion on
+the host cores; the random 1e6 x 5e5 ill-conditioned matrix with stage 1 in
+double-float, FP32 and bfloat16 values; none / Jacobi / learned on held-out
+weighted 256^2 grids; the chosen form against the plain solvers on a weighted
+96^3 grid; the condition-number estimate; the measured FP32 and FP64 GEMM rates.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -44,7 +48,7 @@ MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
 # this workload (--set full, one warm launch each); None where the kernel
 # changed after its capture
-TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_row_f32_32x4": 315_316_480}
+TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_tma_f32_32x4": 311_810_304}
 UNIT = "s"
 # FP32 operations per product of the anchored FP64-class Gram accumulation in
 # the FP32 mode (fma, subtract, fma, add)
@@ -418,9 +422,10 @@ def run_gpu(args, world, rank, local):
     c3 = config3_report(B, wl, sp, dev, torch) if not args.skip_c3 else None
     c4 = config4_report(B, wl, sp, args.c4_seeds)
     c5 = config5_report(B, wl, sp)
-    fp32_peak = sgemm_peak(torch, dev)
+    fp32_peak = gemm_peak(torch, dev, torch.float32, 8192)
+    fp64_peak = gemm_peak(torch, dev, torch.float64, 4096)
     return dict(times=t_chosen, stats=st_chosen, clocks=clocks, relerr=relerr, nconv=nconv, rnorm=rnorm,
-                native=native, c1=c1, c3=c3, c4=c4, c5=c5, fp32_peak=fp32_peak, sigma=sigma,
+                native=native, c1=c1, c3=c3, c4=c4, c5=c5, fp32_peak=fp32_peak, fp64_peak=fp64_peak, sigma=sigma,
                 t_plain=t_plain, st_plain=st_plain, relerr_plain=relerr_p, t_gdk=t_gdk, st_gdk=st_gdk,
                 relerr_gdk=relerr_g, t_e2e=t_e2e, h2d=h2d, d2h=d2h, t_dyn=t_dyn, st_dyn=st_dyn,
                 relerr_dyn=relerr_d, cond=cond,
@@ -660,14 +665,16 @@ def config5_report(B, wl, sp):
     return out
 
 
-def sgemm_peak(torch, dev):
-    """FP32 SIMT throughput measured with cuBLAS SGEMM (TF32 off), 8192^3, best
-    of 5: the measured FP32-pipe denominator of the Gram's issue analysis."""
+def gemm_peak(torch, dev, dtype, n):
+    """Arithmetic throughput of cuBLAS GEMM in dtype (TF32 off for float32),
+    n^3, best of 5, TFLOP/s: float32 measures the FP32 SIMT pipe (the
+    denominator of the Gram's issue analysis), float64 the FP64 pipe (the
+    reason the FP64-class mode is double-float)."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        a = torch.randn(8192, 8192, device=dev)
-        b = torch.randn(8192, 8192, device=dev)
+        a = torch.randn(n, n, device=dev, dtype=dtype)
+        b = torch.randn(n, n, device=dev, dtype=dtype)
         for _ in range(2):
             torch.mm(a, b)
         best = 1e30
@@ -678,7 +685,7 @@ def sgemm_peak(torch, dev):
             e1.record()
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1) / 1e3)
-        return 2 * 8192 ** 3 / best / 1e12
+        return 2 * n ** 3 / best / 1e12
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
@@ -821,9 +828,9 @@ def main():
     # at the solve's shape (g = 32 basis columns, b = 4) over its CUDA-event time
     g32 = res["orth"]["f32_gram"]
     gprod = A.n * 32 * BLOCK
-    gram_roof = dict(bound="hbm", kernel=f"k_gram_anc (FP32, Gram 32 x {BLOCK} columns, FP64-class anchored "
-                                         f"accumulation)", achieved=g32["gbs"], peak=peak, unit="GB/s",
-                     frac=g32["gbs"] / peak, peak_kind=peak_kind, traffic=TRAFFIC.get("gram_anc_f32_32x4"),
+    gram_roof = dict(bound="hbm", kernel=f"k_gram_tma (FP32, Gram 32 x {BLOCK} columns, TMA-fed, FP64-class "
+                                         f"anchored accumulation)", achieved=g32["gbs"], peak=peak, unit="GB/s",
+                     frac=g32["gbs"] / peak, peak_kind=peak_kind, traffic=TRAFFIC.get("gram_tma_f32_32x4"),
                      bytes_per_launch=g32["bytes"], ms_per_launch=round(g32["ms"], 5),
                      fp32_issue=dict(ops_per_product=GRAM_OPS,
                                      achieved_tops=GRAM_OPS * gprod / (g32["ms"] * 1e-3) / 1e12,
@@ -876,6 +883,8 @@ def main():
                           matvecs=int(res["st_dyn"][-1]["matvecs_stage1"] + res["st_dyn"][-1]["matvecs_stage2"]),
                           max_rel_sigma_err=res["relerr_dyn"]),
         condest=res["cond"],
+        fp_rates_measured=dict(sgemm_tflops=round(res["fp32_peak"], 2), dgemm_tflops=round(res["fp64_peak"], 3),
+                               note="cuBLAS SGEMM 8192^3 (TF32 off) and DGEMM 4096^3, best of 5, CUDA events"),
         gpu_launches=launches,
         clocks=res["clocks"],
     )

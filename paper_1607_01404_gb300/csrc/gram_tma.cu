@@ -436,12 +436,12 @@ cudaError_t run(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long lo
   return cudaGetLastError();
 }
 
-template <class P, int TPR>
+template <class P, int TPR, int KP = 4>
 cudaError_t run_q4(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long long r0, long long r1, int p, int q,
                    void* partial, int max_blocks, int* nb, cudaStream_t st) {
-  if (q <= 1) return run<P, TPR, 4, 1>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-  if (q <= 2) return run<P, TPR, 4, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-  return run<P, TPR, 4, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (q <= 1) return run<P, TPR, KP, 1>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (q <= 2) return run<P, TPR, KP, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  return run<P, TPR, KP, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
 }
 
 template <class P>
@@ -450,10 +450,16 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
   constexpr int E = P::id == kF32 ? 1 : 2;
   const int q = Q.nc;
   // lanes per row (tpr) and P columns per lane (kp) so that a lane owns at
-  // most 16 pairs: 4 columns for q <= 4, 2 for q <= 8
-  const int kp = q <= 4 ? 4 : 2;
+  // most 16 pairs: 4 columns for q <= 4 (3 for 32 < p <= 48, where 16 x 4
+  // columns would leave a quarter or more of the lanes' products on padding),
+  // 2 for q <= 8
+  int kp = q <= 4 ? 4 : 2;
   int tpr = 2;
   while (tpr * kp < p) tpr *= 2;
+  if (kp == 4 && p > 32 && p <= 48) {
+    tpr = 16;
+    kp = 3;
+  }
   const int nq = q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : 8;  // Q columns of the kernel instance
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -502,6 +508,7 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
   }
   if ((size_t)plan.bar_off * 4 + kBarBytes > (size_t)kMaxSmem) return cudaErrorNotSupported;
   for (int s = nseg + 1; s < kMaxSeg; ++s) maps[s] = maps[nseg];  // unused slots: any valid map
+  if (kp == 3) return run_q4<P, 16, 3>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
   if (kp == 4) {
     if (tpr == 2) return run_q4<P, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
     if (tpr == 4) return run_q4<P, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
