@@ -267,10 +267,27 @@ def ortho_roofline(dev, torch, B, prec, L, g, b, reps=20):
     coef = torch.from_numpy(B.coef_convert(prec, np.full((g, b), 1e-3))).to(dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
+    # the Ritz kernel (X = V Y, R = W Y - X diag(theta), norms) on a second basis W,
+    # and the in-place restart V <- V Z to 18 columns (Z = the first 18 columns of
+    # the identity, so the values stay put over the repeated launches)
+    W = torch.randn(L * ldv * words, dtype=torch.float32, device=dev)
+    if words == 2:
+        W.view(-1, 2)[:, 1] = 0
+    Y = torch.from_numpy(B.coef_convert(prec, np.full((g, b), 1e-2))).to(dev)
+    th = torch.from_numpy(B.coef_convert(prec, np.arange(1.0, b + 1))).to(dev)
+    X = torch.zeros(L * b * words, dtype=torch.float32, device=dev)
+    R = torch.zeros(L * b * words, dtype=torch.float32, device=dev)
+    nrm = torch.zeros(b, dtype=torch.float64, device=dev)
+    rscratch = torch.zeros(B.ritz_scratch_bytes(b), dtype=torch.uint8, device=dev)
+    qr = 18
+    Z = torch.from_numpy(B.coef_convert(prec, np.eye(g, qr))).to(dev)
     res = {}
     for name, fn, alg in (
         ("gram", lambda: B.gram(prec, 0, L, V, ldv, g, T, b, b, G, scratch, stream=sp), L * (g + b) * s),
         ("combine", lambda: B.combine(prec, L, V, ldv, g, coef, T, b, 1, T, b, b, stream=sp), L * (g + 2 * b) * s),
+        ("ritz", lambda: B.ritz_residual(prec, L, V, W, ldv, g, Y, th, X, R, b, b, nrm, rscratch, stream=sp),
+         L * (2 * g + 2 * b) * s),
+        ("restart", lambda: B.combine(prec, L, V, ldv, g, Z, None, 0, 0, V, ldv, qr, stream=sp), L * (g + qr) * s),
     ):
         for _ in range(3):
             fn()
@@ -861,7 +878,9 @@ def main():
                          matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
                          inner_steps=st["inner_steps"], outer1_jdqmr=st["outer_stage1_jdqmr"],
                          stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],
-                         precond_s=st["seconds_precond"]),
+                         precond_s=st["seconds_precond"], host_syncs=st["host_syncs"],
+                         sync_wait_s=st["seconds_sync_wait"], host_eig_s=st["seconds_host_eig"],
+                         kernel_launches=st["kernel_launches"], precond_fallback=st["precond_fallback"]),
         roofline=gram_roof,
         roofline_spmm=dict(bound="hbm", kernel=f"{dom} (FP32, b={BLOCK})", achieved=achieved, peak=peak, unit="GB/s",
                       frac=achieved / peak, peak_kind=peak_kind, traffic=TRAFFIC.get(dom),

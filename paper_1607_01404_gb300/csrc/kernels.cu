@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 
@@ -810,6 +812,31 @@ __global__ void __launch_bounds__(64) k_ortho_small(int stage, int prec, int g, 
   for (int e = t; e < nb * nb; e += blockDim.x) store_coef(prec, stage == 2 ? rinv : coef, e, Ri[e]);
 }
 
+// CTAs of `kernel` that are resident on the whole GPU at once (per device and
+// kernel, cached): a grid-stride kernel launched with more CTAs than this runs
+// a partial last wave.
+inline int resident_ctas(const void* kernel, int threads) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, kernel});
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const int r = std::max(1, per_sm) * std::max(1, sms);
+  cache[{dev, kernel}] = r;
+  return r;
+}
+
 inline int persistent_grid(long long work_items, int per_block) {
   long long g = (work_items + per_block - 1) / per_block;
   const long long cap = 152LL * 16;
@@ -1362,7 +1389,7 @@ __device__ __forceinline__ void load16(const typename P::S* p, typename P::A (&x
 // input segment or In.  The coefficients (and R^-1) sit in shared memory and
 // every lane of a warp reads the same address (a broadcast).
 template <class P, int QT, bool VEC>
-__global__ void __launch_bounds__(kThreads, 2) k_combine_row(long long L, SegArr segs, int p, int q,
+__global__ void __launch_bounds__(kThreads, (QT <= 4 && P::id != kDF64) ? 4 : 2) k_combine_row(long long L, SegArr segs, int p, int q,
                                                           const typename P::C* __restrict__ coef,
                                                           const typename P::S* In, long long ldin, int alpha_one,
                                                           typename P::S* Out, long long ldout,
@@ -1575,8 +1602,29 @@ __global__ void __launch_bounds__(kThreads) k_ritz_row(long long L, const typena
     int c1 = 0;  // first column of the scalar tail
     if constexpr (VEC) {
       constexpr int WW = (int)(16 / sizeof(S));
+      constexpr int U = 2;  // row segments of V and W in flight per thread
       c1 = g - g % WW;
-      for (int c = 0; c < c1; c += WW) {
+      int c = 0;
+      for (; c + U * WW <= c1; c += U * WW) {
+        A xv[U][WW], xw[U][WW];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          load16<P>(vr + c + u * WW, xv[u]);
+          load16<P>(wr + c + u * WW, xw[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int w = 0; w < WW; ++w) {
+            const C* yr = ys + (c + u * WW + w) * Q + j0;
+#pragma unroll
+            for (int j = 0; j < QT; ++j) {
+              ax[j] = P::fmac(ax[j], xv[u][w], yr[j]);
+              ar[j] = P::fmac(ar[j], xw[u][w], yr[j]);
+            }
+          }
+      }
+      for (; c < c1; c += WW) {
         A xv[WW], xw[WW];
         load16<P>(vr + c, xv);
         load16<P>(wr + c, xw);
@@ -1654,6 +1702,11 @@ cudaError_t ritz_row_p(long long L, SegV V, SegV W, int g, const void* Y, const 
   {                                                                                                                \
     long long grid = (L + kThreads / TPRV - 1) / (kThreads / TPRV);                                                \
     if (grid > max_blocks) grid = max_blocks;                                                                      \
+    {                                                                                                              \
+      const int res = resident_ctas(vec ? reinterpret_cast<const void*>(k_ritz_row<P, TPRV, true>)                 \
+                                        : reinterpret_cast<const void*>(k_ritz_row<P, TPRV, false>), kThreads);    \
+      if (grid > res) grid = res; /* one full wave: no partial last wave */                                        \
+    }                                                                                                              \
     if (grid < 1) grid = 1;                                                                                        \
     *nblocks = (int)grid;                                                                                          \
     if (vec)                                                                                                       \
