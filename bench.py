@@ -673,6 +673,7 @@ def config5_report(B, wl, sp):
         sig[name] = s_
         out[name] = dict(seconds=round(secs, 4), numConverged=nconv, matvecs=int(st["matvecs_stage1"] + st["matvecs_stage2"]),
                          outer=int(st["outer_stage1"] + st["outer_stage2"]), fallback=st["precond_fallback"],
+                         matvecs_lowprec=int(st["matvecs_stage1_lowprec"]),
                          max_rnorm_over_normA=float(np.max(rn) / st["aNorm"]))
     for name in ("chosen", "plain_native_fp64"):
         out[name]["max_rel_sigma_diff_vs_plain_df64"] = float(np.max(np.abs(sig[name] - sig["plain_df64"])

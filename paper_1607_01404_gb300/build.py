@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphsvds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "gram_tma.cu", "tiled.cu", "engine.cpp", "hostla.cpp", "api.cpp", "noalloc.cu", "jdqmr.cu", "gnn.cu",
-           "bjacobi.cu"]
+SOURCES = ["kernels.cu", "gram_tma.cu", "combine_tma.cu", "tiled.cu", "engine.cpp", "hostla.cpp", "api.cpp",
+           "noalloc.cu", "jdqmr.cu", "gnn.cu", "bjacobi.cu"]
 
 
 def nvcc() -> str:

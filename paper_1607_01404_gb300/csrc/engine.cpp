@@ -1077,12 +1077,19 @@ struct RefinedCfg : RunCfg {
 // Fresh QR of (W - tau V): Q <- W - tau V, then CholQR2; returns R (column-major).
 std::vector<double> fresh_qr(Ctx& c, RunBufs& B, int g, double tau) {
   const int prec = B.prec;
-  std::vector<double> coef((size_t)2 * g * g, 0.0);
-  for (int j = 0; j < g; ++j) {
-    coef[(size_t)j * g + j] = 1.0;             // W rows of the coefficient (first g rows)
-    coef[(size_t)(g + j) * g + j] = -tau;      // V rows
+  // Q = W - tau V in column blocks of 32: each block is a combine of the two
+  // matching column blocks with the coefficient [I; -tau I], whose table
+  // stays small for any basis width
+  for (int j0 = 0; j0 < g; j0 += 32) {
+    const int w = std::min(32, g - j0);
+    std::vector<double> coef((size_t)2 * w * w, 0.0);
+    for (int j = 0; j < w; ++j) {
+      coef[(size_t)j * w + j] = 1.0;         // W rows of the coefficient (first w rows)
+      coef[(size_t)(w + j) * w + j] = -tau;  // V rows
+    }
+    combine(c, prec, B.L, {SegV{off(B.W, j0, prec), B.ldv, w}, SegV{off(B.V, j0, prec), B.ldv, w}}, coef, nullptr,
+            0, false, off(B.Q, j0, prec), B.ldv, w);
   }
-  combine(c, prec, B.L, {SegV{B.W, B.ldv, g}, SegV{B.V, B.ldv, g}}, coef, nullptr, 0, false, B.Q, B.ldv, g);
   OrthoRes o = ortho(c, prec, B.L, {}, B.Q, B.ldv, g, nullptr, 0);
   std::vector<double> R((size_t)g * g);
   for (int i = 0; i < g; ++i)
@@ -1454,9 +1461,12 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     reqs.push_back({(void**)&c.dstatus, 256});
     reqs.push_back({(void**)&c.dflag, 256});
     c.nslots = 64;
-    // one slot holds the largest coefficient block: a basis-by-basis restart
-    // matrix of the widest basis (8-byte coefficients)
-    c.slot_bytes = std::max<size_t>((size_t)2 * 256 * 256, ((size_t)(ldv + 8) * (ldv + 8) * 8 + 255) & ~size_t(255));
+    // one slot holds the largest coefficient block (8-byte coefficients): a
+    // basis-by-basis restart matrix of the widest basis, or the 2g x g block of
+    // the refined extraction's fresh QR of W - tau V
+    c.slot_bytes = std::max<size_t>({(size_t)2 * 256 * 256, (size_t)(ldv + 8) * (ldv + 8) * 8,
+                                     (size_t)2 * ldv * ldv * 8});
+    c.slot_bytes = (c.slot_bytes + 255) & ~size_t(255);
     reqs.push_back({(void**)&c.dstage, (size_t)c.nslots * c.slot_bytes});
     size_t total = 0;
     for (auto& r : reqs) total += (r.bytes + 255) & ~size_t(255);
@@ -1691,10 +1701,15 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c1.jdK = Kinner;
     if (lowprec) {
       init_block(kF32, X1a, kk, b0);
-      // bfloat16 values that round A (or C) perturb the operator by ~2^-8 relative:
-      // the FP32 phase then stops at that floor
+      // bfloat16 values that round A (or C) perturb the operator by ~2^-8 of
+      // ||C||: for the largest values the FP32 phase stops at that floor.  The
+      // smallest eigenvalues of the rounded operator move far less than that
+      // bound (random rounding errors), but a pair accepted at a 2^-8 ||C||
+      // residual has no accuracy at all when its value is far below it, and
+      // such vectors steer the FP64-class phase away from the smallest pair;
+      // for the smallest values the phase runs to its arithmetic's floor
       const bool exact_vals = A.exact16 && (A.nnzC > 0 ? A.exactC : A.exact32);
-      c1.u = (bf16 && !exact_vals) ? std::ldexp(1.0, -8) : unit_roundoff(kF32);
+      c1.u = (bf16 && !exact_vals && !smallest) ? std::ldexp(1.0, -8) : unit_roundoff(kF32);
       c1.conv = stage1_conv(c1.u);
       c1.dscale = (jac || jac_fb) ? d1a : nullptr;
       c1.fb_dscale = d1a;

@@ -52,17 +52,18 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace phsvds {
 
 namespace {
 
+using namespace tma;
+
 constexpr int kT = 256;       // threads per CTA
 constexpr int kStages = 4;    // tiles in flight per CTA
 constexpr int kMaxSeg = 4;    // up to 3 P segments and Q
 constexpr int kMaxP = 64;
-constexpr long long kWaitCycles = 1LL << 31;
-constexpr unsigned kSuspendNs = 20000;  // a waiting thread sleeps until the phase completes or 20 us pass
 constexpr int kMaxSmem = 200 * 1024 + 128;  // largest dynamic shared memory of a plan
 constexpr int kBarBytes = kStages * 8 + kStages * 4 + 16;  // stage barriers, arrival counters, failure word
 constexpr int kRingTwoCtas = 110 * 1024;         // a plan at most this large lets two CTAs share an SM
@@ -80,43 +81,6 @@ struct TmaPlan {
   int R;             // rows per stage
   int bar_off;       // float offset of the stage barriers (after the ring and the reduction buffer)
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait on one phase of a stage's barrier
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // ---- anchored accumulation (see the file header) ----
 __device__ __forceinline__ float hi_of(float x) { return x; }
@@ -192,7 +156,7 @@ __global__ void __launch_bounds__(kT, 2)
     float* base = smem + (size_t)st * plan.stage_floats;
     mbar_expect_tx(&full[st], tx_bytes);
     const int y = (int)(r0 + ch * R);
-    for (int sg = 0; sg < nseg; ++sg) tma_load_2d(base + plan.seg[sg].soff, maps[sg], 0, y, &full[st]);
+    for (int sg = 0; sg < nseg; ++sg) load_2d(base + plan.seg[sg].soff, maps[sg], 0, y, &full[st]);
   };
 
   if (threadIdx.x == 0) {
@@ -201,7 +165,7 @@ __global__ void __launch_bounds__(kT, 2)
       arrived[st] = 0;
     }
     *fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbar_init();
     for (int st = 0; st < kStages; ++st) {
       const long long ch = blockIdx.x + (long long)st * gridDim.x;
       if (ch < nchunks) issue(ch, st);
@@ -258,8 +222,11 @@ __global__ void __launch_bounds__(kT, 2)
   int it = 0, pairs = 0;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
     const int stage = it % kStages;
-    if (atomicAdd(fail, 0) || !mbar_wait(&full[stage], (unsigned)((it / kStages) & 1))) {
-      atomicOr(fail, 1);
+    // warp-uniform decision: every lane of a warp leaves the loop together
+    const bool ok =
+        __all_sync(0xffffffffu, !atomicAdd(fail, 0) && mbar_wait(&full[stage], (unsigned)((it / kStages) & 1)));
+    if (!ok) {
+      if (lane == 0) atomicOr(fail, 1);
       break;
     }
     const float* tile = smem + (size_t)stage * plan.stage_floats;
@@ -344,7 +311,7 @@ __global__ void __launch_bounds__(kT, 2)
         const long long nx = ch + (long long)kStages * gridDim.x;
         if (nx < nchunks) {
           __threadfence_block();
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          fence_proxy_async();
           issue(nx, stage);
         }
       }
@@ -387,22 +354,6 @@ __global__ void __launch_bounds__(kT, 2)
     for (int w = 1; w < NW; ++w) v = df_add(v, red[w * pq + e]);
     partial[(long long)blockIdx.x * pq + e] = v;
   }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    else
-      cudaGetLastError();
-  });
-  return fn;
 }
 
 // smallest w >= need, w a multiple of 4 floats, w = rho (mod 32) when rho > 0

@@ -751,12 +751,16 @@ __device__ __forceinline__ void store_coef(int prec, void* out, int idx, double 
 
 // Upper Cholesky of the nb x nb row-major matrix S into R (row-major) and its
 // inverse into Ri; returns false if S is not numerically positive definite.
-__device__ bool dev_chol_inv(int nb, const double* S, double* R, double* Ri) {
+// Cholesky factor R (upper, S = R^T R) and its inverse; false when a pivot
+// keeps at most tau of its column's squared norm S_jj (the column depends on
+// the earlier ones: for a duplicated column the pivot is the FP64 rounding of
+// the factorisation, about 1e-16 S_jj, of either sign) or is not finite.
+__device__ bool dev_chol_inv(int nb, const double* S, double* R, double* Ri, double tau) {
   for (int e = 0; e < nb * nb; ++e) R[e] = Ri[e] = 0.0;
   for (int j = 0; j < nb; ++j) {
     double d = S[j * nb + j];
     for (int k = 0; k < j; ++k) d -= R[k * nb + j] * R[k * nb + j];
-    if (!(d > 0.0) || !isfinite(d)) return false;
+    if (!(d > tau * S[j * nb + j]) || !isfinite(d)) return false;
     const double rjj = sqrt(d);
     R[j * nb + j] = rjj;
     for (int i = j + 1; i < nb; ++i) {
@@ -802,7 +806,7 @@ __global__ void __launch_bounds__(64) k_ortho_small(int stage, int prec, int g, 
     if (stage == 2)
       for (int j = 0; j < nb; ++j)
         if (!(S[j * nb + j] > drop2 * fmax(work[j], 1e-300))) st |= 1;
-    if (!dev_chol_inv(nb, S, R, Ri)) {
+    if (!dev_chol_inv(nb, S, R, Ri, 1e-14)) {  // the host repair's rank rule
       st |= 2;
       for (int e = 0; e < nb * nb; ++e) Ri[e] = (e / nb == e % nb) ? 1.0 : 0.0;
     }
@@ -1521,6 +1525,11 @@ cudaError_t launch_combine(int prec, long long L, const SegV* Pp, int nseg, cons
   int p;
   SegArr sa = make_segs(Pp, nseg, &p);
   if (nseg < 1 || nseg > 3 || p < 1) return cudaErrorInvalidValue;
+  if (prec != kF64) {
+    const cudaError_t e =
+        launch_combine_tma(prec, L, Pp, nseg, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (p <= kRowCombP && q <= 32 && (!Rinv || q <= 8)) {
     PHSVDS_DISPATCH(prec, combine_row_p<P>(L, sa, p, coef, In, ldin, alpha_one, Out, ldout, q, Rinv, Out2, ldout2,
                                            st))

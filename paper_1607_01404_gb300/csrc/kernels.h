@@ -48,6 +48,13 @@ cudaError_t launch_gram(int prec, long long r0, long long r1, const SegV* P, int
 // preconditions do not hold (the caller then uses the row kernels).
 cudaError_t launch_gram_tma(int prec, long long r0, long long r1, const SegV* P, int nseg, SegV Q, void* partial,
                             int max_blocks, int* nblocks, cudaStream_t st);
+// TMA-fed basis update for F32/DF64, p <= 64, q <= 32 (R^-1: q <= 8), every
+// segment, In, Out and Out2 16-byte aligned with 16-byte-multiple strides:
+// same contract as launch_combine; cudaErrorNotSupported when its
+// preconditions do not hold (the caller then uses the row kernels).
+cudaError_t launch_combine_tma(int prec, long long L, const SegV* P, int nseg, const void* coef, const void* In,
+                               long long ldin, int alpha_one, void* Out, long long ldout, int q, const void* Rinv,
+                               void* Out2, long long ldout2, cudaStream_t st);
 // Sum the partials in fixed order into G (p x q, row-major doubles, device).
 cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st);
 // Bytes of partial storage that launch_gram may use.

@@ -175,6 +175,41 @@ def test_combine_and_inplace_restart(prec, aligned, p, q):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L", [1, 255, 256, 257, 100003])
+@pytest.mark.parametrize("p,q", [(1, 1), (4, 3), (32, 4), (32, 18), (35, 5), (64, 12), (64, 32), (17, 23)])
+def test_combine_row_tiles(prec, L, p, q):
+    """Out = In + P C on 16-byte-aligned blocks (the TMA-fed update: 256-row
+    tiles, ragged last tile, every output-width bucket), then the in-place CGS
+    step T <- (T - V C) R^-1 with Out = In, and the in-place restart V <- V Z."""
+    ldp, ldq = ((p + 3) // 4) * 4, ((q + 3) // 4) * 4
+    P = wl.dense_block(L, p, seed=13)
+    T = wl.dense_block(L, q, seed=14)
+    Cm = wl.dense_block(p, q, seed=15)
+    Pd, Td = to_device(prec, P, ld=ldp), to_device(prec, T, ld=ldq)
+    Ps, Ts = to_host(prec, Pd, L, ldp)[:, :p], to_host(prec, Td, L, ldq)[:, :q]
+    Cd = coef_device(prec, Cm)
+    Out = to_device(prec, np.zeros((L, ldq)))
+    B.combine(prec, L, Pd, ldp, p, Cd, Td, ldq, 1, Out, ldq, q)
+    got = to_host(prec, Out, L, ldq)[:, :q]
+    scale = np.abs(Ts) + np.abs(Ps) @ np.abs(Cm)
+    assert np.all(np.abs(got - (Ts + Ps @ Cm)) <= 4 * TOL[prec] * scale)
+    if q <= 8:
+        R = np.triu(wl.dense_block(q, q, seed=16)) + 3 * np.eye(q)
+        Ri = np.linalg.inv(R)
+        B.combine(prec, L, Pd, ldp, p, coef_device(prec, -Cm), Td, ldq, 1, Td, ldq, q, coef_device(prec, Ri))
+        got = to_host(prec, Td, L, ldq)[:, :q]
+        ref = (Ts - Ps @ Cm) @ Ri
+        sc = (np.abs(Ts) + np.abs(Ps) @ np.abs(Cm)) @ np.abs(Ri)
+        assert np.all(np.abs(got - ref) <= 4 * TOL[prec] * sc)
+    nz = min(p, q)
+    Z = np.linalg.qr(wl.dense_block(p, p, seed=17))[0][:, :nz]
+    B.combine(prec, L, Pd, ldp, p, coef_device(prec, Z), None, 0, 0, Pd, ldp, nz)
+    got = to_host(prec, Pd, L, ldp)[:, :p]
+    assert np.all(np.abs(got[:, :nz] - Ps @ Z) <= 4 * TOL[prec] * (np.abs(Ps) @ np.abs(Z)))
+    assert np.array_equal(got[:, nz:], Ps[:, nz:])
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8), (20, 13)])
 def test_ritz_residual(prec, aligned, g, nb):
