@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 
       }
     }
     // warp-uniform decision: every lane of a warp leaves the loop together
-    const bool ok = __all_sync(0xffffffffu, !atomicAdd(fail, 0) && mbar_wait(&full[stage], (unsigned)((it / NS) & 1)));
+    const bool ok = __all_sync(0xffffffffu, !*reinterpret_cast<volatile int*>(fail) && mbar_wait(&full[stage], (unsigned)((it / NS) & 1)));
     if (!ok) {
       if (lane == 0) atomicOr(fail, 1);
       break;

@@ -10,16 +10,19 @@
 // warps wait on it independently, and the last warp to finish a stage (an
 // arrival counter in shared memory) refills it with the CTA's next chunk, so
 // no CTA-wide barrier and no idle producer warp sit in the loop.  The bytes in
-// flight cost no registers: a CTA keeps kStages tiles in flight.
+// flight cost no registers: a CTA keeps its ring's tiles in flight.
 // Rows past r1 and columns past the segment are outside the tensor maps and
-// arrive as zeros, so the ragged tail needs no masks.  Tile rows are padded so
-// that the lanes of a warp (TPR lanes per row, 32 / TPR rows) read distinct
-// shared-memory banks.
+// arrive as zeros, so the ragged tail needs no masks.  Each of the TPR lanes
+// of a row owns KP consecutive columns of a tile row (a segment's columns
+// counted from its copy boundary, so a window that starts inside a 16-byte
+// word brings a few columns before it, whose products are dropped) and reads
+// them, and the row's Q columns, with 16- or 8-byte shared-memory loads; tile
+// rows are padded so that the rows one load instruction touches start on
+// distinct banks.
 //
-// Arithmetic side: the lane layout of the row Gram (lane `part` of a row owns
-// P columns part + TPR k and every Q column), FP64-class accumulation of
-// every product, and a fixed-order double-float reduction of the lanes
-// (deterministic).
+// Arithmetic side: FP64-class accumulation of every product of a lane's
+// columns with the row's Q columns, and a fixed-order double-float reduction
+// of the lanes (deterministic).
 // * DF64 storage: Dot2 (Ogita, Rump and Oishi 2005): the exact product of the
 //   hi parts (TwoProd by FMA) plus the cross terms, TwoSum into hi, rounding
 //   errors into lo, renormalised every 2 rows; accurate to about 2^-48 of
@@ -61,24 +64,28 @@ namespace {
 using namespace tma;
 
 constexpr int kT = 256;       // threads per CTA
-constexpr int kStages = 4;    // tiles in flight per CTA
+constexpr int kMaxStages = 4;  // ring stages per CTA, at most
 constexpr int kMaxSeg = 4;    // up to 3 P segments and Q
 constexpr int kMaxP = 64;
 constexpr int kMaxSmem = 200 * 1024 + 128;  // largest dynamic shared memory of a plan
-constexpr int kBarBytes = kStages * 8 + kStages * 4 + 16;  // stage barriers, arrival counters, failure word
+constexpr int kBarBytes = kMaxStages * 8 + kMaxStages * 4 + 16;  // stage barriers, arrival counters, failure word
 constexpr int kRingTwoCtas = 110 * 1024;         // a plan at most this large lets two CTAs share an SM
 
 struct TmaSeg {
-  int soff;  // float offset of the segment's tile inside a stage
-  int bw;    // floats per tile row (box width)
-  int xoff;  // float offset of the segment's column 0 inside a tile row
-  int nc;    // columns (elements)
+  int soff;    // float offset of the segment's tile inside a stage
+  int bw;      // floats per tile row (box width)
+  int pstart;  // first lane column of the segment (lane columns: see the kernel)
+  int ncp;     // lane columns of the segment: xe + nc rounded up to KP
+  int xe;      // elements before the segment's first column in its tile rows
+  int nc;      // columns
+  int c0;      // first column of the segment in P
 };
 struct TmaPlan {
   TmaSeg seg[kMaxSeg];  // [0, nP): P segments, [nP]: Q
   int nP;
   int stage_floats;  // a multiple of 32 (every tile starts on a 128-byte boundary)
   int R;             // rows per stage
+  int stages;        // ring stages (2 .. kMaxStages)
   int bar_off;       // float offset of the stage barriers (after the ring and the reduction buffer)
 };
 
@@ -117,16 +124,40 @@ __device__ __forceinline__ void anc_move(float& s, float& c, float so, float sn)
   s = t;
 }
 
+// N consecutive floats from shared memory in the widest aligned pieces (the
+// callers' offsets are multiples of the piece)
+template <int N>
+__device__ __forceinline__ void lds_n(const float* p, float (&v)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 t = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = t.x;
+      v[4 * i + 1] = t.y;
+      v[4 * i + 2] = t.z;
+      v[4 * i + 3] = t.w;
+    }
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float2 t = reinterpret_cast<const float2*>(p)[i];
+      v[2 * i] = t.x;
+      v[2 * i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
 template <class P>
-__device__ __forceinline__ typename P::A lds(const float* p);
+__device__ __forceinline__ typename P::A elem(const float* v, int i);
 template <>
-__device__ __forceinline__ float lds<PF32>(const float* p) {
-  return *p;
+__device__ __forceinline__ float elem<PF32>(const float* v, int i) {
+  return v[i];
 }
 template <>
-__device__ __forceinline__ df lds<PDF64>(const float* p) {
-  const float2 v = *reinterpret_cast<const float2*>(p);
-  return df{v.x, v.y};
+__device__ __forceinline__ df elem<PDF64>(const float* v, int i) {
+  return df{v[2 * i], v[2 * i + 1]};
 }
 
 template <class P, int TPR, int KP, int NQ>
@@ -142,8 +173,9 @@ __global__ void __launch_bounds__(kT, 2)
   constexpr bool kAnchored = P::id == kF32;
   extern __shared__ __align__(128) float smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + plan.bar_off);
-  int* arrived = reinterpret_cast<int*>(full + kStages);
-  int* fail = arrived + kStages;
+  int* arrived = reinterpret_cast<int*>(full + kMaxStages);
+  int* fail = arrived + kMaxStages;
+  const int NS = plan.stages;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int R = plan.R;
   const long long nchunks = (r1 - r0 + R - 1) / R;
@@ -160,13 +192,13 @@ __global__ void __launch_bounds__(kT, 2)
   };
 
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) {
+    for (int st = 0; st < NS; ++st) {
       mbar_init(&full[st], 1);
       arrived[st] = 0;
     }
     *fail = 0;
     fence_mbar_init();
-    for (int st = 0; st < kStages; ++st) {
+    for (int st = 0; st < NS; ++st) {
       const long long ch = blockIdx.x + (long long)st * gridDim.x;
       if (ch < nchunks) issue(ch, st);
     }
@@ -174,24 +206,22 @@ __global__ void __launch_bounds__(kT, 2)
   __syncthreads();
 
   // ---- the P columns of this lane ----
-  // Columns p .. TPR KP - 1 fall past the end of the last segment, inside its
-  // tile rows (the planner widened that box) where the copies wrote zeros, so
-  // every lane loads all KP columns and all NQ Q columns without predicates.
+  // Lane columns: segment s occupies lane columns [pstart, pstart + ncp), in
+  // the order of its tile rows: xe elements before its first column (the copy
+  // starts on a 16-byte boundary), its nc columns, then zeros (the copies read
+  // past the data) up to a multiple of KP.  Lane `part` owns the KP
+  // consecutive lane columns from part KP, inside one segment, and reads them
+  // with vector loads; lane columns past the last segment lie inside its
+  // widened tile rows (zeros).  Products of the prefix and padding columns are
+  // computed and dropped.
   const int part = threadIdx.x % TPR;
-  int co[KP], cw[KP];
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    int c = part + TPR * k;
-    int sg = 0;
-    while (sg < plan.nP - 1 && c >= plan.seg[sg].nc) {
-      c -= plan.seg[sg].nc;
-      ++sg;
-    }
-    co[k] = plan.seg[sg].soff + plan.seg[sg].xoff + c * E;
-    cw[k] = plan.seg[sg].bw;
-  }
+  const int pc0 = part * KP;
+  int sgl = 0;
+  while (sgl < plan.nP - 1 && pc0 >= plan.seg[sgl + 1].pstart) ++sgl;
+  const int po = plan.seg[sgl].soff + (pc0 - plan.seg[sgl].pstart) * E;  // tile-row offset of the lane's columns
+  const int pw = plan.seg[sgl].bw;
   const TmaSeg qs = plan.seg[plan.nP];
-  const int qo = qs.soff + qs.xoff;
+  const int qo = qs.soff;  // Q lane columns 0 .. NQ - 1 = the Q tile row from its start
 
   float sa[KP][NQ], ca[KP][NQ];
   // anchors a_k, b_j (powers of two), the running sums of squares and the
@@ -221,10 +251,10 @@ __global__ void __launch_bounds__(kT, 2)
   const int row0 = threadIdx.x / TPR;
   int it = 0, pairs = 0;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
-    const int stage = it % kStages;
+    const int stage = it % NS;
     // warp-uniform decision: every lane of a warp leaves the loop together
     const bool ok =
-        __all_sync(0xffffffffu, !atomicAdd(fail, 0) && mbar_wait(&full[stage], (unsigned)((it / kStages) & 1)));
+        __all_sync(0xffffffffu, !*reinterpret_cast<volatile int*>(fail) && mbar_wait(&full[stage], (unsigned)((it / NS) & 1)));
     if (!ok) {
       if (lane == 0) atomicOr(fail, 1);
       break;
@@ -233,15 +263,22 @@ __global__ void __launch_bounds__(kT, 2)
     for (int ra = row0; ra < R; ra += 2 * RPC, ++pairs) {
       const int rb = ra + RPC;
       A xa[KP], xb[KP], ya[NQ], yb[NQ];
+      {
+        float va[KP * E], vb[KP * E], wa[NQ * E], wb[NQ * E];
+        lds_n<KP * E>(tile + po + ra * pw, va);
+        lds_n<KP * E>(tile + po + rb * pw, vb);
+        lds_n<NQ * E>(tile + qo + ra * qs.bw, wa);
+        lds_n<NQ * E>(tile + qo + rb * qs.bw, wb);
 #pragma unroll
-      for (int k = 0; k < KP; ++k) {
-        xa[k] = lds<P>(tile + co[k] + ra * cw[k]);
-        xb[k] = lds<P>(tile + co[k] + rb * cw[k]);
-      }
+        for (int k = 0; k < KP; ++k) {
+          xa[k] = elem<P>(va, k);
+          xb[k] = elem<P>(vb, k);
+        }
 #pragma unroll
-      for (int j = 0; j < NQ; ++j) {
-        ya[j] = lds<P>(tile + qo + ra * qs.bw + j * E);
-        yb[j] = lds<P>(tile + qo + rb * qs.bw + j * E);
+        for (int j = 0; j < NQ; ++j) {
+          ya[j] = elem<P>(wa, j);
+          yb[j] = elem<P>(wb, j);
+        }
       }
       if constexpr (kAnchored) {
 #pragma unroll
@@ -308,7 +345,7 @@ __global__ void __launch_bounds__(kT, 2)
       __threadfence_block();
       if (atomicAdd(&arrived[stage], 1) == NW - 1) {
         arrived[stage] = 0;
-        const long long nx = ch + (long long)kStages * gridDim.x;
+        const long long nx = ch + (long long)NS * gridDim.x;
         if (nx < nchunks) {
           __threadfence_block();
           fence_proxy_async();
@@ -323,9 +360,9 @@ __global__ void __launch_bounds__(kT, 2)
     // copies still in flight land in this CTA's shared memory: wait for them
     // (bounded) before leaving, then report NaN partial sums
     if (threadIdx.x == 0)
-      for (int j = 0; j < kStages; ++j) {
+      for (int j = 0; j < NS; ++j) {
         const long long ch = blockIdx.x + (long long)(it + j) * gridDim.x;
-        if (ch < nchunks) mbar_wait(&full[(it + j) % kStages], (unsigned)(((it + j) / kStages) & 1));
+        if (ch < nchunks) mbar_wait(&full[(it + j) % NS], (unsigned)(((it + j) / NS) & 1));
       }
     __syncthreads();
     for (int e = threadIdx.x; e < pq; e += kT) partial[(long long)blockIdx.x * pq + e] = df{__int_as_float(0x7fc00000), 0.f};
@@ -345,8 +382,12 @@ __global__ void __launch_bounds__(kT, 2)
 #pragma unroll
       for (int off = 16; off >= TPR; off >>= 1)
         g = df_add(g, df{__shfl_down_sync(0xffffffffu, g.hi, off), __shfl_down_sync(0xffffffffu, g.lo, off)});
-      const int c = part + TPR * k;
-      if (lane < TPR && c < p && j < q) red[(warp * p + c) * q + j] = g;
+      // the lane column's place in P and Q (prefix and padding columns are dropped)
+      const TmaSeg& sg = plan.seg[sgl];
+      const int e = pc0 + k - sg.pstart - sg.xe;
+      const int c = sg.c0 + e;
+      const int jq = j - qs.xe;
+      if (lane < TPR && e >= 0 && e < sg.nc && jq >= 0 && jq < q) red[(warp * p + c) * q + jq] = g;
     }
   __syncthreads();
   for (int e = threadIdx.x; e < pq; e += kT) {
@@ -389,9 +430,9 @@ cudaError_t run(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long lo
 
 template <class P, int TPR, int KP = 4>
 cudaError_t run_q4(const CUtensorMap (&maps)[kMaxSeg], const TmaPlan& plan, long long r0, long long r1, int p, int q,
-                   void* partial, int max_blocks, int* nb, cudaStream_t st) {
-  if (q <= 1) return run<P, TPR, KP, 1>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-  if (q <= 2) return run<P, TPR, KP, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+                   int nq, void* partial, int max_blocks, int* nb, cudaStream_t st) {
+  if (nq <= 1) return run<P, TPR, KP, 1>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (nq <= 2) return run<P, TPR, KP, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
   return run<P, TPR, KP, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
 }
 
@@ -400,71 +441,105 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
                        int max_blocks, int* nb, cudaStream_t st) {
   constexpr int E = P::id == kF32 ? 1 : 2;
   const int q = Q.nc;
-  // lanes per row (tpr) and P columns per lane (kp) so that a lane owns at
-  // most 16 pairs: 4 columns for q <= 4 (3 for 32 < p <= 48, where 16 x 4
-  // columns would leave a quarter or more of the lanes' products on padding),
-  // 2 for q <= 8
-  int kp = q <= 4 ? 4 : 2;
-  int tpr = 2;
-  while (tpr * kp < p) tpr *= 2;
-  if (kp == 4 && p > 32 && p <= 48) {
-    tpr = 16;
-    kp = 3;
+  // elements between each block's 16-byte copy boundary and its first column
+  int xe[kMaxSeg];
+  for (int s = 0; s <= nseg; ++s) {
+    const SegV& g = s < nseg ? segs[s] : Q;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(g.p);
+    if (a % (4 * E) != 0 || (g.ld * (long long)(4 * E)) % 16 != 0) return cudaErrorNotSupported;
+    xe[s] = (int)((a & uintptr_t(15)) / (4 * E));
   }
-  const int nq = q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : 8;  // Q columns of the kernel instance
+  // Q lane columns (prefix and q columns) and P columns per lane: a lane owns
+  // at most 16 pairs, 4 P columns for up to 4 Q lane columns, else 2
+  const int nql = xe[nseg] + q;
+  if (nql > 8) return cudaErrorNotSupported;
+  const int nq = nql <= 1 ? 1 : nql <= 2 ? 2 : nql <= 4 ? 4 : 8;
+  auto lane_cols = [&](int kp) {
+    int pp = 0;
+    for (int s = 0; s < nseg; ++s) pp += (xe[s] + segs[s].nc + kp - 1) / kp * kp;
+    return pp;
+  };
+  int kp = nq <= 4 ? 4 : 2;
+  int tpr = 2;
+  while (tpr * kp < lane_cols(kp)) tpr *= 2;
+  // 3 columns per lane where 16 lanes of 3 cover what 16 of 4 would leave a
+  // quarter or more idle (32 < p <= 48)
+  if (kp == 4 && tpr == 16 && lane_cols(3) <= 48 && lane_cols(4) <= 48) kp = 3;
+  if (tpr > 32) return cudaErrorNotSupported;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  // bank padding: the 32 / tpr rows a warp reads at once start on distinct banks
-  const int rho = E == 1 ? std::max(tpr, 4) % 32 : (2 * tpr) % 32;
-  // rows per stage: four passes of the consumers (two when the ring would
-  // keep two CTAs from sharing an SM)
+  // bank padding: the rows that one shared-memory wavefront reads start on
+  // distinct banks (tpr kp E floats per row of lanes)
+  const int rho = kp == 3 ? 0 : (tpr * kp * E) % 32;
+  // tile rows of every block: lane columns, their first lane column and the
+  // box width (the last P segment also covers the lane columns past it, Q its
+  // nq lane columns)
+  int ncpv[kMaxSeg], pstv[kMaxSeg], bwv[kMaxSeg];
+  for (int s = 0, pstart = 0; s <= nseg; ++s) {
+    const int nc = s < nseg ? segs[s].nc : q;
+    ncpv[s] = s < nseg ? (xe[s] + nc + kp - 1) / kp * kp : nq;
+    pstv[s] = pstart;
+    const int cover = s == nseg - 1 ? tpr * kp - pstart : ncpv[s];
+    bwv[s] = padded_width(cover * E, s < nseg ? rho : std::max(4, nq * E) % 32);
+    if (bwv[s] > 256) return cudaErrorNotSupported;
+    if (s < nseg) pstart += ncpv[s];
+  }
+  // (rows per stage, stages): the first candidate whose ring lets two CTAs
+  // share an SM, else the first that fits at all; more rows per stage spread
+  // the stage hand-over over more rows, more stages keep more tiles in flight
   const int rpc = kT / tpr;
-  TmaPlan plan{};
-  CUtensorMap maps[kMaxSeg];
-  for (int R : {std::min(4 * rpc, 256), 2 * rpc}) {
-    plan = TmaPlan{};
-    plan.nP = nseg;
-    plan.R = R;
-    std::memset(maps, 0, sizeof(maps));
+  const int cands[4][2] = {{std::min(8 * rpc, 256), 3}, {std::min(4 * rpc, 256), 4}, {2 * rpc, 4}, {2 * rpc, 3}};
+  auto smem_of = [&](int R, int stages) {
     int soff = 0;
-    for (int s = 0; s <= nseg; ++s) {
-      const SegV& g = s < nseg ? segs[s] : Q;
-      const uintptr_t a = reinterpret_cast<uintptr_t>(g.p);
-      const uintptr_t base = a & ~uintptr_t(15);
-      const long long stride = g.ld * (long long)(4 * E);
-      if (stride % 16 != 0 || a % (4 * E) != 0) return cudaErrorNotSupported;
-      const int xoff = (int)((a - base) / 4);
-      const int need = xoff + g.nc * E;
-      // the tile also covers the columns that lanes read past the data (zeros):
-      // up to TPR KP columns of P in the last segment, NQ columns of Q
-      const int cover = s < nseg ? (s == nseg - 1 ? g.nc + (tpr * kp - p) : g.nc) : nq;
-      const int bw = padded_width(xoff + cover * E, rho);
-      if (bw > 256 || need * 4LL > stride) return cudaErrorNotSupported;
-      const cuuint64_t dims[2] = {(cuuint64_t)need, (cuuint64_t)r1};
-      const cuuint64_t strides[1] = {(cuuint64_t)stride};
-      const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)R};
-      const cuuint32_t estr[2] = {1, 1};
-      const CUresult cr = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, reinterpret_cast<void*>(base), dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (cr != CUDA_SUCCESS) return cudaErrorNotSupported;
-      plan.seg[s] = TmaSeg{soff, bw, xoff, g.nc};
-      soff += (bw * R + 31) & ~31;
-    }
-    plan.stage_floats = soff;
-    const int ring = kStages * soff;
+    for (int s = 0; s <= nseg; ++s) soff += (bwv[s] * R + 31) & ~31;
     const int red = (kT / 32) * p * q * (int)(sizeof(df) / 4);
-    plan.bar_off = (std::max(ring, red) + 31) & ~31;
-    if ((size_t)plan.bar_off * 4 + kBarBytes <= (size_t)kRingTwoCtas) break;
+    return (size_t)((std::max(stages * soff, red) + 31) & ~31) * 4 + kBarBytes;
+  };
+  int pick = -1;
+  for (int pass = 0; pass < 2 && pick < 0; ++pass)
+    for (int ci = 0; ci < 4 && pick < 0; ++ci)
+      if (smem_of(cands[ci][0], cands[ci][1]) <= (size_t)(pass == 0 ? kRingTwoCtas : kMaxSmem)) pick = ci;
+  if (pick < 0) return cudaErrorNotSupported;
+  const int R = cands[pick][0];
+  TmaPlan plan{};
+  plan.nP = nseg;
+  plan.R = R;
+  plan.stages = cands[pick][1];
+  CUtensorMap maps[kMaxSeg];
+  std::memset(maps, 0, sizeof(maps));
+  int soff = 0, c0 = 0;
+  for (int s = 0; s <= nseg; ++s) {
+    const SegV& g = s < nseg ? segs[s] : Q;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(g.p) & ~uintptr_t(15);
+    const long long stride = g.ld * (long long)(4 * E);
+    const int need = (xe[s] + g.nc) * E;  // floats of data from the copy boundary
+    if (need * 4LL > stride) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)need, (cuuint64_t)r1};
+    const cuuint64_t strides[1] = {(cuuint64_t)stride};
+    const cuuint32_t box[2] = {(cuuint32_t)bwv[s], (cuuint32_t)R};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult cr = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, reinterpret_cast<void*>(base), dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorNotSupported;
+    plan.seg[s] = TmaSeg{soff, bwv[s], pstv[s], ncpv[s], xe[s], g.nc, c0};
+    soff += (bwv[s] * R + 31) & ~31;
+    if (s < nseg) c0 += g.nc;
+  }
+  plan.stage_floats = soff;
+  {
+    const int red = (kT / 32) * p * q * (int)(sizeof(df) / 4);
+    plan.bar_off = (std::max(plan.stages * soff, red) + 31) & ~31;
   }
   if ((size_t)plan.bar_off * 4 + kBarBytes > (size_t)kMaxSmem) return cudaErrorNotSupported;
   for (int s = nseg + 1; s < kMaxSeg; ++s) maps[s] = maps[nseg];  // unused slots: any valid map
-  if (kp == 3) return run_q4<P, 16, 3>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+  if (kp == 3) return run_q4<P, 16, 3>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
   if (kp == 4) {
-    if (tpr == 2) return run_q4<P, 2>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-    if (tpr == 4) return run_q4<P, 4>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-    if (tpr == 8) return run_q4<P, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
-    return run_q4<P, 16>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
+    if (tpr == 2) return run_q4<P, 2>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
+    if (tpr == 4) return run_q4<P, 4>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
+    if (tpr == 8) return run_q4<P, 8>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
+    if (tpr == 16) return run_q4<P, 16>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
+    return run_q4<P, 32>(maps, plan, r0, r1, p, q, nq, partial, max_blocks, nb, st);
   }
   if (tpr == 2) return run<P, 2, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);
   if (tpr == 4) return run<P, 4, 2, 8>(maps, plan, r0, r1, p, q, partial, max_blocks, nb, st);

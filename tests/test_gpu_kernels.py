@@ -118,19 +118,22 @@ def _ld(p, aligned):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("p,q,r0,r1", [(35, 4, 0, 100003), (9, 1, 17, 5000), (3, 8, 0, 1), (40, 13, 5, 77777),
-                                       (256, 2, 0, 3000), (7, 3, 64, 64)])
-def test_gram_matches_fp64(prec, aligned, p, q, r0, r1):
+                                       (256, 2, 0, 3000), (7, 3, 64, 64), (32, 4, 0, 70001), (64, 7, 3, 50000)])
+@pytest.mark.parametrize("pshift,qshift", [(0, 0), (0, 1), (1, 1)])
+def test_gram_matches_fp64(prec, aligned, p, q, r0, r1, pshift, qshift):
     L = max(r1, 10)
-    P = wl.dense_block(L, p, seed=1)
-    Q = wl.dense_block(L, q + 1, seed=2)
-    ldp, ldq = _ld(p, aligned), _ld(q + 1, aligned)
+    P = wl.dense_block(L, p + pshift, seed=1)
+    Q = wl.dense_block(L, q + qshift, seed=2)
+    ldp, ldq = _ld(p + pshift, aligned), _ld(q + qshift, aligned)
     Pd, Qd = to_device(prec, P, ld=ldp), to_device(prec, Q, ld=ldq)
-    Ps, Qs = to_host(prec, Pd, L, ldp)[:, :p], to_host(prec, Qd, L, ldq)[:, 1:q + 1]
+    Ps = to_host(prec, Pd, L, ldp)[:, pshift:p + pshift]
+    Qs = to_host(prec, Qd, L, ldq)[:, qshift:q + qshift]
     G = torch.zeros(p * q, dtype=torch.float64, device="cuda:0")
     scratch = torch.zeros(B.gram_scratch_bytes(p, q), dtype=torch.uint8, device="cuda:0")
     esz = 1 if prec == B.PREC_F32 or prec == B.PREC_F64 else 2
-    # Q starts at column 1: a window that is not 16-byte aligned inside its row
-    B.gram(prec, r0, r1, Pd, ldp, p, Qd[esz:], ldq, q, G, scratch)
+    # P and Q start at columns pshift and qshift: 1 is a window that is not
+    # 16-byte aligned inside its rows
+    B.gram(prec, r0, r1, Pd[pshift * esz:], ldp, p, Qd[qshift * esz:], ldq, q, G, scratch)
     Gh = G.cpu().numpy().reshape(p, q)
     ref = Ps[r0:r1].T @ Qs[r0:r1]
     norm = np.abs(Ps[r0:r1]).T @ np.abs(Qs[r0:r1])
