@@ -479,6 +479,310 @@ cudaError_t combine_tma_t(long long L, const SegV* segs, int nseg, const void* c
   return cudaErrorNotSupported;
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed Ritz vectors and residuals (Sec. 3.3 residual kernel):
+// X = V Y, R = W Y - X diag(theta), T = diag(dscale) R (optional), and per-CTA
+// FP64-class partial sums of ||R_j||^2.  V and W row tiles share one ring
+// stage; a row belongs to NP threads (one per group of QH output columns: one
+// thread per row for F32, one per column for double-float, whose Dot2 work
+// per row is 12 times larger and wants more warps in flight).
+// ---------------------------------------------------------------------------
+constexpr int kTR = 128;  // threads per CTA of the Ritz kernel
+
+struct RitzPlan {
+  int bw;            // floats per tile row of V and of W
+  int ncp;           // columns read per row (g rounded up to a 16-byte multiple)
+  int stage_floats;  // V tile then W tile, each a multiple of 32 floats
+  int stages;
+  int coef_off, red_off, bar_off;  // float offsets of Y and theta, the norm reduction, the barriers
+};
+
+template <class P, int QH, int NP>
+__global__ void __launch_bounds__(kTR)
+    k_ritz_tma(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mw, const RitzPlan plan,
+               long long L, int g, int nb, const typename P::C* __restrict__ Y, const typename P::C* __restrict__ theta,
+               typename P::S* X, typename P::S* Rr, long long ldb, const typename P::S* __restrict__ dscale,
+               typename P::S* T, int vst, df* __restrict__ partial) {
+  using C = typename P::C;
+  using A = typename P::A;
+  constexpr bool kDF = P::id != kF32;
+  constexpr int E = kDF ? 2 : 1;
+  constexpr int W = 4 / E;           // elements per 16-byte piece
+  constexpr int R = kTR / NP;        // rows per stage
+  constexpr int NBT = QH * NP;       // output columns of the table (nb padded)
+  constexpr int NW = kTR / 32;
+  static_assert(R % 32 == 0, "a warp's threads share one output part");
+  extern __shared__ __align__(128) float smem[];
+  C* ys = reinterpret_cast<C*>(smem + plan.coef_off);  // g padded rows x NBT, then theta (NBT)
+  C* th = ys + plan.ncp * NBT;
+  df* red = reinterpret_cast<df*>(smem + plan.red_off);  // NW x QH
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + plan.bar_off);
+  int* arrived = reinterpret_cast<int*>(full + kMaxStages);
+  int* fail = arrived + kMaxStages;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int prow = threadIdx.x % R;
+  const int part = threadIdx.x / R;  // output columns part QH .. part QH + QH - 1 (warp-uniform)
+  const int j0 = part * QH;
+  const int NS = plan.stages;
+  const long long nchunks = (L + R - 1) / R;
+  const unsigned tx_bytes = (unsigned)(2 * plan.bw * R * 4);
+  auto issue = [&](long long ch, int st) {
+    float* base = smem + (size_t)st * plan.stage_floats;
+    mbar_expect_tx(&full[st], tx_bytes);
+    const int y = (int)(ch * R);
+    load_2d(base, &mv, 0, y, &full[st]);
+    load_2d(base + plan.stage_floats / 2, &mw, 0, y, &full[st]);
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NS; ++st) {
+      mbar_init(&full[st], 1);
+      arrived[st] = 0;
+    }
+    *fail = 0;
+    fence_mbar_init();
+    for (int st = 0; st < NS; ++st) {
+      const long long ch = blockIdx.x + (long long)st * gridDim.x;
+      if (ch < nchunks) issue(ch, st);
+    }
+  }
+  for (int e = threadIdx.x; e < plan.ncp * NBT; e += kTR) {
+    const int c = e / NBT, j = e % NBT;
+    ys[e] = (c < g && j < nb) ? Y[(long long)c * nb + j] : C{};
+  }
+  for (int j = threadIdx.x; j < NBT; j += kTR) th[j] = j < nb ? theta[j] : C{};
+  __syncthreads();
+  A thv[QH];
+#pragma unroll
+  for (int jj = 0; jj < QH; ++jj) thv[jj] = th[j0 + jj];
+  df nrm[QH];
+#pragma unroll
+  for (int jj = 0; jj < QH; ++jj) nrm[jj] = df{0.f, 0.f};
+
+  int it = 0;
+  for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
+    const int stage = it % NS;
+    const bool ok = __all_sync(0xffffffffu, !*reinterpret_cast<volatile int*>(fail) &&
+                                                mbar_wait(&full[stage], (unsigned)((it / NS) & 1)));
+    if (!ok) {
+      if (lane == 0) atomicOr(fail, 1);
+      break;
+    }
+    const long long r = ch * R + prow;
+    A dr{};
+    if (T && r < L) dr = P::load(dscale + r);
+    const float* tile = smem + (size_t)stage * plan.stage_floats;
+    const float4* vrow = reinterpret_cast<const float4*>(tile + prow * plan.bw);
+    const float4* wrow = reinterpret_cast<const float4*>(tile + plan.stage_floats / 2 + prow * plan.bw);
+    float xh[QH], xl[QH], zh[QH], zl[QH];  // X = V Y and Z = W Y (low words: double-float only)
+#pragma unroll
+    for (int jj = 0; jj < QH; ++jj) xh[jj] = xl[jj] = zh[jj] = zl[jj] = 0.f;
+    for (int c = 0; c < plan.ncp; c += W) {
+      const float4 a = vrow[c / W], b = wrow[c / W];
+      if constexpr (kDF) {
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          const df xv = w == 0 ? df{a.x, a.y} : df{a.z, a.w};
+          const df wv = w == 0 ? df{b.x, b.y} : df{b.z, b.w};
+          const C* yr = ys + (c + w) * NBT + j0;
+#pragma unroll
+          for (int jj = 0; jj < QH; ++jj) {
+            const df y = yr[jj];
+            dot2_step(xh[jj], xl[jj], xv, y);
+            dot2_step(zh[jj], zl[jj], wv, y);
+          }
+        }
+      } else {
+        const float xv[4] = {a.x, a.y, a.z, a.w}, wv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float* yr = reinterpret_cast<const float*>(ys) + (c + w) * NBT + j0;
+          float y[QH];
+          if constexpr (QH % 4 == 0) {
+#pragma unroll
+            for (int v = 0; v < QH / 4; ++v) {
+              const float4 t = reinterpret_cast<const float4*>(yr)[v];
+              y[4 * v] = t.x;
+              y[4 * v + 1] = t.y;
+              y[4 * v + 2] = t.z;
+              y[4 * v + 3] = t.w;
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < QH; ++jj) y[jj] = yr[jj];
+          }
+#pragma unroll
+          for (int jj = 0; jj < QH; ++jj) {
+            xh[jj] = __fmaf_rn(xv[w], y[jj], xh[jj]);
+            zh[jj] = __fmaf_rn(wv[w], y[jj], zh[jj]);
+          }
+        }
+      }
+    }
+    // this warp is done with the stage; the last warp to finish refills it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&arrived[stage], 1) == NW - 1) {
+        arrived[stage] = 0;
+        const long long nx = ch + (long long)NS * gridDim.x;
+        if (nx < nchunks) {
+          __threadfence_block();
+          fence_proxy_async();
+          issue(nx, stage);
+        }
+      }
+    }
+    if (r < L) {
+      A xo[QH], ro[QH];
+#pragma unroll
+      for (int jj = 0; jj < QH; ++jj) {
+        if constexpr (kDF) {
+          const df xd = two_sum(xh[jj], xl[jj]);
+          const df zd = two_sum(zh[jj], zl[jj]);
+          xo[jj] = xd;
+          ro[jj] = df_add(zd, df_neg(df_mul(xd, thv[jj])));
+        } else {
+          xo[jj] = xh[jj];
+          ro[jj] = P::sub(zh[jj], P::mulc(xh[jj], thv[jj]));
+        }
+        if (j0 + jj < nb) nrm[jj] = P::gfma(nrm[jj], ro[jj], ro[jj]);
+      }
+      // stores: 16-byte pieces of this thread's columns where they all lie
+      // inside nb and the rows allow them, else element by element
+      typename P::S* xd = X + r * ldb + j0;
+      typename P::S* rd = Rr + r * ldb + j0;
+      typename P::S* td = T ? T + r * ldb + j0 : nullptr;
+      if (vst && j0 + QH <= nb && (QH * E) % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < QH * E / 4; ++v) {
+          float4 fx, fr, ft;
+          if constexpr (kDF) {
+            fx = make_float4(xo[2 * v].hi, xo[2 * v].lo, xo[2 * v + 1].hi, xo[2 * v + 1].lo);
+            fr = make_float4(ro[2 * v].hi, ro[2 * v].lo, ro[2 * v + 1].hi, ro[2 * v + 1].lo);
+          } else {
+            fx = make_float4(xo[4 * v], xo[4 * v + 1], xo[4 * v + 2], xo[4 * v + 3]);
+            fr = make_float4(ro[4 * v], ro[4 * v + 1], ro[4 * v + 2], ro[4 * v + 3]);
+          }
+          reinterpret_cast<float4*>(xd)[v] = fx;
+          reinterpret_cast<float4*>(rd)[v] = fr;
+          if (td) {
+            if constexpr (kDF) {
+              const df t0 = df_mul(dr, ro[2 * v]), t1 = df_mul(dr, ro[2 * v + 1]);
+              ft = make_float4(t0.hi, t0.lo, t1.hi, t1.lo);
+            } else {
+              ft = make_float4(dr * ro[4 * v], dr * ro[4 * v + 1], dr * ro[4 * v + 2], dr * ro[4 * v + 3]);
+            }
+            reinterpret_cast<float4*>(td)[v] = ft;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < QH; ++jj)
+          if (j0 + jj < nb) {
+            P::store(xd + jj, xo[jj]);
+            P::store(rd + jj, ro[jj]);
+            if (td) {
+              if constexpr (kDF)
+                P::store(td + jj, df_mul(dr, ro[jj]));
+              else
+                P::store(td + jj, dr * ro[jj]);
+            }
+          }
+      }
+    }
+  }
+  __syncthreads();
+  if (*fail) {
+    if (threadIdx.x == 0)
+      for (int j = 0; j < NS; ++j) {
+        const long long ch = blockIdx.x + (long long)(it + j) * gridDim.x;
+        if (ch < nchunks) mbar_wait(&full[(it + j) % NS], (unsigned)(((it + j) / NS) & 1));
+      }
+    if ((int)threadIdx.x < nb) partial[(long long)blockIdx.x * nb + threadIdx.x] = df{__int_as_float(0x7fc00000), 0.f};
+    return;
+  }
+  // norms: the warp's rows, then the warps of each part in order
+#pragma unroll
+  for (int jj = 0; jj < QH; ++jj) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+      nrm[jj] = df_add(nrm[jj], df{__shfl_down_sync(0xffffffffu, nrm[jj].hi, o),
+                                   __shfl_down_sync(0xffffffffu, nrm[jj].lo, o)});
+    if (lane == 0) red[warp * QH + jj] = nrm[jj];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nb) {
+    const int j = threadIdx.x, pj = j / QH, jj = j % QH;
+    constexpr int WPP = R / 32;  // warps per part
+    df v = red[(pj * WPP) * QH + jj];
+    for (int w = 1; w < WPP; ++w) v = df_add(v, red[(pj * WPP + w) * QH + jj]);
+    partial[(long long)blockIdx.x * nb + j] = v;
+  }
+}
+
+template <class P, int QH, int NP>
+cudaError_t ritz_run(long long L, const SegV& V, const SegV& Wm, int g, const void* Y, const void* theta, void* X,
+                     void* Rr, long long ldb, int nb, const void* dscale, void* T, void* partial, int max_blocks,
+                     int* nblocks, cudaStream_t st) {
+  using S = typename P::S;
+  using C = typename P::C;
+  constexpr int E = P::id == kF32 ? 1 : 2;
+  constexpr int W = 4 / E;
+  constexpr int SZ = 4 * E;
+  constexpr int R = kTR / NP;
+  constexpr int NBT = QH * NP;
+  for (const SegV* s : {&V, &Wm})
+    if (reinterpret_cast<uintptr_t>(s->p) % 16 != 0 || (s->ld * SZ) % 16 != 0 || s->ld < g)
+      return cudaErrorNotSupported;
+  RitzPlan plan{};
+  plan.ncp = (g + W - 1) / W * W;
+  plan.bw = odd_width(plan.ncp * E);
+  if (plan.bw > 256) return cudaErrorNotSupported;
+  CUtensorMap mv, mw;
+  if (!encode_rows(&mv, V.p, (long long)g * E, L, V.ld * SZ, plan.bw, R) ||
+      !encode_rows(&mw, Wm.p, (long long)g * E, L, Wm.ld * SZ, plan.bw, R))
+    return cudaErrorNotSupported;
+  plan.stage_floats = 2 * ((plan.bw * R + 31) & ~31);
+  auto layout = [&](int stages) {
+    plan.stages = stages;
+    plan.coef_off = stages * plan.stage_floats;
+    plan.red_off = plan.coef_off + (((plan.ncp * NBT + NBT) * (int)sizeof(C) / 4 + 31) & ~31);
+    plan.bar_off = plan.red_off + (((kTR / 32) * QH * (int)sizeof(df) / 4 + 31) & ~31);
+    return (size_t)plan.bar_off * 4 + kBarBytes;
+  };
+  // the most CTAs per SM (up to 4) whose rings hold at least 3 stages, else
+  // one CTA with the deepest ring
+  int stages = 0;
+  for (int c = 4; c >= 1 && !stages; --c)
+    for (int s = kMaxStages; s >= 3 && !stages; --s)
+      if (layout(s) <= (size_t)kMaxSmem && layout(s) * c + 1024 * c <= 228 * 1024) stages = s;
+  if (!stages)
+    for (int s = kMaxStages; s >= 2 && !stages; --s)
+      if (layout(s) <= (size_t)kMaxSmem) stages = s;
+  if (!stages) return cudaErrorNotSupported;
+  const size_t sm = layout(stages);
+  auto kern = k_ritz_tma<P, QH, NP>;
+  cudaError_t e = smem_optin(reinterpret_cast<const void*>(kern), kMaxSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTR, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long nchunks = (L + R - 1) / R;
+  long long grid = std::min<long long>((long long)std::max(per_sm, 1) * std::max(sms, 1), nchunks);
+  grid = std::max<long long>(1, std::min<long long>(grid, max_blocks));
+  *nblocks = (int)grid;
+  const auto al = [&](const void* ptr) { return !ptr || reinterpret_cast<uintptr_t>(ptr) % 16 == 0; };
+  const int vst = al(X) && al(Rr) && al(T) && (ldb * SZ) % 16 == 0 ? 1 : 0;
+  kern<<<(int)grid, kTR, sm, st>>>(mv, mw, plan, L, g, nb, reinterpret_cast<const C*>(Y),
+                                   reinterpret_cast<const C*>(theta), reinterpret_cast<S*>(X), reinterpret_cast<S*>(Rr),
+                                   ldb, reinterpret_cast<const S*>(dscale), reinterpret_cast<S*>(T), vst,
+                                   reinterpret_cast<df*>(partial));
+  return cudaGetLastError();
+}
+
 bool tma_combine_enabled() {
   static const bool on = [] {
     const char* v = std::getenv("PHSVDS_COMBINE_TMA");
@@ -488,6 +792,27 @@ bool tma_combine_enabled() {
 }
 
 }  // namespace
+
+cudaError_t launch_ritz_tma(int prec, long long L, SegV V, SegV W, int g, const void* Y, const void* theta, void* X,
+                            void* R, long long ldb, int nb, const void* dscale, void* T, void* partial,
+                            int max_blocks, int* nblocks, cudaStream_t st) {
+  if (!tma_combine_enabled()) return cudaErrorNotSupported;
+  if (g < 1 || g > 64 || nb < 1 || nb > 8 || L < 1 || L > (long long)INT_MAX - kTR || max_blocks < 1)
+    return cudaErrorNotSupported;
+  // F32: one thread per row with all nb outputs; double-float: one thread per
+  // output column
+  if (prec == kF32) {
+    if (nb <= 4) return ritz_run<PF32, 4, 1>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, partial, max_blocks,
+                                             nblocks, st);
+    return ritz_run<PF32, 8, 1>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, partial, max_blocks, nblocks, st);
+  }
+  if (prec == kDF64) {
+    if (nb <= 4) return ritz_run<PDF64, 1, 4>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, partial, max_blocks,
+                                              nblocks, st);
+    return ritz_run<PDF64, 2, 4>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, partial, max_blocks, nblocks, st);
+  }
+  return cudaErrorNotSupported;
+}
 
 cudaError_t launch_combine_tma(int prec, long long L, const SegV* P, int nseg, const void* coef, const void* In,
                                long long ldin, int alpha_one, void* Out, long long ldout, int q, const void* Rinv,

@@ -1736,6 +1736,11 @@ cudaError_t launch_ritz_residual(int prec, long long L, SegV V, SegV W, int g, c
                                  void* X, void* R, long long ldb, int nb, const void* dscale, void* T,
                                  void* norm_partial, int max_blocks, int* nblocks, cudaStream_t st) {
   if (g < 1 || nb < 1) return cudaErrorInvalidValue;
+  if (prec != kF64) {
+    const cudaError_t e = launch_ritz_tma(prec, L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial,
+                                          max_blocks, nblocks, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (g <= kRowCombP && nb <= 8 && V.ld == W.ld) {
     PHSVDS_DISPATCH(prec, ritz_row_p<P>(L, V, W, g, Y, theta, X, R, ldb, nb, dscale, T, norm_partial, max_blocks,
                                         nblocks, st))

@@ -55,6 +55,13 @@ cudaError_t launch_gram_tma(int prec, long long r0, long long r1, const SegV* P,
 cudaError_t launch_combine_tma(int prec, long long L, const SegV* P, int nseg, const void* coef, const void* In,
                                long long ldin, int alpha_one, void* Out, long long ldout, int q, const void* Rinv,
                                void* Out2, long long ldout2, cudaStream_t st);
+// TMA-fed Ritz vectors and residuals for F32/DF64, g <= 64, nb <= 8, V and W
+// 16-byte aligned with 16-byte-multiple strides: same contract as
+// launch_ritz_residual; cudaErrorNotSupported when its preconditions do not
+// hold (the caller then uses the row kernels).
+cudaError_t launch_ritz_tma(int prec, long long L, SegV V, SegV W, int g, const void* Y, const void* theta, void* X,
+                            void* R, long long ldb, int nb, const void* dscale, void* T, void* partial,
+                            int max_blocks, int* nblocks, cudaStream_t st);
 // Sum the partials in fixed order into G (p x q, row-major doubles, device).
 cudaError_t launch_gram_reduce(int prec, const void* partial, int nblocks, int pq, double* G, cudaStream_t st);
 // Bytes of partial storage that launch_gram may use.

@@ -214,7 +214,7 @@ def test_combine_row_tiles(prec, L, p, q):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("aligned", [True, False])
-@pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8), (20, 13)])
+@pytest.mark.parametrize("g,nb", [(35, 4), (6, 1), (17, 3), (44, 8), (20, 13), (32, 4), (64, 8), (1, 2), (64, 5)])
 def test_ritz_residual(prec, aligned, g, nb):
     L = 50001
     ldv = _ld(g, aligned)
