@@ -166,35 +166,43 @@ __global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 
   __syncthreads();
 
   const bool stores = part * QH < q;  // a part whose columns all lie past q stores nothing
+  // In values of row prow of chunk ch for this thread's part (zeros past L or q)
+  auto load_in = [&](long long ch, float (&dst)[OBW]) {
+#pragma unroll
+    for (int k = 0; k < OBW; ++k) dst[k] = 0.f;
+    const long long r = ch * R + prow;
+    const int nin = min(OBW, q * E - part * OBW);
+    if (ch >= nchunks || r >= L || nin <= 0) return;
+    const float* src = reinterpret_cast<const float*>(In) + r * ldin * E + part * OBW;
+    if (in_vec && nin == OBW) {
+#pragma unroll
+      for (int v = 0; v < OBW / 4; ++v) {
+        const float4 t = reinterpret_cast<const float4*>(src)[v];
+        dst[4 * v] = t.x;
+        dst[4 * v + 1] = t.y;
+        dst[4 * v + 2] = t.z;
+        dst[4 * v + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < OBW; ++k)
+        if (k < nin) dst[k] = src[k];
+    }
+  };
+  float inn[OBW];
+#pragma unroll
+  for (int k = 0; k < OBW; ++k) inn[k] = 0.f;
+  if (In) load_in(blockIdx.x, inn);
   int it = 0;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
     const int stage = it % NS;
-    // this thread's part of its In row (read from global memory before the
-    // stage wait, added after the products)
+    // this thread's part of its In row, loaded from global memory one chunk
+    // ahead (the load's latency overlaps a whole chunk) and added after the
+    // products
     float inv[OBW];
 #pragma unroll
-    for (int k = 0; k < OBW; ++k) inv[k] = 0.f;
-    if (In) {
-      const long long r = ch * R + prow;
-      const int nin = min(OBW, q * E - part * OBW);
-      if (r < L && nin > 0) {
-        const float* src = reinterpret_cast<const float*>(In) + r * ldin * E + part * OBW;
-        if (in_vec && nin == OBW) {
-#pragma unroll
-          for (int v = 0; v < OBW / 4; ++v) {
-            const float4 t = reinterpret_cast<const float4*>(src)[v];
-            inv[4 * v] = t.x;
-            inv[4 * v + 1] = t.y;
-            inv[4 * v + 2] = t.z;
-            inv[4 * v + 3] = t.w;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < OBW; ++k)
-            if (k < nin) inv[k] = src[k];
-        }
-      }
-    }
+    for (int k = 0; k < OBW; ++k) inv[k] = inn[k];
+    if (In) load_in(ch + gridDim.x, inn);
     // warp-uniform decision: every lane of a warp leaves the loop together
     const bool ok = __all_sync(0xffffffffu, !*reinterpret_cast<volatile int*>(fail) && mbar_wait(&full[stage], (unsigned)((it / NS) & 1)));
     if (!ok) {

@@ -221,7 +221,10 @@ __global__ void __launch_bounds__(kT, 2)
   const int po = plan.seg[sgl].soff + (pc0 - plan.seg[sgl].pstart) * E;  // tile-row offset of the lane's columns
   const int pw = plan.seg[sgl].bw;
   const TmaSeg qs = plan.seg[plan.nP];
-  const int qo = qs.soff;  // Q lane columns 0 .. NQ - 1 = the Q tile row from its start
+  // Q columns 0 .. NQ - 1 from the first column of Q (xe elements into its
+  // tile rows): 16/8-byte loads when that is a word boundary, else scalar
+  const int qo = qs.soff + qs.xe * E;
+  const bool qvec = qs.xe == 0;
 
   float sa[KP][NQ], ca[KP][NQ];
   // anchors a_k, b_j (powers of two), the running sums of squares and the
@@ -267,8 +270,16 @@ __global__ void __launch_bounds__(kT, 2)
         float va[KP * E], vb[KP * E], wa[NQ * E], wb[NQ * E];
         lds_n<KP * E>(tile + po + ra * pw, va);
         lds_n<KP * E>(tile + po + rb * pw, vb);
-        lds_n<NQ * E>(tile + qo + ra * qs.bw, wa);
-        lds_n<NQ * E>(tile + qo + rb * qs.bw, wb);
+        if (qvec) {
+          lds_n<NQ * E>(tile + qo + ra * qs.bw, wa);
+          lds_n<NQ * E>(tile + qo + rb * qs.bw, wb);
+        } else {
+#pragma unroll
+          for (int i = 0; i < NQ * E; ++i) {
+            wa[i] = tile[qo + ra * qs.bw + i];
+            wb[i] = tile[qo + rb * qs.bw + i];
+          }
+        }
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
           xa[k] = elem<P>(va, k);
@@ -386,8 +397,7 @@ __global__ void __launch_bounds__(kT, 2)
       const TmaSeg& sg = plan.seg[sgl];
       const int e = pc0 + k - sg.pstart - sg.xe;
       const int c = sg.c0 + e;
-      const int jq = j - qs.xe;
-      if (lane < TPR && e >= 0 && e < sg.nc && jq >= 0 && jq < q) red[(warp * p + c) * q + jq] = g;
+      if (lane < TPR && e >= 0 && e < sg.nc && j < q) red[(warp * p + c) * q + j] = g;
     }
   __syncthreads();
   for (int e = threadIdx.x; e < pq; e += kT) {
@@ -449,11 +459,9 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
     if (a % (4 * E) != 0 || (g.ld * (long long)(4 * E)) % 16 != 0) return cudaErrorNotSupported;
     xe[s] = (int)((a & uintptr_t(15)) / (4 * E));
   }
-  // Q lane columns (prefix and q columns) and P columns per lane: a lane owns
-  // at most 16 pairs, 4 P columns for up to 4 Q lane columns, else 2
-  const int nql = xe[nseg] + q;
-  if (nql > 8) return cudaErrorNotSupported;
-  const int nq = nql <= 1 ? 1 : nql <= 2 ? 2 : nql <= 4 ? 4 : 8;
+  // Q columns of the kernel instance and P columns per lane: a lane owns at
+  // most 16 pairs, 4 P columns for up to 4 Q columns, else 2
+  const int nq = q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : 8;
   auto lane_cols = [&](int kp) {
     int pp = 0;
     for (int s = 0; s < nseg; ++s) pp += (xe[s] + segs[s].nc + kp - 1) / kp * kp;
@@ -473,13 +481,13 @@ cudaError_t gram_tma_p(const SegV* segs, int nseg, SegV Q, long long r0, long lo
   const int rho = kp == 3 ? 0 : (tpr * kp * E) % 32;
   // tile rows of every block: lane columns, their first lane column and the
   // box width (the last P segment also covers the lane columns past it, Q its
-  // nq lane columns)
+  // xe prefix and nq columns)
   int ncpv[kMaxSeg], pstv[kMaxSeg], bwv[kMaxSeg];
   for (int s = 0, pstart = 0; s <= nseg; ++s) {
     const int nc = s < nseg ? segs[s].nc : q;
     ncpv[s] = s < nseg ? (xe[s] + nc + kp - 1) / kp * kp : nq;
     pstv[s] = pstart;
-    const int cover = s == nseg - 1 ? tpr * kp - pstart : ncpv[s];
+    const int cover = s == nseg - 1 ? tpr * kp - pstart : s < nseg ? ncpv[s] : xe[s] + nq;
     bwv[s] = padded_width(cover * E, s < nseg ? rho : std::max(4, nq * E) % 32);
     if (bwv[s] > 256) return cudaErrorNotSupported;
     if (s < nseg) pstart += ncpv[s];
