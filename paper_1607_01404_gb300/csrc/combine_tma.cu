@@ -90,7 +90,7 @@ __device__ __forceinline__ void dot2_step(float& hi, float& lo, df x, df c) {
 }
 
 template <class P, int QT, int TPRW>
-__global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 32) ? 2 : 1)
+__global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) < 32) ? 2 : 1)
     k_combine_tma(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
                   const __grid_constant__ CUtensorMap m2, const CmbPlan plan, long long L, int q,
                   const typename P::C* __restrict__ coef, const typename P::C* __restrict__ Rinv,
@@ -122,14 +122,29 @@ __global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 
   float* obuf = smem + plan.obuf_off + warp * 32 * OBS;
   const int NS = plan.stages;
   const long long nchunks = (L + R - 1) / R;
+  // the segments' fields in registers (constant indices: a run-time index
+  // into the parameter block would copy it to the stack)
+  int s_soff[3], s_bw[3], s_ncp[3], s_pst[3], s_nc[3], s_c0[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s_soff[i] = plan.seg[i].soff;
+    s_bw[i] = plan.seg[i].bw;
+    s_ncp[i] = plan.seg[i].ncp;
+    s_pst[i] = plan.seg[i].pstart;
+    s_nc[i] = plan.seg[i].nc;
+    s_c0[i] = plan.seg[i].c0;
+  }
   unsigned tx_bytes = 0;
-  for (int sg = 0; sg < plan.nP; ++sg) tx_bytes += (unsigned)(plan.seg[sg].bw * R * 4);
+#pragma unroll
+  for (int sg = 0; sg < 3; ++sg)
+    if (sg < plan.nP) tx_bytes += (unsigned)(s_bw[sg] * R * 4);
   auto issue = [&](long long ch, int st) {
-    const CUtensorMap* maps[3] = {&m0, &m1, &m2};
     float* base = smem + (size_t)st * plan.stage_floats;
     mbar_expect_tx(&full[st], tx_bytes);
     const int y = (int)(ch * R);
-    for (int sg = 0; sg < plan.nP; ++sg) load_2d(base + plan.seg[sg].soff, maps[sg], 0, y, &full[st]);
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg)
+      if (sg < plan.nP) load_2d(base + s_soff[sg], sg == 0 ? &m0 : sg == 1 ? &m1 : &m2, 0, y, &full[st]);
   };
 
   if (threadIdx.x == 0) {
@@ -150,10 +165,12 @@ __global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 
     C* ct = reinterpret_cast<C*>(cs);
     for (int e = threadIdx.x; e < plan.ppad * QT; e += kT) {
       const int r = e / QT, j = e % QT;
-      int sg = 0;
-      while (sg < plan.nP - 1 && r >= plan.seg[sg + 1].pstart) ++sg;
-      const int c = r - plan.seg[sg].pstart;
-      ct[e] = (c < plan.seg[sg].nc && j < q) ? coef[(long long)(plan.seg[sg].c0 + c) * q + j] : C{};
+      const int sg = (plan.nP > 1 && r >= s_pst[1]) ? ((plan.nP > 2 && r >= s_pst[2]) ? 2 : 1) : 0;
+      const int pst = sg == 0 ? s_pst[0] : sg == 1 ? s_pst[1] : s_pst[2];
+      const int nc = sg == 0 ? s_nc[0] : sg == 1 ? s_nc[1] : s_nc[2];
+      const int cz = sg == 0 ? s_c0[0] : sg == 1 ? s_c0[1] : s_c0[2];
+      const int c = r - pst;
+      ct[e] = (c < nc && j < q) ? coef[(long long)(cz + c) * q + j] : C{};
     }
     if (QT <= 8 && Rinv) {
       C* rt = reinterpret_cast<C*>(rs);
@@ -213,11 +230,12 @@ __global__ void __launch_bounds__(kT, ((QT / TPRW) * (P::id == kF32 ? 1 : 2) <= 
     float hi[QH], lo[QH];
 #pragma unroll
     for (int j = 0; j < QH; ++j) hi[j] = lo[j] = 0.f;
-    for (int sg = 0; sg < plan.nP; ++sg) {
-      const CmbSeg g = plan.seg[sg];
-      const float4* row = reinterpret_cast<const float4*>(tile + g.soff + prow * g.bw);
-      const float4* cb = reinterpret_cast<const float4*>(cs + g.pstart * QT * E) + part * CVH;
-      for (int c = 0; c < g.ncp; c += W) {
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) {
+      if (sg >= plan.nP) break;
+      const float4* row = reinterpret_cast<const float4*>(tile + s_soff[sg] + prow * s_bw[sg]);
+      const float4* cb = reinterpret_cast<const float4*>(cs + s_pst[sg] * QT * E) + part * CVH;
+      for (int c = 0; c < s_ncp[sg]; c += W) {
         const float4 xv = row[c / W];
         if constexpr (kDF) {
           const df x0{xv.x, xv.y}, x1{xv.z, xv.w};

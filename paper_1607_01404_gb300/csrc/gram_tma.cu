@@ -184,11 +184,13 @@ __global__ void __launch_bounds__(kT, 2)
   for (int sg = 0; sg < nseg; ++sg) tx_bytes += (unsigned)(plan.seg[sg].bw * R * 4);
   // copies of chunk ch into stage st (one thread)
   auto issue = [&](long long ch, int st) {
-    const CUtensorMap* maps[kMaxSeg] = {&m0, &m1, &m2, &m3};
     float* base = smem + (size_t)st * plan.stage_floats;
     mbar_expect_tx(&full[st], tx_bytes);
     const int y = (int)(r0 + ch * R);
-    for (int sg = 0; sg < nseg; ++sg) load_2d(base + plan.seg[sg].soff, maps[sg], 0, y, &full[st]);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const CUtensorMap* m = sg == 0 ? &m0 : sg == 1 ? &m1 : sg == 2 ? &m2 : &m3;
+      load_2d(base + plan.seg[sg].soff, m, 0, y, &full[st]);
+    }
   };
 
   if (threadIdx.x == 0) {
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(kT, 2)
   const int pw = plan.seg[sgl].bw;
   const TmaSeg qs = plan.seg[plan.nP];
   // Q columns 0 .. NQ - 1 from the first column of Q (xe elements into its
-  // tile rows): 16/8-byte loads when that is a word boundary, else scalar
+  // tile rows): F32 reads them with 16/8-byte loads when that is a word
+  // boundary, else one by one; double-float with 8-byte loads
   const int qo = qs.soff + qs.xe * E;
   const bool qvec = qs.xe == 0;
 
@@ -270,7 +273,17 @@ __global__ void __launch_bounds__(kT, 2)
         float va[KP * E], vb[KP * E], wa[NQ * E], wb[NQ * E];
         lds_n<KP * E>(tile + po + ra * pw, va);
         lds_n<KP * E>(tile + po + rb * pw, vb);
-        if (qvec) {
+        if constexpr (E == 2) {  // 8-byte elements: 8-byte loads at any element offset
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const float2 ta = *reinterpret_cast<const float2*>(tile + qo + ra * qs.bw + 2 * i);
+            const float2 tb = *reinterpret_cast<const float2*>(tile + qo + rb * qs.bw + 2 * i);
+            wa[2 * i] = ta.x;
+            wa[2 * i + 1] = ta.y;
+            wb[2 * i] = tb.x;
+            wb[2 * i + 1] = tb.y;
+          }
+        } else if (qvec) {
           lds_n<NQ * E>(tile + qo + ra * qs.bw, wa);
           lds_n<NQ * E>(tile + qo + rb * qs.bw, wb);
         } else {
