@@ -48,7 +48,7 @@ MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
 # this workload (--set full, one warm launch each); None where the kernel
 # changed after its capture
-TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_tma_f32_32x4": 305_532_416}
+TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_tma_f32_32x4": 305_533_440}
 UNIT = "s"
 # FP32 operations per product of the anchored FP64-class Gram accumulation in
 # the FP32 mode (fma, subtract, fma, add)
