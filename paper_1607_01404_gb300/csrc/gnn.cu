@@ -105,21 +105,28 @@ __device__ __forceinline__ float bf16r(float x) {
   return __uint_as_float(((u + 0x7fffu + ((u >> 16) & 1u)) >> 16) << 16);
 }
 
-// z = h W1 + Eh W2 + b, hout = relu(z).  A CTA takes tiles of 64 rows: h and
-// Eh of the tile are staged in shared memory with coalesced loads (rows
-// padded by one float against bank conflicts), thread t computes outputs
-// [8 (t mod 4), 8 (t mod 4) + 8) of row t / 4 with the weights from shared
-// memory, and z and hout leave as 32-byte row segments (a warp writes 8 whole
-// rows).
-constexpr int kLRows = 64;
+// z = h W1 + Eh W2 + b, hout = relu(z).  A CTA takes tiles of 128 rows: h and
+// Eh of the tile are staged in shared memory with coalesced 16-byte loads
+// (rows padded against bank conflicts).  Thread t computes outputs
+// [8 (t mod 4), 8 (t mod 4) + 8) of rows t / 4 and t / 4 + 64, so each pair of
+// 16-byte weight loads from shared memory serves two rows (the weights, not
+// the rows, were the shared-memory traffic of one row per thread); z and hout
+// leave as 32-byte row segments (a warp writes 8 whole rows at a time).  The
+// multiply-adds of an output run in column order, as in the backward pass.
+constexpr int kLRows = 128;
 template <int FIN>
 __global__ void __launch_bounds__(kT) k_layer_fwd(long long n, const float* __restrict__ h,
                                                   const float* __restrict__ Eh, const float* __restrict__ W1,
                                                   const float* __restrict__ W2, const float* __restrict__ b,
                                                   float* __restrict__ z, float* __restrict__ hout) {
-  static_assert(kT == 4 * kLRows, "four threads per row");
-  __shared__ float w1[FIN * kW], w2[FIN * kW], bb[kW];
-  __shared__ float hs[kLRows * (FIN + 1)], es[kLRows * (FIN + 1)];
+  static_assert(2 * kT == 4 * kLRows, "four threads per row, two rows per thread");
+  // staged row stride: FIN + 4 floats (rows start on 16-byte boundaries for
+  // 16-byte staging, 8 consecutive rows on distinct banks) when FIN is a
+  // multiple of 4, else FIN + 1
+  constexpr int HS = FIN % 4 == 0 ? FIN + 4 : FIN + 1;
+  __shared__ __align__(16) float w1[FIN * kW], w2[FIN * kW];
+  __shared__ float bb[kW];
+  __shared__ __align__(16) float hs[kLRows * HS], es[kLRows * HS];
   for (int e = threadIdx.x; e < FIN * kW; e += blockDim.x) {
     w1[e] = bf16r(W1[e]);
     w2[e] = bf16r(W2[e]);
@@ -129,28 +136,53 @@ __global__ void __launch_bounds__(kT) k_layer_fwd(long long n, const float* __re
   for (long long r0 = (long long)blockIdx.x * kLRows; r0 < n; r0 += (long long)gridDim.x * kLRows) {
     const int rows = (int)(n - r0 < kLRows ? n - r0 : kLRows);
     __syncthreads();  // weights staged / previous tile consumed
-    for (int e = threadIdx.x; e < rows * FIN; e += kT) {
-      const int rr = e / FIN, c = e % FIN;
-      hs[rr * (FIN + 1) + c] = h[r0 * FIN + e];
-      es[rr * (FIN + 1) + c] = Eh[r0 * FIN + e];
+    if constexpr (FIN % 4 == 0) {
+      const float4* h4 = reinterpret_cast<const float4*>(h + r0 * FIN);
+      const float4* e4 = reinterpret_cast<const float4*>(Eh + r0 * FIN);
+      for (int e = threadIdx.x; e < rows * (FIN / 4); e += kT) {
+        const int rr = e / (FIN / 4), c = 4 * (e % (FIN / 4));
+        *reinterpret_cast<float4*>(hs + rr * HS + c) = h4[e];
+        *reinterpret_cast<float4*>(es + rr * HS + c) = e4[e];
+      }
+    } else {
+      for (int e = threadIdx.x; e < rows * FIN; e += kT) {
+        const int rr = e / FIN, c = e % FIN;
+        hs[rr * HS + c] = h[r0 * FIN + e];
+        es[rr * HS + c] = Eh[r0 * FIN + e];
+      }
     }
     __syncthreads();
-    if (row < rows) {
-      float acc[8];
+    float a0[8], a1[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] = bb[j0 + j];
+    for (int j = 0; j < 8; ++j) a0[j] = a1[j] = bb[j0 + j];
+    const int rb = row + kLRows / 2;
+    const int ra_s = row < rows ? row : 0, rb_s = rb < rows ? rb : 0;  // rows past the tile read row 0
 #pragma unroll 4
-      for (int c = 0; c < FIN; ++c) {
-        const float hv = hs[row * (FIN + 1) + c], ev = es[row * (FIN + 1) + c];
+    for (int c = 0; c < FIN; ++c) {
+      const float4 u0 = *reinterpret_cast<const float4*>(w1 + c * kW + j0);
+      const float4 u1 = *reinterpret_cast<const float4*>(w1 + c * kW + j0 + 4);
+      const float4 v0 = *reinterpret_cast<const float4*>(w2 + c * kW + j0);
+      const float4 v1 = *reinterpret_cast<const float4*>(w2 + c * kW + j0 + 4);
+      const float wa[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      const float wb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+      const float ha = hs[ra_s * HS + c], ea = es[ra_s * HS + c];
+      const float hb = hs[rb_s * HS + c], eb = es[rb_s * HS + c];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = fmaf(hv, w1[c * kW + j0 + j], fmaf(ev, w2[c * kW + j0 + j], acc[j]));
+      for (int j = 0; j < 8; ++j) {
+        a0[j] = fmaf(ha, wa[j], fmaf(ea, wb[j], a0[j]));
+        a1[j] = fmaf(hb, wa[j], fmaf(eb, wb[j], a1[j]));
       }
-      float4* zo = reinterpret_cast<float4*>(z + (r0 + row) * kW + j0);
-      float4* ho = reinterpret_cast<float4*>(hout + (r0 + row) * kW + j0);
-      zo[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-      zo[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-      ho[0] = make_float4(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f), fmaxf(acc[2], 0.f), fmaxf(acc[3], 0.f));
-      ho[1] = make_float4(fmaxf(acc[4], 0.f), fmaxf(acc[5], 0.f), fmaxf(acc[6], 0.f), fmaxf(acc[7], 0.f));
+    }
+    for (int t = 0; t < 2; ++t) {
+      const int rr = t == 0 ? row : rb;
+      if (rr >= rows) continue;
+      const float* a = t == 0 ? a0 : a1;
+      float4* zo = reinterpret_cast<float4*>(z + (r0 + rr) * kW + j0);
+      float4* ho = reinterpret_cast<float4*>(hout + (r0 + rr) * kW + j0);
+      zo[0] = make_float4(a[0], a[1], a[2], a[3]);
+      zo[1] = make_float4(a[4], a[5], a[6], a[7]);
+      ho[0] = make_float4(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f), fmaxf(a[2], 0.f), fmaxf(a[3], 0.f));
+      ho[1] = make_float4(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f), fmaxf(a[6], 0.f), fmaxf(a[7], 0.f));
     }
   }
 }
