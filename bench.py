@@ -424,7 +424,7 @@ def run_gpu(args, world, rank, local):
             h.close()
         torch.cuda.synchronize()
         t_e2e_all.append(time.perf_counter() - te0)
-    t_e2e = statistics.median(t_e2e_all)
+    t_e2e = statistics.mean(t_e2e_all)  # the e2e steps' total time / steps
     h2d = A.rowptr.nbytes + A.colidx.nbytes + A.vals.nbytes
     d2h = 8 * K * (A.m + A.n + 2)
     # roofline of the dominant kernel family (CSR SpMM, FP32 phase and FP64-class)
@@ -433,7 +433,7 @@ def run_gpu(args, world, rank, local):
     # orthogonalisation kernels at the solve's sizes (basis 32 columns, block 4)
     orth = {f"{nm}_{k}": v for nm, pr in (("f32", B.PREC_F32), ("df64", B.PREC_DF64))
             for k, v in ortho_roofline(dev, torch, B, pr, A.n, 32, BLOCK).items()}
-    ms_step = statistics.median(t_chosen) * 1e3
+    ms_step = statistics.mean(t_chosen) * 1e3  # the K timed steps' total time / K
     ms_step = max_over_ranks(ms_step, world)
     c1 = config1_report(B, wl, sp)
     c3 = config3_report(B, wl, sp, dev, torch) if not args.skip_c3 else None
@@ -861,7 +861,8 @@ def main():
         dtype="f32+df64", data="synthetic",
         config=bench_config(A, args.gpus),
         max_rel_sigma_err_vs_closed_form=res["relerr"], numConverged=res["nconv"],
-        plain_fp64=dict(value=statistics.median(res["t_plain"]), unit=UNIT,
+        step_seconds=[round(t, 5) for t in res["times"]],
+        plain_fp64=dict(value=statistics.mean(res["t_plain"]), unit=UNIT,
                         form="JDQMR, double-float (FP64-class, u ~ 2^-48) inner and outer, Jacobi",
                         matvecs=mv_plain, max_rel_sigma_err=res["relerr_plain"]),
         plain_native_fp64={k: dict(value=v["seconds"], unit=UNIT, numConverged=v["nconv"],
@@ -897,7 +898,7 @@ def main():
         config3_randill_1e6x5e5=res["c3"],
         config4_wgrid2d_N256=res["c4"],
         config5_wgrid3d_N96=res["c5"],
-        chosen_jdqmr=dict(value=statistics.median(res["t_dyn"]), unit=UNIT,
+        chosen_jdqmr=dict(value=statistics.mean(res["t_dyn"]), unit=UNIT,
                           form="chosen form with JDQMR corrections at every stage-1 outer iteration",
                           outer1=int(res["st_dyn"][-1]["outer_stage1"]),
                           matvecs=int(res["st_dyn"][-1]["matvecs_stage1"] + res["st_dyn"][-1]["matvecs_stage2"]),
