@@ -772,7 +772,10 @@ def main():
         out = {"f32": spmm_roofline(A, dev, torch, B, B.PREC_F32, BLOCK, reps=args.steps),
                "df64": spmm_roofline(A, dev, torch, B, B.PREC_DF64, BLOCK, reps=args.steps),
                "ortho_f32": ortho_roofline(dev, torch, B, B.PREC_F32, A.n, 32, BLOCK, reps=args.steps),
-               "ortho_df64": ortho_roofline(dev, torch, B, B.PREC_DF64, A.n, 32, BLOCK, reps=args.steps)}
+               "ortho_df64": ortho_roofline(dev, torch, B, B.PREC_DF64, A.n, 32, BLOCK, reps=args.steps),
+               # the narrow blocks of the solve's GD+k corrections (1 and 2 unconverged columns)
+               "f32_b1": spmm_roofline(A, dev, torch, B, B.PREC_F32, 1, reps=args.steps),
+               "f32_b2": spmm_roofline(A, dev, torch, B, B.PREC_F32, 2, reps=args.steps)}
         print(json.dumps(out))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
