@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __
                                                    const int* __restrict__ colidx, const float* __restrict__ v32,
                                                    const float* __restrict__ v32lo, const double* __restrict__ v64,
                                                    const typename P::S* __restrict__ X, long long ldx,
-                                                   typename P::S* __restrict__ Y, long long ldy) {
+                                                   typename P::S* __restrict__ Y, long long ldy, int yvec) {
   using A = typename P::A;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= rows) return;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(long long rows, const int* __
   for (int c = 0; c < NB; ++c) acc[c] = P::zero();
   row_product<P, NB, VMODE, VEC, spmm_unroll<P, NB>()>(__ldg(rowptr + i), __ldg(rowptr + i + 1), colidx, v32, v32lo,
                                                         v64, X, ldx, acc);
-  store_yrow<P, NB, VEC>(Y + i * ldy, acc);
+  store_yrow<P, NB, VEC>(Y + i * ldy, acc, yvec != 0);
 }
 
 // Short rows (at most a few nonzeros): each thread handles two consecutive rows
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm2(long long rows, const int* _
                                                     const int* __restrict__ colidx, const float* __restrict__ v32,
                                                     const float* __restrict__ v32lo, const double* __restrict__ v64,
                                                     const typename P::S* __restrict__ X, long long ldx,
-                                                    typename P::S* __restrict__ Y, long long ldy) {
+                                                    typename P::S* __restrict__ Y, long long ldy, int yvec) {
   using A = typename P::A;
   const long long i0 = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   if (i0 >= rows) return;
@@ -105,12 +105,13 @@ __global__ void __launch_bounds__(kThreads) k_spmm2(long long rows, const int* _
     if (ua) spmm_accum<P, NB, VMODE, VEC>(ka + t, v32, v32lo, v64, xa, acc0);
     if (ub) spmm_accum<P, NB, VMODE, VEC>(kb + t, v32, v32lo, v64, xb, acc1);
   }
-  store_yrow<P, NB, VEC>(Y + i0 * ldy, acc0);
-  if (two) store_yrow<P, NB, VEC>(Y + (i0 + 1) * ldy, acc1);
+  store_yrow<P, NB, VEC>(Y + i0 * ldy, acc0, yvec != 0);
+  if (two) store_yrow<P, NB, VEC>(Y + (i0 + 1) * ldy, acc1, yvec != 0);
 }
 
 template <class P, int NB, bool VEC>
-cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t st) {
+cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, int yvec,
+                     cudaStream_t st) {
   if (P::id == kF32 && A.rows > 0 && A.nnz <= 4 * A.rows) {  // short rows (FP32): two rows per thread
     using S = typename P::S;
     const int grid = grid_for((A.rows + 1) / 2, kThreads);
@@ -120,20 +121,20 @@ cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, lon
       if (A.v16)
         k_spmm2<P, NB, 4, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx,
                                                           reinterpret_cast<const float*>(A.v16), nullptr, nullptr, x,
-                                                          ldx, y, ldy);
+                                                          ldx, y, ldy, yvec);
       else
         k_spmm2<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx,
-                                                          y, ldy);
+                                                          y, ldy, yvec);
     } else if constexpr (P::id == kDF64) {
       if (A.v32lo == nullptr)
         k_spmm2<P, NB, 1, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx,
-                                                          y, ldy);
+                                                          y, ldy, yvec);
       else
         k_spmm2<P, NB, 2, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, A.v32lo, nullptr, x, ldx,
-                                                          y, ldy);
+                                                          y, ldy, yvec);
     } else {
       k_spmm2<P, NB, 3, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, nullptr, nullptr, A.v64, x, ldx, y,
-                                                        ldy);
+                                                        ldy, yvec);
     }
     return cudaGetLastError();
   }
@@ -145,20 +146,20 @@ cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, lon
     if (A.v16)
       k_spmm<P, NB, 4, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx,
                                                        reinterpret_cast<const float*>(A.v16), nullptr, nullptr, x, ldx,
-                                                       y, ldy);
+                                                       y, ldy, yvec);
     else
       k_spmm<P, NB, 0, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
-                                                       ldy);
+                                                       ldy, yvec);
   } else if constexpr (P::id == kDF64) {
     if (A.v32lo == nullptr)
       k_spmm<P, NB, 1, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, nullptr, nullptr, x, ldx, y,
-                                                       ldy);
+                                                       ldy, yvec);
     else
       k_spmm<P, NB, 2, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, A.v32, A.v32lo, nullptr, x, ldx, y,
-                                                       ldy);
+                                                       ldy, yvec);
   } else {
     k_spmm<P, NB, 3, VEC><<<grid, kThreads, 0, st>>>(A.rows, A.rowptr, A.colidx, nullptr, nullptr, A.v64, x, ldx, y,
-                                                     ldy);
+                                                     ldy, yvec);
   }
   return cudaGetLastError();
 }
@@ -166,12 +167,14 @@ cudaError_t spmm_nbv(const CsrDev& A, const void* X, long long ldx, void* Y, lon
 template <class P, int NB>
 cudaError_t spmm_nb(const CsrDev& A, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t st) {
   constexpr size_t es = sizeof(typename P::S);
-  const bool vec = (NB * es) % 16 == 0 && (ldx * es) % 16 == 0 && (ldy * es) % 16 == 0 &&
-                   reinterpret_cast<uintptr_t>(X) % 16 == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0;
+  // 16-byte gathers need X's rows on 16-byte boundaries; 16-byte stores need
+  // Y's (decided per launch inside the kernel)
+  const bool vec = (NB * es) % 16 == 0 && (ldx * es) % 16 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+  const int yvec = (ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0 ? 1 : 0;
   if constexpr ((NB * es) % 16 == 0) {
-    if (vec) return spmm_nbv<P, NB, true>(A, X, ldx, Y, ldy, st);
+    if (vec) return spmm_nbv<P, NB, true>(A, X, ldx, Y, ldy, yvec, st);
   }
-  return spmm_nbv<P, NB, false>(A, X, ldx, Y, ldy, st);
+  return spmm_nbv<P, NB, false>(A, X, ldx, Y, ldy, 0, st);
 }
 
 template <class P>

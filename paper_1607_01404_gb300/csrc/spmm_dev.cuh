@@ -66,10 +66,12 @@ __device__ __forceinline__ void spmm_accum(const int k, const float* __restrict_
   }
 }
 
+// VEC: 16-byte stores when vst also holds (Y row starts on 16-byte
+// boundaries); element stores otherwise.
 template <class P, int NB, bool VEC>
-__device__ __forceinline__ void store_yrow(typename P::S* yr, const typename P::A (&acc)[NB]) {
+__device__ __forceinline__ void store_yrow(typename P::S* yr, const typename P::A (&acc)[NB], bool vst = true) {
   using S = typename P::S;
-  if constexpr (VEC) {
+  if (VEC && vst) {
     constexpr int W = (int)(NB * sizeof(S) / 16);
     float buf[NB * sizeof(S) / 4];
 #pragma unroll

@@ -58,6 +58,36 @@ def test_spmm_matches_oracle(prec, b):
         assert err <= TOL[prec], (A.name, err)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("b,col", [(4, 1), (4, 3), (8, 2), (2, 1)])
+def test_spmm_into_unaligned_columns(prec, b, col):
+    """Y = A X written into columns col .. col + b of a wider block (its rows do
+    not start on 16-byte boundaries) from an aligned X: 16-byte gathers with
+    element stores; the columns around the window keep their values."""
+    for A in (wl.random_illconditioned(3001, 1203, 16, seed=3), wl.grid_difference(9, 3)):  # long and 2-entry rows
+        _spmm_window(prec, A, b, col)
+
+
+def _spmm_window(prec, A, b, col):
+    d = csr_device(A)
+    X = wl.dense_block(A.n, b, seed=b)
+    Xd = to_device(prec, X)
+    Xs = to_host(prec, Xd, A.n, b)
+    ld = ((b + col + 3) // 4) * 4
+    Y0 = wl.dense_block(A.m, ld, seed=7)
+    Yd = to_device(prec, Y0)
+    Yb = to_host(prec, Yd, A.m, ld)
+    esz = 1 if prec == B.PREC_F32 or prec == B.PREC_F64 else 2
+    lo = None if d["exact"] else d["v32lo"]
+    B.spmm(prec, A.m, A.n, d["rp"], d["ci"], d["v32"], lo, d["v64"], Xd, b, Yd[col * esz:], ld, b)
+    Y = to_host(prec, Yd, A.m, ld)
+    Aabs = A.to_scipy().copy()
+    Aabs.data = np.abs(Aabs.data)
+    norm = np.abs(Aabs @ np.abs(Xs)).max()
+    assert np.abs(Y[:, col:col + b] - oracle.spmm(A, Xs)).max() / norm <= TOL[prec]
+    assert np.array_equal(Y[:, :col], Yb[:, :col]) and np.array_equal(Y[:, col + b:], Yb[:, col + b:])
+
+
 @pytest.mark.parametrize("prec", [B.PREC_DF64, B.PREC_F64])
 def test_spmm_transpose_and_ld(prec):
     A = wl.random_illconditioned(2000, 700, 16, seed=9)
