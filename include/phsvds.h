@@ -32,6 +32,7 @@ extern "C" {
 #define SVDS_ERR_NOMEM (-5)    /* device or host allocation failed, or workspace too small */
 #define SVDS_ERR_CUDA (-6)     /* CUDA runtime error; svds_last_error() has the message */
 #define SVDS_ERR_NUMERIC (-7)  /* unrecoverable breakdown in a small dense problem */
+#define SVDS_ERR_OPERATOR (-8) /* a caller-supplied operator (svds_create_op) returned non-zero */
 #define SVDS_ERR_MAXIT 1       /* budget exhausted: the first *numConverged triplets are valid */
 
 /* ---- enumerations ---- */
@@ -165,6 +166,36 @@ int svds_opts_default(svds_opts *opts);
  * of every precision mode and the Jacobi diagonals (Sec. 3.3: the operator must
  * apply both A and A^T).  *h receives a new handle owned by the caller. */
 int svds_create(svds_handle **h, const svds_csr *A, const svds_opts *opts);
+
+/* Caller-supplied operators (Sec. 3.4: the C and B operators may be given
+ * directly instead of the matrix).  The library calls
+ *     apply(op, rows, nb, X, ldx, Y, ldy, stream, ctx)
+ * with op = SVDS_OP_C for Y = A^T A X (rows = n) or op = SVDS_OP_B for
+ * Y = [0 A^T; A 0] X (rows = n + m; the first n rows of a block are its right
+ * part, the next m its left part, so Y[0:n] = A^T X[n:n+m] and
+ * Y[n:n+m] = A X[0:n]).  X and Y are row-major FP64 device blocks of nb
+ * columns with leading dimensions ldx, ldy (elements, >= nb); the function
+ * must leave X unchanged and finish writing Y in stream order on `stream` (a
+ * cudaStream_t): enqueue its kernels there, or synchronise before returning.
+ * A non-zero return stops the solve with SVDS_ERR_OPERATOR.  In the reduced-
+ * precision and double-float modes the library converts its blocks to FP64
+ * around each call.  The operator is called from the thread that calls
+ * svds_solve / svds_condest. */
+#define SVDS_OP_C 1
+#define SVDS_OP_B 2
+typedef int (*svds_apply_fn)(int op, int64_t rows, int nb, const double *X, int64_t ldx, double *Y,
+                             int64_t ldy, void *stream, void *ctx);
+
+/* A handle on an m x n matrix given by its operators (m >= n >= 1: the tall
+ * orientation, as the library stores a CSR matrix).  diagC: host array of the
+ * n diagonal entries of A^T A (copied), needed for SVDS_PRECOND_JACOBI, else
+ * NULL.  Options as for svds_create, except that precond is SVDS_PRECOND_NONE
+ * or SVDS_PRECOND_JACOBI, stage1_precision is not SVDS_BF16 (there are no
+ * matrix values to round) and normalOperator is unused.  The operator's norm
+ * must stay within the FP32 exponent range in the double-float and FP32 modes
+ * (the library does not rescale it).  ctx is passed through unchanged. */
+int svds_create_op(svds_handle **h, int64_t m, int64_t n, svds_apply_fn apply, void *ctx, const double *diagC,
+                   const svds_opts *opts);
 
 /* Compute k singular triplets (Algorithm 1).  Outputs are caller-owned host
  * arrays: sigma[k] (descending for SVDS_LARGEST, ascending for SVDS_SMALLEST),

@@ -23,7 +23,10 @@ SVDS_ERR_VALUE = -4
 SVDS_ERR_NOMEM = -5
 SVDS_ERR_CUDA = -6
 SVDS_ERR_NUMERIC = -7
+SVDS_ERR_OPERATOR = -8
 SVDS_ERR_MAXIT = 1
+SVDS_OP_C = 1
+SVDS_OP_B = 2
 SVDS_LARGEST = 0
 SVDS_SMALLEST = 1
 SVDS_GDPK = 0
@@ -84,10 +87,16 @@ class svds_stats(C.Structure):
 
 _lib = None
 
+# caller-supplied operator: int apply(op, rows, nb, X, ldx, Y, ldy, stream, ctx)
+APPLY_FN = C.CFUNCTYPE(C.c_int, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                       C.c_void_p, C.c_void_p)
+
 # exported symbol -> (restype, argtypes)
 _SIGS = {
     "svds_opts_default": (C.c_int, [C.POINTER(svds_opts)]),
     "svds_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(svds_csr), C.POINTER(svds_opts)]),
+    "svds_create_op": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, C.c_int64, APPLY_FN, C.c_void_p, C.c_void_p,
+                                 C.POINTER(svds_opts)]),
     "svds_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.POINTER(C.c_int), C.POINTER(svds_stats)]),
     "svds_destroy": (None, [C.c_void_p]),
@@ -178,7 +187,8 @@ def exported_symbols() -> list[str]:
 class SvdsError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = lib().svds_strerror(code).decode()
-        extra = lib().svds_last_error().decode() if code in (SVDS_ERR_CUDA, SVDS_ERR_NUMERIC) else ""
+        detailed = (SVDS_ERR_CUDA, SVDS_ERR_NUMERIC, SVDS_ERR_OPERATOR)
+        extra = lib().svds_last_error().decode() if code in detailed else ""
         super().__init__(f"{where}: {msg} ({code}) {extra}".strip())
         self.code = code
 
@@ -260,6 +270,26 @@ def svds_create(rowptr, colidx, vals, m: int, n: int, opts: svds_opts | None = N
     h = C.c_void_p()
     _check(lib().svds_create(C.byref(h), C.byref(A), C.byref(opts) if opts is not None else None), "svds_create")
     return Handle(h, m, n, keep)
+
+
+def svds_create_op(m: int, n: int, apply, diagC=None, opts: svds_opts | None = None) -> Handle:
+    """Create a handle on an m x n matrix (m >= n) given by its operators.
+    apply(op, rows, nb, X_ptr, ldx, Y_ptr, ldy, stream) is a Python function on
+    device pointers (row-major FP64 blocks, see svds_create_op in phsvds.h)
+    returning 0 on success; diagC: optional host array of diag(A^T A)."""
+
+    def tramp(op, rows, nb, X, ldx, Y, ldy, stream, ctx):
+        try:
+            return int(apply(op, rows, nb, X, ldx, Y, ldy, stream) or 0)
+        except Exception:  # an exception must not cross the C frames
+            return 1
+
+    fn = APPLY_FN(tramp)
+    d = None if diagC is None else np.ascontiguousarray(diagC, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib().svds_create_op(C.byref(h), m, n, fn, None, d.ctypes.data if d is not None else None,
+                                C.byref(opts) if opts is not None else None), "svds_create_op")
+    return Handle(h, m, n, (fn, tramp, apply))
 
 
 def svds_solve(h: Handle, k: int, target: int, tol: float, want_vectors: bool = True, U=None, V=None):

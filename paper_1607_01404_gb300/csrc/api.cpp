@@ -148,6 +148,27 @@ int create_impl(svds_handle* h, const svds_csr* A) {
   return 0;
 }
 
+int check_opts(const svds_opts& o) {
+  if (o.stage1_precision != SVDS_DF64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_BF16 &&
+      o.stage1_precision != SVDS_NATIVE_FP64)
+    return SVDS_ERR_ARG;
+  if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
+  if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR && o.method_stage1 != SVDS_DYNAMIC) ||
+      (o.method_stage2 != SVDS_GDPK && o.method_stage2 != SVDS_JDQMR) || o.innerMaxIt < 0 || o.innerRelTol < 0)
+    return SVDS_ERR_ARG;
+  if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_DF64) return SVDS_ERR_ARG;
+  if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
+  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED &&
+      o.precond != SVDS_PRECOND_BLOCKJACOBI)
+    return SVDS_ERR_ARG;
+  if (o.normalOperator != SVDS_NORMAL_AUTO && o.normalOperator != SVDS_NORMAL_TWOPASS &&
+      o.normalOperator != SVDS_NORMAL_EXPLICIT)
+    return SVDS_ERR_ARG;
+  if (!(o.relTol >= 0) || !std::isfinite(o.relTol)) return SVDS_ERR_ARG;
+  if (o.precondBlockSize < 0 || o.precondBlockSize > phsvds::kBjMaxBlock) return SVDS_ERR_ARG;
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -177,23 +198,7 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
     o = *opts;
   else
     svds_opts_default(&o);
-  if (o.stage1_precision != SVDS_DF64 && o.stage1_precision != SVDS_FP32 && o.stage1_precision != SVDS_BF16 &&
-      o.stage1_precision != SVDS_NATIVE_FP64)
-    return SVDS_ERR_ARG;
-  if (o.maxBlockSize < 0 || o.maxBlockSize > 64 || o.maxBasisSize < 0 || o.minRestartSize < 0) return SVDS_ERR_ARG;
-  if ((o.method_stage1 != SVDS_GDPK && o.method_stage1 != SVDS_JDQMR && o.method_stage1 != SVDS_DYNAMIC) ||
-      (o.method_stage2 != SVDS_GDPK && o.method_stage2 != SVDS_JDQMR) || o.innerMaxIt < 0 || o.innerRelTol < 0)
-    return SVDS_ERR_ARG;
-  if (o.innerPrecision != 0 && o.innerPrecision != SVDS_FP32 && o.innerPrecision != SVDS_DF64) return SVDS_ERR_ARG;
-  if (o.initSize < 0 || (o.initSize > 0 && !o.initV)) return SVDS_ERR_ARG;
-  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI && o.precond != SVDS_PRECOND_LEARNED &&
-      o.precond != SVDS_PRECOND_BLOCKJACOBI)
-    return SVDS_ERR_ARG;
-  if (o.normalOperator != SVDS_NORMAL_AUTO && o.normalOperator != SVDS_NORMAL_TWOPASS &&
-      o.normalOperator != SVDS_NORMAL_EXPLICIT)
-    return SVDS_ERR_ARG;
-  if (!(o.relTol >= 0) || !std::isfinite(o.relTol)) return SVDS_ERR_ARG;
-  if (o.precondBlockSize < 0 || o.precondBlockSize > phsvds::kBjMaxBlock) return SVDS_ERR_ARG;
+  if (check_opts(o)) return SVDS_ERR_ARG;
   std::vector<float> gnn_params;
   if (o.precond == SVDS_PRECOND_LEARNED) {
     gnn_params.resize(phsvds_gnn_num_params());
@@ -233,6 +238,70 @@ int svds_create(svds_handle** out, const svds_csr* A, const svds_opts* opts) {
   }
   if (o.initSize > 0) {
     h->initV.assign(o.initV, o.initV + (size_t)o.initSize * A->n);
+    h->opts.initV = h->initV.data();
+    h->opts.initSize = o.initSize;
+  }
+  *out = h;
+  return SVDS_OK;
+}
+
+int svds_create_op(svds_handle** out, int64_t m, int64_t n, svds_apply_fn apply, void* ctx, const double* diagC,
+                   const svds_opts* opts) {
+  if (!out || !apply) return SVDS_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || m < n || m > 2147483646LL) return SVDS_ERR_SHAPE;
+  svds_opts o;
+  if (opts)
+    o = *opts;
+  else
+    svds_opts_default(&o);
+  if (check_opts(o)) return SVDS_ERR_ARG;
+  // no matrix values: no bfloat16 rounding, no explicit A^T A, and only the
+  // Jacobi preconditioner from the caller's diagonal of A^T A
+  if (o.stage1_precision == SVDS_BF16) return SVDS_ERR_ARG;
+  if (o.precond != SVDS_PRECOND_NONE && o.precond != SVDS_PRECOND_JACOBI) return SVDS_ERR_ARG;
+  if (o.precond == SVDS_PRECOND_JACOBI && !diagC) return SVDS_ERR_ARG;
+  if (diagC)
+    for (int64_t i = 0; i < n; ++i)
+      if (!std::isfinite(diagC[i]) || diagC[i] < 0) return SVDS_ERR_VALUE;
+  svds_handle* h = new svds_handle();
+  h->opts = o;
+  h->opts.initV = nullptr;
+  h->opts.initSize = 0;
+  h->opts.precondParams = nullptr;
+  h->opts.precondModel = nullptr;
+  cudaGetDevice(&h->device);
+  if (o.stream) {
+    h->stream = reinterpret_cast<cudaStream_t>(o.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return cuda_fail(cudaGetLastError(), "cudaStreamCreateWithFlags");
+    }
+    h->own_stream = true;
+  }
+  phsvds::DevMatrix& D = h->A;
+  D.m = m;
+  D.n = n;
+  D.nnz = 0;
+  D.nnzC = 0;  // C is the caller's operator
+  D.user = apply;
+  D.user_ctx = ctx;
+  if (diagC) {
+    int rc = dalloc(h, &D.colsq, n);
+    if (!rc) {
+      const cudaError_t e = cudaMemcpyAsync(D.colsq, diagC, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess && cudaStreamSynchronize(h->stream) == cudaSuccess) rc = 0;
+      else rc = cuda_fail(e != cudaSuccess ? e : cudaGetLastError(), "diagC upload");
+    }
+    if (rc) {
+      release(h);
+      delete h;
+      return rc;
+    }
+  }
+  if (o.initSize > 0) {
+    h->initV.assign(o.initV, o.initV + (size_t)o.initSize * n);
     h->opts.initV = h->initV.data();
     h->opts.initSize = o.initSize;
   }
@@ -298,6 +367,7 @@ const char* svds_strerror(int code) {
     case SVDS_ERR_NOMEM: return "out of memory";
     case SVDS_ERR_CUDA: return "CUDA error";
     case SVDS_ERR_NUMERIC: return "numerical breakdown";
+    case SVDS_ERR_OPERATOR: return "the caller-supplied operator failed";
     case SVDS_ERR_MAXIT: return "matvec or time budget exhausted";
     default: return "unknown error";
   }

@@ -31,6 +31,10 @@ struct CudaFail {
   cudaError_t e;
   const char* where;
 };
+// a caller-supplied operator returned non-zero
+struct OpFail {
+  int rc;
+};
 struct NumFail {
   const char* what;
 };
@@ -59,6 +63,8 @@ struct Ctx {
   svds_handle* h = nullptr;
   cudaStream_t st = nullptr;
   const DevMatrix* A = nullptr;
+  double* ux = nullptr;  // FP64 staging of a caller-supplied operator's input and output blocks
+  double* uy = nullptr;
   void* partial = nullptr;
   int maxblk = 0;
   double* dG = nullptr;
@@ -194,6 +200,31 @@ void combine(Ctx& c, int prec, long long L, const std::vector<SegV>& P, const st
 void apply_op(Ctx& c, int prec, int op, const void* X, long long ldx, void* Y, long long ldy, int nb, void* tmp,
               int tmp_cols) {
   const DevMatrix& A = *c.A;
+  if (A.user) {
+    // the caller's operator on row-major FP64 blocks (converted from and to
+    // the mode's storage unless the mode is native FP64)
+    const long long rows = op == OP_C ? A.n : A.n + A.m;
+    for (int c0 = 0; c0 < nb; c0 += tmp_cols) {
+      const int w = std::min(tmp_cols, nb - c0);
+      const void* Xc = off(X, c0, prec);
+      void* Yc = off(Y, c0, prec);
+      const bool direct = prec == kF64;
+      if (!direct) {
+        CK(launch_rows_to_f64(prec, rows, w, Xc, ldx, c.ux, w, c.st));
+        c.launches += 1;
+      }
+      const int rc = A.user(op == OP_C ? SVDS_OP_C : SVDS_OP_B, rows, w,
+                            direct ? static_cast<const double*>(Xc) : c.ux, direct ? ldx : w,
+                            direct ? static_cast<double*>(Yc) : c.uy, direct ? ldy : w, c.st, A.user_ctx);
+      if (rc) throw OpFail{rc};
+      if (!direct) {
+        CK(launch_rows_from_f64(prec, rows, w, c.uy, w, Yc, ldy, c.st));
+        c.launches += 1;
+      }
+      c.mv += 2LL * w;
+    }
+    return;
+  }
   for (int c0 = 0; c0 < nb; c0 += tmp_cols) {
     const int w = std::min(tmp_cols, nb - c0);
     const void* Xc = off(X, c0, prec);
@@ -784,7 +815,7 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
   for (int k = 0; k < cfg.jd_maxk; ++k) {
     // w = op(q), fused with the step's first dot products when op is C
     int ready = 0;
-    if (cfg.op == OP_C) {
+    if (cfg.op == OP_C && !Am.user) {
       if (Am.nnzC > 0) {
         CK(qmr_op_dots(pin, L, nbk, c.op(pin, 2), q, nbk, w, x, q, c.partial, B.jdots, B.jtick, de, B.jS, &ready,
                        c.st));
@@ -805,7 +836,8 @@ void jd_correction(Ctx& c, RunBufs& B, const RunCfg& cfg, int nbk, const std::ve
         if (Am.nnzC > 0) c.mv += 2LL * nbk;
       }
     }
-    if (!ready && !(cfg.op == OP_C && Am.nnzC <= 0)) apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
+    if (!ready && (Am.user || !(cfg.op == OP_C && Am.nnzC <= 0)))
+      apply_op(c, pin, cfg.op, q, nbk, w, nbk, nbk, B.jtmp, nbk);
     CK(qmr_step(pin, L, nbk, x, w, ready, B.jtick, kx, cfg.jdinv, cfg.jdK, B.ju, de, cfg.jd_xi, cfg.jd_maxk, q, r, d,
                 sol, B.jS, c.partial, B.jdots, c.st));
     c.launches += qmr_step_launches(nbk, cfg.jdK != nullptr, ready, (nbk & (nbk - 1)) == 0);
@@ -1455,6 +1487,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     c.gcap = 256 * 256;
     reqs.push_back({&c.partial, gram_partial_bytes(std::max(c.maxblk, 152 * 16), 256, 8)});
     reqs.push_back({(void**)&c.dG, c.gcap * 8});
+    if (A.user) {  // FP64 staging of the caller's operator: blocks of up to b columns of B
+      reqs.push_back({(void**)&c.ux, (size_t)L2 * b * 8});
+      reqs.push_back({(void**)&c.uy, (size_t)L2 * b * 8});
+    }
     reqs.push_back({(void**)&c.dGo, sizeof(double) * 264 * 8});
     reqs.push_back({(void**)&c.dwork, sizeof(double) * 128});
     for (int i = 0; i < 4; ++i) reqs.push_back({&c.dco[i], sizeof(double) * 264 * 8});
@@ -1791,9 +1827,17 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     for (int j = 0; j < k; ++j) normA = std::max(normA, smallest ? 0.0 : sig[j]);
     // u = A v / sigma (bottom m rows of Xfin)
     void* Ufin = off(Xfin, n * kk, p2);
-    CK(launch_spmm(p2, A.csr(false), Xfin, kk, Ufin, kk, k, c.st));
-    c.launches += spmm_launches(k);
-    c.mv += k;
+    if (A.user) {
+      // [0; A v] = B [v; 0]: the lower rows of B applied to x with a zero left part
+      CK(cudaMemsetAsync(Ufin, 0, (size_t)m * kk * e2, c.st));
+      apply_op(c, p2, OP_B, Xfin, kk, BXfin, kk, k, B2.tmp, b);
+      CK(launch_copy_cols(p2, m, off(BXfin, n * kk, p2), kk, Ufin, kk, k, c.st));
+      c.launches += 1;
+    } else {
+      CK(launch_spmm(p2, A.csr(false), Xfin, kk, Ufin, kk, k, c.st));
+      c.launches += spmm_launches(k);
+      c.mv += k;
+    }
     {
       std::vector<double> D((size_t)k * k, 0.0);
       for (int j = 0; j < k; ++j) D[(size_t)j * k + j] = sig[j] > 0 ? 1.0 / sig[j] : 1.0;
@@ -2016,6 +2060,10 @@ int solve(svds_handle* h, int k, int target, double tol, double* sigma, double* 
     set_last_error(f.what);
     if (stats) *stats = S;
     return SVDS_ERR_NUMERIC;
+  } catch (const OpFail& f) {
+    set_last_error("the caller-supplied operator returned " + std::to_string(f.rc));
+    if (stats) *stats = S;
+    return SVDS_ERR_OPERATOR;
   } catch (const BudgetOut&) {
     cudaStreamSynchronize(c.st);
     if (numConverged) *numConverged = 0;

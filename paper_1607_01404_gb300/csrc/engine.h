@@ -42,6 +42,10 @@ struct DevMatrix {
   uint16_t* v16T = nullptr;
   uint16_t* v16C = nullptr;
   bool exact16 = true;  // every value is a bfloat16 number
+  // caller-supplied operators (svds_create_op): no CSR; C and B are applied
+  // by the caller's function on row-major FP64 blocks
+  svds_apply_fn user = nullptr;
+  void* user_ctx = nullptr;
   CsrDev csrC() const {
     CsrDev c;
     c.rows = n;

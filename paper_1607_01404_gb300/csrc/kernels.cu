@@ -499,6 +499,40 @@ __global__ void k_from_f64(long long L, int nc, const double* src, long long lds
   }
 }
 
+// Row-major blocks in the mode's storage <-> row-major FP64 blocks (the
+// interface of caller-supplied operators): element (r, j) at r * ld + j.
+template <class P>
+__global__ void k_rows_f64(long long L, int nc, const typename P::S* src, long long lds, double* dst, long long ldd) {
+  const long long total = L * nc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / nc;
+    const int j = (int)(e - r * nc);
+    const typename P::S v = src[r * lds + j];
+    if constexpr (P::id == kDF64)
+      dst[r * ldd + j] = (double)v.hi + (double)v.lo;
+    else
+      dst[r * ldd + j] = (double)v;
+  }
+}
+template <class P>
+__global__ void k_rows_from_f64(long long L, int nc, const double* src, long long lds, typename P::S* dst,
+                                long long ldd) {
+  const long long total = L * nc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / nc;
+    const int j = (int)(e - r * nc);
+    const double z = src[r * lds + j];
+    if constexpr (P::id == kF32) {
+      dst[r * ldd + j] = (float)z;
+    } else if constexpr (P::id == kDF64) {
+      const float hi = (float)z;
+      dst[r * ldd + j] = df{hi, (float)(z - (double)hi)};
+    } else {
+      dst[r * ldd + j] = z;
+    }
+  }
+}
+
 template <class P>
 __global__ void k_to_f64(long long L, int nc, const typename P::S* src, long long lds, double* dst, long long ldd,
                          double scale) {
@@ -1826,6 +1860,22 @@ static cudaError_t from_p(long long L, int nc, const double* src, long long lds,
                                                                         reinterpret_cast<typename P::S*>(dst), ldd, scale);
   return cudaGetLastError();
 }
+cudaError_t launch_rows_to_f64(int prec, long long L, int nc, const void* src, long long lds, double* dst,
+                               long long ldd, cudaStream_t st) {
+  if (L * nc == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, (k_rows_f64<P><<<persistent_grid(L * nc, kThreads), kThreads, 0, st>>>(
+                            L, nc, reinterpret_cast<const typename P::S*>(src), lds, dst, ldd),
+                        cudaGetLastError()))
+}
+
+cudaError_t launch_rows_from_f64(int prec, long long L, int nc, const double* src, long long lds, void* dst,
+                                 long long ldd, cudaStream_t st) {
+  if (L * nc == 0) return cudaSuccess;
+  PHSVDS_DISPATCH(prec, (k_rows_from_f64<P><<<persistent_grid(L * nc, kThreads), kThreads, 0, st>>>(
+                            L, nc, src, lds, reinterpret_cast<typename P::S*>(dst), ldd),
+                        cudaGetLastError()))
+}
+
 cudaError_t launch_from_f64_colmajor(int prec, long long L, int nc, const double* src, long long lds, void* dst,
                                      long long ldd, double scale, cudaStream_t st) {
   if (L * nc == 0) return cudaSuccess;

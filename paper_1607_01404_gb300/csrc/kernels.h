@@ -103,6 +103,11 @@ cudaError_t launch_fill_normal(int prec, long long L, void* Dst, long long ldd, 
                                cudaStream_t st);
 
 // Conversions between FP64 column-major (device) and mode storage row-major.
+// Row-major blocks in the mode's storage <-> row-major FP64 blocks.
+cudaError_t launch_rows_to_f64(int prec, long long L, int nc, const void* src, long long lds, double* dst,
+                               long long ldd, cudaStream_t st);
+cudaError_t launch_rows_from_f64(int prec, long long L, int nc, const double* src, long long lds, void* dst,
+                                 long long ldd, cudaStream_t st);
 cudaError_t launch_from_f64_colmajor(int prec, long long L, int nc, const double* src, long long lds, void* dst,
                                      long long ldd, double scale, cudaStream_t st);
 cudaError_t launch_to_f64_colmajor(int prec, long long L, int nc, const void* src, long long lds, double* dst,
