@@ -814,7 +814,10 @@ def main():
         return 0
     if res.get("solve_only"):
         print(json.dumps(dict(solve_only=True, seconds=res["times"],
-                              kernel_launches=[s["kernel_launches"] for s in res["stats"]])))
+                              kernel_launches=[s["kernel_launches"] for s in res["stats"]],
+                              setup_s=[s["seconds_setup"] for s in res["stats"]],
+                              norm_s=[s["seconds_norm"] for s in res["stats"]],
+                              norm_steps=[s["norm_steps"] for s in res["stats"]])))
         return 0
     A = res["A"]
     peak, peak_kind = measured_peaks()
@@ -879,7 +882,8 @@ def main():
         plain_fp64_gdk=dict(value=res["t_gdk"][0], unit=UNIT, form="GD+k, FP64-class, Jacobi",
                             matvecs=int(res["st_gdk"][0]["matvecs_stage1"] + res["st_gdk"][0]["matvecs_stage2"]),
                             max_rel_sigma_err=res["relerr_gdk"]),
-        solve_stats=dict(matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
+        solve_stats=dict(norm_s=st["seconds_norm"], norm_steps=st["norm_steps"],
+                         matvecs_stage1=st["matvecs_stage1"], matvecs_lowprec=st["matvecs_stage1_lowprec"],
                          matvecs_stage2=st["matvecs_stage2"], outer1=st["outer_stage1"], outer2=st["outer_stage2"],
                          inner_steps=st["inner_steps"], outer1_jdqmr=st["outer_stage1_jdqmr"],
                          stage2_used=st["stage2_used"], setup_s=st["seconds_setup"],

@@ -155,6 +155,8 @@ typedef struct {
   int64_t outer_stage1_jdqmr; /* stage-1 outer iterations whose correction came from JDQMR */
   int precond_fallback;       /* 0, or the learned preconditioner was replaced by Jacobi: 1 = M
                                  rejected (non-finite value or non-positive diagonal), 2 = stall */
+  double seconds_norm;        /* the ||A|| estimate inside seconds_setup (0 when aNorm was given) */
+  int norm_steps;             /* its Arnoldi steps on C */
 } svds_stats;
 
 typedef struct svds_handle svds_handle;

@@ -79,7 +79,9 @@ class svds_stats(C.Structure):
                 ("inner_steps", C.c_int64), ("seconds_precond", C.c_double), ("normal_nnz", C.c_int64),
                 ("seconds_output", C.c_double),
                 ("outer_stage1_jdqmr", C.c_int64),
-                ("precond_fallback", C.c_int)]
+                ("precond_fallback", C.c_int),
+                ("seconds_norm", C.c_double),
+                ("norm_steps", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

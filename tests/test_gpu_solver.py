@@ -80,8 +80,9 @@ def test_grid2d_closed_form_and_oracle(target):
     # vectors: each in the closed-form subspace of its value (the 5th value is
     # double and cut at k = 5, so its vector may be any unit vector of that plane)
     check_grid_vectors(A, 32, 2, r)
-    # the ||A|| estimate is a Lanczos lower bound within a few 1e-4 (clustered top)
-    assert s[-1] * (1 - 2e-3) <= r["stats"]["aNorm"] <= s[-1] * (1 + 1e-12)
+    # the ||A|| estimate is a Lanczos lower bound within a few 1e-3 (clustered
+    # top; the steps stop once the top Ritz value moves by <= 1e-3 relative)
+    assert s[-1] * (1 - 1e-2) <= r["stats"]["aNorm"] <= s[-1] * (1 + 1e-12)
 
 
 @pytest.mark.parametrize("target", ["smallest", "largest"])
