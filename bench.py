@@ -46,12 +46,14 @@ METRIC = ("sec to k triplets at ||r||<=1e-10||A|| (chosen: DYNAMIC GD+k/JDQMR st
           "FP32 stage-1 phase, learned preconditioner)")
 MODELS = os.path.join(ROOT, "paper_1607_01404_gb300", "gnn_models")
 # DRAM bytes (read + write) of one launch from ncu captures of these kernels on
-# this workload (--set full, one warm launch each); None where the kernel
-# changed after its capture
-TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_tma_f32_32x4": 305_533_440}
+# this workload (SpMM: --set full, one warm launch each; Gram: the dram__bytes
+# counters, mean of two warm launches); None where the kernel changed after
+# its capture
+TRAFFIC = {"spmm_C": 179_408_000, "spmm_A": 292_114_000, "spmm_AT": None, "gram_tma_f32_32x4": 303_501_440}
 UNIT = "s"
 # FP32 operations per product of the anchored FP64-class Gram accumulation in
-# the FP32 mode (fma, subtract, fma, add)
+# the FP32 mode (fma, subtract, fma, add; issued in pairs as packed f32x2
+# instructions)
 GRAM_OPS = 4
 # The oracle run to completion on this workload (python -m oracle.full_solve):
 # its own wall time and product count; the CPU baseline of every run scales the

@@ -33,7 +33,9 @@
 //   partial sums (SP, SQ: running sums of squares), so that
 //       s' = fma(p, q, s),  z = s' - s  (exact: Sterbenz),  d = fma(p, q, -z)
 //   is the rounding error of the update to FP32 precision, summed in c:
-//   4 FP32 operations per product instead of Dot2's 10.  An outgrown anchor
+//   4 FP32 operations per product instead of Dot2's 10, issued as packed
+//   f32x2 instructions for pairs of Q columns (2 instructions per product,
+//   each half rounded as the scalar operation).  An outgrown anchor
 //   is raised with 4x headroom and its pairs move to it by an error-free
 //   FastTwoSum; every 8 rows c is folded into s.  The error of a product is
 //   about 2^-47 sigma_ij, i.e. 2^-43 of the Cauchy-Schwarz bound of the
@@ -54,6 +56,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -230,6 +233,13 @@ __global__ void __launch_bounds__(kT, 2)
   const bool qvec = qs.xe == 0;
 
   float sa[KP][NQ], ca[KP][NQ];
+  // FP32 storage with two or more Q columns: the sums of Q columns 2h and
+  // 2h + 1 travel as one register pair and update with packed instructions
+  // (the same roundings as the scalar updates, half the instructions)
+  constexpr bool kPack = kAnchored && NQ >= 2;
+  constexpr int NH = NQ >= 2 ? NQ / 2 : 1;
+  float2 s2[KP][NH], c2[KP][NH];
+  const float2 neg1{-1.f, -1.f};
   // anchors a_k, b_j (powers of two), the running sums of squares and the
   // thresholds a^2 / 4.5 above which an anchor is raised
   float an[KP], bn[NQ], sp[KP], sq[NQ], ta[KP], tb[NQ];
@@ -252,6 +262,13 @@ __global__ void __launch_bounds__(kT, 2)
     for (int j = 0; j < NQ; ++j) {
       sa[k][j] = kAnchored ? kFloor * kFloor : 0.f;
       ca[k][j] = 0.f;
+    }
+#pragma unroll
+  for (int k = 0; k < KP; ++k)
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      s2[k][h] = float2{kFloor * kFloor, kFloor * kFloor};
+      c2[k][h] = float2{0.f, 0.f};
     }
 
   const int row0 = threadIdx.x / TPR;
@@ -304,7 +321,92 @@ __global__ void __launch_bounds__(kT, 2)
           yb[j] = elem<P>(wb, j);
         }
       }
-      if constexpr (kAnchored) {
+      if constexpr (kPack) {
+        // running sums of squares: P columns in pairs where KP is even
+        if constexpr (KP % 2 == 0) {
+#pragma unroll
+          for (int k = 0; k < KP; k += 2) {
+            float2 v = x2::fma2(float2{xa[k], xa[k + 1]}, float2{xa[k], xa[k + 1]}, float2{sp[k], sp[k + 1]});
+            v = x2::fma2(float2{xb[k], xb[k + 1]}, float2{xb[k], xb[k + 1]}, v);
+            sp[k] = v.x;
+            sp[k + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < KP; ++k) {
+            sp[k] = __fmaf_rn(xa[k], xa[k], sp[k]);
+            sp[k] = __fmaf_rn(xb[k], xb[k], sp[k]);
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          float2 v = x2::fma2(float2{ya[2 * h], ya[2 * h + 1]}, float2{ya[2 * h], ya[2 * h + 1]},
+                              float2{sq[2 * h], sq[2 * h + 1]});
+          v = x2::fma2(float2{yb[2 * h], yb[2 * h + 1]}, float2{yb[2 * h], yb[2 * h + 1]}, v);
+          sq[2 * h] = v.x;
+          sq[2 * h + 1] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+          if (sp[k] > ta[k]) {
+            const float a1 = anc_anchor(sp[k]);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+              anc_move(s2[k][h].x, c2[k][h].x, an[k] * bn[2 * h], a1 * bn[2 * h]);
+              anc_move(s2[k][h].y, c2[k][h].y, an[k] * bn[2 * h + 1], a1 * bn[2 * h + 1]);
+            }
+            an[k] = a1;
+            ta[k] = a1 * a1 * (1.0f / 4.5f);
+          }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j)
+          if (sq[j] > tb[j]) {
+            const float b1 = anc_anchor(sq[j]);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+              float& sv = (j & 1) ? s2[k][j >> 1].y : s2[k][j >> 1].x;
+              float& cv = (j & 1) ? c2[k][j >> 1].y : c2[k][j >> 1].x;
+              anc_move(sv, cv, an[k] * bn[j], an[k] * b1);
+            }
+            bn[j] = b1;
+            tb[j] = b1 * b1 * (1.0f / 4.5f);
+          }
+        // s' = fma(x, y, s), z = s' - s, e = fma(x, -y, z) = -d exactly,
+        // c - e = c + d: the anchored update of the file header, two Q
+        // columns per instruction
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const float* xr = r == 0 ? xa : xb;
+          const float* yr = r == 0 ? ya : yb;
+          float2 y2[NH], yn[NH];
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            y2[h] = float2{yr[2 * h], yr[2 * h + 1]};
+            yn[h] = x2::mul2(y2[h], neg1);
+          }
+#pragma unroll
+          for (int k = 0; k < KP; ++k) {
+            const float2 xx{xr[k], xr[k]};
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+              const float2 t = s2[k][h];
+              s2[k][h] = x2::fma2(xx, y2[h], t);
+              const float2 z = x2::sub2(s2[k][h], t);
+              c2[k][h] = x2::sub2(c2[k][h], x2::fma2(xx, yn[h], z));
+            }
+          }
+        }
+        if ((pairs & 3) == 3) {  // every 8 rows: fold c into s (|s| >= |c|)
+#pragma unroll
+          for (int k = 0; k < KP; ++k)
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+              const float2 t = x2::add2(s2[k][h], c2[k][h]);
+              c2[k][h] = x2::sub2(c2[k][h], x2::sub2(t, s2[k][h]));
+              s2[k][h] = t;
+            }
+        }
+      } else if constexpr (kAnchored) {
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
           sp[k] = __fmaf_rn(hi_of(xa[k]), hi_of(xa[k]), sp[k]);
@@ -391,6 +493,17 @@ __global__ void __launch_bounds__(kT, 2)
     __syncthreads();
     for (int e = threadIdx.x; e < pq; e += kT) partial[(long long)blockIdx.x * pq + e] = df{__int_as_float(0x7fc00000), 0.f};
     return;
+  }
+  if constexpr (kPack) {
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        sa[k][2 * h] = s2[k][h].x;
+        sa[k][2 * h + 1] = s2[k][h].y;
+        ca[k][2 * h] = c2[k][h].x;
+        ca[k][2 * h + 1] = c2[k][h].y;
+      }
   }
   df* red = reinterpret_cast<df*>(smem);
 #pragma unroll
