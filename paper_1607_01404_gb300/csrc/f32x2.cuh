@@ -50,5 +50,26 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {  // a b
   return d;
 }
 
+// Two Dot2 steps (Ogita, Rump and Oishi 2005) at once: hi + lo += x c for
+// double-float operands x = xh + xl and c = ch + cl, in the scalar step's
+// order: p = x_hi c_hi with its error pe = fma(x_hi, c_hi, -p), the cross
+// terms pl = fma(x_hi, c_lo, fma(x_lo, c_hi, pe)), TwoSum(hi, p), then
+// lo + (e + pl).  fma has no negated addend here, so the error terms come out
+// negated from the negated operand (nch, ncl) = -(ch, cl):
+// fma(a, -b, c) = -fma(a, b, -c) exactly in round-to-nearest, and
+// lo + (e + pl) = lo + (e - (-pl)).  The results equal the scalar steps' (up
+// to the sign of a zero low word).
+__device__ __forceinline__ void dot2x2(float2& hi, float2& lo, float2 xh, float2 xl, float2 ch, float2 nch,
+                                       float2 ncl) {
+  const float2 p = mul2(xh, ch);
+  const float2 npe = fma2(xh, nch, p);
+  const float2 npl = fma2(xh, ncl, fma2(xl, nch, npe));
+  const float2 s = add2(hi, p);
+  const float2 bb = sub2(s, hi);
+  const float2 e = add2(sub2(hi, sub2(s, bb)), sub2(p, bb));
+  hi = s;
+  lo = add2(lo, sub2(e, npl));
+}
+
 }  // namespace x2
 }  // namespace phsvds

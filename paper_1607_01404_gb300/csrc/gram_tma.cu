@@ -25,7 +25,8 @@
 // of the lanes (deterministic).
 // * DF64 storage: Dot2 (Ogita, Rump and Oishi 2005): the exact product of the
 //   hi parts (TwoProd by FMA) plus the cross terms, TwoSum into hi, rounding
-//   errors into lo, renormalised every 2 rows; accurate to about 2^-48 of
+//   errors into lo, renormalised every 2 rows (two Q columns per packed
+//   f32x2 instruction where there are two or more); accurate to about 2^-48 of
 //   the products, as the double-float data.
 // * FP32 storage: anchored accumulation.  Pair (i, j) of a lane accumulates
 //   into s = sigma_ij + partial sum, sigma_ij = a_i b_j a power of two of at
@@ -94,6 +95,8 @@ struct TmaPlan {
 
 // ---- anchored accumulation (see the file header) ----
 __device__ __forceinline__ float hi_of(float x) { return x; }
+__device__ __forceinline__ float hi_of(df x) { return x.hi; }
+__device__ __forceinline__ float lo_of(df x) { return x.lo; }
 
 __device__ __forceinline__ void anc_add(float& s, float& c, float x, float y) {
   const float t = s;
@@ -233,10 +236,10 @@ __global__ void __launch_bounds__(kT, 2)
   const bool qvec = qs.xe == 0;
 
   float sa[KP][NQ], ca[KP][NQ];
-  // FP32 storage with two or more Q columns: the sums of Q columns 2h and
-  // 2h + 1 travel as one register pair and update with packed instructions
-  // (the same roundings as the scalar updates, half the instructions)
-  constexpr bool kPack = kAnchored && NQ >= 2;
+  // two or more Q columns: the sums of Q columns 2h and 2h + 1 travel as one
+  // register pair and update with packed instructions (the scalar updates'
+  // roundings, half the instructions)
+  constexpr bool kPack = NQ >= 2;
   constexpr int NH = NQ >= 2 ? NQ / 2 : 1;
   float2 s2[KP][NH], c2[KP][NH];
   const float2 neg1{-1.f, -1.f};
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kT, 2)
   for (int k = 0; k < KP; ++k)
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
-      s2[k][h] = float2{kFloor * kFloor, kFloor * kFloor};
+      s2[k][h] = kAnchored ? float2{kFloor * kFloor, kFloor * kFloor} : float2{0.f, 0.f};
       c2[k][h] = float2{0.f, 0.f};
     }
 
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kT, 2)
           yb[j] = elem<P>(wb, j);
         }
       }
-      if constexpr (kPack) {
+      if constexpr (kAnchored && kPack) {
         // running sums of squares: P columns in pairs where KP is even
         if constexpr (KP % 2 == 0) {
 #pragma unroll
@@ -452,6 +455,37 @@ __global__ void __launch_bounds__(kT, 2)
               sa[k][j] = t;
             }
         }
+      } else if constexpr (kPack) {
+        // Dot2 of two Q columns per instruction: the error terms come out
+        // negated from the negated Q pair, built once per row
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const A* xr = r == 0 ? xa : xb;
+          const A* yr = r == 0 ? ya : yb;
+          float2 yh[NH], yl[NH], nyh[NH], nyl[NH];
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            yh[h] = float2{hi_of(yr[2 * h]), hi_of(yr[2 * h + 1])};
+            yl[h] = float2{lo_of(yr[2 * h]), lo_of(yr[2 * h + 1])};
+            nyh[h] = x2::mul2(yh[h], neg1);
+            nyl[h] = x2::mul2(yl[h], neg1);
+          }
+#pragma unroll
+          for (int k = 0; k < KP; ++k) {
+            const float2 xh{hi_of(xr[k]), hi_of(xr[k])}, xl{lo_of(xr[k]), lo_of(xr[k])};
+#pragma unroll
+            for (int h = 0; h < NH; ++h) x2::dot2x2(s2[k][h], c2[k][h], xh, xl, yh[h], nyh[h], nyl[h]);
+          }
+        }
+        // renormalise every 2 rows (FastTwoSum)
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const float2 t = x2::add2(s2[k][h], c2[k][h]);
+            c2[k][h] = x2::sub2(c2[k][h], x2::sub2(t, s2[k][h]));
+            s2[k][h] = t;
+          }
       } else {
 #pragma unroll
         for (int k = 0; k < KP; ++k)
