@@ -349,31 +349,40 @@ __global__ void __launch_bounds__(kT, 2)
           sq[2 * h] = v.x;
           sq[2 * h + 1] = v.y;
         }
+        // anchors are raised rarely: one test of all thresholds keeps the
+        // raises out of the common path
+        bool raise = false;
 #pragma unroll
-        for (int k = 0; k < KP; ++k)
-          if (sp[k] > ta[k]) {
-            const float a1 = anc_anchor(sp[k]);
+        for (int k = 0; k < KP; ++k) raise |= sp[k] > ta[k];
 #pragma unroll
-            for (int h = 0; h < NH; ++h) {
-              anc_move(s2[k][h].x, c2[k][h].x, an[k] * bn[2 * h], a1 * bn[2 * h]);
-              anc_move(s2[k][h].y, c2[k][h].y, an[k] * bn[2 * h + 1], a1 * bn[2 * h + 1]);
+        for (int j = 0; j < NQ; ++j) raise |= sq[j] > tb[j];
+        if (raise) {
+#pragma unroll
+          for (int k = 0; k < KP; ++k)
+            if (sp[k] > ta[k]) {
+              const float a1 = anc_anchor(sp[k]);
+#pragma unroll
+              for (int h = 0; h < NH; ++h) {
+                anc_move(s2[k][h].x, c2[k][h].x, an[k] * bn[2 * h], a1 * bn[2 * h]);
+                anc_move(s2[k][h].y, c2[k][h].y, an[k] * bn[2 * h + 1], a1 * bn[2 * h + 1]);
+              }
+              an[k] = a1;
+              ta[k] = a1 * a1 * (1.0f / 4.5f);
             }
-            an[k] = a1;
-            ta[k] = a1 * a1 * (1.0f / 4.5f);
-          }
 #pragma unroll
-        for (int j = 0; j < NQ; ++j)
-          if (sq[j] > tb[j]) {
-            const float b1 = anc_anchor(sq[j]);
+          for (int j = 0; j < NQ; ++j)
+            if (sq[j] > tb[j]) {
+              const float b1 = anc_anchor(sq[j]);
 #pragma unroll
-            for (int k = 0; k < KP; ++k) {
-              float& sv = (j & 1) ? s2[k][j >> 1].y : s2[k][j >> 1].x;
-              float& cv = (j & 1) ? c2[k][j >> 1].y : c2[k][j >> 1].x;
-              anc_move(sv, cv, an[k] * bn[j], an[k] * b1);
+              for (int k = 0; k < KP; ++k) {
+                float& sv = (j & 1) ? s2[k][j >> 1].y : s2[k][j >> 1].x;
+                float& cv = (j & 1) ? c2[k][j >> 1].y : c2[k][j >> 1].x;
+                anc_move(sv, cv, an[k] * bn[j], an[k] * b1);
+              }
+              bn[j] = b1;
+              tb[j] = b1 * b1 * (1.0f / 4.5f);
             }
-            bn[j] = b1;
-            tb[j] = b1 * b1 * (1.0f / 4.5f);
-          }
+        }
         // s' = fma(x, y, s), z = s' - s, e = fma(x, -y, z) = -d exactly,
         // c - e = c + d: the anchored update of the file header, two Q
         // columns per instruction
@@ -420,24 +429,31 @@ __global__ void __launch_bounds__(kT, 2)
           sq[j] = __fmaf_rn(hi_of(ya[j]), hi_of(ya[j]), sq[j]);
           sq[j] = __fmaf_rn(hi_of(yb[j]), hi_of(yb[j]), sq[j]);
         }
+        bool raise = false;  // as in the packed path: one test of all thresholds
 #pragma unroll
-        for (int k = 0; k < KP; ++k)
-          if (sp[k] > ta[k]) {
-            const float a1 = anc_anchor(sp[k]);
+        for (int k = 0; k < KP; ++k) raise |= sp[k] > ta[k];
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], a1 * bn[j]);
-            an[k] = a1;
-            ta[k] = a1 * a1 * (1.0f / 4.5f);
-          }
+        for (int j = 0; j < NQ; ++j) raise |= sq[j] > tb[j];
+        if (raise) {
 #pragma unroll
-        for (int j = 0; j < NQ; ++j)
-          if (sq[j] > tb[j]) {
-            const float b1 = anc_anchor(sq[j]);
+          for (int k = 0; k < KP; ++k)
+            if (sp[k] > ta[k]) {
+              const float a1 = anc_anchor(sp[k]);
 #pragma unroll
-            for (int k = 0; k < KP; ++k) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], an[k] * b1);
-            bn[j] = b1;
-            tb[j] = b1 * b1 * (1.0f / 4.5f);
-          }
+              for (int j = 0; j < NQ; ++j) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], a1 * bn[j]);
+              an[k] = a1;
+              ta[k] = a1 * a1 * (1.0f / 4.5f);
+            }
+#pragma unroll
+          for (int j = 0; j < NQ; ++j)
+            if (sq[j] > tb[j]) {
+              const float b1 = anc_anchor(sq[j]);
+#pragma unroll
+              for (int k = 0; k < KP; ++k) anc_move(sa[k][j], ca[k][j], an[k] * bn[j], an[k] * b1);
+              bn[j] = b1;
+              tb[j] = b1 * b1 * (1.0f / 4.5f);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < KP; ++k)
 #pragma unroll
