@@ -171,3 +171,30 @@ def test_condest_and_kernel_entry_argument_checks():
     assert B.block_jacobi_nnz(64, 64) == 64 * 64 and B.block_jacobi_nnz(10, 65) == 0
     assert L.phsvds_block_jacobi(10, None, None, None, 4, None, None, None, None, None) == B.SVDS_ERR_ARG
     assert B.spmm_dots_scratch_bytes(4) >= 2048 * 4 * 4 * 8
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of svds_csr, svds_opts and svds_stats have the
+    header's size and field offsets (compiled against include/phsvds.h)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("svds_csr", B.svds_csr), ("svds_opts", B.svds_opts), ("svds_stats", B.svds_stats)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "phsvds.h"', "int main(void) {"]
+    for name, py in structs:
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (line.split() for line in out if line)}
+    for name, py in structs:
+        assert got[(name, "sizeof")] == C.sizeof(py), name
+        for f, _ in py._fields_:
+            assert got[(name, f)] == getattr(py, f).offset, (name, f)
